@@ -1,0 +1,262 @@
+"""Pins for the CPU oracle (no GPU): each test checks the oracle against something other than
+itself -- a closed form, an invariant, a textbook/library routine, or an independent solver.
+
+The solved problem is div((1/rho) grad p) = f on the periodic staggered grid (Sec. 3.4 of
+arXiv:1601.05448), with f replaced by f - <f> (the compatibility constant chi' of App. A) and
+the zero-mean p returned.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import vdp_inputs as V
+
+TWO_PI = 2.0 * math.pi
+
+
+def centres(shape, L):
+    nz, ny, nx = shape
+    x = (np.arange(nx) + 0.5) * (L / nx)
+    y = (np.arange(ny) + 0.5) * (L / ny)
+    z = (np.arange(nz) + 0.5) * (L / nz)
+    return np.meshgrid(z, y, x, indexing="ij")[::-1]  # X, Y, Z arrays of shape (nz, ny, nx)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ---- 1. constant density: the discrete Fourier modes are exact eigenvectors -------------------
+
+FOURIER_CASES = [
+    ((8, 8, 8), TWO_PI, (1, 0, 0)),
+    ((16, 12, 10), TWO_PI, (2, 3, 1)),
+    ((12, 16, 8), 3.0, (1, -2, 3)),
+    ((32, 32, 32), TWO_PI, (4, 1, -2)),
+]
+
+
+def _mode(shape, L, k):
+    """cos of the discrete mode k sampled on cell centres, and its exact eigenvalue of the
+    constant-coefficient second-difference Laplacian: -sum_d 4 sin^2(pi k_d / n_d) / h_d^2."""
+    nz, ny, nx = shape
+    X, Y, Z = centres(shape, L)
+    kx, ky, kz = k
+    theta = TWO_PI * (kx * X / L + ky * Y / L + kz * Z / L)
+    lam = -4.0 * sum(math.sin(math.pi * kd / nd) ** 2 / (L / nd) ** 2 for kd, nd in zip(k, (nx, ny, nz)))
+    return np.cos(theta + 0.3), lam
+
+
+@pytest.mark.parametrize("shape,L,k", FOURIER_CASES)
+def test_constant_density_fourier_eigenvector(shape, L, k):
+    rho0 = 1.7
+    rho = np.full(shape, rho0)
+    u, lam = _mode(shape, L, k)
+    Au = oracle.apply_rho(rho, L, u)
+    # A = (1/rho0) * Laplacian_h  =>  A u = (lam / rho0) u, exactly up to rounding
+    assert rel(Au, (lam / rho0) * u) < 1e-12
+
+
+@pytest.mark.parametrize("shape,L,k", FOURIER_CASES)
+def test_constant_density_fourier_solution(shape, L, k):
+    rho0 = 0.6
+    rho = np.full(shape, rho0)
+    f, lam = _mode(shape, L, k)
+    p, info = oracle.solve_cg(rho, f, L, tol=1e-13)
+    assert info["status"] == "ok"
+    exact = rho0 * f / lam
+    exact -= exact.mean()
+    assert rel(p, exact) < 1e-11
+
+
+# ---- 2. density varying along one axis: flux integration closed form ---------------------------
+
+def closed_form_1d(rho_line, f_line, h):
+    """Periodic 1-D problem (b_{i+1}(p_{i+1}-p_i) - b_i(p_i-p_{i-1})) = f_i with
+    b_i = 2/(rho_{i-1}+rho_i)/h^2.  The face flux q_i = b_i (p_i - p_{i-1}) obeys
+    q_{i+1} - q_i = f_i, so q_i = q_0 + sum_{m<i} f_m; periodicity of p fixes q_0 through
+    sum_i q_i / b_i = 0.  Then p_i = p_{i-1} + q_i / b_i, shifted to zero mean."""
+    n = len(rho_line)
+    b = [2.0 / (rho_line[i - 1] + rho_line[i]) / h ** 2 for i in range(n)]
+    f0 = [fi - sum(f_line) / n for fi in f_line]
+    partial = [0.0] * n
+    for i in range(1, n):
+        partial[i] = partial[i - 1] + f0[i - 1]
+    q0 = -sum(partial[i] / b[i] for i in range(n)) / sum(1.0 / b[i] for i in range(n))
+    q = [q0 + partial[i] for i in range(n)]
+    p = [0.0] * n
+    for i in range(1, n):
+        p[i] = p[i - 1] + q[i] / b[i]
+    m = sum(p) / n
+    return np.array([pi - m for pi in p])
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])  # direction x, y, z
+def test_one_dimensional_closed_form(axis):
+    shape = (10, 12, 14)  # (nz, ny, nx): different n per direction
+    L = 2.5
+    nz, ny, nx = shape
+    ndir = (nx, ny, nz)[axis]
+    rng = np.random.default_rng(11 + axis)
+    rho_line = rng.uniform(0.3, 3.0, ndir)       # density ratio ~10, jagged
+    f_line = rng.standard_normal(ndir) + 0.7      # nonzero mean on purpose
+    bshape = [1, 1, 1]
+    bshape[2 - axis] = ndir
+    rho = np.broadcast_to(rho_line.reshape(bshape), shape).copy()
+    f = np.broadcast_to(f_line.reshape(bshape), shape).copy()
+    p, info = oracle.solve_cg(rho, f, L, tol=1e-13)
+    assert info["status"] == "ok"
+    assert abs(info["rhs_mean"] - f_line.mean()) < 1e-14
+    exact_line = closed_form_1d(list(rho_line), list(f_line), L / ndir)
+    exact = np.broadcast_to(exact_line.reshape(bshape), shape)
+    assert rel(p, exact) < 1e-11
+
+
+# ---- 3. operator invariants ---------------------------------------------------------------
+
+def test_operator_symmetry_nullspace_energy():
+    shape = (9, 10, 12)
+    L = 1.3
+    rng = np.random.default_rng(5)
+    rho = rng.uniform(0.2, 2.0, shape)
+    u = rng.standard_normal(shape)
+    v = rng.standard_normal(shape)
+    b = oracle.face_coefficients(rho, L)
+    Au, Av = oracle.apply(b, u), oracle.apply(b, v)
+    # symmetric
+    s1, s2 = float((u * Av).sum()), float((Au * v).sum())
+    assert abs(s1 - s2) <= 1e-12 * abs(s1)
+    # constants are in the null space, exactly
+    assert np.all(oracle.apply(b, np.full(shape, 3.25)) == 0.0)
+    # columns sum to zero (the left side integrates to zero over the periodic box, App. A)
+    assert abs(float(Av.sum())) <= 1e-12 * float(np.abs(Av).sum())
+    # negative semi-definite, with -<v, A v> = sum over faces of b * (jump of v)^2
+    energy = 0.0
+    for d, bd in enumerate(b):
+        jump = v - np.roll(v, 1, axis=2 - d)   # v[c] - v[c - e_d] across the low face of c
+        energy += float((bd * jump * jump).sum())
+    assert abs(-float((v * Av).sum()) - energy) <= 1e-12 * energy
+
+
+# ---- 4. dense direct solve on tiny grids (library LU) --------------------------------------
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (8, 8, 8), (4, 6, 8)])
+def test_dense_direct(shape):
+    nz, ny, nx = shape
+    N = nx * ny * nz
+    L = 2.0
+    rng = np.random.default_rng(N)
+    rho = rng.uniform(0.25, 2.5, shape)
+    f = rng.standard_normal(shape)
+    h = (L / nx, L / ny, L / nz)
+    # assemble from a list of faces: every face couples its two cells with weight 1/rho_face/h^2
+    M = np.zeros((N, N))
+    flat = lambda i, j, k: (i % nx) + nx * ((j % ny) + ny * (k % nz))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                for d, (di, dj, dk) in enumerate(((1, 0, 0), (0, 1, 0), (0, 0, 1))):
+                    a, c = flat(i, j, k), flat(i + di, j + dj, k + dk)
+                    w = 1.0 / (0.5 * (rho[k, j, i] + rho[(k + dk) % nz, (j + dj) % ny, (i + di) % nx])) / h[d] ** 2
+                    M[a, a] -= w
+                    M[c, c] -= w
+                    M[a, c] += w
+                    M[c, a] += w
+    f0 = f.ravel() - f.mean()
+    # A p = f0 with sum(p) = 0  <=>  (A - 11^T) p = f0  (A 1 = 0, 1^T f0 = 0)
+    p_ref = np.linalg.solve(M - np.ones((N, N)), f0)
+    p, info = oracle.solve_cg(rho, f, L, tol=1e-13)
+    assert info["status"] == "ok"
+    assert rel(p.ravel(), p_ref) < 1e-11
+
+
+# ---- 5. second-order convergence to a smooth continuous solution -----------------------------
+
+def manufactured(n):
+    """rho = 1 + 0.5 sin x cos y sin z, p* = sin x cos 2y + cos z sin y on [0, 2pi)^3;
+    f = div(grad p*/rho) = lap(p*)/rho - grad(rho).grad(p*)/rho^2, differentiated by hand."""
+    shape = (n, n, n)
+    X, Y, Z = centres(shape, TWO_PI)
+    sx, cx, sy, cy, sz, cz = np.sin(X), np.cos(X), np.sin(Y), np.cos(Y), np.sin(Z), np.cos(Z)
+    rho = 1.0 + 0.5 * sx * cy * sz
+    rx, ry, rz = 0.5 * cx * cy * sz, -0.5 * sx * sy * sz, 0.5 * sx * cy * cz
+    p = sx * np.cos(2 * Y) + cz * sy
+    px = cx * np.cos(2 * Y)
+    py = -2.0 * sx * np.sin(2 * Y) + cz * cy
+    pz = -sz * sy
+    lap = -5.0 * sx * np.cos(2 * Y) - 2.0 * cz * sy
+    f = lap / rho - (rx * px + ry * py + rz * pz) / rho ** 2
+    return rho, f, p - p.mean()
+
+
+def test_second_order_convergence():
+    errs = []
+    for n in (16, 32, 64):
+        rho, f, pex = manufactured(n)
+        p, info = oracle.solve_cg(rho, f, TWO_PI, tol=1e-12)
+        assert info["status"] == "ok"
+        errs.append(float(np.sqrt(np.mean((p - pex) ** 2))))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.6 < r1 < 4.4 and 3.8 < r2 < 4.2, errs
+
+
+# ---- 6. the paper's own iteration (Eq. (Pois)) reaches the same discrete solution ------------
+
+def test_paper_fixed_point_matches_cg():
+    prob = V.config0()
+    p_cg, i_cg = oracle.solve_cg(prob.rho, prob.f, prob.L, tol=1e-13)
+    p_fp, i_fp = oracle.solve_fixed_point(prob.rho, prob.f, prob.L, tol=1e-12, maxit=200)
+    assert i_cg["status"] == "ok" and i_fp["status"] == "ok"
+    assert rel(p_fp, p_cg) < 1e-11
+
+
+def test_inverse_laplacian_is_exact_on_a_mode():
+    shape, L, k = (12, 10, 8), 2.0, (2, -1, 3)
+    u, lam = _mode(shape, L, k)
+    u = u - u.mean()
+    assert rel(oracle.inverse_laplacian(u, L), u / lam) < 1e-12
+
+
+# ---- 7. compatibility, gauge and degenerate inputs ------------------------------------------
+
+def test_rhs_mean_is_removed_and_reported():
+    prob = V.smooth_problem((12, 12, 12), seed=3)
+    p1, i1 = oracle.solve_cg(prob.rho, prob.f, prob.L, tol=1e-13)
+    p2, i2 = oracle.solve_cg(prob.rho, prob.f + 5.0, prob.L, tol=1e-13)
+    assert abs(i2["rhs_mean"] - i1["rhs_mean"] - 5.0) < 1e-12
+    assert rel(p2, p1) < 1e-11
+    assert abs(float(p2.mean())) < 1e-14 * float(np.abs(p2).max())
+
+
+def test_zero_and_constant_rhs_give_zero_pressure():
+    rho = np.random.default_rng(0).uniform(0.5, 2.0, (6, 6, 6))
+    for f in (np.zeros((6, 6, 6)), np.full((6, 6, 6), 2.5)):
+        p, info = oracle.solve_cg(rho, f, 1.0, tol=1e-12)
+        assert info["status"] == "ok" and info["iters"] == 0
+        assert np.all(p == 0.0)
+
+
+def test_bad_density_is_rejected():
+    f = np.ones((4, 4, 4))
+    for bad in (0.0, -1.0, np.nan, np.inf):
+        rho = np.ones((4, 4, 4))
+        rho[1, 2, 3] = bad
+        p, info = oracle.solve_cg(rho, f, 1.0)
+        assert info["status"] == "edensity"
+
+
+# ---- 8. the input recipes --------------------------------------------------------------------
+
+def test_config0_inputs():
+    a, b = V.config0(), V.config0()
+    assert np.array_equal(a.rho, b.rho) and np.array_equal(a.f, b.f)      # seeded
+    assert abs(a.rho.max() / a.rho.min() - 3.0) < 1e-12                   # ratio 3 exactly
+    assert abs(float(a.f.mean())) < 1e-13 * float(np.abs(a.f).max())       # divergence: mean-free
+
+
+def test_hotspot_ratio_targeting():
+    prob = V.hotspot_problem(32, seed=4, nspots=40, target_ratio=6.0)
+    assert abs(prob.rho.max() / prob.rho.min() - 6.0) < 1e-9
+    assert prob.rho.min() > 0
