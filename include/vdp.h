@@ -1,0 +1,152 @@
+/*
+ * vdp.h -- C ABI of libvdp, a GB300 (sm_103a) solver for the variable-coefficient pressure
+ * Poisson equation of a low-Mach variable-density flow,
+ *
+ *        div( (1/rho) grad p ) = f ,                                   (Sec. 3.4 of [1])
+ *
+ * on a uniform, triply periodic, staggered grid (Sec. 3.1 and Sec. 3.2 case 1 of [1]).
+ *
+ * [1] H. Pouransari, M. Mortazavi, A. Mani, "Parallel variable-density particle-laden turbulence
+ *     simulation", CTR Annual Research Briefs (arXiv:1601.05448).
+ *
+ * Discretisation (the paper gives only the continuous equation and "staggered, second order"):
+ *   cell (i,j,k), index c = i + nx*(j + ny*k) (x fastest), spacing h_d = L/n_d, periodic wrap;
+ *   1/rho on a face = 1 / (arithmetic mean of the two adjacent cell-centre densities) -- the
+ *   averaging App. B of [1] uses to move rho off the cell centres;
+ *   (A p)_c = sum_d b_d[c+e_d](p[c+e_d]-p[c]) - b_d[c](p[c]-p[c-e_d]),
+ *   b_d[c] = 2/(rho[c-e_d]+rho[c]) / h_d^2 on the low d-face of cell c.
+ * Compatibility (App. A of [1], the constant chi'): on the periodic box the left side integrates
+ * to zero, so the solver replaces f by f - <f> (cell mean) and reports <f>.  The pressure is
+ * returned with zero cell mean.  Convergence: relative L2 residual
+ * ||(f - <f>) - A p||_2 / ||f - <f>||_2 <= tol, evaluated in FP64 from p itself.
+ *
+ * Memory conventions: every field is a contiguous array of nx*ny*nz doubles in the layout above.
+ * Pointers passed to vdp_set_density / vdp_solve may be device pointers (e.g. torch CUDA
+ * tensors' data_ptr()) or host pointers (pageable or pinned); host data is staged through
+ * library-owned device buffers on the context's stream; device pointers must be 16-byte
+ * aligned (VDP_EINVAL otherwise).  The caller keeps ownership of all
+ * arrays it passes; the library never frees them and keeps no caller pointer after a call
+ * returns.  All work is ordered on the context's stream (vdp_opts.stream; NULL = the legacy
+ * default stream) and every call below returns only after its work has finished.
+ *
+ * Threading: a context may be used by one host thread at a time; distinct contexts are
+ * independent.  Errors: functions return a vdp_status; vdp_strerror() names it.  No call
+ * aborts the process.
+ */
+#ifndef VDP_H
+#define VDP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VDP_OK = 0,
+  VDP_EINVAL = 1,      /* bad argument, or call out of order (solve before set_density) */
+  VDP_ENOMEM = 2,      /* device allocation failed, or a batch/HBM budget is exhausted */
+  VDP_EDENSITY = 3,    /* rho has an entry <= 0, NaN or Inf */
+  VDP_ENOTCONV = 4,    /* max_iter reached; p holds the best iterate (zero mean) */
+  VDP_EBREAKDOWN = 5,  /* Krylov breakdown (non-positive curvature or non-finite value) */
+  VDP_ETIMEOUT = 6,    /* a bounded device-side wait gave up; the context stays usable */
+  VDP_ECUDA = 7        /* a CUDA runtime call failed (the message is in vdp_last_cuda_error) */
+} vdp_status;
+
+typedef enum {
+  VDP_FP64 = 0,        /* FP64 everywhere */
+  VDP_MIXED = 1,       /* FP32 inner Krylov with FP32 face coefficients, FP64 refinement */
+  VDP_MIXED_BF16 = 2   /* as VDP_MIXED with BF16-stored face coefficients (ablation) */
+} vdp_precision;
+
+typedef enum {
+  VDP_PRECOND_JACOBI = 0, /* diagonal (Jacobi) scaling, folded into the operator */
+  VDP_PRECOND_CHEB = 1    /* Jacobi + fixed-degree Chebyshev polynomial sweep */
+} vdp_precond;
+
+typedef struct {
+  int precision;       /* vdp_precision (default VDP_FP64) */
+  int max_iter;        /* cap on the total number of inner Krylov iterations (default 20000) */
+  double inner_tol;    /* mixed precision: relative residual reduction per inner solve
+                          (default 1e-4); FP64 derives its inner target from tol */
+  int precond;         /* vdp_precond (default VDP_PRECOND_JACOBI) */
+  int cheb_degree;     /* polynomial degree for VDP_PRECOND_CHEB (default 4) */
+  int use_guess;       /* 1: p on entry to vdp_solve is the initial guess; 0: start from p = 0 */
+  void *stream;        /* cudaStream_t for all work of this context (default NULL) */
+  int tile_y;          /* rows per work unit (0 = automatic) */
+  int tile_z;          /* planes per work unit (0 = automatic) */
+  int steps_per_sync;  /* device sweeps per host convergence check (0 = automatic) */
+} vdp_opts;
+
+typedef struct {
+  int status;          /* vdp_status of the last solve */
+  int iters;           /* total inner Krylov iterations */
+  int outer_iters;     /* FP64 residual evaluations (refinement steps + final check) */
+  double rel_res;      /* final FP64 relative residual ||(f-<f>) - A p|| / ||f-<f>|| */
+  double rhs_mean;     /* <f> removed from the right-hand side (chi' of App. A) */
+  double ms;           /* device time of the last solve in milliseconds */
+  int sweeps;          /* device sweeps (kernel work phases) executed */
+  int launches;        /* kernels launched by the solve (including idle steps after convergence) */
+} vdp_stats;
+
+typedef struct vdp_ctx vdp_ctx;
+
+/* Fill *o with the defaults listed in vdp_opts. */
+void vdp_default_options(vdp_opts *o);
+
+/*
+ * Create a solver for an nx x ny x nz periodic box of side L (h_d = L / n_d).
+ * nx must be a multiple of 8 and at least 8 (16-byte aligned rows in every storage precision);
+ * ny, nz >= 1.  Allocates all device memory the solve needs.  *out = NULL on failure.
+ */
+int vdp_create(int nx, int ny, int nz, double L, vdp_ctx **out);
+
+/* Replace the options (takes effect at the next set_density / solve). */
+int vdp_set_options(vdp_ctx *ctx, const vdp_opts *opts);
+int vdp_get_options(const vdp_ctx *ctx, vdp_opts *opts);
+
+/*
+ * rho: cell-centred density, nx*ny*nz doubles.  Builds the face coefficients b_d, the Jacobi
+ * scaling and the inner-precision copies.  Returns VDP_EDENSITY (and keeps the previous
+ * density, if any) when an entry is <= 0 or not finite.
+ */
+int vdp_set_density(vdp_ctx *ctx, const double *rho);
+
+/*
+ * Solve A p = rhs - <rhs> to relative residual tol (tol > 0).  rhs: nx*ny*nz doubles (not
+ * modified).  p: nx*ny*nz doubles, output (and initial guess when use_guess = 1).  On return p
+ * has zero mean.  A zero (or constant) rhs gives p = 0.  VDP_ENOTCONV / VDP_EBREAKDOWN leave the
+ * last iterate (zero mean) in p.  Requires a prior successful vdp_set_density.
+ */
+int vdp_solve(vdp_ctx *ctx, const double *rhs, double *p, double tol);
+
+/* Statistics of the last vdp_solve. */
+int vdp_get_stats(const vdp_ctx *ctx, vdp_stats *stats);
+
+/* Release the context and all its device memory.  NULL-safe. */
+void vdp_destroy(vdp_ctx *ctx);
+
+/* Name of a vdp_status. */
+const char *vdp_strerror(int status);
+
+/* Text of the last CUDA error seen by the library in this process ("" if none). */
+const char *vdp_last_cuda_error(void);
+
+/* ABI version of this library (incremented on incompatible changes). */
+int vdp_version(void);
+
+/* ------------------------------------------------------------------------------------------ */
+/* Single operator application, for tests and for callers that embed the operator elsewhere.    */
+/* ------------------------------------------------------------------------------------------ */
+
+/*
+ * out = A p with the context's FP64 face coefficients (after vdp_set_density).  p and out are
+ * nx*ny*nz doubles (device or host); out must not alias p.
+ */
+int vdp_apply(vdp_ctx *ctx, const double *p, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VDP_H */

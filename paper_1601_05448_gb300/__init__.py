@@ -1,0 +1,278 @@
+"""GB300 (sm_103a) solver for the variable-density pressure Poisson equation div((1/rho) grad p) = f
+on a triply periodic staggered grid (Sec. 3.4 of Pouransari, Mortazavi & Mani, arXiv:1601.05448).
+
+This package is a thin ctypes binding over ``libvdp.so`` (built from ``csrc/`` by ``build.py``);
+the functions keep the C names of ``include/vdp.h`` and only marshal arguments.  Every step of
+the solve runs in the library's CUDA kernels; there is no Python or CPU fallback -- importing
+works without the library, but any call raises ``VdpUnavailable`` if ``libvdp.so`` is missing.
+
+Arrays are float64, contiguous, shape (nz, ny, nx) (x fastest): torch CUDA tensors (device
+pointers), or torch CPU tensors / numpy arrays (host pointers, staged by the library).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvdp.so")
+
+VDP_OK, VDP_EINVAL, VDP_ENOMEM, VDP_EDENSITY, VDP_ENOTCONV, VDP_EBREAKDOWN, VDP_ETIMEOUT, VDP_ECUDA = range(8)
+VDP_FP64, VDP_MIXED, VDP_MIXED_BF16 = 0, 1, 2
+VDP_PRECOND_JACOBI, VDP_PRECOND_CHEB = 0, 1
+PRECISIONS = {"fp64": VDP_FP64, "mixed": VDP_MIXED, "mixed_bf16": VDP_MIXED_BF16}
+
+
+class VdpUnavailable(RuntimeError):
+    """libvdp.so is not built (run __graft_entry__.build() or paper_1601_05448_gb300.build)."""
+
+
+class VdpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {vdp_strerror(status)}"
+        if status == VDP_ECUDA:
+            msg += f" ({vdp_last_cuda_error()})"
+        super().__init__(msg)
+
+
+class vdp_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("precond", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("use_guess", ctypes.c_int),
+                ("stream", ctypes.c_void_p), ("tile_y", ctypes.c_int), ("tile_z", ctypes.c_int),
+                ("steps_per_sync", ctypes.c_int)]
+
+
+class vdp_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("rhs_mean", ctypes.c_double), ("ms", ctypes.c_double),
+                ("sweeps", ctypes.c_int), ("launches", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes) of every entry point declared in include/vdp.h
+_P = ctypes.c_void_p
+_SIGS = {
+    "vdp_default_options": (None, [ctypes.POINTER(vdp_opts)]),
+    "vdp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                  ctypes.POINTER(ctypes.c_void_p)]),
+    "vdp_set_options": (ctypes.c_int, [_P, ctypes.POINTER(vdp_opts)]),
+    "vdp_get_options": (ctypes.c_int, [_P, ctypes.POINTER(vdp_opts)]),
+    "vdp_set_density": (ctypes.c_int, [_P, _P]),
+    "vdp_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
+    "vdp_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(vdp_stats)]),
+    "vdp_destroy": (None, [_P]),
+    "vdp_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "vdp_last_cuda_error": (ctypes.c_char_p, []),
+    "vdp_version": (ctypes.c_int, []),
+    "vdp_apply": (ctypes.c_int, [_P, _P, _P]),
+}
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects (those declared in include/vdp.h)."""
+    return list(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    """Load libvdp.so (no build); raises VdpUnavailable when it is absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise VdpUnavailable(f"{path} not found: build it with paper_1601_05448_gb300.build.build()")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+# ---- the C entry points, same names -------------------------------------------------------------
+
+def vdp_default_options() -> vdp_opts:
+    o = vdp_opts()
+    load().vdp_default_options(ctypes.byref(o))
+    return o
+
+
+def vdp_create(nx: int, ny: int, nz: int, L: float) -> int:
+    h = ctypes.c_void_p()
+    st = load().vdp_create(int(nx), int(ny), int(nz), float(L), ctypes.byref(h))
+    if st != VDP_OK:
+        raise VdpError(st, "vdp_create")
+    return h.value
+
+
+def vdp_set_options(ctx: int, opts: vdp_opts) -> int:
+    return load().vdp_set_options(ctx, ctypes.byref(opts))
+
+
+def vdp_get_options(ctx: int) -> vdp_opts:
+    o = vdp_opts()
+    st = load().vdp_get_options(ctx, ctypes.byref(o))
+    if st != VDP_OK:
+        raise VdpError(st, "vdp_get_options")
+    return o
+
+
+def vdp_set_density(ctx: int, rho) -> int:
+    return load().vdp_set_density(ctx, _ptr(rho))
+
+
+def vdp_solve(ctx: int, rhs, p, tol: float) -> int:
+    return load().vdp_solve(ctx, _ptr(rhs), _ptr(p, writable=True), float(tol))
+
+
+def vdp_get_stats(ctx: int) -> vdp_stats:
+    s = vdp_stats()
+    load().vdp_get_stats(ctx, ctypes.byref(s))
+    return s
+
+
+def vdp_destroy(ctx) -> None:
+    if ctx:
+        load().vdp_destroy(ctx)
+
+
+def vdp_strerror(status: int) -> str:
+    return load().vdp_strerror(int(status)).decode()
+
+
+def vdp_last_cuda_error() -> str:
+    return load().vdp_last_cuda_error().decode()
+
+
+def vdp_version() -> int:
+    return load().vdp_version()
+
+
+def vdp_apply(ctx: int, p, out) -> int:
+    return load().vdp_apply(ctx, _ptr(p), _ptr(out, writable=True))
+
+
+# ---- marshalling ------------------------------------------------------------------------------
+
+def _ptr(a, writable: bool = False) -> int:
+    """Data pointer of a contiguous float64 torch tensor (CUDA or CPU) or numpy array."""
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        return a.data_ptr()
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a contiguous float64 numpy array")
+    if writable and not a.flags["WRITEABLE"]:
+        raise TypeError("output array is read-only")
+    return a.ctypes.data
+
+
+def _numel(a) -> int:
+    return int(a.numel()) if hasattr(a, "numel") else int(a.size)
+
+
+@dataclass
+class Stats:
+    status: int
+    iters: int
+    outer_iters: int
+    rel_res: float
+    rhs_mean: float
+    ms: float
+    sweeps: int
+    launches: int
+
+    @property
+    def ok(self) -> bool:
+        return self.status == VDP_OK
+
+
+class Solver:
+    """Owns one vdp context: ``Solver(nx, ny, nz, L, precision="fp64")``; ``set_density(rho)``;
+    ``solve(rhs, p, tol) -> Stats``.  Raises VdpError on any status other than OK (and, for
+    solve, other than ENOTCONV/EBREAKDOWN when ``check=False``)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, L: float, precision: str = "fp64", stream=None,
+                 **opts):
+        self.shape = (nz, ny, nx)
+        self.L = float(L)
+        self.ctx = vdp_create(nx, ny, nz, L)
+        o = vdp_default_options()
+        o.precision = PRECISIONS[precision]
+        if stream is not None:
+            o.stream = stream if isinstance(stream, int) else stream.cuda_stream
+        for k, v in opts.items():
+            setattr(o, k, v)
+        st = vdp_set_options(self.ctx, o)
+        if st != VDP_OK:
+            self.close()
+            raise VdpError(st, "vdp_set_options")
+
+    @property
+    def n(self) -> int:
+        nz, ny, nx = self.shape
+        return nx * ny * nz
+
+    def options(self) -> vdp_opts:
+        return vdp_get_options(self.ctx)
+
+    def set_options(self, **kw) -> None:
+        o = vdp_get_options(self.ctx)
+        for k, v in kw.items():
+            if k == "precision" and isinstance(v, str):
+                v = PRECISIONS[v]
+            setattr(o, k, v)
+        st = vdp_set_options(self.ctx, o)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_set_options")
+
+    def _check(self, a, name):
+        if _numel(a) != self.n:
+            raise ValueError(f"{name}: expected {self.n} elements, got {_numel(a)}")
+
+    def set_density(self, rho) -> None:
+        self._check(rho, "rho")
+        st = vdp_set_density(self.ctx, rho)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_set_density")
+
+    def solve(self, rhs, p, tol: float, check: bool = True) -> Stats:
+        self._check(rhs, "rhs")
+        self._check(p, "p")
+        st = vdp_solve(self.ctx, rhs, p, tol)
+        s = vdp_get_stats(self.ctx)
+        out = Stats(s.status, s.iters, s.outer_iters, s.rel_res, s.rhs_mean, s.ms, s.sweeps, s.launches)
+        if st != VDP_OK and (check or st not in (VDP_ENOTCONV, VDP_EBREAKDOWN)):
+            raise VdpError(st, "vdp_solve")
+        return out
+
+    def apply(self, p, out) -> None:
+        self._check(p, "p")
+        self._check(out, "out")
+        st = vdp_apply(self.ctx, p, out)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_apply")
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            vdp_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,466 @@
+// vdp_api.cu -- the C ABI of libvdp (include/vdp.h): contexts, device buffers, the solve driver.
+//
+// A solve is one instance of the per-instance state machine in vdp_kernels.cu, advanced by the
+// step kernel.  The driver launches a captured CUDA graph of `steps_per_sync` step launches,
+// copies the instance's 200-byte state to pinned host memory after each graph, and keeps two
+// graphs in flight so that the convergence check on the host overlaps with device work.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vdp.h"
+#include "vdp_internal.cuh"
+#include "vdp_launch.h"
+
+using namespace vdp;
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_last_cuda_error;
+
+int cuda_fail(cudaError_t e, const char* where) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_last_cuda_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? VDP_ENOMEM : VDP_ECUDA;
+}
+
+#define VDP_CK(call)                                   \
+  do {                                                 \
+    cudaError_t _e = (call);                           \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct vdp_ctx {
+  int nx = 0, ny = 0, nz = 0;
+  double L = 0;
+  long long n = 0;
+  int device = 0;
+  vdp_opts opts{};
+  cudaStream_t stream = nullptr;   // work stream (opts.stream)
+  cudaStream_t cap = nullptr;      // private stream used only to capture graphs
+  // FP64 operator data
+  double *bx = nullptr, *by = nullptr, *bz = nullptr, *sinv = nullptr;
+  // inner-precision data (sized for FP64, reinterpreted for FP32 / BF16)
+  void *sx = nullptr, *sy = nullptr, *sz = nullptr;
+  void *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr, *q = nullptr;
+  int scaled_prec = -1;            // precision the scaled coefficients were built for
+  bool has_density = false;
+  // bookkeeping
+  double* part = nullptr;
+  unsigned int* ticket = nullptr;
+  InstState* st = nullptr;
+  InstDesc* desc = nullptr;
+  UnitRef* units = nullptr;
+  int* flag = nullptr;
+  double *stage_a = nullptr, *stage_b = nullptr;  // staging for host pointers
+  InstState* hstate = nullptr;     // pinned, 2 entries
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs[2] = {nullptr, nullptr};
+  // layout
+  int ty = 0, tz = 0, uy = 0, uz = 0, nunits = 0;
+  size_t smem = 0;
+  bool layout_dirty = true;
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  int g_prec = -1, g_steps = 0;
+  vdp_stats stats{};
+};
+
+extern "C" {
+
+void vdp_default_options(vdp_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = VDP_FP64;
+  o->max_iter = 20000;
+  o->inner_tol = 1e-4;
+  o->precond = VDP_PRECOND_JACOBI;
+  o->cheb_degree = 4;
+  o->use_guess = 0;
+  o->stream = nullptr;
+  o->tile_y = 0;
+  o->tile_z = 0;
+  o->steps_per_sync = 0;
+}
+
+const char* vdp_strerror(int s) {
+  switch (s) {
+    case VDP_OK: return "VDP_OK";
+    case VDP_EINVAL: return "VDP_EINVAL: invalid argument or call order";
+    case VDP_ENOMEM: return "VDP_ENOMEM: out of device memory or budget";
+    case VDP_EDENSITY: return "VDP_EDENSITY: density not positive and finite";
+    case VDP_ENOTCONV: return "VDP_ENOTCONV: iteration limit reached";
+    case VDP_EBREAKDOWN: return "VDP_EBREAKDOWN: Krylov breakdown";
+    case VDP_ETIMEOUT: return "VDP_ETIMEOUT: bounded device wait expired";
+    case VDP_ECUDA: return "VDP_ECUDA: CUDA runtime error";
+    default: return "VDP_?: unknown status";
+  }
+}
+
+const char* vdp_last_cuda_error(void) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_last_cuda_error.c_str();
+}
+
+int vdp_version(void) { return 1; }
+
+}  // extern "C"
+
+namespace {
+
+void free_ctx(vdp_ctx* c) {
+  if (!c) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  void* bufs[] = {c->bx, c->by, c->bz, c->sinv, c->sx, c->sy, c->sz, c->x, c->r, c->d0, c->d1,
+                  c->q, c->part, c->ticket, c->st, c->desc, c->units, c->flag, c->stage_a,
+                  c->stage_b};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (c->hstate) cudaFreeHost(c->hstate);
+  cudaEvent_t evs[] = {c->ev0, c->ev1, c->evs[0], c->evs[1]};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete c;
+}
+
+// Work-unit shape: full x rows; about 1024 cells per plane per unit; enough units to fill the
+// GPU several times over.
+void auto_layout(int nx, int ny, int nz, int* ty, int* tz) {
+  int t = std::max(1, std::min(ny, 1024 / std::max(nx, 1)));
+  int uy = (ny + t - 1) / t;
+  const int target_units = 152 * 4;
+  int z = (int)((long long)nz * uy / target_units);
+  z = std::max(2, std::min(z, 32));
+  z = std::min(z, nz);
+  *ty = t;
+  *tz = z;
+}
+
+int configure_layout(vdp_ctx* c) {
+  int ty = c->opts.tile_y, tz = c->opts.tile_z;
+  int aty, atz;
+  auto_layout(c->nx, c->ny, c->nz, &aty, &atz);
+  if (ty <= 0) ty = aty;
+  if (tz <= 0) tz = atz;
+  ty = std::min(ty, c->ny);
+  tz = std::min(tz, c->nz);
+  size_t smem = (size_t)3 * (ty + 2) * c->nx * sizeof(double);
+  if (smem > 200 * 1024) return VDP_EINVAL;
+  c->ty = ty;
+  c->tz = tz;
+  c->uy = (c->ny + ty - 1) / ty;
+  c->uz = (c->nz + tz - 1) / tz;
+  c->nunits = c->uy * c->uz;
+  c->smem = smem;
+  std::vector<UnitRef> u(c->nunits);
+  for (int i = 0; i < c->nunits; ++i) u[i] = UnitRef{0, i};
+  VDP_CK(cudaMemcpyAsync(c->units, u.data(), sizeof(UnitRef) * u.size(), cudaMemcpyHostToDevice,
+                         c->stream));
+  InstDesc d{};
+  d.nx = c->nx;
+  d.ny = c->ny;
+  d.nz = c->nz;
+  d.ty = ty;
+  d.tz = tz;
+  d.uy = c->uy;
+  d.uz = c->uz;
+  d.nunits = c->nunits;
+  d.ncell = c->n;
+  d.bx = c->bx;
+  d.by = c->by;
+  d.bz = c->bz;
+  d.sinv = c->sinv;
+  d.sx = c->sx;
+  d.sy = c->sy;
+  d.sz = c->sz;
+  d.x = c->x;
+  d.r = c->r;
+  d.d0 = c->d0;
+  d.d1 = c->d1;
+  d.q = c->q;
+  d.part = c->part;
+  d.ticket = c->ticket;
+  d.st = c->st;
+  VDP_CK(cudaMemcpyAsync(c->desc, &d, sizeof(d), cudaMemcpyHostToDevice, c->stream));
+  VDP_CK(cudaStreamSynchronize(c->stream));
+  for (int p = 0; p < 3; ++p) VDP_CK(prepare_step(p, std::max(smem, (size_t)1)));
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->layout_dirty = false;
+  return VDP_OK;
+}
+
+int steps_per_sync(const vdp_ctx* c) {
+  if (c->opts.steps_per_sync > 0) return c->opts.steps_per_sync;
+  return 32;
+}
+
+int ensure_graph(vdp_ctx* c, int prec) {
+  int m = steps_per_sync(c);
+  if (c->gexec && c->g_prec == prec && c->g_steps == m) return VDP_OK;
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  VDP_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < m; ++i) {
+    cudaError_t e = launch_step(prec, c->desc, c->units, c->nunits, c->smem, c->cap);
+    if (e != cudaSuccess) {
+      cudaGraph_t junk;
+      cudaStreamEndCapture(c->cap, &junk);
+      if (junk) cudaGraphDestroy(junk);
+      return cuda_fail(e, "launch_step (capture)");
+    }
+  }
+  VDP_CK(cudaStreamEndCapture(c->cap, &g));
+  cudaError_t e = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  c->g_prec = prec;
+  c->g_steps = m;
+  return VDP_OK;
+}
+
+int ensure_scaled(vdp_ctx* c, int prec) {
+  if (c->scaled_prec == prec) return VDP_OK;
+  VDP_CK(launch_scaled(prec, c->bx, c->by, c->bz, c->sinv, c->nx, c->ny, c->nz, c->sx, c->sy,
+                       c->sz, c->stream));
+  c->scaled_prec = prec;
+  return VDP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vdp_create(int nx, int ny, int nz, double L, vdp_ctx** out) {
+  if (!out) return VDP_EINVAL;
+  *out = nullptr;
+  if (nx < 8 || nx % 8 != 0 || ny < 1 || nz < 1 || !(L > 0.0) || !std::isfinite(L))
+    return VDP_EINVAL;
+  if ((long long)nx * ny * nz > (1LL << 34)) return VDP_EINVAL;
+  vdp_ctx* c = new (std::nothrow) vdp_ctx();
+  if (!c) return VDP_ENOMEM;
+  c->nx = nx;
+  c->ny = ny;
+  c->nz = nz;
+  c->L = L;
+  c->n = (long long)nx * ny * nz;
+  vdp_default_options(&c->opts);
+  cudaGetDevice(&c->device);
+  size_t bytes = sizeof(double) * (size_t)c->n;
+  size_t maxunits = (size_t)ny * nz;
+  cudaError_t e = cudaSuccess;
+  double** f64[] = {&c->bx, &c->by, &c->bz, &c->sinv};
+  for (double** b : f64)
+    if (e == cudaSuccess) e = cudaMalloc((void**)b, bytes);
+  void** vv[] = {&c->sx, &c->sy, &c->sz, &c->x, &c->r, &c->d0, &c->d1, &c->q};
+  for (void** b : vv)
+    if (e == cudaSuccess) e = cudaMalloc(b, bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->part, sizeof(double) * kSlots * maxunits);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->ticket, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->st, sizeof(InstState));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->desc, sizeof(InstDesc));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->units, sizeof(UnitRef) * maxunits);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hstate, 2 * sizeof(InstState));
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->evs[0], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->evs[1], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemset(c->ticket, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    int s = cuda_fail(e, "vdp_create");
+    free_ctx(c);
+    return s;
+  }
+  std::memset(c->hstate, 0, 2 * sizeof(InstState));
+  int s = configure_layout(c);
+  if (s != VDP_OK) {
+    free_ctx(c);
+    return s;
+  }
+  *out = c;
+  return VDP_OK;
+}
+
+void vdp_destroy(vdp_ctx* c) { free_ctx(c); }
+
+int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
+  if (!c || !o) return VDP_EINVAL;
+  if (o->precision < VDP_FP64 || o->precision > VDP_MIXED_BF16) return VDP_EINVAL;
+  if (o->max_iter < 1 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return VDP_EINVAL;
+  if (o->precond != VDP_PRECOND_JACOBI && o->precond != VDP_PRECOND_CHEB) return VDP_EINVAL;
+  if (o->tile_y < 0 || o->tile_z < 0 || o->steps_per_sync < 0) return VDP_EINVAL;
+  bool relayout = o->tile_y != c->opts.tile_y || o->tile_z != c->opts.tile_z ||
+                  o->stream != c->opts.stream;
+  vdp_opts old = c->opts;
+  c->opts = *o;
+  c->stream = (cudaStream_t)o->stream;
+  if (relayout) {
+    int s = configure_layout(c);
+    if (s != VDP_OK) {
+      c->opts = old;
+      c->stream = (cudaStream_t)old.stream;
+      configure_layout(c);
+      return s;
+    }
+  }
+  return VDP_OK;
+}
+
+int vdp_get_options(const vdp_ctx* c, vdp_opts* o) {
+  if (!c || !o) return VDP_EINVAL;
+  *o = c->opts;
+  return VDP_OK;
+}
+
+int vdp_set_density(vdp_ctx* c, const double* rho) {
+  if (!c || !rho) return VDP_EINVAL;
+  const double* src = rho;
+  size_t bytes = sizeof(double) * (size_t)c->n;
+  if (!is_device_ptr(rho)) {
+    if (!c->stage_a) VDP_CK(cudaMalloc((void**)&c->stage_a, bytes));
+    VDP_CK(cudaMemcpyAsync(c->stage_a, rho, bytes, cudaMemcpyHostToDevice, c->stream));
+    src = c->stage_a;
+  }
+  VDP_CK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+  VDP_CK(launch_check_density(src, c->n, c->flag, c->stream));
+  int bad = 0;
+  VDP_CK(cudaMemcpyAsync(&bad, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  VDP_CK(cudaStreamSynchronize(c->stream));
+  if (bad) return VDP_EDENSITY;
+  VDP_CK(launch_build_coefficients(src, c->nx, c->ny, c->nz, c->L, c->bx, c->by, c->bz, c->sinv,
+                                   c->stream));
+  c->scaled_prec = -1;
+  int s = ensure_scaled(c, c->opts.precision);
+  if (s != VDP_OK) return s;
+  VDP_CK(cudaStreamSynchronize(c->stream));
+  c->has_density = true;
+  return VDP_OK;
+}
+
+int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
+  if (!c || !rhs || !p || !(tol > 0.0) || !std::isfinite(tol)) return VDP_EINVAL;
+  if (!c->has_density) return VDP_EINVAL;
+  const int prec = c->opts.precision;
+  size_t bytes = sizeof(double) * (size_t)c->n;
+  const bool host_rhs = !is_device_ptr(rhs), host_p = !is_device_ptr(p);
+  if ((!host_rhs && ((uintptr_t)rhs & 15)) || (!host_p && ((uintptr_t)p & 15))) return VDP_EINVAL;
+  int s;
+  if ((s = ensure_scaled(c, prec)) != VDP_OK) return s;
+  if (c->layout_dirty && (s = configure_layout(c)) != VDP_OK) return s;
+  if ((s = ensure_graph(c, prec)) != VDP_OK) return s;
+  const double* drhs = rhs;
+  double* dp = p;
+  if (host_rhs) {
+    if (!c->stage_a) VDP_CK(cudaMalloc((void**)&c->stage_a, bytes));
+    VDP_CK(cudaMemcpyAsync(c->stage_a, rhs, bytes, cudaMemcpyHostToDevice, c->stream));
+    drhs = c->stage_a;
+  }
+  if (host_p) {
+    if (!c->stage_b) VDP_CK(cudaMalloc((void**)&c->stage_b, bytes));
+    if (c->opts.use_guess)
+      VDP_CK(cudaMemcpyAsync(c->stage_b, p, bytes, cudaMemcpyHostToDevice, c->stream));
+    dp = c->stage_b;
+  }
+  VDP_CK(cudaEventRecord(c->ev0, c->stream));
+  VDP_CK(launch_init(c->desc, drhs, dp, tol, c->opts.inner_tol, c->opts.max_iter,
+                     c->opts.max_iter, c->opts.use_guess ? 1 : 0, prec, c->stream));
+  // Upper bound on sweeps: two per inner iteration plus the outer phases; the state machine
+  // itself stops at max_iter, this only guards the host loop.
+  const long long max_sweeps = 2LL * c->opts.max_iter + 4096;
+  const int m = c->g_steps;
+  const long long max_graphs = (max_sweeps + m - 1) / m;
+  long long issued = 0, checked = 0;
+  bool done = false;
+  auto issue = [&]() -> int {
+    VDP_CK(cudaGraphLaunch(c->gexec, c->stream));
+    VDP_CK(cudaMemcpyAsync(&c->hstate[issued & 1], c->st, sizeof(InstState),
+                           cudaMemcpyDeviceToHost, c->stream));
+    VDP_CK(cudaEventRecord(c->evs[issued & 1], c->stream));
+    ++issued;
+    return VDP_OK;
+  };
+  if ((s = issue()) != VDP_OK) return s;
+  while (!done) {
+    if (issued < max_graphs && (s = issue()) != VDP_OK) return s;
+    VDP_CK(cudaEventSynchronize(c->evs[checked & 1]));
+    if (c->hstate[checked & 1].phase >= PH_DONE) done = true;
+    ++checked;
+    if (!done && checked == issued) break;
+  }
+  VDP_CK(cudaEventRecord(c->ev1, c->stream));
+  if (host_p) VDP_CK(cudaMemcpyAsync(p, dp, bytes, cudaMemcpyDeviceToHost, c->stream));
+  VDP_CK(cudaStreamSynchronize(c->stream));
+  const InstState& hs = c->hstate[(checked - 1) & 1];
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  c->stats.status = done ? hs.status : VDP_ETIMEOUT;
+  c->stats.iters = hs.iters;
+  c->stats.outer_iters = hs.outer;
+  c->stats.rel_res = hs.rel_res;
+  c->stats.rhs_mean = hs.mu_f;
+  c->stats.ms = ms;
+  c->stats.sweeps = hs.sweeps;
+  c->stats.launches = (int)(1 + issued * m);
+  return c->stats.status;
+}
+
+int vdp_get_stats(const vdp_ctx* c, vdp_stats* s) {
+  if (!c || !s) return VDP_EINVAL;
+  *s = c->stats;
+  return VDP_OK;
+}
+
+int vdp_apply(vdp_ctx* c, const double* p, double* out) {
+  if (!c || !p || !out || p == out) return VDP_EINVAL;
+  if (!c->has_density) return VDP_EINVAL;
+  size_t bytes = sizeof(double) * (size_t)c->n;
+  const bool hp = !is_device_ptr(p), ho = !is_device_ptr(out);
+  const double* dp = p;
+  double* dout = out;
+  if (hp) {
+    if (!c->stage_a) VDP_CK(cudaMalloc((void**)&c->stage_a, bytes));
+    VDP_CK(cudaMemcpyAsync(c->stage_a, p, bytes, cudaMemcpyHostToDevice, c->stream));
+    dp = c->stage_a;
+  }
+  if (ho) {
+    if (!c->stage_b) VDP_CK(cudaMalloc((void**)&c->stage_b, bytes));
+    dout = c->stage_b;
+  }
+  VDP_CK(launch_apply(c->bx, c->by, c->bz, dp, c->nx, c->ny, c->nz, dout, c->stream));
+  if (ho) VDP_CK(cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, c->stream));
+  VDP_CK(cudaStreamSynchronize(c->stream));
+  return VDP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// vdp_internal.cuh -- device-side data structures shared by the solver kernels and the host
+// driver of libvdp.  Not part of the public ABI (include/vdp.h is).
+//
+// The solve is a small state machine per problem instance, advanced one "sweep" at a time by
+// the step kernel.  Every sweep is a pass over the instance's grid split into work units
+// (full x rows, ty rows, tz planes); each unit writes its partial sums into its own slot and
+// the last unit to finish (atomic ticket) reduces the slots in a fixed order and moves the
+// instance to its next phase.  Results are therefore bitwise reproducible for a fixed unit
+// shape, whether an instance runs alone or inside a batch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace vdp {
+
+// Phases of one solve (see the step kernel for what each sweep does).
+enum Phase : int {
+  PH_MEANF = 0,    // <f>; p := 0 unless the caller gave a guess
+  PH_RES64 = 1,    // FP64 residual r = (f - <f>) - A p, inner rhs rt = D^-1/2 r, norms, sum(p)
+  PH_STENCIL = 2,  // d = rt + beta d_old; q = At d; <d, q>
+  PH_UPDATE = 3,   // x += alpha d; rt -= alpha q; <rt, rt>
+  PH_CORRECT = 4,  // p -= D^-1/2 x   (refinement step of the outer FP64 loop)
+  PH_FINAL = 5,    // p -= <p>  (gauge)
+  PH_DONE = 6
+};
+
+enum Prec : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_MIXED_BF16 = 2 };
+
+constexpr int kSlots = 4;          // partial-sum slots per unit
+constexpr int kThreads = 256;      // threads per work unit (CTA)
+
+// Mutable per-instance solver state (device memory).
+struct InstState {
+  int phase;
+  int status;          // vdp_status
+  int iters;           // total inner iterations
+  int inner_iters;     // iterations of the current inner solve
+  int outer;           // FP64 residual evaluations
+  int parity;          // which direction buffer holds the current search direction
+  int first_res;       // next RES64 also measures ||f - <f>||
+  int zero_sol;        // f - <f> == 0: the answer is p = 0
+  int sweeps;          // sweeps executed (all phases)
+  int max_iter;
+  int inner_max;
+  int use_guess;
+  int precision;
+  int pad0;
+  double tol;          // requested relative residual
+  double inner_tol;    // mixed: minimum relative reduction per inner solve
+  double mu_f;         // <f>
+  double fn2;          // ||f - <f>||^2
+  double f2;           // ||f||^2
+  double rr64;         // ||r||^2 at the last RES64
+  double rr64_prev;    // ... at the RES64 before
+  double rr;           // <rt, rt> (current inner)
+  double rr0;          // <rt, rt> at the start of the inner solve
+  double alpha, beta;
+  double tau2;         // inner stop: rr <= tau2 * rr0
+  double eta;          // observed ratio between FP64 and scaled inner residual reductions
+  double inner_ratio;  // sqrt(rr / rr0) at the end of the last inner solve
+  double sum_p;        // sum of p at the last RES64
+  double rel_res;      // FP64 relative residual at the last RES64
+};
+
+// Constant per-instance description (device memory).
+struct InstDesc {
+  int nx, ny, nz;
+  int ty, tz;          // unit shape: rows, planes
+  int uy, uz;          // units along y, z
+  int nunits;
+  long long ncell;
+  const double* rhs;   // caller's f (set per solve)
+  double* p;           // caller's p (set per solve)
+  const double* bx;    // FP64 face coefficients 2/(rho_l+rho_r)/h^2 on the low faces
+  const double* by;
+  const double* bz;
+  const double* sinv;  // D^-1/2, D = sum of the six face coefficients of a cell
+  const void* sx;      // scaled coefficients bt = b sinv_l sinv_r in the inner storage type
+  const void* sy;
+  const void* sz;
+  void* x;             // inner solution (correction), inner type
+  void* r;             // inner residual
+  void* d0;            // search direction, double buffered
+  void* d1;
+  void* q;             // At d
+  double* part;        // kSlots x nunits partial sums
+  unsigned int* ticket;
+  InstState* st;
+};
+
+struct UnitRef {
+  int inst;            // index into the batch's InstDesc table
+  int unit;            // unit index within the instance
+};
+
+}  // namespace vdp

@@ -1,0 +1,26 @@
+// vdp_launch.h -- host-side launchers of the kernels in vdp_kernels.cu (internal to libvdp).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "vdp_internal.cuh"
+
+namespace vdp {
+
+cudaError_t launch_check_density(const double* rho, long long n, int* bad, cudaStream_t s);
+cudaError_t launch_build_coefficients(const double* rho, int nx, int ny, int nz, double L,
+                                      double* bx, double* by, double* bz, double* sinv,
+                                      cudaStream_t s);
+cudaError_t launch_scaled(int prec, const double* bx, const double* by, const double* bz,
+                          const double* sinv, int nx, int ny, int nz, void* sx, void* sy, void* sz,
+                          cudaStream_t s);
+cudaError_t launch_apply(const double* bx, const double* by, const double* bz, const double* p,
+                         int nx, int ny, int nz, double* out, cudaStream_t s);
+cudaError_t launch_init(InstDesc* desc, const double* rhs, double* p, double tol, double inner_tol,
+                        int max_iter, int inner_max, int use_guess, int precision,
+                        cudaStream_t s);
+cudaError_t prepare_step(int prec, size_t smem_bytes);
+cudaError_t launch_step(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
+                        size_t smem_bytes, cudaStream_t s);
+
+}  // namespace vdp

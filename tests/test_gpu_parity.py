@@ -1,0 +1,181 @@
+"""GPU parity: the sm_103a library (through its C ABI) against the FP64 CPU oracle on the same
+seeded inputs.
+
+Tolerances: relative L2 pressure error <= 1e-9 for the FP64 path and <= 1e-8 for the mixed
+FP32/BF16-inside-FP64-refinement paths; the library's own FP64 residual must meet the requested
+tolerance, and the oracle's operator must agree that it does.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import paper_1601_05448_gb300 as vdp  # noqa: E402
+import vdp_inputs as V  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_solve(prob, precision="fp64", tol=None, **opts):
+    nz, ny, nx = prob.shape
+    rho = torch.from_numpy(prob.rho).to(DEV)
+    f = torch.from_numpy(prob.f).to(DEV)
+    p = torch.empty_like(f)
+    with vdp.Solver(nx, ny, nz, prob.L, precision=precision, **opts) as s:
+        s.set_density(rho)
+        st = s.solve(f, p, prob.tol if tol is None else tol)
+    return p.cpu().numpy(), st
+
+
+_ORACLE = {}
+
+
+def oracle_solution(prob, key):
+    if key not in _ORACLE:
+        p, info = oracle.solve_cg(prob.rho, prob.f, prob.L, tol=1e-13)
+        assert info["status"] == "ok"
+        _ORACLE[key] = p
+    return _ORACLE[key]
+
+
+# (nz, ny, nx): cubic, ragged against the default unit shape, odd y/z, thin, 1-D in x
+SHAPES = [(8, 8, 8), (12, 20, 24), (32, 32, 32), (17, 9, 16), (40, 36, 48), (3, 5, 64), (1, 1, 8), (24, 30, 8)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fp64_matches_oracle(shape):
+    prob = V.smooth_problem(shape, seed=sum(shape))
+    p, st = gpu_solve(prob, "fp64", tol=1e-10)
+    ref = oracle_solution(prob, ("smooth", shape))
+    assert st.ok and st.rel_res <= 1e-10
+    assert rel(p, ref) <= 1e-9, (st, rel(p, ref))
+    assert abs(float(p.mean())) <= 1e-13 * float(np.abs(p).max())
+    assert oracle.relative_residual(prob.rho, prob.L, prob.f, p) <= 1.01e-10
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (40, 36, 48), (17, 9, 16)])
+def test_mixed_matches_oracle(shape, precision):
+    prob = V.smooth_problem(shape, seed=sum(shape))
+    p, st = gpu_solve(prob, precision, tol=1e-9)
+    ref = oracle_solution(prob, ("smooth", shape))
+    assert st.ok and st.rel_res <= 1e-9, st
+    assert rel(p, ref) <= 1e-8, (st, rel(p, ref))
+    assert oracle.relative_residual(prob.rho, prob.L, prob.f, p) <= 1.01e-9
+
+
+def test_config0_fp64():
+    prob = V.config0()
+    p, st = gpu_solve(prob, "fp64")
+    ref = oracle_solution(prob, "c0")
+    err = rel(p, ref)
+    print(f"config0 fp64: iters={st.iters} outer={st.outer_iters} rel_res={st.rel_res:.3e} err={err:.3e}")
+    assert st.ok and err <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
+def test_config0_mixed(precision):
+    prob = V.config0()
+    p, st = gpu_solve(prob, precision, tol=1e-8)
+    ref = oracle_solution(prob, "c0")
+    err = rel(p, ref)
+    print(f"config0 {precision} tol 1e-8: iters={st.iters} outer={st.outer_iters} rel_res={st.rel_res:.3e} err={err:.3e}")
+    assert st.ok and st.rel_res <= 1e-8
+
+
+def test_hotspot_96_all_precisions():
+    prob = V.hotspot_problem(96, seed=21, nspots=int(round(20000 * 96 ** 3 / 256 ** 3)), target_ratio=8.0)
+    ref = oracle_solution(prob, "hot96")
+    for precision, tol, bound in (("fp64", 1e-10, 1e-9), ("mixed", 1e-9, 1e-8), ("mixed_bf16", 1e-9, 1e-8)):
+        p, st = gpu_solve(prob, precision, tol=tol)
+        err = rel(p, ref)
+        print(f"hot96 {precision}: iters={st.iters} outer={st.outer_iters} rel_res={st.rel_res:.3e} err={err:.3e}")
+        assert st.ok and st.rel_res <= tol and err <= bound
+
+
+def test_operator_matches_oracle():
+    prob = V.smooth_problem((20, 12, 16), seed=3)
+    nz, ny, nx = prob.shape
+    u = np.random.default_rng(1).standard_normal(prob.shape)
+    out = torch.empty(prob.shape, dtype=torch.float64, device=DEV)
+    with vdp.Solver(nx, ny, nz, prob.L) as s:
+        s.set_density(torch.from_numpy(prob.rho).to(DEV))
+        s.apply(torch.from_numpy(u).to(DEV), out)
+    ref = oracle.apply_rho(prob.rho, prob.L, u)
+    assert rel(out.cpu().numpy(), ref) <= 1e-14
+
+
+def test_deterministic_and_host_pointers():
+    prob = V.smooth_problem((16, 16, 32), seed=9)
+    p1, s1 = gpu_solve(prob, "mixed", tol=1e-9)
+    p2, s2 = gpu_solve(prob, "mixed", tol=1e-9)
+    assert np.array_equal(p1, p2) and s1.iters == s2.iters
+    nz, ny, nx = prob.shape
+    ph = np.empty_like(prob.f)
+    with vdp.Solver(nx, ny, nz, prob.L, precision="mixed") as s:
+        s.set_density(prob.rho)            # host pointers: staged by the library
+        s.solve(prob.f, ph, 1e-9)
+    assert np.array_equal(ph, p1)
+
+
+def test_compatibility_gauge_and_degenerate_rhs():
+    prob = V.smooth_problem((16, 12, 24), seed=4)
+    nz, ny, nx = prob.shape
+    with vdp.Solver(nx, ny, nz, prob.L) as s:
+        s.set_density(torch.from_numpy(prob.rho).to(DEV))
+        p0 = torch.empty(prob.shape, dtype=torch.float64, device=DEV)
+        st0 = s.solve(torch.from_numpy(prob.f).to(DEV), p0, 1e-11)
+        p1 = torch.empty_like(p0)
+        st1 = s.solve(torch.from_numpy(prob.f + 3.5).to(DEV), p1, 1e-11)  # nonzero mean
+        assert abs(st1.rhs_mean - st0.rhs_mean - 3.5) < 1e-12
+        assert rel(p1.cpu().numpy(), p0.cpu().numpy()) < 1e-9
+        for const in (0.0, 2.0):
+            pz = torch.full(prob.shape, 7.0, dtype=torch.float64, device=DEV)
+            stz = s.solve(torch.full(prob.shape, const, dtype=torch.float64, device=DEV), pz, 1e-10)
+            assert stz.ok and stz.iters == 0 and bool((pz == 0).all())
+
+
+def test_initial_guess_and_errors():
+    prob = V.smooth_problem((8, 8, 16), seed=5)
+    nz, ny, nx = prob.shape
+    ref = oracle_solution(prob, "guess")
+    with vdp.Solver(nx, ny, nz, prob.L, use_guess=1) as s:
+        f = torch.from_numpy(prob.f).to(DEV)
+        p = torch.from_numpy(ref.copy()).to(DEV)
+        with pytest.raises(vdp.VdpError) as e:   # solve before set_density
+            s.solve(f, p, 1e-10)
+        assert e.value.status == vdp.VDP_EINVAL
+        s.set_density(torch.from_numpy(prob.rho).to(DEV))
+        st = s.solve(f, p, 1e-10)                # the exact answer as a guess: no iteration
+        assert st.ok and st.iters == 0 and st.outer_iters == 1
+        bad = prob.rho.copy()
+        bad[3, 2, 1] = -1.0
+        with pytest.raises(vdp.VdpError) as e:
+            s.set_density(torch.from_numpy(bad).to(DEV))
+        assert e.value.status == vdp.VDP_EDENSITY
+        bad[3, 2, 1] = float("nan")
+        with pytest.raises(vdp.VdpError):
+            s.set_density(torch.from_numpy(bad).to(DEV))
+        st = s.solve(f, p, 1e-10)                # previous density kept
+        assert st.ok
+        with pytest.raises(vdp.VdpError) as e:   # misaligned device pointer
+            s.solve(f, torch.empty(prob.f.size + 1, dtype=torch.float64, device=DEV)[1:], 1e-10)
+        assert e.value.status == vdp.VDP_EINVAL
+
+
+def test_iteration_cap_reports_notconv():
+    prob = V.smooth_problem((32, 32, 32), seed=6)
+    nz, ny, nx = prob.shape
+    with vdp.Solver(nx, ny, nz, prob.L, max_iter=5) as s:
+        s.set_density(torch.from_numpy(prob.rho).to(DEV))
+        p = torch.empty(prob.shape, dtype=torch.float64, device=DEV)
+        st = s.solve(torch.from_numpy(prob.f).to(DEV), p, 1e-10, check=False)
+    assert st.status == vdp.VDP_ENOTCONV and st.iters == 5
+    pc = p.cpu().numpy()
+    assert np.isfinite(pc).all() and abs(float(pc.mean())) < 1e-12 * float(np.abs(pc).max())
