@@ -1,0 +1,317 @@
+"""Benchmark: Poisson solves/s of the variable-density pressure solve on one GB300.
+
+One step = one complete solve (all phases: rhs mean removal, Krylov iterations with FP64
+refinement, gauge) of the 256^3 periodic hot-spot workload: rho = T0/T with 20k Gaussian hot
+spots (density ratio 4), rhs = divergence of a random low-k velocity field, FP64, relative
+residual 1e-10.  Inputs are resident in HBM when timing starts; the working set (~1.6 GB) is far
+larger than L2.  The JSON line also carries the end-to-end number through the C ABI with host
+buffers, the roofline of the step kernel, the mixed-precision paths on the same input (solves/s
+to 1e-8 for FP64, FP32-inside-FP64 and BF16-coefficient ablation) and the CPU oracle baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  torchrun --nproc-per-node N bench.py --gpus N ...   (N independent replicas, weak scaling)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solves/s and % HBM roofline to 1e-8 rel. residual, mixed vs FP64"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64 vector peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# Algorithmic bytes and flops per cell of one sweep (inner type T bytes, coefficient bytes B):
+#   stencil: read rt, d_old, 3 coefficients; write d, q          -> 4T + 3B + (BF16: diag B)
+#   update : read x, d, q, rt; write x, rt  (x not read on the first inner iteration)  -> 6T
+#   res64  : read p, f, sinv, 3 FP64 coefficients; write rt        -> 6*8 + T
+#   correct: read p, sinv, x; write p                              -> 24 + T
+#   meanf  : read f, write p                                        -> 16;  final: 16
+# flops per cell and inner iteration: 8 FMA in the stencil sweep (d, six faces, <d,q>) and 3 FMA
+# in the update sweep (x, rt, <rt,rt>): 22 flop.
+SIZES = {"fp64": (8, 8, False), "mixed": (4, 4, False), "mixed_bf16": (4, 2, True)}
+
+
+def algorithmic(prec: str, ncell: int, iters: int, outer: int):
+    T, B, diag = SIZES[prec]
+    per_iter = (4 * T + 3 * B + (B if diag else 0)) + 6 * T
+    total = iters * per_iter + outer * (48 + T) + max(outer - 1, 0) * (24 + T) + 32
+    return total * ncell, 22.0 * iters * ncell
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
+    except Exception:
+        return dict(PEAKS_FALLBACK, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(prob, iters_per_sample: int = 12):
+    """The CPU oracle (FP64 Jacobi-PCG, all host cores) on a bounded sample of the workload:
+    `iters_per_sample` iterations of the 256^3 solve, scaled to solves/s with the oracle's own
+    iteration count to 1e-10 on this input (tests/golden/oracle_iterations.json)."""
+    import oracle
+    golden = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+    with open(golden) as fh:
+        g = json.load(fh)
+    n_it = int(g["oracle_iterations"])
+    t0 = time.perf_counter()
+    _, info = oracle.solve_cg(prob.rho, prob.f, prob.L, tol=0.0, maxit=iters_per_sample)
+    dt = time.perf_counter() - t0
+    t_iter = dt / max(info["iters"], 1)
+    return {"value": 1.0 / (t_iter * n_it), "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{info['iters']} FP64 Jacobi-PCG iterations of the 256^3 workload in {dt:.1f} s "
+                      f"(incl. set-up), scaled by the oracle's {n_it} iterations to 1e-10"}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the CPU oracle as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return 0
+    import vdp_inputs as V
+    prob = V.config1()
+    for _ in range(args.warmup):
+        cpu_baseline(prob, iters_per_sample=2)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(prob, iters_per_sample=args.ref_iters)
+        secs.append(time.perf_counter() - t0)
+        vals.append(cb["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": prob.name, "grid": "256^3", "tol": prob.tol, "density_ratio": prob.info["ratio"],
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"] + f"; median of {args.steps} samples"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-iters", type=int, default=10, help="oracle iterations per reference-arm sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip mixed paths, e2e and CPU baseline")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    import paper_1601_05448_gb300 as vdp
+    import vdp_inputs as V
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    prob = V.config1()
+    nz, ny, nx = prob.shape
+    ncell = nx * ny * nz
+    rho = torch.from_numpy(prob.rho).to(dev)
+    f = torch.from_numpy(prob.f).to(dev)
+    p = torch.empty_like(f)
+    stream = torch.cuda.current_stream(dev)
+    solver = vdp.Solver(nx, ny, nz, prob.L, precision="fp64", stream=stream)
+    solver.set_density(rho)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(args.warmup, 3)):
+        solver.solve(f, p, prob.tol)
+    barrier()
+    stats = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            stats.append(solver.solve(f, p, prob.tol))
+        ev1.record(stream)
+        barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if pg is not None:
+        t = torch.tensor([elapsed], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed = float(t.item())
+    solves = world * args.steps
+    value = solves / elapsed
+    launches = sum(s.launches for s in stats)
+    iters = stats[-1].iters
+    outer = stats[-1].outer_iters
+
+    # roofline of the step kernel (it is every launch in the timed region but the per-solve init)
+    peaks = load_peaks()
+    b_per_solve, fl_per_solve = algorithmic("fp64", ncell, iters, outer)
+    t_launch = elapsed / launches
+    b_launch = b_per_solve * args.steps / launches
+    f_launch = fl_per_solve * args.steps / launches
+    hbm = {"bound": "hbm", "achieved": b_launch / t_launch / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    hbm["frac"] = hbm["achieved"] / hbm["peak"]
+    alu = {"bound": "alu", "achieved": f_launch / t_launch / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    alu["frac"] = alu["achieved"] / alu["peak"]
+    # the binding roof is the one that needs more time for the algorithmic work
+    roof = alu if fl_per_solve / (FP64_PEAK_TFLOPS * 1e12) > b_per_solve / (peaks["hbm_gbs"] * 1e9) else hbm
+    roof = dict(roof, traffic=None, kernel="k_step<double,double>", peak_source=peaks["source"] if roof is hbm
+                else "nominal: 152 SM x 2 DFMA/clk x 2.07 GHz")
+    other = hbm if roof["bound"] == "alu" else alu
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "256^3 periodic box L=2pi, rho=T0/T (20k hot spots, density ratio 4), "
+                               "rhs=div of random |k|<=4 velocity; FP64 Jacobi-scaled CG + FP64 refinement, "
+                               "tol 1e-10", "grid": [nx, ny, nz], "tol": prob.tol,
+                   "density_ratio": round(prob.info["ratio"], 4), "l2": "inputs larger than L2 (~1.6 GB working set)",
+                   "replicas": world},
+        "iterations": iters, "outer_iterations": outer, "rel_res": stats[-1].rel_res,
+        "gdof_iter_per_s": ncell * iters * args.steps * world / elapsed / 1e9,
+        "gpu_launches": launches + args.steps,
+        "roofline": roof, "roofline_other": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")},
+        "clocks": clk.summary(),
+    }
+
+    if not args.no_extras:
+        # end to end through the C ABI with host buffers: H2D of rhs and D2H of p inside the timing
+        fh = torch.from_numpy(prob.f).pin_memory()
+        ph = torch.empty(prob.shape, dtype=torch.float64).pin_memory()
+        solver.solve(fh, ph, prob.tol)
+        barrier()
+        t0 = time.perf_counter()
+        ee0 = torch.cuda.Event(enable_timing=True)
+        ee1 = torch.cuda.Event(enable_timing=True)
+        ee0.record(stream)
+        for _ in range(args.steps):
+            solver.solve(fh, ph, prob.tol)
+        ee1.record(stream)
+        barrier()
+        e_el = max(ee0.elapsed_time(ee1) / 1e3, 1e-9)
+        line["e2e"] = {"value": world * args.steps / e_el, "unit": "solves/s",
+                       "h2d_bytes_per_step": int(prob.f.nbytes), "d2h_bytes_per_step": int(prob.f.nbytes),
+                       "wall_s": time.perf_counter() - t0}
+        # mixed vs FP64 at equal final accuracy (relative residual 1e-8), same input
+        import oracle
+        paths = {}
+        for prec in ("fp64", "mixed", "mixed_bf16"):
+            with vdp.Solver(nx, ny, nz, prob.L, precision=prec, stream=stream) as s2:
+                s2.set_density(rho)
+                pp = torch.empty_like(f)
+                s2.solve(f, pp, 1e-8, check=False)
+                ts = [s2.solve(f, pp, 1e-8, check=False) for _ in range(3)]
+                best = min(ts, key=lambda s: s.ms)
+                b, fl = algorithmic(prec, ncell, best.iters, best.outer_iters)
+                paths[prec] = {"solves_per_s": 1e3 / best.ms, "ms": best.ms, "iters": best.iters,
+                               "outer": best.outer_iters, "status": vdp.vdp_strerror(best.status),
+                               "rel_res": best.rel_res,
+                               "hbm_frac": b / (best.ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                               "oracle_rel_res": oracle.relative_residual(prob.rho, prob.L, prob.f,
+                                                                          pp.cpu().numpy())}
+        line["mixed_vs_fp64_at_1e-8"] = paths
+        if rank == 0:
+            try:
+                line["cpu_baseline"] = cpu_baseline(prob)
+            except Exception as e:  # the stored iteration count is missing
+                line["cpu_baseline"] = {"value": None, "unit": "solves/s", "kind": "oracle", "error": str(e)}
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

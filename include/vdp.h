@@ -73,8 +73,9 @@ typedef struct {
   int cheb_degree;     /* polynomial degree for VDP_PRECOND_CHEB (default 4) */
   int use_guess;       /* 1: p on entry to vdp_solve is the initial guess; 0: start from p = 0 */
   void *stream;        /* cudaStream_t for all work of this context (default NULL) */
-  int tile_y;          /* rows per work unit (0 = automatic) */
-  int tile_z;          /* planes per work unit (0 = automatic) */
+  int tile_y;          /* rows per row tile of a work unit (0 = automatic) */
+  int units;           /* work units (thread blocks) per sweep (0 = automatic) */
+  int stages;          /* shared-memory pipeline stages of the stencil sweep, 4..8 (0 = auto) */
   int steps_per_sync;  /* device sweeps per host convergence check (0 = automatic) */
 } vdp_opts;
 

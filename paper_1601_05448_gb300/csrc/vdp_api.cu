@@ -61,7 +61,7 @@ struct vdp_ctx {
   // FP64 operator data
   double *bx = nullptr, *by = nullptr, *bz = nullptr, *sinv = nullptr;
   // inner-precision data (sized for FP64, reinterpreted for FP32 / BF16)
-  void *sx = nullptr, *sy = nullptr, *sz = nullptr;
+  void *sx = nullptr, *sy = nullptr, *sz = nullptr, *sd = nullptr;
   void *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr, *q = nullptr;
   int scaled_prec = -1;            // precision the scaled coefficients were built for
   bool has_density = false;
@@ -76,8 +76,9 @@ struct vdp_ctx {
   InstState* hstate = nullptr;     // pinned, 2 entries
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs[2] = {nullptr, nullptr};
   // layout
-  int ty = 0, tz = 0, uy = 0, uz = 0, nunits = 0;
+  int ty = 0, nunits = 0;
   size_t smem = 0;
+  int layout_prec = -1;
   bool layout_dirty = true;
   // graph cache
   cudaGraphExec_t gexec = nullptr;
@@ -98,7 +99,8 @@ void vdp_default_options(vdp_opts* o) {
   o->use_guess = 0;
   o->stream = nullptr;
   o->tile_y = 0;
-  o->tile_z = 0;
+  o->units = 0;
+  o->stages = 0;
   o->steps_per_sync = 0;
 }
 
@@ -133,7 +135,7 @@ void free_ctx(vdp_ctx* c) {
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
-  void* bufs[] = {c->bx, c->by, c->bz, c->sinv, c->sx, c->sy, c->sz, c->x, c->r, c->d0, c->d1,
+  void* bufs[] = {c->bx, c->by, c->bz, c->sinv, c->sx, c->sy, c->sz, c->sd, c->x, c->r, c->d0, c->d1,
                   c->q, c->part, c->ticket, c->st, c->desc, c->units, c->flag, c->stage_a,
                   c->stage_b};
   for (void* b : bufs)
@@ -147,35 +149,53 @@ void free_ctx(vdp_ctx* c) {
   delete c;
 }
 
-// Work-unit shape: full x rows; about 1024 cells per plane per unit; enough units to fill the
-// GPU several times over.
-void auto_layout(int nx, int ny, int nz, int* ty, int* tz) {
-  int t = std::max(1, std::min(ny, 1024 / std::max(nx, 1)));
-  int uy = (ny + t - 1) / t;
-  const int target_units = 152 * 4;
-  int z = (int)((long long)nz * uy / target_units);
-  z = std::max(2, std::min(z, 32));
-  z = std::min(z, nz);
-  *ty = t;
-  *tz = z;
+constexpr size_t kSmemBudget = 225 * 1024;  // dynamic shared memory per work unit
+
+size_t inner_size(int prec) { return prec == PREC_FP64 ? 8 : 4; }
+size_t coef_size(int prec) { return prec == PREC_FP64 ? 8 : (prec == PREC_MIXED ? 4 : 2); }
+
+// Work-unit shape for precision `prec`: full x rows, row tiles of about 1024 cells; as many
+// pipeline stages as fit in shared memory (at most 6); one unit per SM (the stencil sweep
+// keeps about 100-200 KB of shared memory per unit in flight).
+struct Layout {
+  int ty, uy, nunits, stages;
+  long long npairs;
+  size_t smem;
+};
+
+int choose_layout(const vdp_ctx* c, int prec, Layout* out) {
+  const int nx = c->nx, ny = c->ny, nz = c->nz;
+  const size_t ts = inner_size(prec), bs = coef_size(prec);
+  int ty = c->opts.tile_y > 0 ? c->opts.tile_y : std::max(1, std::min(ny, 1024 / nx));
+  ty = std::min(ty, ny);
+  // shrink the tile until at least three stages fit
+  const bool diag = prec == PREC_MIXED_BF16;
+  while (ty > 1 && 4 * stage_bytes(nx, ty, (int)ts, (int)bs, diag) > kSmemBudget) --ty;
+  const size_t sb = stage_bytes(nx, ty, (int)ts, (int)bs, diag);
+  int fit = (int)(kSmemBudget / sb);
+  if (fit < 4) return VDP_EINVAL;  // rows too long for the shared-memory pipeline
+  int stages = c->opts.stages > 0 ? c->opts.stages : std::min(fit, 6);
+  if (stages < 4 || stages > kMaxStages || stages > fit) return VDP_EINVAL;
+  const int uy = (ny + ty - 1) / ty;
+  const long long npairs = (long long)uy * nz;
+  long long units = c->opts.units > 0 ? c->opts.units : 152;
+  units = std::min(units, npairs);
+  out->ty = ty;
+  out->uy = uy;
+  out->nunits = (int)units;
+  out->stages = stages;
+  out->npairs = npairs;
+  out->smem = std::max((size_t)stages * sb, ring_bytes(nx, ty));
+  return VDP_OK;
 }
 
-int configure_layout(vdp_ctx* c) {
-  int ty = c->opts.tile_y, tz = c->opts.tile_z;
-  int aty, atz;
-  auto_layout(c->nx, c->ny, c->nz, &aty, &atz);
-  if (ty <= 0) ty = aty;
-  if (tz <= 0) tz = atz;
-  ty = std::min(ty, c->ny);
-  tz = std::min(tz, c->nz);
-  size_t smem = (size_t)3 * (ty + 2) * c->nx * sizeof(double);
-  if (smem > 200 * 1024) return VDP_EINVAL;
-  c->ty = ty;
-  c->tz = tz;
-  c->uy = (c->ny + ty - 1) / ty;
-  c->uz = (c->nz + tz - 1) / tz;
-  c->nunits = c->uy * c->uz;
-  c->smem = smem;
+int configure_layout(vdp_ctx* c, int prec) {
+  Layout lay;
+  int s = choose_layout(c, prec, &lay);
+  if (s != VDP_OK) return s;
+  c->ty = lay.ty;
+  c->nunits = lay.nunits;
+  c->smem = lay.smem;
   std::vector<UnitRef> u(c->nunits);
   for (int i = 0; i < c->nunits; ++i) u[i] = UnitRef{0, i};
   VDP_CK(cudaMemcpyAsync(c->units, u.data(), sizeof(UnitRef) * u.size(), cudaMemcpyHostToDevice,
@@ -184,11 +204,11 @@ int configure_layout(vdp_ctx* c) {
   d.nx = c->nx;
   d.ny = c->ny;
   d.nz = c->nz;
-  d.ty = ty;
-  d.tz = tz;
-  d.uy = c->uy;
-  d.uz = c->uz;
-  d.nunits = c->nunits;
+  d.ty = lay.ty;
+  d.uy = lay.uy;
+  d.nunits = lay.nunits;
+  d.stages = lay.stages;
+  d.npairs = lay.npairs;
   d.ncell = c->n;
   d.bx = c->bx;
   d.by = c->by;
@@ -197,6 +217,7 @@ int configure_layout(vdp_ctx* c) {
   d.sx = c->sx;
   d.sy = c->sy;
   d.sz = c->sz;
+  d.sd = c->sd;
   d.x = c->x;
   d.r = c->r;
   d.d0 = c->d0;
@@ -207,11 +228,12 @@ int configure_layout(vdp_ctx* c) {
   d.st = c->st;
   VDP_CK(cudaMemcpyAsync(c->desc, &d, sizeof(d), cudaMemcpyHostToDevice, c->stream));
   VDP_CK(cudaStreamSynchronize(c->stream));
-  for (int p = 0; p < 3; ++p) VDP_CK(prepare_step(p, std::max(smem, (size_t)1)));
+  VDP_CK(prepare_step(prec, c->smem));
   if (c->gexec) {
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
   }
+  c->layout_prec = prec;
   c->layout_dirty = false;
   return VDP_OK;
 }
@@ -251,7 +273,7 @@ int ensure_graph(vdp_ctx* c, int prec) {
 int ensure_scaled(vdp_ctx* c, int prec) {
   if (c->scaled_prec == prec) return VDP_OK;
   VDP_CK(launch_scaled(prec, c->bx, c->by, c->bz, c->sinv, c->nx, c->ny, c->nz, c->sx, c->sy,
-                       c->sz, c->stream));
+                       c->sz, c->sd, c->stream));
   c->scaled_prec = prec;
   return VDP_OK;
 }
@@ -276,12 +298,13 @@ int vdp_create(int nx, int ny, int nz, double L, vdp_ctx** out) {
   vdp_default_options(&c->opts);
   cudaGetDevice(&c->device);
   size_t bytes = sizeof(double) * (size_t)c->n;
-  size_t maxunits = (size_t)ny * nz;
+  size_t maxunits = (size_t)std::max(ny * (size_t)nz, (size_t)152 * 16);
   cudaError_t e = cudaSuccess;
   double** f64[] = {&c->bx, &c->by, &c->bz, &c->sinv};
   for (double** b : f64)
     if (e == cudaSuccess) e = cudaMalloc((void**)b, bytes);
   void** vv[] = {&c->sx, &c->sy, &c->sz, &c->x, &c->r, &c->d0, &c->d1, &c->q};
+  if (e == cudaSuccess) e = cudaMalloc(&c->sd, sizeof(uint16_t) * (size_t)c->n);
   for (void** b : vv)
     if (e == cudaSuccess) e = cudaMalloc(b, bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->part, sizeof(double) * kSlots * maxunits);
@@ -303,10 +326,10 @@ int vdp_create(int nx, int ny, int nz, double L, vdp_ctx** out) {
     return s;
   }
   std::memset(c->hstate, 0, 2 * sizeof(InstState));
-  int s = configure_layout(c);
-  if (s != VDP_OK) {
+  Layout lay;
+  if (choose_layout(c, c->opts.precision, &lay) != VDP_OK) {  // rows too long for any stage
     free_ctx(c);
-    return s;
+    return VDP_EINVAL;
   }
   *out = c;
   return VDP_OK;
@@ -319,21 +342,18 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
   if (o->precision < VDP_FP64 || o->precision > VDP_MIXED_BF16) return VDP_EINVAL;
   if (o->max_iter < 1 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return VDP_EINVAL;
   if (o->precond != VDP_PRECOND_JACOBI && o->precond != VDP_PRECOND_CHEB) return VDP_EINVAL;
-  if (o->tile_y < 0 || o->tile_z < 0 || o->steps_per_sync < 0) return VDP_EINVAL;
-  bool relayout = o->tile_y != c->opts.tile_y || o->tile_z != c->opts.tile_z ||
-                  o->stream != c->opts.stream;
+  if (o->tile_y < 0 || o->units < 0 || o->stages < 0 || o->steps_per_sync < 0) return VDP_EINVAL;
+  if (o->units > 152 * 16 || o->stages > kMaxStages || (o->stages > 0 && o->stages < 4))
+    return VDP_EINVAL;
   vdp_opts old = c->opts;
   c->opts = *o;
-  c->stream = (cudaStream_t)o->stream;
-  if (relayout) {
-    int s = configure_layout(c);
-    if (s != VDP_OK) {
-      c->opts = old;
-      c->stream = (cudaStream_t)old.stream;
-      configure_layout(c);
-      return s;
-    }
+  Layout lay;
+  if (choose_layout(c, o->precision, &lay) != VDP_OK) {
+    c->opts = old;
+    return VDP_EINVAL;
   }
+  c->stream = (cudaStream_t)o->stream;
+  c->layout_dirty = true;
   return VDP_OK;
 }
 
@@ -377,7 +397,8 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   if ((!host_rhs && ((uintptr_t)rhs & 15)) || (!host_p && ((uintptr_t)p & 15))) return VDP_EINVAL;
   int s;
   if ((s = ensure_scaled(c, prec)) != VDP_OK) return s;
-  if (c->layout_dirty && (s = configure_layout(c)) != VDP_OK) return s;
+  if ((c->layout_dirty || c->layout_prec != prec) && (s = configure_layout(c, prec)) != VDP_OK)
+    return s;
   if ((s = ensure_graph(c, prec)) != VDP_OK) return s;
   const double* drhs = rhs;
   double* dp = p;

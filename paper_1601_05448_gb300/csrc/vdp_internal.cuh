@@ -2,11 +2,14 @@
 // driver of libvdp.  Not part of the public ABI (include/vdp.h is).
 //
 // The solve is a small state machine per problem instance, advanced one "sweep" at a time by
-// the step kernel.  Every sweep is a pass over the instance's grid split into work units
-// (full x rows, ty rows, tz planes); each unit writes its partial sums into its own slot and
-// the last unit to finish (atomic ticket) reduces the slots in a fixed order and moves the
-// instance to its next phase.  Results are therefore bitwise reproducible for a fixed unit
-// shape, whether an instance runs alone or inside a batch.
+// the step kernel.  A sweep is a pass over the instance's grid.  The grid is cut into row tiles
+// (full x rows, ty rows); the (row tile, z plane) pairs, ordered tile-major with z fastest, are
+// split into `nunits` equal contiguous ranges, one per work unit (CTA).  A unit therefore walks
+// one or two long runs of consecutive z planes ("segments") of at most two row tiles, which is
+// what the z-marching stencil sweeps need.  Each unit writes its partial sums into its own slot
+// and the last unit to finish (atomic ticket) reduces the slots in a fixed order and moves the
+// instance to its next phase.  Results are therefore bitwise reproducible for a fixed
+// (ty, nunits), whether an instance runs alone or inside a batch.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,7 +20,7 @@ namespace vdp {
 
 // Phases of one solve (see the step kernel for what each sweep does).
 enum Phase : int {
-  PH_MEANF = 0,    // <f>; p := 0 unless the caller gave a guess
+  PH_MEANF = 0,    // <f>, ||f||; p := 0 unless the caller gave a guess
   PH_RES64 = 1,    // FP64 residual r = (f - <f>) - A p, inner rhs rt = D^-1/2 r, norms, sum(p)
   PH_STENCIL = 2,  // d = rt + beta d_old; q = At d; <d, q>
   PH_UPDATE = 3,   // x += alpha d; rt -= alpha q; <rt, rt>
@@ -30,6 +33,7 @@ enum Prec : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_MIXED_BF16 = 2 };
 
 constexpr int kSlots = 4;          // partial-sum slots per unit
 constexpr int kThreads = 256;      // threads per work unit (CTA)
+constexpr int kMaxStages = 8;      // shared-memory pipeline stages of the stencil sweep
 
 // Mutable per-instance solver state (device memory).
 struct InstState {
@@ -46,7 +50,7 @@ struct InstState {
   int inner_max;
   int use_guess;
   int precision;
-  int pad0;
+  int fault;           // a unit's bounded wait expired (reported as VDP_ETIMEOUT)
   double tol;          // requested relative residual
   double inner_tol;    // mixed: minimum relative reduction per inner solve
   double mu_f;         // <f>
@@ -67,9 +71,12 @@ struct InstState {
 // Constant per-instance description (device memory).
 struct InstDesc {
   int nx, ny, nz;
-  int ty, tz;          // unit shape: rows, planes
-  int uy, uz;          // units along y, z
-  int nunits;
+  int ty;              // rows per row tile
+  int uy;              // row tiles
+  int nunits;          // work units (CTAs) per sweep
+  int stages;          // shared-memory pipeline stages of the stencil sweep
+  int pad0;
+  long long npairs;    // uy * nz (row tile, plane) pairs
   long long ncell;
   const double* rhs;   // caller's f (set per solve)
   double* p;           // caller's p (set per solve)
@@ -80,6 +87,7 @@ struct InstDesc {
   const void* sx;      // scaled coefficients bt = b sinv_l sinv_r in the inner storage type
   const void* sy;
   const void* sz;
+  const void* sd;      // BF16 only: diagonal correction of the stored inner operator
   void* x;             // inner solution (correction), inner type
   void* r;             // inner residual
   void* d0;            // search direction, double buffered
@@ -94,5 +102,19 @@ struct UnitRef {
   int inst;            // index into the batch's InstDesc table
   int unit;            // unit index within the instance
 };
+
+// Bytes of one stencil pipeline stage: d/rt and d_old rows with one halo row on each side,
+// then the three coefficient arrays (x: ty rows, y: ty + 1 rows, z: ty rows) and, for BF16
+// coefficients, the diagonal correction (ty rows); each piece is a whole number of rows, so
+// 16-byte aligned whenever a row is.
+__host__ __device__ inline size_t stage_bytes(int nx, int ty, int tsize, int bsize, bool diag) {
+  size_t b = (size_t)2 * (ty + 2) * nx * tsize + (size_t)(3 * ty + 1 + (diag ? ty : 0)) * nx * bsize;
+  return (b + 127) & ~(size_t)127;
+}
+
+// Bytes of the three-plane ring of the FP64 residual sweep.
+__host__ __device__ inline size_t ring_bytes(int nx, int ty) {
+  return (size_t)3 * (ty + 2) * nx * sizeof(double);
+}
 
 }  // namespace vdp

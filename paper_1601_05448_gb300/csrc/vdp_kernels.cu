@@ -14,10 +14,16 @@
 // inner solver (FP64, or FP32 with FP32/BF16 coefficients), and applies p -= D^-1/2 x.
 //
 // Kernels: the coefficient builders (set-up), and one step kernel that performs one sweep of
-// the phase each instance is in (see vdp_internal.cuh).  A sweep is split into work units of
-// full x rows x ty rows x tz planes; stencil sweeps march in z through a three-plane ring in
-// shared memory that holds the rows of the unit plus one halo row on each side, so every
-// value that feeds the 7-point stencil is loaded from global memory once per unit.
+// the phase each instance is in (see vdp_internal.cuh).
+//
+// The stencil sweep (the hot kernel) marches each unit through consecutive z planes.  For every
+// plane, one thread issues TMA bulk copies (cp.async.bulk, global -> shared, completion counted
+// on an mbarrier) of whole contiguous row blocks: rt and d_old with one halo row above and below
+// the tile, and the three coefficient arrays.  `stages` planes are in flight, so HBM streams
+// while the CTA computes.  The search direction d = rt + beta d_old is formed in place in the
+// stage buffer (once per cell, halo rows included), and the 7-point product q = At d reads the
+// z-1, z and z+1 planes of d from three live stages; every value is fetched from global memory
+// once per unit, x neighbours wrap inside the row, and only the halo rows are re-read from L2.
 #include "vdp_internal.cuh"
 #include "vdp_launch.h"
 
@@ -31,19 +37,13 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__device__ __forceinline__ float ldc(const float* p, long long i) { return __ldg(p + i); }
-__device__ __forceinline__ double ldc(const double* p, long long i) { return __ldg(p + i); }
-__device__ __forceinline__ float ldc(const __nv_bfloat16* p, long long i) {
-  return __bfloat162float(p[i]);
-}
-
 template <class T> __device__ __forceinline__ T from_double_rn(double v);
 template <> __device__ __forceinline__ double from_double_rn<double>(double v) { return v; }
 template <> __device__ __forceinline__ float from_double_rn<float>(double v) {
   return __double2float_rn(v);
 }
 
-// global row index of ring row ry (0 = halo row above the unit, ty_eff + 1 = halo row below)
+// global row index of ring row ry (0 = halo row above the tile, ty + 1 = halo row below)
 __device__ __forceinline__ int ring_gy(int ry, int y0, int ny) {
   int gy = y0 + ry - 1;
   if (gy < 0) gy += ny;
@@ -51,18 +51,145 @@ __device__ __forceinline__ int ring_gy(int ry, int y0, int ny) {
   return gy;
 }
 
-struct Unit {
-  int y0, ty, z0, tz;
+// Vector width per thread: 16-byte accesses of the inner type.
+template <class T> struct VecW;
+template <> struct VecW<float> { static constexpr int V = 4; };
+template <> struct VecW<double> { static constexpr int V = 2; };
+
+template <class T, int V> struct VecIO;
+template <> struct VecIO<float, 4> {
+  static __device__ __forceinline__ void ld(const float* p, float (&o)[4]) {
+    float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  }
+  static __device__ __forceinline__ void st(float* p, const float (&o)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+};
+template <> struct VecIO<double, 2> {
+  static __device__ __forceinline__ void ld(const double* p, double (&o)[2]) {
+    double2 t = *reinterpret_cast<const double2*>(p);
+    o[0] = t.x; o[1] = t.y;
+  }
+  static __device__ __forceinline__ void st(double* p, const double (&o)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+  }
 };
 
-__device__ __forceinline__ Unit unit_geometry(const InstDesc& I, int unit) {
-  Unit u;
-  int uyi = unit % I.uy, uzi = unit / I.uy;
-  u.y0 = uyi * I.ty;
-  u.ty = min(I.ty, I.ny - u.y0);
-  u.z0 = uzi * I.tz;
-  u.tz = min(I.tz, I.nz - u.z0);
-  return u;
+// V coefficients of storage type BT into arithmetic type T
+template <class BT, class T, int V> struct CoefIO;
+template <> struct CoefIO<float, float, 4> {
+  static __device__ __forceinline__ void ld(const float* p, float (&o)[4]) {
+    VecIO<float, 4>::ld(p, o);
+  }
+};
+template <> struct CoefIO<double, double, 2> {
+  static __device__ __forceinline__ void ld(const double* p, double (&o)[2]) {
+    VecIO<double, 2>::ld(p, o);
+  }
+};
+template <> struct CoefIO<__nv_bfloat16, float, 4> {
+  static __device__ __forceinline__ void ld(const __nv_bfloat16* p, float (&o)[4]) {
+    uint2 u = *reinterpret_cast<const uint2*>(p);
+    __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&u.x);
+    __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&u.y);
+    float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    o[0] = fa.x; o[1] = fa.y; o[2] = fb.x; o[3] = fb.y;
+  }
+};
+
+__device__ __forceinline__ float ld1(const float* p) { return *p; }
+__device__ __forceinline__ double ld1(const double* p) { return *p; }
+__device__ __forceinline__ float ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// ---- TMA bulk copies and mbarriers (inline PTX) -----------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// order this thread's earlier generic-proxy shared accesses before later async-proxy (TMA) ones
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after ~2 s (returns false); no hang.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+#pragma unroll 1
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > 2000000000ull) return false;
+  }
+}
+
+// ---- unit geometry -------------------------------------------------------------------------------
+
+struct Seg {
+  int y0, ty;   // row tile: first row, rows
+  int z0, nzs;  // first plane, planes
+};
+
+// Calls fn(seg) for the one or more z runs that make up work unit `unit`.
+template <class F>
+__device__ __forceinline__ void for_each_segment(const InstDesc& I, int unit, F&& fn) {
+  long long b = (long long)unit * I.npairs / I.nunits;
+  const long long e = (long long)(unit + 1) * I.npairs / I.nunits;
+  while (b < e) {
+    const int tile = (int)(b / I.nz);
+    const int z0 = (int)(b - (long long)tile * I.nz);
+    const int nzs = (int)min((long long)(I.nz - z0), e - b);
+    Seg s;
+    s.y0 = tile * I.ty;
+    s.ty = min(I.ty, I.ny - s.y0);
+    s.z0 = z0;
+    s.nzs = nzs;
+    fn(s);
+    b += nzs;
+  }
 }
 
 // ---- reductions: per-unit partial slots, last unit reduces them in a fixed order --------------
@@ -73,6 +200,7 @@ __device__ __forceinline__ void store_partials(double (&v)[kSlots], double* part
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < kSlots; ++k) v[k] = warp_sum(v[k]);
+  __syncthreads();  // red[] may still be read by a previous use
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < kSlots; ++k) red[warp][k] = v[k];
@@ -112,6 +240,11 @@ __device__ __forceinline__ double sum_slot(const double* part, int nunits) {
 
 __device__ void transition(const InstDesc& I, InstState* st, int phase, const double (&S)[kSlots]) {
   st->sweeps += 1;
+  if (st->fault && phase != PH_FINAL) {  // a bounded wait expired: stop with what p holds
+    st->status = 6;                      // VDP_ETIMEOUT
+    st->phase = PH_FINAL;
+    return;
+  }
   switch (phase) {
     case PH_MEANF:
       st->mu_f = S[0] / (double)I.ncell;
@@ -120,21 +253,21 @@ __device__ void transition(const InstDesc& I, InstState* st, int phase, const do
       st->phase = PH_RES64;
       break;
     case PH_RES64: {
-      double rr64 = S[0], rrt = S[1];
+      const double rr64 = S[0], rrt = S[1];
       st->sum_p = S[2];
       if (st->first_res) {
         st->fn2 = S[3];
         st->first_res = 0;
       }
       st->outer += 1;
-      double fn2 = st->fn2;
+      const double fn2 = st->fn2;
       if (fn2 <= 1e-28 * st->f2) {  // f is constant up to rounding: p = 0
         st->zero_sol = 1;
         st->rel_res = 0.0;
         st->phase = PH_FINAL;
         break;
       }
-      double rel = sqrt(rr64 / fn2);
+      const double rel = sqrt(rr64 / fn2);
       st->rel_res = rel;
       if (!isfinite(rel)) {
         st->status = 5;  // VDP_EBREAKDOWN
@@ -151,7 +284,7 @@ __device__ void transition(const InstDesc& I, InstState* st, int phase, const do
         // How far the FP64 residual fell during the last inner solve compared with the scaled
         // inner residual; the next inner target is tightened by it (at least 1).
         if (st->outer > 1 && st->inner_ratio > 0.0) {
-          double obs = sqrt(rr64 / st->rr64_prev) / st->inner_ratio;
+          const double obs = sqrt(rr64 / st->rr64_prev) / st->inner_ratio;
           st->eta = fmax(1.0, fmin(obs, 1e6));
         }
         double tau = 0.5 * st->tol * sqrt(fn2 / rr64) / st->eta;
@@ -159,7 +292,6 @@ __device__ void transition(const InstDesc& I, InstState* st, int phase, const do
         tau = fmin(tau, 0.5);
         st->tau2 = tau * tau;
         st->rr64_prev = rr64;
-        st->rr64 = rr64;
         st->rr = rrt;
         st->rr0 = rrt;
         st->beta = 0.0;
@@ -170,7 +302,7 @@ __device__ void transition(const InstDesc& I, InstState* st, int phase, const do
       break;
     }
     case PH_STENCIL: {
-      double dq = S[0];
+      const double dq = S[0];
       if (dq > 0.0 && isfinite(dq)) {
         st->alpha = st->rr / dq;
         st->phase = PH_UPDATE;
@@ -185,7 +317,7 @@ __device__ void transition(const InstDesc& I, InstState* st, int phase, const do
       break;
     }
     case PH_UPDATE: {
-      double rn = S[0];
+      const double rn = S[0];
       st->inner_iters += 1;
       st->iters += 1;
       if (!isfinite(rn)) {
@@ -214,28 +346,54 @@ __device__ void transition(const InstDesc& I, InstState* st, int phase, const do
   }
 }
 
-// ---- sweeps -----------------------------------------------------------------------------------
+// ---- flat (element-wise) sweeps ------------------------------------------------------------------
+// A unit's cells are the contiguous blocks (ty rows x nx) of its (row tile, plane) pairs.  The
+// flat sweeps walk them as one index space of 16-byte vectors, four vectors per thread in
+// flight.
 
-// <f>, and p := 0 unless p is the caller's initial guess.
-template <class T>
-__device__ void sweep_meanf(const InstDesc& I, const InstState* st, const Unit& u,
-                            double (&acc)[kSlots]) {
-  const long long plane = (long long)I.nx * I.ny;
+struct FlatRange {
+  long long pair0;   // first pair of the unit
+  long long npairs;  // pairs in the unit
+};
+
+__device__ __forceinline__ FlatRange unit_pairs(const InstDesc& I, int unit) {
+  FlatRange r;
+  r.pair0 = (long long)unit * I.npairs / I.nunits;
+  r.npairs = (long long)(unit + 1) * I.npairs / I.nunits - r.pair0;
+  return r;
+}
+
+// element offset of vector `v` (width V) of the unit; vpp = vectors per (full) pair
+__device__ __forceinline__ long long flat_offset(const InstDesc& I, const FlatRange& r, long long v,
+                                                 int V, int* ok) {
+  const int vrow = I.nx / V;
+  const long long vpp = (long long)I.ty * vrow;
+  const long long pi = v / vpp;
+  const int w = (int)(v - pi * vpp);
+  const long long pair = r.pair0 + pi;
+  const int tile = (int)(pair / I.nz);
+  const int z = (int)(pair - (long long)tile * I.nz);
+  const int row = tile * I.ty + w / vrow;
+  *ok = row < I.ny;  // the last row tile may be short
+  return ((long long)z * I.ny + row) * I.nx + (long long)(w % vrow) * V;
+}
+
+// <f>, ||f||^2; p := 0 unless p is the caller's initial guess.
+__device__ void sweep_meanf(const InstDesc& I, const InstState* st, int unit, double (&acc)[kSlots]) {
+  const FlatRange r = unit_pairs(I, unit);
+  const long long nv = r.npairs * (long long)I.ty * (I.nx / 2);
   const bool zero_p = !st->use_guess;
-  const int len = u.ty * I.nx;  // multiple of 8: nx is
   double s = 0.0, s2 = 0.0;
-  for (int k = 0; k < u.tz; ++k) {
-    long long base = (long long)(u.z0 + k) * plane + (long long)u.y0 * I.nx;
-    const double2* f2 = reinterpret_cast<const double2*>(I.rhs + base);
-    double2* p2 = reinterpret_cast<double2*>(I.p + base);
-    for (int v = threadIdx.x; v < len / 2; v += kThreads) {
-      double2 fv = __ldg(f2 + v);
-      s += fv.x;
-      s += fv.y;
-      s2 = fma(fv.x, fv.x, s2);
-      s2 = fma(fv.y, fv.y, s2);
-      if (zero_p) p2[v] = make_double2(0.0, 0.0);
-    }
+  for (long long v = threadIdx.x; v < nv; v += kThreads) {
+    int ok;
+    const long long c = flat_offset(I, r, v, 2, &ok);
+    if (!ok) continue;
+    const double2 fv = __ldg(reinterpret_cast<const double2*>(I.rhs + c));
+    s += fv.x;
+    s += fv.y;
+    s2 = fma(fv.x, fv.x, s2);
+    s2 = fma(fv.y, fv.y, s2);
+    if (zero_p) *reinterpret_cast<double2*>(I.p + c) = make_double2(0.0, 0.0);
   }
   acc[0] = s;
   acc[1] = s2;
@@ -243,88 +401,182 @@ __device__ void sweep_meanf(const InstDesc& I, const InstState* st, const Unit& 
 
 // p -= D^-1/2 x (x in the inner type)
 template <class T>
-__device__ void sweep_correct(const InstDesc& I, const Unit& u) {
-  const long long plane = (long long)I.nx * I.ny;
-  const int len = u.ty * I.nx;
+__device__ void sweep_correct(const InstDesc& I, int unit) {
+  const FlatRange r = unit_pairs(I, unit);
+  const long long nv = r.npairs * (long long)I.ty * (I.nx / 2);
   const T* x = static_cast<const T*>(I.x);
-  for (int k = 0; k < u.tz; ++k) {
-    long long base = (long long)(u.z0 + k) * plane + (long long)u.y0 * I.nx;
-    for (int v = threadIdx.x; v < len; v += kThreads) {
-      long long c = base + v;
-      I.p[c] = fma(-__ldg(I.sinv + c), (double)x[c], I.p[c]);
-    }
+  for (long long v = threadIdx.x; v < nv; v += kThreads) {
+    int ok;
+    const long long c = flat_offset(I, r, v, 2, &ok);
+    if (!ok) continue;
+    const double2 s = __ldg(reinterpret_cast<const double2*>(I.sinv + c));
+    double2 p = *reinterpret_cast<double2*>(I.p + c);
+    p.x = fma(-s.x, (double)x[c], p.x);
+    p.y = fma(-s.y, (double)x[c + 1], p.y);
+    *reinterpret_cast<double2*>(I.p + c) = p;
   }
 }
 
 // p -= <p>   (or p = 0 when the right-hand side was constant)
-__device__ void sweep_final(const InstDesc& I, const InstState* st, const Unit& u) {
-  const long long plane = (long long)I.nx * I.ny;
-  const int len = u.ty * I.nx;
+__device__ void sweep_final(const InstDesc& I, const InstState* st, int unit) {
+  const FlatRange r = unit_pairs(I, unit);
+  const long long nv = r.npairs * (long long)I.ty * (I.nx / 2);
   const double mp = st->sum_p / (double)I.ncell;
   const bool zero = st->zero_sol != 0;
-  for (int k = 0; k < u.tz; ++k) {
-    long long base = (long long)(u.z0 + k) * plane + (long long)u.y0 * I.nx;
-    double2* p2 = reinterpret_cast<double2*>(I.p + base);
-    for (int v = threadIdx.x; v < len / 2; v += kThreads) {
-      double2 pv = p2[v];
-      p2[v] = zero ? make_double2(0.0, 0.0) : make_double2(pv.x - mp, pv.y - mp);
-    }
+  for (long long v = threadIdx.x; v < nv; v += kThreads) {
+    int ok;
+    const long long c = flat_offset(I, r, v, 2, &ok);
+    if (!ok) continue;
+    double2 p = *reinterpret_cast<double2*>(I.p + c);
+    p = zero ? make_double2(0.0, 0.0) : make_double2(p.x - mp, p.y - mp);
+    *reinterpret_cast<double2*>(I.p + c) = p;
   }
 }
 
 // x += alpha d (x = alpha d on the first inner iteration); rt -= alpha q; <rt, rt>
 template <class T>
-__device__ void sweep_update(const InstDesc& I, const InstState* st, const Unit& u,
+__device__ void sweep_update(const InstDesc& I, const InstState* st, int unit,
                              double (&acc)[kSlots]) {
-  const long long plane = (long long)I.nx * I.ny;
-  const int len = u.ty * I.nx;
+  constexpr int V = VecW<T>::V;
+  constexpr int U = 4;  // vectors per thread per round
+  const FlatRange r = unit_pairs(I, unit);
+  const long long nv = r.npairs * (long long)I.ty * (I.nx / V);
   const T alpha = (T)st->alpha;
   const bool first = st->inner_iters == 0;
   const T* d = static_cast<const T*>(st->parity ? I.d0 : I.d1);  // written by the last stencil
   const T* q = static_cast<const T*>(I.q);
   T* x = static_cast<T*>(I.x);
-  T* r = static_cast<T*>(I.r);
+  T* rt = static_cast<T*>(I.r);
   T s = 0;
-  for (int k = 0; k < u.tz; ++k) {
-    long long base = (long long)(u.z0 + k) * plane + (long long)u.y0 * I.nx;
-    for (int v = threadIdx.x; v < len; v += kThreads) {
-      long long c = base + v;
-      T dv = d[c], qv = q[c];
-      T xv = first ? (T)0 : x[c];
-      x[c] = fma(alpha, dv, xv);
-      T rv = fma(-alpha, qv, r[c]);
-      r[c] = rv;
-      s = fma(rv, rv, s);
+  for (long long v0 = threadIdx.x; v0 < nv; v0 += (long long)U * kThreads) {
+    long long c[U];
+    int ok[U];
+    T dv[U][V], qv[U][V], xv[U][V], rv[U][V];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long v = v0 + (long long)u * kThreads;
+      ok[u] = 0;
+      c[u] = 0;
+      if (v < nv) c[u] = flat_offset(I, r, v, V, &ok[u]);
+      if (ok[u]) {
+        VecIO<T, V>::ld(d + c[u], dv[u]);
+        VecIO<T, V>::ld(q + c[u], qv[u]);
+        VecIO<T, V>::ld(rt + c[u], rv[u]);
+        if (!first) VecIO<T, V>::ld(x + c[u], xv[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        xv[u][k] = fma(alpha, dv[u][k], first ? (T)0 : xv[u][k]);
+        rv[u][k] = fma(-alpha, qv[u][k], rv[u][k]);
+        s = fma(rv[u][k], rv[u][k], s);
+      }
+      VecIO<T, V>::st(x + c[u], xv[u]);
+      VecIO<T, V>::st(rt + c[u], rv[u]);
     }
   }
   acc[0] = (double)s;
 }
 
-// d = rt + beta d_old on ring slot `slot` for plane zg (all ring rows of the unit)
-template <class T>
-__device__ __forceinline__ void fill_direction(const InstDesc& I, const Unit& u, T* ring,
-                                               int stride, int slot, int zg, const T* rt,
-                                               const T* dold, T beta, bool use_old) {
+// ---- the stencil sweep: TMA-fed z march -----------------------------------------------------------
+
+// BF16 coefficients carry a per-cell diagonal correction (see k_diag_correction).
+template <class BT> struct CoefTraits { static constexpr bool kDiag = false; };
+template <> struct CoefTraits<__nv_bfloat16> { static constexpr bool kDiag = true; };
+
+template <class T, class BT>
+struct StageLayout {
+  int nx, ty;
+  __device__ __forceinline__ size_t r_off() const { return 0; }
+  __device__ __forceinline__ size_t o_off() const { return (size_t)(ty + 2) * nx * sizeof(T); }
+  __device__ __forceinline__ size_t bx_off() const { return (size_t)2 * (ty + 2) * nx * sizeof(T); }
+  __device__ __forceinline__ size_t by_off() const { return bx_off() + (size_t)ty * nx * sizeof(BT); }
+  __device__ __forceinline__ size_t bz_off() const {
+    return by_off() + (size_t)(ty + 1) * nx * sizeof(BT);
+  }
+  __device__ __forceinline__ size_t bd_off() const { return bz_off() + (size_t)ty * nx * sizeof(BT); }
+};
+
+// Issue the bulk copies of plane `j` (j = -1 .. nzs) of segment `sg` into stage buffer `buf`
+// (thread 0 only).  Plane -1 needs only rt / d_old (it supplies d below the segment); plane
+// nzs needs rt / d_old and the z coefficients (its low z face is the high face of the last
+// plane).
+template <class T, class BT>
+__device__ __forceinline__ void issue_stage(const InstDesc& I, const Seg& sg, int j,
+                                            unsigned char* buf, uint64_t* bar, const T* rt,
+                                            const T* dold, bool use_old, const BT* sx,
+                                            const BT* sy, const BT* sz, const BT* sd) {
+  const StageLayout<T, BT> L{I.nx, I.ty};
+  int zg = sg.z0 + j;
+  if (zg < 0) zg += I.nz;
+  if (zg >= I.nz) zg -= I.nz;
   const int nx = I.nx;
-  const int cells = (u.ty + 2) * nx;
-  const long long pz = (long long)zg * nx * I.ny;
-  T* dst = ring + slot * stride;
-  for (int m = threadIdx.x; m < cells; m += kThreads) {
-    int ry = m / nx, x = m - ry * nx;
-    long long c = pz + (long long)ring_gy(ry, u.y0, I.ny) * nx + x;
-    T v = rt[c];
-    if (use_old) v = fma(beta, dold[c], v);
-    dst[m] = v;
+  const long long plane = (long long)zg * I.ny;
+  const int top = ring_gy(0, sg.y0, I.ny), bot = ring_gy(sg.ty + 1, sg.y0, I.ny);
+  const uint32_t rowT = nx * sizeof(T), rowB = nx * sizeof(BT);
+  const bool need_xy = j >= 0 && j < sg.nzs;
+  const bool need_z = j >= 0;
+  uint32_t bytes = (uint32_t)(sg.ty + 2) * rowT * (use_old ? 2 : 1);
+  if (need_xy) bytes += (uint32_t)(2 * sg.ty + 1 + (CoefTraits<BT>::kDiag ? sg.ty : 0)) * rowB;
+  if (need_z) bytes += (uint32_t)sg.ty * rowB;
+  mbar_arrive_expect_tx(bar, bytes);
+  unsigned char* R = buf + L.r_off();
+  bulk_g2s(R, rt + (plane + top) * nx, rowT, bar);
+  bulk_g2s(R + rowT, rt + (plane + sg.y0) * nx, sg.ty * rowT, bar);
+  bulk_g2s(R + (sg.ty + 1) * rowT, rt + (plane + bot) * nx, rowT, bar);
+  if (use_old) {
+    unsigned char* O = buf + L.o_off();
+    bulk_g2s(O, dold + (plane + top) * nx, rowT, bar);
+    bulk_g2s(O + rowT, dold + (plane + sg.y0) * nx, sg.ty * rowT, bar);
+    bulk_g2s(O + (sg.ty + 1) * rowT, dold + (plane + bot) * nx, rowT, bar);
+  }
+  if (need_xy) {
+    bulk_g2s(buf + L.bx_off(), sx + (plane + sg.y0) * nx, sg.ty * rowB, bar);
+    unsigned char* BY = buf + L.by_off();
+    if (sg.y0 + sg.ty < I.ny) {
+      bulk_g2s(BY, sy + (plane + sg.y0) * nx, (sg.ty + 1) * rowB, bar);
+    } else {  // the row below the tile wraps to row 0
+      bulk_g2s(BY, sy + (plane + sg.y0) * nx, sg.ty * rowB, bar);
+      bulk_g2s(BY + sg.ty * rowB, sy + plane * nx, rowB, bar);
+    }
+    if (CoefTraits<BT>::kDiag)
+      bulk_g2s(buf + L.bd_off(), sd + (plane + sg.y0) * nx, sg.ty * rowB, bar);
+  }
+  if (need_z) bulk_g2s(buf + L.bz_off(), sz + (plane + sg.y0) * nx, sg.ty * rowB, bar);
+}
+
+// d = rt + beta d_old in place over all ring rows of a stage
+template <class T>
+__device__ __forceinline__ void form_direction(T* R, const T* O, int cells, T beta) {
+  constexpr int V = VecW<T>::V;
+  for (int v = threadIdx.x; v < cells / V; v += kThreads) {
+    T a[V], b[V];
+    VecIO<T, V>::ld(R + v * V, a);
+    VecIO<T, V>::ld(O + v * V, b);
+#pragma unroll
+    for (int k = 0; k < V; ++k) a[k] = fma(beta, b[k], a[k]);
+    VecIO<T, V>::st(R + v * V, a);
   }
 }
 
-// d = rt + beta d_old (formed on the fly), q = At d, <d, q>; writes d and q for the unit
+// One z march per segment.  Iteration k (plane k of the segment) forms d two planes ahead
+// (plane k + 2, stage k + 3) while it applies the stencil to plane k from the stages of planes
+// k - 1, k, k + 1, so one block barrier per plane separates the two; the barrier also frees the
+// stage of plane k - 1, which thread 0 then refills with plane k - 1 + S.  S >= 4 stages.
 template <class T, class BT>
-__device__ void sweep_stencil(const InstDesc& I, const InstState* st, const Unit& u,
-                              double (&acc)[kSlots], T* ring) {
-  const int nx = I.nx, ny = I.ny, nz = I.nz;
-  const int stride = (I.ty + 2) * nx;
-  const long long plane = (long long)nx * ny;
+__device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, double (&acc)[kSlots],
+                              unsigned char* smem) {
+  constexpr int V = VecW<T>::V;
+  constexpr bool kDiag = CoefTraits<BT>::kDiag;
+  __shared__ __align__(8) uint64_t bars[kMaxStages];
+  __shared__ int timed_out;
+  const int S = I.stages;
+  const int nx = I.nx;
+  const StageLayout<T, BT> L{nx, I.ty};
+  const size_t sbytes = stage_bytes(nx, I.ty, sizeof(T), sizeof(BT), kDiag);
   const T beta = (T)st->beta;
   const bool use_old = st->inner_iters > 0;
   const T* rt = static_cast<const T*>(I.r);
@@ -334,64 +586,134 @@ __device__ void sweep_stencil(const InstDesc& I, const InstState* st, const Unit
   const BT* sx = static_cast<const BT*>(I.sx);
   const BT* sy = static_cast<const BT*>(I.sy);
   const BT* sz = static_cast<const BT*>(I.sz);
+  const BT* sd = static_cast<const BT*>(I.sd);
 
-  int zm = u.z0 - 1;
-  if (zm < 0) zm += nz;
-  fill_direction<T>(I, u, ring, stride, 0, zm, rt, dold, beta, use_old);
-  fill_direction<T>(I, u, ring, stride, 1, u.z0, rt, dold, beta, use_old);
-  T s = 0;
-  const int own = u.ty * nx;
-  for (int k = 0; k < u.tz; ++k) {
-    const int z = u.z0 + k;
-    const int zp = z + 1 == nz ? 0 : z + 1;
-    const int sm = k % 3, sc = (k + 1) % 3, sp = (k + 2) % 3;
-    fill_direction<T>(I, u, ring, stride, sp, zp, rt, dold, beta, use_old);
-    __syncthreads();
-    const T* Rm = ring + sm * stride;
-    const T* Rc = ring + sc * stride;
-    const T* Rp = ring + sp * stride;
-    for (int m = threadIdx.x; m < own; m += kThreads) {
-      const int ry = m / nx + 1, x = m - (ry - 1) * nx;
-      const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-      const int gy = u.y0 + ry - 1;
-      const int gyp = gy + 1 == ny ? 0 : gy + 1;
-      const long long row = (long long)z * plane + (long long)gy * nx;
-      const long long c = row + x;
-      const int o = ry * nx;
-      T dc = Rc[o + x];
-      T qv = dc;
-      qv = fma(-(T)ldc(sx, c), Rc[o + xm], qv);
-      qv = fma(-(T)ldc(sx, row + xp), Rc[o + xp], qv);
-      qv = fma(-(T)ldc(sy, c), Rc[o - nx + x], qv);
-      qv = fma(-(T)ldc(sy, (long long)z * plane + (long long)gyp * nx + x), Rc[o + nx + x], qv);
-      qv = fma(-(T)ldc(sz, c), Rm[o + x], qv);
-      qv = fma(-(T)ldc(sz, (long long)zp * plane + (long long)gy * nx + x), Rp[o + x], qv);
-      dnew[c] = dc;
-      q[c] = qv;
-      s = fma(dc, qv, s);
-    }
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+    timed_out = 0;
   }
-  acc[0] = (double)s;
+  __syncthreads();
+  uint32_t parity = 0;  // bit s: phase parity of the next completion of stage s
+  T sum = 0;
+
+  auto stage_ptr = [&](int jj) { return smem + (size_t)(jj % S) * sbytes; };
+  auto wait_stage = [&](int jj) {
+    const int s = jj % S;
+    if (!timed_out && !mbar_wait(&bars[s], (parity >> s) & 1u)) timed_out = 1;
+    parity ^= 1u << s;
+  };
+  auto ready = [&](int jj, int ring_cells) {  // wait for stage jj and form d in it
+    wait_stage(jj);
+    if (use_old) {
+      unsigned char* b = stage_ptr(jj);
+      form_direction<T>(reinterpret_cast<T*>(b + L.r_off()),
+                        reinterpret_cast<const T*>(b + L.o_off()), ring_cells, beta);
+    }
+  };
+
+  for_each_segment(I, unit, [&](const Seg& sg) {
+    const int np = sg.nzs + 2;  // planes -1 .. nzs, stage index jj = j + 1
+    const int ring_cells = (sg.ty + 2) * nx;
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();  // stage buffers were last touched by ordinary loads/stores
+      for (int jj = 0; jj < min(S, np); ++jj)
+        issue_stage<T, BT>(I, sg, jj - 1, stage_ptr(jj), &bars[jj % S], rt, dold, use_old, sx, sy,
+                           sz, sd);
+    }
+    ready(0, ring_cells);  // plane -1
+    ready(1, ring_cells);  // plane 0
+    ready(2, ring_cells);  // plane 1 (exists: np >= 3)
+    __syncthreads();
+    const int vrow = nx / V;
+    const int own = sg.ty * vrow;  // vectors in the tile's own rows
+    for (int k = 0; k < sg.nzs; ++k) {
+      const int z = sg.z0 + k;
+      if (k + 3 < np) ready(k + 3, ring_cells);  // plane k + 2
+      const unsigned char* bm = stage_ptr(k);
+      const unsigned char* bc = stage_ptr(k + 1);
+      const unsigned char* bp = stage_ptr(k + 2);
+      const T* Dm = reinterpret_cast<const T*>(bm + L.r_off());
+      const T* Dc = reinterpret_cast<const T*>(bc + L.r_off());
+      const T* Dp = reinterpret_cast<const T*>(bp + L.r_off());
+      const BT* Bx = reinterpret_cast<const BT*>(bc + L.bx_off());
+      const BT* By = reinterpret_cast<const BT*>(bc + L.by_off());
+      const BT* Bz = reinterpret_cast<const BT*>(bc + L.bz_off());
+      const BT* Bd = reinterpret_cast<const BT*>(bc + L.bd_off());
+      const BT* Bzp = reinterpret_cast<const BT*>(bp + L.bz_off());
+      for (int v = threadIdx.x; v < own; v += kThreads) {
+        const int row = v / vrow;               // 0 .. ty-1
+        const int x0 = (v - row * vrow) * V;
+        const int o = (row + 1) * nx;           // ring row of this tile row
+        const int ob = row * nx;                // coefficient row
+        T dc[V], du[V], dd[V], dzm[V], dzp[V];
+        T bx[V], by[V], byd[V], bz[V], bzp[V], bd[V];
+        VecIO<T, V>::ld(Dc + o + x0, dc);
+        VecIO<T, V>::ld(Dc + o - nx + x0, du);
+        VecIO<T, V>::ld(Dc + o + nx + x0, dd);
+        VecIO<T, V>::ld(Dm + o + x0, dzm);
+        VecIO<T, V>::ld(Dp + o + x0, dzp);
+        CoefIO<BT, T, V>::ld(Bx + ob + x0, bx);
+        CoefIO<BT, T, V>::ld(By + ob + x0, by);
+        CoefIO<BT, T, V>::ld(By + ob + nx + x0, byd);
+        CoefIO<BT, T, V>::ld(Bz + ob + x0, bz);
+        CoefIO<BT, T, V>::ld(Bzp + ob + x0, bzp);
+        if (kDiag) CoefIO<BT, T, V>::ld(Bd + ob + x0, bd);
+        const int xl = x0 == 0 ? nx - 1 : x0 - 1;
+        const int xr = x0 + V == nx ? 0 : x0 + V;
+        const T dl = Dc[o + xl], dr = Dc[o + xr];
+        const T bxr = (T)ld1(Bx + ob + xr);
+        T qv[V];
+#pragma unroll
+        for (int k2 = 0; k2 < V; ++k2) {
+          const T left = k2 == 0 ? dl : dc[k2 - 1];
+          const T right = k2 == V - 1 ? dr : dc[k2 + 1];
+          const T bright = k2 == V - 1 ? bxr : bx[k2 + 1];
+          T a = dc[k2];
+          if (kDiag) a = fma(bd[k2], dc[k2], a);
+          a = fma(-bx[k2], left, a);
+          a = fma(-bright, right, a);
+          a = fma(-by[k2], du[k2], a);
+          a = fma(-byd[k2], dd[k2], a);
+          a = fma(-bz[k2], dzm[k2], a);
+          a = fma(-bzp[k2], dzp[k2], a);
+          qv[k2] = a;
+          sum = fma(dc[k2], a, sum);
+        }
+        const long long g = ((long long)z * I.ny + sg.y0 + row) * nx + x0;
+        VecIO<T, V>::st(dnew + g, dc);
+        VecIO<T, V>::st(q + g, qv);
+      }
+      fence_proxy_async_smem();  // this thread's shared accesses before the refill's TMA writes
+      __syncthreads();           // stage k (plane k - 1) is free; plane k + 2 is formed
+      if (threadIdx.x == 0 && k + S < np) {
+        issue_stage<T, BT>(I, sg, k + S - 1, stage_ptr(k + S), &bars[(k + S) % S], rt, dold,
+                           use_old, sx, sy, sz, sd);
+      }
+    }
+  });
+  if (timed_out && threadIdx.x == 0) atomicExch(&st->fault, 1);
+  acc[0] = (double)sum;
 }
 
-// copy plane zg of p (all ring rows) into ring slot
-__device__ __forceinline__ void fill_p(const InstDesc& I, const Unit& u, double* ring, int stride,
+// ---- the FP64 residual sweep (a few times per solve): z march through a three-plane ring ---------
+
+__device__ __forceinline__ void fill_p(const InstDesc& I, const Seg& sg, double* ring, int stride,
                                        int slot, int zg) {
   const int nx = I.nx;
-  const int cells = (u.ty + 2) * nx;
+  const int cells = (sg.ty + 2) * nx;
   const long long pz = (long long)zg * nx * I.ny;
   double* dst = ring + slot * stride;
   for (int m = threadIdx.x; m < cells; m += kThreads) {
-    int ry = m / nx, x = m - ry * nx;
-    dst[m] = I.p[pz + (long long)ring_gy(ry, u.y0, I.ny) * nx + x];
+    const int ry = m / nx, x = m - ry * nx;
+    dst[m] = I.p[pz + (long long)ring_gy(ry, sg.y0, I.ny) * nx + x];
   }
 }
 
-// FP64 residual r = (f - <f>) - A p; rt = D^-1/2 r in the inner type; sums of r^2, rt^2, p and,
-// on the first call, (f - <f>)^2
+// r = (f - <f>) - A p; rt = D^-1/2 r in the inner type; sums of r^2, rt^2, p and, on the first
+// call, (f - <f>)^2
 template <class T>
-__device__ void sweep_res64(const InstDesc& I, const InstState* st, const Unit& u,
+__device__ void sweep_res64(const InstDesc& I, const InstState* st, int unit,
                             double (&acc)[kSlots], double* ring) {
   const int nx = I.nx, ny = I.ny, nz = I.nz;
   const int stride = (I.ty + 2) * nx;
@@ -399,46 +721,49 @@ __device__ void sweep_res64(const InstDesc& I, const InstState* st, const Unit& 
   const double mu = st->mu_f;
   const bool first = st->first_res != 0;
   T* rt = static_cast<T*>(I.r);
-  int zm = u.z0 - 1;
-  if (zm < 0) zm += nz;
-  fill_p(I, u, ring, stride, 0, zm);
-  fill_p(I, u, ring, stride, 1, u.z0);
   double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-  const int own = u.ty * nx;
-  for (int k = 0; k < u.tz; ++k) {
-    const int z = u.z0 + k;
-    const int zp = z + 1 == nz ? 0 : z + 1;
-    const int sm = k % 3, sc = (k + 1) % 3, sp = (k + 2) % 3;
-    fill_p(I, u, ring, stride, sp, zp);
-    __syncthreads();
-    const double* Rm = ring + sm * stride;
-    const double* Rc = ring + sc * stride;
-    const double* Rp = ring + sp * stride;
-    for (int m = threadIdx.x; m < own; m += kThreads) {
-      const int ry = m / nx + 1, x = m - (ry - 1) * nx;
-      const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-      const int gy = u.y0 + ry - 1;
-      const int gyp = gy + 1 == ny ? 0 : gy + 1;
-      const long long row = (long long)z * plane + (long long)gy * nx;
-      const long long c = row + x;
-      const int o = ry * nx;
-      const double pc = Rc[o + x];
-      double ap = __ldg(I.bx + row + xp) * (Rc[o + xp] - pc) - __ldg(I.bx + c) * (pc - Rc[o + xm]);
-      ap += __ldg(I.by + (long long)z * plane + (long long)gyp * nx + x) * (Rc[o + nx + x] - pc) -
-            __ldg(I.by + c) * (pc - Rc[o - nx + x]);
-      ap += __ldg(I.bz + (long long)zp * plane + (long long)gy * nx + x) * (Rp[o + x] - pc) -
-            __ldg(I.bz + c) * (pc - Rm[o + x]);
-      const double f0 = __ldg(I.rhs + c) - mu;
-      const double r = f0 - ap;
-      const T tv = from_double_rn<T>(__ldg(I.sinv + c) * r);
-      rt[c] = tv;
-      a0 = fma(r, r, a0);
-      a1 = fma((double)tv, (double)tv, a1);
-      a2 += pc;
-      if (first) a3 = fma(f0, f0, a3);
+  for_each_segment(I, unit, [&](const Seg& sg) {
+    int zm = sg.z0 - 1;
+    if (zm < 0) zm += nz;
+    __syncthreads();  // ring reuse across segments
+    fill_p(I, sg, ring, stride, 0, zm);
+    fill_p(I, sg, ring, stride, 1, sg.z0);
+    const int own = sg.ty * nx;
+    for (int k = 0; k < sg.nzs; ++k) {
+      const int z = sg.z0 + k;
+      const int zp = z + 1 == nz ? 0 : z + 1;
+      const int sm = k % 3, sc = (k + 1) % 3, sp = (k + 2) % 3;
+      fill_p(I, sg, ring, stride, sp, zp);
+      __syncthreads();
+      const double* Rm = ring + sm * stride;
+      const double* Rc = ring + sc * stride;
+      const double* Rp = ring + sp * stride;
+      for (int m = threadIdx.x; m < own; m += kThreads) {
+        const int ry = m / nx + 1, x = m - (ry - 1) * nx;
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        const int gy = sg.y0 + ry - 1;
+        const int gyp = gy + 1 == ny ? 0 : gy + 1;
+        const long long row = (long long)z * plane + (long long)gy * nx;
+        const long long c = row + x;
+        const int o = ry * nx;
+        const double pc = Rc[o + x];
+        double ap = __ldg(I.bx + row + xp) * (Rc[o + xp] - pc) - __ldg(I.bx + c) * (pc - Rc[o + xm]);
+        ap += __ldg(I.by + (long long)z * plane + (long long)gyp * nx + x) * (Rc[o + nx + x] - pc) -
+              __ldg(I.by + c) * (pc - Rc[o - nx + x]);
+        ap += __ldg(I.bz + (long long)zp * plane + (long long)gy * nx + x) * (Rp[o + x] - pc) -
+              __ldg(I.bz + c) * (pc - Rm[o + x]);
+        const double f0 = __ldg(I.rhs + c) - mu;
+        const double r = f0 - ap;
+        const T tv = from_double_rn<T>(__ldg(I.sinv + c) * r);
+        rt[c] = tv;
+        a0 = fma(r, r, a0);
+        a1 = fma((double)tv, (double)tv, a1);
+        a2 += pc;
+        if (first) a3 = fma(f0, f0, a3);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-  }
+  });
   acc[0] = a0;
   acc[1] = a1;
   acc[2] = a2;
@@ -450,21 +775,20 @@ __device__ void sweep_res64(const InstDesc& I, const InstState* st, const Unit& 
 template <class T, class BT>
 __global__ void __launch_bounds__(kThreads) k_step(const InstDesc* __restrict__ insts,
                                                    const UnitRef* __restrict__ units) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const UnitRef ur = units[blockIdx.x];
   const InstDesc& I = insts[ur.inst];
   InstState* st = I.st;
   const int phase = st->phase;
   if (phase >= PH_DONE) return;
-  const Unit u = unit_geometry(I, ur.unit);
   double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
   switch (phase) {
-    case PH_MEANF: sweep_meanf<T>(I, st, u, acc); break;
-    case PH_RES64: sweep_res64<T>(I, st, u, acc, reinterpret_cast<double*>(smem_raw)); break;
-    case PH_STENCIL: sweep_stencil<T, BT>(I, st, u, acc, reinterpret_cast<T*>(smem_raw)); break;
-    case PH_UPDATE: sweep_update<T>(I, st, u, acc); break;
-    case PH_CORRECT: sweep_correct<T>(I, u); break;
-    case PH_FINAL: sweep_final(I, st, u); break;
+    case PH_MEANF: sweep_meanf(I, st, ur.unit, acc); break;
+    case PH_RES64: sweep_res64<T>(I, st, ur.unit, acc, reinterpret_cast<double*>(smem_raw)); break;
+    case PH_STENCIL: sweep_stencil<T, BT>(I, st, ur.unit, acc, smem_raw); break;
+    case PH_UPDATE: sweep_update<T>(I, st, ur.unit, acc); break;
+    case PH_CORRECT: sweep_correct<T>(I, ur.unit); break;
+    case PH_FINAL: sweep_final(I, st, ur.unit); break;
     default: break;
   }
   store_partials(acc, I.part, I.nunits, ur.unit);
@@ -509,7 +833,7 @@ __global__ void k_init(InstDesc* desc, const double* rhs, double* p, double tol,
 __global__ void k_check_density(const double* __restrict__ rho, long long n, int* bad) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
-    double v = rho[c];
+    const double v = rho[c];
     if (!(v > 0.0) || !isfinite(v)) atomicOr(bad, 1);
   }
 }
@@ -521,13 +845,13 @@ __global__ void k_faces(const double* __restrict__ rho, int nx, int ny, int nz, 
   const long long plane = (long long)nx * ny;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
-    int x = (int)(c % nx);
-    int y = (int)((c / nx) % ny);
-    int z = (int)(c / plane);
-    long long cxm = c - x + (x == 0 ? nx - 1 : x - 1);
-    long long cym = c + (long long)((y == 0 ? ny - 1 : y - 1) - y) * nx;
-    long long czm = c + (long long)((z == 0 ? nz - 1 : z - 1) - z) * plane;
-    double rc = rho[c];
+    const int x = (int)(c % nx);
+    const int y = (int)((c / nx) % ny);
+    const int z = (int)(c / plane);
+    const long long cxm = c - x + (x == 0 ? nx - 1 : x - 1);
+    const long long cym = c + (long long)((y == 0 ? ny - 1 : y - 1) - y) * nx;
+    const long long czm = c + (long long)((z == 0 ? nz - 1 : z - 1) - z) * plane;
+    const double rc = rho[c];
     bx[c] = 2.0 / (rho[cxm] + rc) * ihx2;
     by[c] = 2.0 / (rho[cym] + rc) * ihy2;
     bz[c] = 2.0 / (rho[czm] + rc) * ihz2;
@@ -541,24 +865,25 @@ __global__ void k_diag(const double* __restrict__ bx, const double* __restrict__
   const long long plane = (long long)nx * ny;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
-    int x = (int)(c % nx);
-    int y = (int)((c / nx) % ny);
-    int z = (int)(c / plane);
-    long long cxp = c - x + (x == nx - 1 ? 0 : x + 1);
-    long long cyp = c + (long long)((y == ny - 1 ? 0 : y + 1) - y) * nx;
-    long long czp = c + (long long)((z == nz - 1 ? 0 : z + 1) - z) * plane;
-    double D = bx[c] + bx[cxp] + by[c] + by[cyp] + bz[c] + bz[czp];
+    const int x = (int)(c % nx);
+    const int y = (int)((c / nx) % ny);
+    const int z = (int)(c / plane);
+    const long long cxp = c - x + (x == nx - 1 ? 0 : x + 1);
+    const long long cyp = c + (long long)((y == ny - 1 ? 0 : y + 1) - y) * nx;
+    const long long czp = c + (long long)((z == nz - 1 ? 0 : z + 1) - z) * plane;
+    const double D = bx[c] + bx[cxp] + by[c] + by[cyp] + bz[c] + bz[czp];
     sinv[c] = 1.0 / sqrt(D);
   }
 }
 
+// Rounded to nearest: the rounding errors of the stored off-diagonals have no common sign, so
+// they do not add up to a spurious diagonal shift that would swamp the operator's smallest
+// eigenvalues (a directed rounding would, at BF16 precision).
 template <class BT> __device__ __forceinline__ BT to_coef(double v);
 template <> __device__ __forceinline__ double to_coef<double>(double v) { return v; }
-// rounded toward zero: the stored off-diagonals never exceed the exact ones, so the inner
-// operator stays diagonally dominant (positive definite) after rounding
-template <> __device__ __forceinline__ float to_coef<float>(double v) { return __double2float_rz(v); }
+template <> __device__ __forceinline__ float to_coef<float>(double v) { return __double2float_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 to_coef<__nv_bfloat16>(double v) {
-  return __float2bfloat16_rz(__double2float_rz(v));
+  return __double2bfloat16(v);
 }
 
 // bt_d[c] = b_d[c] sinv[c - e_d] sinv[c]
@@ -570,16 +895,51 @@ __global__ void k_scaled(const double* __restrict__ bx, const double* __restrict
   const long long plane = (long long)nx * ny;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
-    int x = (int)(c % nx);
-    int y = (int)((c / nx) % ny);
-    int z = (int)(c / plane);
-    long long cxm = c - x + (x == 0 ? nx - 1 : x - 1);
-    long long cym = c + (long long)((y == 0 ? ny - 1 : y - 1) - y) * nx;
-    long long czm = c + (long long)((z == 0 ? nz - 1 : z - 1) - z) * plane;
-    double s = sinv[c];
+    const int x = (int)(c % nx);
+    const int y = (int)((c / nx) % ny);
+    const int z = (int)(c / plane);
+    const long long cxm = c - x + (x == 0 ? nx - 1 : x - 1);
+    const long long cym = c + (long long)((y == 0 ? ny - 1 : y - 1) - y) * nx;
+    const long long czm = c + (long long)((z == 0 ? nz - 1 : z - 1) - z) * plane;
+    const double s = sinv[c];
     sx[c] = to_coef<BT>(bx[c] * sinv[cxm] * s);
     sy[c] = to_coef<BT>(by[c] * sinv[cym] * s);
     sz[c] = to_coef<BT>(bz[c] * sinv[czm] * s);
+  }
+}
+
+// BF16 coefficients: the rounded off-diagonals no longer sum (with the weights sqrt(D)) to the
+// unit diagonal, and at BF16 precision that inconsistency is large enough to create spurious
+// near-zero or negative eigenvalues.  The correction dg = sum_faces bt' s_nb / s_c - 1 (s =
+// sqrt(D), bt' the stored BF16 values) restores sqrt(D) as an exact null vector of the stored
+// inner operator  (1 + dg) I - offdiag(bt'), which is then congruent to a graph Laplacian with
+// non-negative weights, i.e. symmetric positive semi-definite.
+__global__ void k_diag_correction(const __nv_bfloat16* __restrict__ sx,
+                                  const __nv_bfloat16* __restrict__ sy,
+                                  const __nv_bfloat16* __restrict__ sz,
+                                  const double* __restrict__ sinv, int nx, int ny, int nz,
+                                  __nv_bfloat16* dg) {
+  const long long n = (long long)nx * ny * nz;
+  const long long plane = (long long)nx * ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % nx);
+    const int y = (int)((c / nx) % ny);
+    const int z = (int)(c / plane);
+    const long long cxm = c - x + (x == 0 ? nx - 1 : x - 1), cxp = c - x + (x == nx - 1 ? 0 : x + 1);
+    const long long cym = c + (long long)((y == 0 ? ny - 1 : y - 1) - y) * nx;
+    const long long cyp = c + (long long)((y == ny - 1 ? 0 : y + 1) - y) * nx;
+    const long long czm = c + (long long)((z == 0 ? nz - 1 : z - 1) - z) * plane;
+    const long long czp = c + (long long)((z == nz - 1 ? 0 : z + 1) - z) * plane;
+    // s_nb / s_c = sinv_c / sinv_nb
+    const double sc = sinv[c];
+    double g = (double)__bfloat162float(sx[c]) * sc / sinv[cxm] +
+               (double)__bfloat162float(sx[cxp]) * sc / sinv[cxp] +
+               (double)__bfloat162float(sy[c]) * sc / sinv[cym] +
+               (double)__bfloat162float(sy[cyp]) * sc / sinv[cyp] +
+               (double)__bfloat162float(sz[c]) * sc / sinv[czm] +
+               (double)__bfloat162float(sz[czp]) * sc / sinv[czp];
+    dg[c] = __double2bfloat16(g - 1.0);
   }
 }
 
@@ -591,15 +951,15 @@ __global__ void k_apply(const double* __restrict__ bx, const double* __restrict_
   const long long plane = (long long)nx * ny;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
-    int x = (int)(c % nx);
-    int y = (int)((c / nx) % ny);
-    int z = (int)(c / plane);
-    long long cxm = c - x + (x == 0 ? nx - 1 : x - 1), cxp = c - x + (x == nx - 1 ? 0 : x + 1);
-    long long cym = c + (long long)((y == 0 ? ny - 1 : y - 1) - y) * nx;
-    long long cyp = c + (long long)((y == ny - 1 ? 0 : y + 1) - y) * nx;
-    long long czm = c + (long long)((z == 0 ? nz - 1 : z - 1) - z) * plane;
-    long long czp = c + (long long)((z == nz - 1 ? 0 : z + 1) - z) * plane;
-    double pc = p[c];
+    const int x = (int)(c % nx);
+    const int y = (int)((c / nx) % ny);
+    const int z = (int)(c / plane);
+    const long long cxm = c - x + (x == 0 ? nx - 1 : x - 1), cxp = c - x + (x == nx - 1 ? 0 : x + 1);
+    const long long cym = c + (long long)((y == 0 ? ny - 1 : y - 1) - y) * nx;
+    const long long cyp = c + (long long)((y == ny - 1 ? 0 : y + 1) - y) * nx;
+    const long long czm = c + (long long)((z == 0 ? nz - 1 : z - 1) - z) * plane;
+    const long long czp = c + (long long)((z == nz - 1 ? 0 : z + 1) - z) * plane;
+    const double pc = p[c];
     out[c] = bx[cxp] * (p[cxp] - pc) - bx[c] * (pc - p[cxm]) + by[cyp] * (p[cyp] - pc) -
              by[c] * (pc - p[cym]) + bz[czp] * (p[czp] - pc) - bz[c] * (pc - p[czm]);
   }
@@ -622,8 +982,8 @@ cudaError_t launch_check_density(const double* rho, long long n, int* bad, cudaS
 cudaError_t launch_build_coefficients(const double* rho, int nx, int ny, int nz, double L,
                                       double* bx, double* by, double* bz, double* sinv,
                                       cudaStream_t s) {
-  long long n = (long long)nx * ny * nz;
-  double hx = L / nx, hy = L / ny, hz = L / nz;
+  const long long n = (long long)nx * ny * nz;
+  const double hx = L / nx, hy = L / ny, hz = L / nz;
   k_faces<<<grid_for(n), 256, 0, s>>>(rho, nx, ny, nz, 1.0 / (hx * hx), 1.0 / (hy * hy),
                                       1.0 / (hz * hz), bx, by, bz);
   k_diag<<<grid_for(n), 256, 0, s>>>(bx, by, bz, nx, ny, nz, sinv);
@@ -632,24 +992,29 @@ cudaError_t launch_build_coefficients(const double* rho, int nx, int ny, int nz,
 
 cudaError_t launch_scaled(int prec, const double* bx, const double* by, const double* bz,
                           const double* sinv, int nx, int ny, int nz, void* sx, void* sy, void* sz,
-                          cudaStream_t s) {
-  long long n = (long long)nx * ny * nz;
+                          void* sd, cudaStream_t s) {
+  const long long n = (long long)nx * ny * nz;
   if (prec == PREC_FP64)
     k_scaled<double><<<grid_for(n), 256, 0, s>>>(bx, by, bz, sinv, nx, ny, nz, (double*)sx,
                                                  (double*)sy, (double*)sz);
   else if (prec == PREC_MIXED)
     k_scaled<float><<<grid_for(n), 256, 0, s>>>(bx, by, bz, sinv, nx, ny, nz, (float*)sx,
                                                 (float*)sy, (float*)sz);
-  else
+  else {
     k_scaled<__nv_bfloat16><<<grid_for(n), 256, 0, s>>>(bx, by, bz, sinv, nx, ny, nz,
                                                         (__nv_bfloat16*)sx, (__nv_bfloat16*)sy,
                                                         (__nv_bfloat16*)sz);
+    k_diag_correction<<<grid_for(n), 256, 0, s>>>((const __nv_bfloat16*)sx,
+                                                  (const __nv_bfloat16*)sy,
+                                                  (const __nv_bfloat16*)sz, sinv, nx, ny, nz,
+                                                  (__nv_bfloat16*)sd);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const double* bx, const double* by, const double* bz, const double* p,
                          int nx, int ny, int nz, double* out, cudaStream_t s) {
-  long long n = (long long)nx * ny * nz;
+  const long long n = (long long)nx * ny * nz;
   k_apply<<<grid_for(n), 256, 0, s>>>(bx, by, bz, p, nx, ny, nz, out);
   return cudaGetLastError();
 }

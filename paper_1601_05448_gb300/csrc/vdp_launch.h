@@ -13,7 +13,7 @@ cudaError_t launch_build_coefficients(const double* rho, int nx, int ny, int nz,
                                       cudaStream_t s);
 cudaError_t launch_scaled(int prec, const double* bx, const double* by, const double* bz,
                           const double* sinv, int nx, int ny, int nz, void* sx, void* sy, void* sz,
-                          cudaStream_t s);
+                          void* sd, cudaStream_t s);
 cudaError_t launch_apply(const double* bx, const double* by, const double* bz, const double* p,
                          int nx, int ny, int nz, double* out, cudaStream_t s);
 cudaError_t launch_init(InstDesc* desc, const double* rhs, double* p, double tol, double inner_tol,
