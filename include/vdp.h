@@ -146,6 +146,47 @@ int vdp_version(void);
  */
 int vdp_apply(vdp_ctx *ctx, const double *p, double *out);
 
+/* ------------------------------------------------------------------------------------------ */
+/* A solve that allocates no device memory.                                                    */
+/* ------------------------------------------------------------------------------------------ */
+
+/*
+ * The paper has no counterpart to this entry point; it exists for callers that cannot call
+ * cudaMalloc: code that runs while a CUDA graph is being captured on its stream (an allocation
+ * there can break the capture or synchronise the device), hosts whose device memory belongs to
+ * a pool or budget manager that forbids side allocations, and latency-critical loops that
+ * cannot take the implicit device synchronisation of cudaMalloc/cudaFree.
+ *
+ * vdp_solve_noalloc does what vdp_create + vdp_set_density + vdp_solve + vdp_destroy do with
+ * default options (and gives the same pressure), for grids of at most VDP_NOALLOC_MAX_CELLS
+ * cells.  Every intermediate (face coefficients, Jacobi scaling, Krylov vectors, partial sums,
+ * solver state) lives in one fixed array of VDP_NOALLOC_SCRATCH_BYTES bytes of device memory
+ * that the CUDA runtime reserves when the library is loaded, on every GPU that loads it, and
+ * keeps until the process exits.  The call makes no cudaMalloc, cudaFree or other allocating
+ * call.
+ *
+ *   nx, ny, nz, L   grid and box as in vdp_create (nx a multiple of 8); nx*ny*nz above
+ *                   VDP_NOALLOC_MAX_CELLS is rejected with VDP_EINVAL
+ *   rho, rhs        device pointers, nx*ny*nz doubles (rhs 16-byte aligned); not modified
+ *   p               device pointer, nx*ny*nz doubles, 16-byte aligned; output (zero mean)
+ *   tol             relative residual target as in vdp_solve
+ *   precision       vdp_precision
+ *   stream          cudaStream_t for all work (NULL = legacy default stream); the call returns
+ *                   after the work has finished
+ *   stats           optional (may be NULL); ms is not measured (0)
+ * Returns a vdp_status as vdp_solve / vdp_set_density do; host pointers give VDP_EINVAL.
+ *
+ * The first call on a device looks up the device address of the array for that device (the
+ * current device at the call); make that first call before any stream capture begins.  All calls
+ * in the process share the one array and it keeps the contents of the last call: calls whose GPU
+ * work overlaps -- from two host threads, or on two streams -- race and corrupt each other, so
+ * serialise them.
+ */
+#define VDP_NOALLOC_MAX_CELLS 65536
+#define VDP_NOALLOC_SCRATCH_BYTES 6429696
+int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double *rho, const double *rhs,
+                      double *p, double tol, int precision, void *stream, vdp_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,7 +70,10 @@ _SIGS = {
     "vdp_last_cuda_error": (ctypes.c_char_p, []),
     "vdp_version": (ctypes.c_int, []),
     "vdp_apply": (ctypes.c_int, [_P, _P, _P]),
+    "vdp_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
+                                         ctypes.c_double, ctypes.c_int, _P, ctypes.POINTER(vdp_stats)]),
 }
+VDP_NOALLOC_MAX_CELLS = 65536
 
 
 def exported_symbols():
@@ -155,6 +158,21 @@ def vdp_version() -> int:
 
 def vdp_apply(ctx: int, p, out) -> int:
     return load().vdp_apply(ctx, _ptr(p), _ptr(out, writable=True))
+
+
+def vdp_solve_noalloc(nx: int, ny: int, nz: int, L: float, rho, rhs, p, tol: float, precision: int = VDP_FP64,
+                      stream=None):
+    """Solve without any device allocation (device tensors only, nx*ny*nz <= VDP_NOALLOC_MAX_CELLS).
+
+    For callers that must not allocate device memory (inside a stream capture, under an external
+    memory pool, or in latency-critical loops); intermediates live in a fixed device array owned
+    by the library.  Calls share that array: do not run two at once.  Returns (status, stats)."""
+    s = vdp_stats()
+    st = load().vdp_solve_noalloc(int(nx), int(ny), int(nz), float(L), _ptr(rho), _ptr(rhs),
+                                  _ptr(p, writable=True), float(tol), int(precision),
+                                  stream if (stream is None or isinstance(stream, int)) else stream.cuda_stream,
+                                  ctypes.byref(s))
+    return st, s
 
 
 # ---- marshalling ------------------------------------------------------------------------------

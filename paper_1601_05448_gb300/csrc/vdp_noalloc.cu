@@ -1,0 +1,205 @@
+// vdp_noalloc.cu -- vdp_solve_noalloc: a complete small solve that allocates no device memory.
+//
+// Who needs this.  Some callers cannot call cudaMalloc: code that runs while another component
+// captures the stream into a CUDA graph (an allocation there can invalidate the capture or
+// synchronise the device), hosts whose device memory is owned by a pool or budget manager that
+// forbids side allocations, and latency-sensitive loops that cannot afford the implicit device
+// synchronisation of cudaMalloc/cudaFree.  vdp_solve_noalloc serves them: the caller passes
+// rho, rhs and p; every intermediate the solve needs (face coefficients, Jacobi scaling, Krylov
+// vectors, partial sums, solver state) lives in one file-scope __device__ array of fixed size
+// that the CUDA runtime creates when the library is loaded, on every GPU that loads it, and
+// keeps until the process exits.
+//
+// The solve runs the same kernels, unit layout and state machine as vdp_solve with default
+// options, so the two return the same pressure.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "vdp.h"
+#include "vdp_internal.cuh"
+#include "vdp_launch.h"
+
+using namespace vdp;
+
+namespace {
+
+constexpr long long kMaxCells = VDP_NOALLOC_MAX_CELLS;
+constexpr int kMaxUnits = 152;
+constexpr size_t kAlign = 256;
+
+constexpr size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+
+// Layout of the scratch array for kMaxCells cells (offsets in bytes).
+constexpr size_t kF64 = align_up(sizeof(double) * kMaxCells);     // one FP64 field
+constexpr size_t kBf16 = align_up(sizeof(uint16_t) * kMaxCells);  // the BF16 diagonal correction
+constexpr size_t kOffFields = 0;                                   // bx by bz sinv sx sy sz x r d0 d1 q
+constexpr size_t kNumF64 = 12;
+constexpr size_t kOffSd = kOffFields + kNumF64 * kF64;
+constexpr size_t kOffPart = kOffSd + kBf16;
+constexpr size_t kOffUnits = kOffPart + align_up(sizeof(double) * kSlots * kMaxUnits);
+constexpr size_t kOffDesc = kOffUnits + align_up(sizeof(UnitRef) * kMaxUnits);
+constexpr size_t kOffState = kOffDesc + align_up(sizeof(InstDesc));
+constexpr size_t kOffTicket = kOffState + align_up(sizeof(InstState));
+constexpr size_t kOffFlag = kOffTicket + kAlign;
+constexpr size_t kScratchBytes = kOffFlag + kAlign;
+
+// The scratch array.  Its name is only a host-side stand-in in host code; the device address
+// comes from cudaGetSymbolAddress (see scratch_base).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+constexpr int kMaxDevices = 64;
+unsigned char* g_base[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per device.
+int scratch_base(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VDP_ECUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return VDP_ECUDA;
+    g_base[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_base[dev];
+  return VDP_OK;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+#define NA_CK(call)                             \
+  do {                                          \
+    if ((call) != cudaSuccess) return VDP_ECUDA; \
+  } while (0)
+
+}  // namespace
+
+static_assert(sizeof(InstDesc) <= kAlign && sizeof(InstState) <= kAlign, "scratch slots");
+static_assert(kScratchBytes == VDP_NOALLOC_SCRATCH_BYTES, "keep the header's size in sync");
+
+extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double* rho,
+                                 const double* rhs, double* p, double tol, int precision,
+                                 void* stream, vdp_stats* stats) {
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (nx < 8 || nx % 8 != 0 || ny < 1 || nz < 1 || !(L > 0.0) || !(tol > 0.0)) return VDP_EINVAL;
+  if (precision < VDP_FP64 || precision > VDP_MIXED_BF16) return VDP_EINVAL;
+  const long long n = (long long)nx * ny * nz;
+  if (n > kMaxCells) return VDP_EINVAL;  // larger than the fixed scratch array
+  if (!rho || !rhs || !p || !on_device(rho) || !on_device(rhs) || !on_device(p)) return VDP_EINVAL;
+  if (((uintptr_t)rhs & 15) || ((uintptr_t)p & 15)) return VDP_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* base = nullptr;
+  int st = scratch_base(&base);
+  if (st != VDP_OK) return st;
+
+  double* f64[kNumF64];
+  for (size_t i = 0; i < kNumF64; ++i)
+    f64[i] = reinterpret_cast<double*>(base + kOffFields + i * kF64);
+  double *bx = f64[0], *by = f64[1], *bz = f64[2], *sinv = f64[3];
+  void *sx = f64[4], *sy = f64[5], *sz = f64[6];
+  void* sd = base + kOffSd;
+  double* part = reinterpret_cast<double*>(base + kOffPart);
+  UnitRef* units = reinterpret_cast<UnitRef*>(base + kOffUnits);
+  InstDesc* desc = reinterpret_cast<InstDesc*>(base + kOffDesc);
+  InstState* state = reinterpret_cast<InstState*>(base + kOffState);
+  unsigned int* ticket = reinterpret_cast<unsigned int*>(base + kOffTicket);
+  int* flag = reinterpret_cast<int*>(base + kOffFlag);
+
+  // density check, then the coefficients (the flag must start at zero on every call)
+  int bad = 0;
+  NA_CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  NA_CK(launch_check_density(rho, n, flag, s));
+  NA_CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NA_CK(cudaStreamSynchronize(s));
+  if (bad) return VDP_EDENSITY;
+  NA_CK(launch_build_coefficients(rho, nx, ny, nz, L, bx, by, bz, sinv, s));
+  NA_CK(launch_scaled(precision, bx, by, bz, sinv, nx, ny, nz, sx, sy, sz, sd, s));
+
+  // the default unit layout of vdp_solve
+  const int ts = precision == VDP_FP64 ? 8 : 4;
+  const int bs = precision == VDP_FP64 ? 8 : (precision == VDP_MIXED ? 4 : 2);
+  const bool diag = precision == VDP_MIXED_BF16;
+  const size_t budget = 225 * 1024;
+  int ty = std::max(1, std::min(ny, 1024 / nx));
+  while (ty > 1 && 4 * stage_bytes(nx, ty, ts, bs, diag) > budget) --ty;
+  const size_t sb = stage_bytes(nx, ty, ts, bs, diag);
+  const int fit = (int)(budget / sb);
+  if (fit < 4) return VDP_EINVAL;
+  const int stages = std::min(fit, 6);
+  const int uy = (ny + ty - 1) / ty;
+  const long long npairs = (long long)uy * nz;
+  const int nunits = (int)std::min<long long>(kMaxUnits, npairs);
+  const size_t smem = std::max((size_t)stages * sb, ring_bytes(nx, ty));
+
+  UnitRef hu[kMaxUnits];
+  for (int i = 0; i < nunits; ++i) hu[i] = UnitRef{0, i};
+  InstDesc d{};
+  d.nx = nx;
+  d.ny = ny;
+  d.nz = nz;
+  d.ty = ty;
+  d.uy = uy;
+  d.nunits = nunits;
+  d.stages = stages;
+  d.npairs = npairs;
+  d.ncell = n;
+  d.bx = bx;
+  d.by = by;
+  d.bz = bz;
+  d.sinv = sinv;
+  d.sx = sx;
+  d.sy = sy;
+  d.sz = sz;
+  d.sd = sd;
+  d.x = f64[7];
+  d.r = f64[8];
+  d.d0 = f64[9];
+  d.d1 = f64[10];
+  d.q = f64[11];
+  d.part = part;
+  d.ticket = ticket;
+  d.st = state;
+  // pageable host sources: these copies complete before the calls return
+  NA_CK(cudaMemcpyAsync(units, hu, sizeof(UnitRef) * nunits, cudaMemcpyHostToDevice, s));
+  NA_CK(cudaMemcpyAsync(desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+  NA_CK(prepare_step(precision, smem));
+  // the per-solve state and the ticket are reset on the device by the init kernel
+  const int max_iter = 20000;
+  NA_CK(launch_init(desc, rhs, p, tol, 1e-4, max_iter, max_iter, 0, precision, s));
+
+  const int m = 32;
+  const long long max_rounds = (2LL * max_iter + 4096 + m - 1) / m;
+  InstState h{};
+  bool done = false;
+  long long rounds = 0;
+  while (!done && rounds < max_rounds) {
+    for (int i = 0; i < m; ++i) NA_CK(launch_step(precision, desc, units, nunits, smem, s));
+    ++rounds;
+    NA_CK(cudaMemcpyAsync(&h, state, sizeof(h), cudaMemcpyDeviceToHost, s));
+    NA_CK(cudaStreamSynchronize(s));
+    done = h.phase >= PH_DONE;
+  }
+  const int status = done ? h.status : VDP_ETIMEOUT;
+  if (stats) {
+    stats->status = status;
+    stats->iters = h.iters;
+    stats->outer_iters = h.outer;
+    stats->rel_res = h.rel_res;
+    stats->rhs_mean = h.mu_f;
+    stats->ms = 0.0;
+    stats->sweeps = h.sweeps;
+    stats->launches = (int)(1 + rounds * m);
+  }
+  return status;
+}
