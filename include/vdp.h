@@ -76,7 +76,8 @@ typedef struct {
   int tile_y;          /* rows per row tile of a work unit (0 = automatic) */
   int units;           /* work units (thread blocks) per sweep (0 = automatic) */
   int stages;          /* shared-memory pipeline stages of the stencil sweep, 4..8 (0 = auto) */
-  int steps_per_sync;  /* device sweeps per host convergence check (0 = automatic) */
+  int threads;         /* threads per stencil work unit, 64..512, multiple of 32 (0 = auto) */
+  int steps_per_sync;  /* (stencil, flat) launch pairs per host convergence check (0 = auto) */
 } vdp_opts;
 
 typedef struct {
@@ -183,7 +184,7 @@ int vdp_apply(vdp_ctx *ctx, const double *p, double *out);
  * serialise them.
  */
 #define VDP_NOALLOC_MAX_CELLS 65536
-#define VDP_NOALLOC_SCRATCH_BYTES 6429696
+#define VDP_NOALLOC_SCRATCH_BYTES 6436352
 int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double *rho, const double *rhs,
                       double *p, double tol, int precision, void *stream, vdp_stats *stats);
 

@@ -1,9 +1,10 @@
 // vdp_api.cu -- the C ABI of libvdp (include/vdp.h): contexts, device buffers, the solve driver.
 //
 // A solve is one instance of the per-instance state machine in vdp_kernels.cu, advanced by the
-// step kernel.  The driver launches a captured CUDA graph of `steps_per_sync` step launches,
-// copies the instance's 200-byte state to pinned host memory after each graph, and keeps two
-// graphs in flight so that the convergence check on the host overlaps with device work.
+// two sweep kernels (stencil kind, flat kind).  The driver launches a captured CUDA graph of
+// `steps_per_sync` (stencil, flat) launch pairs, copies the instance's 200-byte state to pinned
+// host memory after each graph, and keeps two graphs in flight so that the convergence check on
+// the host overlaps with device work.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -76,8 +77,7 @@ struct vdp_ctx {
   InstState* hstate = nullptr;     // pinned, 2 entries
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs[2] = {nullptr, nullptr};
   // layout
-  int ty = 0, nunits = 0;
-  size_t smem = 0;
+  Layout lay{};
   int layout_prec = -1;
   bool layout_dirty = true;
   // graph cache
@@ -101,6 +101,7 @@ void vdp_default_options(vdp_opts* o) {
   o->tile_y = 0;
   o->units = 0;
   o->stages = 0;
+  o->threads = 0;
   o->steps_per_sync = 0;
 }
 
@@ -149,55 +150,21 @@ void free_ctx(vdp_ctx* c) {
   delete c;
 }
 
-constexpr size_t kSmemBudget = 225 * 1024;  // dynamic shared memory per work unit
-
-size_t inner_size(int prec) { return prec == PREC_FP64 ? 8 : 4; }
-size_t coef_size(int prec) { return prec == PREC_FP64 ? 8 : (prec == PREC_MIXED ? 4 : 2); }
-
-// Work-unit shape for precision `prec`: full x rows, row tiles of about 1024 cells; as many
-// pipeline stages as fit in shared memory (at most 6); one unit per SM (the stencil sweep
-// keeps about 100-200 KB of shared memory per unit in flight).
-struct Layout {
-  int ty, uy, nunits, stages;
-  long long npairs;
-  size_t smem;
-};
-
 int choose_layout(const vdp_ctx* c, int prec, Layout* out) {
-  const int nx = c->nx, ny = c->ny, nz = c->nz;
-  const size_t ts = inner_size(prec), bs = coef_size(prec);
-  int ty = c->opts.tile_y > 0 ? c->opts.tile_y : std::max(1, std::min(ny, 1024 / nx));
-  ty = std::min(ty, ny);
-  // shrink the tile until at least three stages fit
-  const bool diag = prec == PREC_MIXED_BF16;
-  while (ty > 1 && 4 * stage_bytes(nx, ty, (int)ts, (int)bs, diag) > kSmemBudget) --ty;
-  const size_t sb = stage_bytes(nx, ty, (int)ts, (int)bs, diag);
-  int fit = (int)(kSmemBudget / sb);
-  if (fit < 4) return VDP_EINVAL;  // rows too long for the shared-memory pipeline
-  int stages = c->opts.stages > 0 ? c->opts.stages : std::min(fit, 6);
-  if (stages < 4 || stages > kMaxStages || stages > fit) return VDP_EINVAL;
-  const int uy = (ny + ty - 1) / ty;
-  const long long npairs = (long long)uy * nz;
-  long long units = c->opts.units > 0 ? c->opts.units : 152;
-  units = std::min(units, npairs);
-  out->ty = ty;
-  out->uy = uy;
-  out->nunits = (int)units;
-  out->stages = stages;
-  out->npairs = npairs;
-  out->smem = std::max((size_t)stages * sb, ring_bytes(nx, ty));
-  return VDP_OK;
+  return plan_layout(c->nx, c->ny, c->nz, prec, c->opts.tile_y, c->opts.units, c->opts.stages,
+                     c->opts.threads, out)
+             ? VDP_OK
+             : VDP_EINVAL;
 }
 
 int configure_layout(vdp_ctx* c, int prec) {
   Layout lay;
   int s = choose_layout(c, prec, &lay);
   if (s != VDP_OK) return s;
-  c->ty = lay.ty;
-  c->nunits = lay.nunits;
-  c->smem = lay.smem;
-  std::vector<UnitRef> u(c->nunits);
-  for (int i = 0; i < c->nunits; ++i) u[i] = UnitRef{0, i};
+  c->lay = lay;
+  std::vector<UnitRef> u(lay.nunits + lay.nunits_f);
+  for (int i = 0; i < lay.nunits; ++i) u[i] = UnitRef{0, i};
+  for (int i = 0; i < lay.nunits_f; ++i) u[lay.nunits + i] = UnitRef{0, i};
   VDP_CK(cudaMemcpyAsync(c->units, u.data(), sizeof(UnitRef) * u.size(), cudaMemcpyHostToDevice,
                          c->stream));
   InstDesc d{};
@@ -207,6 +174,7 @@ int configure_layout(vdp_ctx* c, int prec) {
   d.ty = lay.ty;
   d.uy = lay.uy;
   d.nunits = lay.nunits;
+  d.nunits_f = lay.nunits_f;
   d.stages = lay.stages;
   d.npairs = lay.npairs;
   d.ncell = c->n;
@@ -228,7 +196,7 @@ int configure_layout(vdp_ctx* c, int prec) {
   d.st = c->st;
   VDP_CK(cudaMemcpyAsync(c->desc, &d, sizeof(d), cudaMemcpyHostToDevice, c->stream));
   VDP_CK(cudaStreamSynchronize(c->stream));
-  VDP_CK(prepare_step(prec, c->smem));
+  VDP_CK(prepare_step(prec, lay.smem));
   if (c->gexec) {
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
@@ -240,7 +208,7 @@ int configure_layout(vdp_ctx* c, int prec) {
 
 int steps_per_sync(const vdp_ctx* c) {
   if (c->opts.steps_per_sync > 0) return c->opts.steps_per_sync;
-  return 32;
+  return 16;
 }
 
 int ensure_graph(vdp_ctx* c, int prec) {
@@ -253,12 +221,15 @@ int ensure_graph(vdp_ctx* c, int prec) {
   cudaGraph_t g = nullptr;
   VDP_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
   for (int i = 0; i < m; ++i) {
-    cudaError_t e = launch_step(prec, c->desc, c->units, c->nunits, c->smem, c->cap);
+    cudaError_t e = launch_stencil(prec, c->desc, c->units, c->lay.nunits, c->lay.threads,
+                                   c->lay.smem, c->cap);
+    if (e == cudaSuccess)
+      e = launch_flat(prec, c->desc, c->units + c->lay.nunits, c->lay.nunits_f, c->cap);
     if (e != cudaSuccess) {
       cudaGraph_t junk;
       cudaStreamEndCapture(c->cap, &junk);
       if (junk) cudaGraphDestroy(junk);
-      return cuda_fail(e, "launch_step (capture)");
+      return cuda_fail(e, "sweep launch (capture)");
     }
   }
   VDP_CK(cudaStreamEndCapture(c->cap, &g));
@@ -298,7 +269,7 @@ int vdp_create(int nx, int ny, int nz, double L, vdp_ctx** out) {
   vdp_default_options(&c->opts);
   cudaGetDevice(&c->device);
   size_t bytes = sizeof(double) * (size_t)c->n;
-  size_t maxunits = (size_t)std::max(ny * (size_t)nz, (size_t)152 * 16);
+  size_t maxunits = (size_t)std::max(ny * (size_t)nz, (size_t)kSMs * 16);
   cudaError_t e = cudaSuccess;
   double** f64[] = {&c->bx, &c->by, &c->bz, &c->sinv};
   for (double** b : f64)
@@ -311,7 +282,7 @@ int vdp_create(int nx, int ny, int nz, double L, vdp_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->ticket, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->st, sizeof(InstState));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->desc, sizeof(InstDesc));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->units, sizeof(UnitRef) * maxunits);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->units, sizeof(UnitRef) * (maxunits + kSMs * 8));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->flag, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hstate, 2 * sizeof(InstState));
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
@@ -342,7 +313,8 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
   if (o->precision < VDP_FP64 || o->precision > VDP_MIXED_BF16) return VDP_EINVAL;
   if (o->max_iter < 1 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return VDP_EINVAL;
   if (o->precond != VDP_PRECOND_JACOBI && o->precond != VDP_PRECOND_CHEB) return VDP_EINVAL;
-  if (o->tile_y < 0 || o->units < 0 || o->stages < 0 || o->steps_per_sync < 0) return VDP_EINVAL;
+  if (o->tile_y < 0 || o->units < 0 || o->stages < 0 || o->threads < 0 || o->steps_per_sync < 0)
+    return VDP_EINVAL;
   if (o->units > 152 * 16 || o->stages > kMaxStages || (o->stages > 0 && o->stages < 4))
     return VDP_EINVAL;
   vdp_opts old = c->opts;
@@ -416,11 +388,11 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   VDP_CK(cudaEventRecord(c->ev0, c->stream));
   VDP_CK(launch_init(c->desc, drhs, dp, tol, c->opts.inner_tol, c->opts.max_iter,
                      c->opts.max_iter, c->opts.use_guess ? 1 : 0, prec, c->stream));
-  // Upper bound on sweeps: two per inner iteration plus the outer phases; the state machine
-  // itself stops at max_iter, this only guards the host loop.
-  const long long max_sweeps = 2LL * c->opts.max_iter + 4096;
+  // Upper bound on launch pairs: one per inner iteration plus the outer phases; the state
+  // machine itself stops at max_iter, this only guards the host loop.
+  const long long max_pairs = 2LL * c->opts.max_iter + 4096;
   const int m = c->g_steps;
-  const long long max_graphs = (max_sweeps + m - 1) / m;
+  const long long max_graphs = (max_pairs + m - 1) / m;
   long long issued = 0, checked = 0;
   bool done = false;
   auto issue = [&]() -> int {
@@ -452,7 +424,7 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   c->stats.rhs_mean = hs.mu_f;
   c->stats.ms = ms;
   c->stats.sweeps = hs.sweeps;
-  c->stats.launches = (int)(1 + issued * m);
+  c->stats.launches = (int)(1 + issued * 2 * m);
   return c->stats.status;
 }
 

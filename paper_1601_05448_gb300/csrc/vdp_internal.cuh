@@ -32,7 +32,8 @@ enum Phase : int {
 enum Prec : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_MIXED_BF16 = 2 };
 
 constexpr int kSlots = 4;          // partial-sum slots per unit
-constexpr int kThreads = 256;      // threads per work unit (CTA)
+constexpr int kMaxThreads = 512;   // threads per stencil work unit (CTA), at most
+constexpr int kFlatThreads = 256;  // threads per flat work unit
 constexpr int kMaxStages = 8;      // shared-memory pipeline stages of the stencil sweep
 
 // Mutable per-instance solver state (device memory).
@@ -68,14 +69,15 @@ struct InstState {
   double rel_res;      // FP64 relative residual at the last RES64
 };
 
-// Constant per-instance description (device memory).
+// Constant per-instance description (device memory).  Stencil sweeps split the (row tile, plane)
+// pairs into `nunits` units; flat sweeps split the cells into `nunits_f` contiguous ranges.
 struct InstDesc {
   int nx, ny, nz;
   int ty;              // rows per row tile
   int uy;              // row tiles
-  int nunits;          // work units (CTAs) per sweep
+  int nunits;          // stencil work units (CTAs) per sweep
   int stages;          // shared-memory pipeline stages of the stencil sweep
-  int pad0;
+  int nunits_f;        // flat work units per sweep
   long long npairs;    // uy * nz (row tile, plane) pairs
   long long ncell;
   const double* rhs;   // caller's f (set per solve)
@@ -115,6 +117,77 @@ __host__ __device__ inline size_t stage_bytes(int nx, int ty, int tsize, int bsi
 // Bytes of the three-plane ring of the FP64 residual sweep.
 __host__ __device__ inline size_t ring_bytes(int nx, int ty) {
   return (size_t)3 * (ty + 2) * nx * sizeof(double);
+}
+
+// ---- work decomposition (host) ------------------------------------------------------------------
+
+constexpr int kSMs = 152;                 // GB300
+constexpr size_t kSmemPerSM = 227 * 1024; // shared memory per SM available to CTAs
+constexpr size_t kSmemBudget = 225 * 1024;
+
+struct Layout {
+  int ty;              // rows per row tile
+  int uy;              // row tiles
+  int stages;          // stencil pipeline stages
+  int threads;         // stencil threads per unit
+  int nunits;          // stencil units
+  int nunits_f;        // flat units
+  long long npairs;
+  size_t smem;         // dynamic shared memory of the stencil kernel
+};
+
+// Inner type size, coefficient size and BF16 diagonal correction per precision.
+inline void prec_sizes(int prec, int* ts, int* bs, bool* diag) {
+  *ts = prec == PREC_FP64 ? 8 : 4;
+  *bs = prec == PREC_FP64 ? 8 : (prec == PREC_MIXED ? 4 : 2);
+  *diag = prec == PREC_MIXED_BF16;
+}
+
+// Unit layout for an nx x ny x nz grid in precision `prec`; zero arguments pick the defaults:
+// FP64 uses 512-thread stencil units with about 2048 cells per plane, FP32/BF16 256-thread units
+// with about 1024; the row tile shrinks until four pipeline stages fit; stages default to what
+// fits (at most 6), or to 4 when that lets two units share an SM; one or two stencil units per SM
+// (as shared memory allows), and flat units of about 4096+ cells (at most 4 per SM).
+// Returns false when the rows are too long for a four-stage pipeline.
+inline bool plan_layout(int nx, int ny, int nz, int prec, int tile_y, int units, int stages,
+                        int threads, Layout* L) {
+  int ts, bs;
+  bool diag;
+  prec_sizes(prec, &ts, &bs, &diag);
+  const int nt = threads > 0 ? threads : (prec == PREC_FP64 ? 512 : 256);
+  if (nt < 64 || nt > kMaxThreads || nt % 32) return false;
+  const int cells = prec == PREC_FP64 ? 2048 : 1024;
+  int ty = tile_y > 0 ? tile_y : (cells / nx > 1 ? cells / nx : 1);
+  if (ty > ny) ty = ny;
+  while (ty > 1 && 4 * stage_bytes(nx, ty, ts, bs, diag) > kSmemBudget) --ty;
+  const size_t sb = stage_bytes(nx, ty, ts, bs, diag);
+  const int fit = (int)(kSmemBudget / sb);
+  if (fit < 4) return false;
+  int S = stages;
+  if (S <= 0) {
+    S = fit < 6 ? fit : 6;
+    if (4 * sb + 1024 <= kSmemPerSM / 2 && 2 * nt <= 2048) S = 4;  // two units per SM
+  }
+  if (S < 4 || S > kMaxStages || S > fit) return false;
+  const size_t smem = (size_t)S * sb > ring_bytes(nx, ty) ? (size_t)S * sb : ring_bytes(nx, ty);
+  const int per_sm = (2 * (smem + 1024) <= kSmemPerSM && 2 * nt <= 2048) ? 2 : 1;
+  const int uy = (ny + ty - 1) / ty;
+  const long long npairs = (long long)uy * nz;
+  long long nu = units > 0 ? units : (long long)kSMs * per_sm;
+  if (nu > npairs) nu = npairs;
+  const long long ncell = (long long)nx * ny * nz;
+  long long nf = ncell / 4096;
+  if (nf > kSMs * 4) nf = kSMs * 4;
+  if (nf < 1) nf = 1;
+  L->ty = ty;
+  L->uy = uy;
+  L->stages = S;
+  L->threads = nt;
+  L->nunits = (int)nu;
+  L->nunits_f = (int)nf;
+  L->npairs = npairs;
+  L->smem = smem;
+  return true;
 }
 
 }  // namespace vdp

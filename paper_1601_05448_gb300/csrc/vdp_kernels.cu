@@ -196,8 +196,9 @@ __device__ __forceinline__ void for_each_segment(const InstDesc& I, int unit, F&
 
 __device__ __forceinline__ void store_partials(double (&v)[kSlots], double* part, int nunits,
                                                int unit) {
-  __shared__ double red[kThreads / 32][kSlots];
+  __shared__ double red[kMaxThreads / 32][kSlots];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < kSlots; ++k) v[k] = warp_sum(v[k]);
   __syncthreads();  // red[] may still be read by a previous use
@@ -209,7 +210,7 @@ __device__ __forceinline__ void store_partials(double (&v)[kSlots], double* part
   if (warp == 0) {
 #pragma unroll
     for (int k = 0; k < kSlots; ++k) {
-      double s = lane < kThreads / 32 ? red[lane][k] : 0.0;
+      double s = lane < nwarps ? red[lane][k] : 0.0;
       s = warp_sum(s);
       if (lane == 0) part[k * nunits + unit] = s;
     }
@@ -347,86 +348,50 @@ __device__ void transition(const InstDesc& I, InstState* st, int phase, const do
 }
 
 // ---- flat (element-wise) sweeps ------------------------------------------------------------------
-// A unit's cells are the contiguous blocks (ty rows x nx) of its (row tile, plane) pairs.  The
-// flat sweeps walk them as one index space of 16-byte vectors, four vectors per thread in
-// flight.
+// Run by k_flat, a kernel without dynamic shared memory (full occupancy).  Flat unit u of
+// nunits_f covers the contiguous cells [flat_begin(u), flat_begin(u + 1)), multiples of 8, so
+// every access is a 16-byte vector; each thread keeps four vectors in flight and several
+// independent partial sums.
 
-struct FlatRange {
-  long long pair0;   // first pair of the unit
-  long long npairs;  // pairs in the unit
-};
-
-__device__ __forceinline__ FlatRange unit_pairs(const InstDesc& I, int unit) {
-  FlatRange r;
-  r.pair0 = (long long)unit * I.npairs / I.nunits;
-  r.npairs = (long long)(unit + 1) * I.npairs / I.nunits - r.pair0;
-  return r;
-}
-
-// element offset of vector `v` (width V) of the unit; vpp = vectors per (full) pair
-__device__ __forceinline__ long long flat_offset(const InstDesc& I, const FlatRange& r, long long v,
-                                                 int V, int* ok) {
-  const int vrow = I.nx / V;
-  const long long vpp = (long long)I.ty * vrow;
-  const long long pi = v / vpp;
-  const int w = (int)(v - pi * vpp);
-  const long long pair = r.pair0 + pi;
-  const int tile = (int)(pair / I.nz);
-  const int z = (int)(pair - (long long)tile * I.nz);
-  const int row = tile * I.ty + w / vrow;
-  *ok = row < I.ny;  // the last row tile may be short
-  return ((long long)z * I.ny + row) * I.nx + (long long)(w % vrow) * V;
+__device__ __forceinline__ long long flat_begin(const InstDesc& I, int u) {
+  return ((long long)u * (I.ncell / 8) / I.nunits_f) * 8;
 }
 
 // <f>, ||f||^2; p := 0 unless p is the caller's initial guess.
-__device__ void sweep_meanf(const InstDesc& I, const InstState* st, int unit, double (&acc)[kSlots]) {
-  const FlatRange r = unit_pairs(I, unit);
-  const long long nv = r.npairs * (long long)I.ty * (I.nx / 2);
+__device__ void sweep_meanf(const InstDesc& I, const InstState* st, long long c0, long long c1,
+                            double (&acc)[kSlots]) {
   const bool zero_p = !st->use_guess;
-  double s = 0.0, s2 = 0.0;
-  for (long long v = threadIdx.x; v < nv; v += kThreads) {
-    int ok;
-    const long long c = flat_offset(I, r, v, 2, &ok);
-    if (!ok) continue;
+  double s[2] = {0.0, 0.0}, s2[2] = {0.0, 0.0};
+  for (long long c = c0 + 2 * threadIdx.x; c < c1; c += 2 * blockDim.x) {
     const double2 fv = __ldg(reinterpret_cast<const double2*>(I.rhs + c));
-    s += fv.x;
-    s += fv.y;
-    s2 = fma(fv.x, fv.x, s2);
-    s2 = fma(fv.y, fv.y, s2);
+    s[0] += fv.x;
+    s[1] += fv.y;
+    s2[0] = fma(fv.x, fv.x, s2[0]);
+    s2[1] = fma(fv.y, fv.y, s2[1]);
     if (zero_p) *reinterpret_cast<double2*>(I.p + c) = make_double2(0.0, 0.0);
   }
-  acc[0] = s;
-  acc[1] = s2;
+  acc[0] = s[0] + s[1];
+  acc[1] = s2[0] + s2[1];
 }
 
 // p -= D^-1/2 x (x in the inner type)
 template <class T>
-__device__ void sweep_correct(const InstDesc& I, int unit) {
-  const FlatRange r = unit_pairs(I, unit);
-  const long long nv = r.npairs * (long long)I.ty * (I.nx / 2);
+__device__ void sweep_correct(const InstDesc& I, long long c0, long long c1) {
   const T* x = static_cast<const T*>(I.x);
-  for (long long v = threadIdx.x; v < nv; v += kThreads) {
-    int ok;
-    const long long c = flat_offset(I, r, v, 2, &ok);
-    if (!ok) continue;
-    const double2 s = __ldg(reinterpret_cast<const double2*>(I.sinv + c));
+  for (long long c = c0 + 2 * threadIdx.x; c < c1; c += 2 * blockDim.x) {
+    const double2 sv = __ldg(reinterpret_cast<const double2*>(I.sinv + c));
     double2 p = *reinterpret_cast<double2*>(I.p + c);
-    p.x = fma(-s.x, (double)x[c], p.x);
-    p.y = fma(-s.y, (double)x[c + 1], p.y);
+    p.x = fma(-sv.x, (double)x[c], p.x);
+    p.y = fma(-sv.y, (double)x[c + 1], p.y);
     *reinterpret_cast<double2*>(I.p + c) = p;
   }
 }
 
 // p -= <p>   (or p = 0 when the right-hand side was constant)
-__device__ void sweep_final(const InstDesc& I, const InstState* st, int unit) {
-  const FlatRange r = unit_pairs(I, unit);
-  const long long nv = r.npairs * (long long)I.ty * (I.nx / 2);
+__device__ void sweep_final(const InstDesc& I, const InstState* st, long long c0, long long c1) {
   const double mp = st->sum_p / (double)I.ncell;
   const bool zero = st->zero_sol != 0;
-  for (long long v = threadIdx.x; v < nv; v += kThreads) {
-    int ok;
-    const long long c = flat_offset(I, r, v, 2, &ok);
-    if (!ok) continue;
+  for (long long c = c0 + 2 * threadIdx.x; c < c1; c += 2 * blockDim.x) {
     double2 p = *reinterpret_cast<double2*>(I.p + c);
     p = zero ? make_double2(0.0, 0.0) : make_double2(p.x - mp, p.y - mp);
     *reinterpret_cast<double2*>(I.p + c) = p;
@@ -435,50 +400,50 @@ __device__ void sweep_final(const InstDesc& I, const InstState* st, int unit) {
 
 // x += alpha d (x = alpha d on the first inner iteration); rt -= alpha q; <rt, rt>
 template <class T>
-__device__ void sweep_update(const InstDesc& I, const InstState* st, int unit,
+__device__ void sweep_update(const InstDesc& I, const InstState* st, long long c0, long long c1,
                              double (&acc)[kSlots]) {
   constexpr int V = VecW<T>::V;
   constexpr int U = 4;  // vectors per thread per round
-  const FlatRange r = unit_pairs(I, unit);
-  const long long nv = r.npairs * (long long)I.ty * (I.nx / V);
   const T alpha = (T)st->alpha;
   const bool first = st->inner_iters == 0;
   const T* d = static_cast<const T*>(st->parity ? I.d0 : I.d1);  // written by the last stencil
   const T* q = static_cast<const T*>(I.q);
   T* x = static_cast<T*>(I.x);
   T* rt = static_cast<T*>(I.r);
-  T s = 0;
-  for (long long v0 = threadIdx.x; v0 < nv; v0 += (long long)U * kThreads) {
-    long long c[U];
-    int ok[U];
+  T s[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) s[u] = 0;
+  const long long step = (long long)V * blockDim.x;
+  for (long long cb = c0 + (long long)V * threadIdx.x; cb < c1; cb += U * step) {
     T dv[U][V], qv[U][V], xv[U][V], rv[U][V];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const long long v = v0 + (long long)u * kThreads;
-      ok[u] = 0;
-      c[u] = 0;
-      if (v < nv) c[u] = flat_offset(I, r, v, V, &ok[u]);
-      if (ok[u]) {
-        VecIO<T, V>::ld(d + c[u], dv[u]);
-        VecIO<T, V>::ld(q + c[u], qv[u]);
-        VecIO<T, V>::ld(rt + c[u], rv[u]);
-        if (!first) VecIO<T, V>::ld(x + c[u], xv[u]);
+      const long long c = cb + u * step;
+      if (c < c1) {
+        VecIO<T, V>::ld(d + c, dv[u]);
+        VecIO<T, V>::ld(q + c, qv[u]);
+        VecIO<T, V>::ld(rt + c, rv[u]);
+        if (!first) VecIO<T, V>::ld(x + c, xv[u]);
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (!ok[u]) continue;
+      const long long c = cb + u * step;
+      if (c >= c1) continue;
 #pragma unroll
       for (int k = 0; k < V; ++k) {
         xv[u][k] = fma(alpha, dv[u][k], first ? (T)0 : xv[u][k]);
         rv[u][k] = fma(-alpha, qv[u][k], rv[u][k]);
-        s = fma(rv[u][k], rv[u][k], s);
+        s[u] = fma(rv[u][k], rv[u][k], s[u]);
       }
-      VecIO<T, V>::st(x + c[u], xv[u]);
-      VecIO<T, V>::st(rt + c[u], rv[u]);
+      VecIO<T, V>::st(x + c, xv[u]);
+      VecIO<T, V>::st(rt + c, rv[u]);
     }
   }
-  acc[0] = (double)s;
+  double tot = 0.0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) tot += (double)s[u];
+  acc[0] = tot;
 }
 
 // ---- the stencil sweep: TMA-fed z march -----------------------------------------------------------
@@ -552,7 +517,7 @@ __device__ __forceinline__ void issue_stage(const InstDesc& I, const Seg& sg, in
 template <class T>
 __device__ __forceinline__ void form_direction(T* R, const T* O, int cells, T beta) {
   constexpr int V = VecW<T>::V;
-  for (int v = threadIdx.x; v < cells / V; v += kThreads) {
+  for (int v = threadIdx.x; v < cells / V; v += blockDim.x) {
     T a[V], b[V];
     VecIO<T, V>::ld(R + v * V, a);
     VecIO<T, V>::ld(O + v * V, b);
@@ -595,7 +560,9 @@ __device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, double
   }
   __syncthreads();
   uint32_t parity = 0;  // bit s: phase parity of the next completion of stage s
-  T sum = 0;
+  T sum[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) sum[k] = 0;
 
   auto stage_ptr = [&](int jj) { return smem + (size_t)(jj % S) * sbytes; };
   auto wait_stage = [&](int jj) {
@@ -641,7 +608,7 @@ __device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, double
       const BT* Bz = reinterpret_cast<const BT*>(bc + L.bz_off());
       const BT* Bd = reinterpret_cast<const BT*>(bc + L.bd_off());
       const BT* Bzp = reinterpret_cast<const BT*>(bp + L.bz_off());
-      for (int v = threadIdx.x; v < own; v += kThreads) {
+      for (int v = threadIdx.x; v < own; v += blockDim.x) {
         const int row = v / vrow;               // 0 .. ty-1
         const int x0 = (v - row * vrow) * V;
         const int o = (row + 1) * nx;           // ring row of this tile row
@@ -678,7 +645,7 @@ __device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, double
           a = fma(-bz[k2], dzm[k2], a);
           a = fma(-bzp[k2], dzp[k2], a);
           qv[k2] = a;
-          sum = fma(dc[k2], a, sum);
+          sum[k2] = fma(dc[k2], a, sum[k2]);
         }
         const long long g = ((long long)z * I.ny + sg.y0 + row) * nx + x0;
         VecIO<T, V>::st(dnew + g, dc);
@@ -693,7 +660,10 @@ __device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, double
     }
   });
   if (timed_out && threadIdx.x == 0) atomicExch(&st->fault, 1);
-  acc[0] = (double)sum;
+  double tot = 0.0;
+#pragma unroll
+  for (int k = 0; k < V; ++k) tot += (double)sum[k];
+  acc[0] = tot;
 }
 
 // ---- the FP64 residual sweep (a few times per solve): z march through a three-plane ring ---------
@@ -704,7 +674,7 @@ __device__ __forceinline__ void fill_p(const InstDesc& I, const Seg& sg, double*
   const int cells = (sg.ty + 2) * nx;
   const long long pz = (long long)zg * nx * I.ny;
   double* dst = ring + slot * stride;
-  for (int m = threadIdx.x; m < cells; m += kThreads) {
+  for (int m = threadIdx.x; m < cells; m += blockDim.x) {
     const int ry = m / nx, x = m - ry * nx;
     dst[m] = I.p[pz + (long long)ring_gy(ry, sg.y0, I.ny) * nx + x];
   }
@@ -738,7 +708,7 @@ __device__ void sweep_res64(const InstDesc& I, const InstState* st, int unit,
       const double* Rm = ring + sm * stride;
       const double* Rc = ring + sc * stride;
       const double* Rp = ring + sp * stride;
-      for (int m = threadIdx.x; m < own; m += kThreads) {
+      for (int m = threadIdx.x; m < own; m += blockDim.x) {
         const int ry = m / nx + 1, x = m - (ry - 1) * nx;
         const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
         const int gy = sg.y0 + ry - 1;
@@ -770,33 +740,31 @@ __device__ void sweep_res64(const InstDesc& I, const InstState* st, int unit,
   acc[3] = a3;
 }
 
-// ---- the step kernel --------------------------------------------------------------------------
+// ---- the step kernels ----------------------------------------------------------------------------
+// One sweep per launch for every instance of the batch whose phase is of the kernel's kind: the
+// stencil kind (RES64, STENCIL: shared-memory z march, stencil units) or the flat kind (MEANF,
+// UPDATE, CORRECT, FINAL: streaming, flat units).  The host alternates the two kinds; a launch
+// whose instances are all in the other kind's phase exits at once.
 
-template <class T, class BT>
-__global__ void __launch_bounds__(kThreads) k_step(const InstDesc* __restrict__ insts,
-                                                   const UnitRef* __restrict__ units) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const UnitRef ur = units[blockIdx.x];
-  const InstDesc& I = insts[ur.inst];
-  InstState* st = I.st;
-  const int phase = st->phase;
-  if (phase >= PH_DONE) return;
-  double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
+// partial-sum slots each phase produces
+__device__ __forceinline__ int phase_slots(int phase) {
   switch (phase) {
-    case PH_MEANF: sweep_meanf(I, st, ur.unit, acc); break;
-    case PH_RES64: sweep_res64<T>(I, st, ur.unit, acc, reinterpret_cast<double*>(smem_raw)); break;
-    case PH_STENCIL: sweep_stencil<T, BT>(I, st, ur.unit, acc, smem_raw); break;
-    case PH_UPDATE: sweep_update<T>(I, st, ur.unit, acc); break;
-    case PH_CORRECT: sweep_correct<T>(I, ur.unit); break;
-    case PH_FINAL: sweep_final(I, st, ur.unit); break;
-    default: break;
+    case PH_MEANF: return 2;
+    case PH_RES64: return 4;
+    case PH_STENCIL:
+    case PH_UPDATE: return 1;
+    default: return 0;
   }
-  store_partials(acc, I.part, I.nunits, ur.unit);
-  if (arrive_last(I.ticket, I.nunits)) {
+}
+
+__device__ __forceinline__ void finish_sweep(const InstDesc& I, InstState* st, int phase, int nunits,
+                                             int unit, double (&acc)[kSlots]) {
+  store_partials(acc, I.part, nunits, unit);
+  if (arrive_last(I.ticket, nunits)) {
     if (threadIdx.x < 32) {
-      double S[kSlots];
-#pragma unroll
-      for (int k = 0; k < kSlots; ++k) S[k] = sum_slot(I.part + k * I.nunits, I.nunits);
+      double S[kSlots] = {0.0, 0.0, 0.0, 0.0};
+      const int ns = phase_slots(phase);
+      for (int k = 0; k < ns; ++k) S[k] = sum_slot(I.part + k * nunits, nunits);
       if (threadIdx.x == 0) {
         transition(I, st, phase, S);
         *I.ticket = 0u;
@@ -804,6 +772,42 @@ __global__ void __launch_bounds__(kThreads) k_step(const InstDesc* __restrict__ 
       }
     }
   }
+}
+
+template <class T, class BT>
+__global__ void __launch_bounds__(kMaxThreads) k_stencil(const InstDesc* __restrict__ insts,
+                                                         const UnitRef* __restrict__ units) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const UnitRef ur = units[blockIdx.x];
+  const InstDesc& I = insts[ur.inst];
+  InstState* st = I.st;
+  const int phase = st->phase;
+  if (phase != PH_RES64 && phase != PH_STENCIL) return;
+  double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
+  if (phase == PH_RES64)
+    sweep_res64<T>(I, st, ur.unit, acc, reinterpret_cast<double*>(smem_raw));
+  else
+    sweep_stencil<T, BT>(I, st, ur.unit, acc, smem_raw);
+  finish_sweep(I, st, phase, I.nunits, ur.unit, acc);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kFlatThreads) k_flat(const InstDesc* __restrict__ insts,
+                                                       const UnitRef* __restrict__ units) {
+  const UnitRef ur = units[blockIdx.x];
+  const InstDesc& I = insts[ur.inst];
+  InstState* st = I.st;
+  const int phase = st->phase;
+  if (phase != PH_MEANF && phase != PH_UPDATE && phase != PH_CORRECT && phase != PH_FINAL) return;
+  const long long c0 = flat_begin(I, ur.unit), c1 = flat_begin(I, ur.unit + 1);
+  double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
+  switch (phase) {
+    case PH_MEANF: sweep_meanf(I, st, c0, c1, acc); break;
+    case PH_UPDATE: sweep_update<T>(I, st, c0, c1, acc); break;
+    case PH_CORRECT: sweep_correct<T>(I, c0, c1); break;
+    default: sweep_final(I, st, c0, c1); break;
+  }
+  finish_sweep(I, st, phase, I.nunits_f, ur.unit, acc);
 }
 
 // Per-solve initialisation of one instance's state.
@@ -1027,25 +1031,34 @@ cudaError_t launch_init(InstDesc* desc, const double* rhs, double* p, double tol
   return cudaGetLastError();
 }
 
-static void* step_fn(int prec) {
-  if (prec == PREC_FP64) return (void*)k_step<double, double>;
-  if (prec == PREC_MIXED) return (void*)k_step<float, float>;
-  return (void*)k_step<float, __nv_bfloat16>;
+static void* stencil_fn(int prec) {
+  if (prec == PREC_FP64) return (void*)k_stencil<double, double>;
+  if (prec == PREC_MIXED) return (void*)k_stencil<float, float>;
+  return (void*)k_stencil<float, __nv_bfloat16>;
 }
 
 cudaError_t prepare_step(int prec, size_t smem_bytes) {
-  return cudaFuncSetAttribute(step_fn(prec), cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(stencil_fn(prec), cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_bytes);
 }
 
-cudaError_t launch_step(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
-                        size_t smem_bytes, cudaStream_t s) {
+cudaError_t launch_stencil(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
+                           int threads, size_t smem_bytes, cudaStream_t s) {
   if (prec == PREC_FP64)
-    k_step<double, double><<<nunits, kThreads, smem_bytes, s>>>(desc, units);
+    k_stencil<double, double><<<nunits, threads, smem_bytes, s>>>(desc, units);
   else if (prec == PREC_MIXED)
-    k_step<float, float><<<nunits, kThreads, smem_bytes, s>>>(desc, units);
+    k_stencil<float, float><<<nunits, threads, smem_bytes, s>>>(desc, units);
   else
-    k_step<float, __nv_bfloat16><<<nunits, kThreads, smem_bytes, s>>>(desc, units);
+    k_stencil<float, __nv_bfloat16><<<nunits, threads, smem_bytes, s>>>(desc, units);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flat(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
+                        cudaStream_t s) {
+  if (prec == PREC_FP64)
+    k_flat<double><<<nunits, kFlatThreads, 0, s>>>(desc, units);
+  else
+    k_flat<float><<<nunits, kFlatThreads, 0, s>>>(desc, units);
   return cudaGetLastError();
 }
 

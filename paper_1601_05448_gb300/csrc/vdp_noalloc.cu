@@ -27,7 +27,7 @@ using namespace vdp;
 namespace {
 
 constexpr long long kMaxCells = VDP_NOALLOC_MAX_CELLS;
-constexpr int kMaxUnits = 152;
+constexpr int kMaxUnits = 320;  // stencil units (at most 2 per SM) plus flat units
 constexpr size_t kAlign = 256;
 
 constexpr size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
@@ -127,32 +127,23 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
   NA_CK(launch_scaled(precision, bx, by, bz, sinv, nx, ny, nz, sx, sy, sz, sd, s));
 
   // the default unit layout of vdp_solve
-  const int ts = precision == VDP_FP64 ? 8 : 4;
-  const int bs = precision == VDP_FP64 ? 8 : (precision == VDP_MIXED ? 4 : 2);
-  const bool diag = precision == VDP_MIXED_BF16;
-  const size_t budget = 225 * 1024;
-  int ty = std::max(1, std::min(ny, 1024 / nx));
-  while (ty > 1 && 4 * stage_bytes(nx, ty, ts, bs, diag) > budget) --ty;
-  const size_t sb = stage_bytes(nx, ty, ts, bs, diag);
-  const int fit = (int)(budget / sb);
-  if (fit < 4) return VDP_EINVAL;
-  const int stages = std::min(fit, 6);
-  const int uy = (ny + ty - 1) / ty;
-  const long long npairs = (long long)uy * nz;
-  const int nunits = (int)std::min<long long>(kMaxUnits, npairs);
-  const size_t smem = std::max((size_t)stages * sb, ring_bytes(nx, ty));
+  Layout lay;
+  if (!plan_layout(nx, ny, nz, precision, 0, 0, 0, 0, &lay)) return VDP_EINVAL;
+  const int nunits = lay.nunits, nunits_f = lay.nunits_f;
 
   UnitRef hu[kMaxUnits];
   for (int i = 0; i < nunits; ++i) hu[i] = UnitRef{0, i};
+  for (int i = 0; i < nunits_f; ++i) hu[nunits + i] = UnitRef{0, i};
   InstDesc d{};
   d.nx = nx;
   d.ny = ny;
   d.nz = nz;
-  d.ty = ty;
-  d.uy = uy;
+  d.ty = lay.ty;
+  d.uy = lay.uy;
   d.nunits = nunits;
-  d.stages = stages;
-  d.npairs = npairs;
+  d.nunits_f = nunits_f;
+  d.stages = lay.stages;
+  d.npairs = lay.npairs;
   d.ncell = n;
   d.bx = bx;
   d.by = by;
@@ -171,20 +162,23 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
   d.ticket = ticket;
   d.st = state;
   // pageable host sources: these copies complete before the calls return
-  NA_CK(cudaMemcpyAsync(units, hu, sizeof(UnitRef) * nunits, cudaMemcpyHostToDevice, s));
+  NA_CK(cudaMemcpyAsync(units, hu, sizeof(UnitRef) * (nunits + nunits_f), cudaMemcpyHostToDevice, s));
   NA_CK(cudaMemcpyAsync(desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
-  NA_CK(prepare_step(precision, smem));
+  NA_CK(prepare_step(precision, lay.smem));
   // the per-solve state and the ticket are reset on the device by the init kernel
   const int max_iter = 20000;
   NA_CK(launch_init(desc, rhs, p, tol, 1e-4, max_iter, max_iter, 0, precision, s));
 
-  const int m = 32;
+  const int m = 16;  // (stencil, flat) launch pairs per convergence check
   const long long max_rounds = (2LL * max_iter + 4096 + m - 1) / m;
   InstState h{};
   bool done = false;
   long long rounds = 0;
   while (!done && rounds < max_rounds) {
-    for (int i = 0; i < m; ++i) NA_CK(launch_step(precision, desc, units, nunits, smem, s));
+    for (int i = 0; i < m; ++i) {
+      NA_CK(launch_stencil(precision, desc, units, nunits, lay.threads, lay.smem, s));
+      NA_CK(launch_flat(precision, desc, units + nunits, nunits_f, s));
+    }
     ++rounds;
     NA_CK(cudaMemcpyAsync(&h, state, sizeof(h), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
@@ -199,7 +193,7 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
     stats->rhs_mean = h.mu_f;
     stats->ms = 0.0;
     stats->sweeps = h.sweeps;
-    stats->launches = (int)(1 + rounds * m);
+    stats->launches = (int)(1 + rounds * 2 * m);
   }
   return status;
 }
