@@ -73,10 +73,12 @@ typedef struct {
   int cheb_degree;     /* polynomial degree for VDP_PRECOND_CHEB (default 4) */
   int use_guess;       /* 1: p on entry to vdp_solve is the initial guess; 0: start from p = 0 */
   void *stream;        /* cudaStream_t for all work of this context (default NULL) */
+  int stencil;         /* stencil sweep: 0 = direct register march (default), 1 = TMA-staged
+                          shared-memory pipeline */
   int tile_y;          /* rows per row tile of a work unit (0 = automatic) */
   int units;           /* work units (thread blocks) per sweep (0 = automatic) */
   int stages;          /* shared-memory pipeline stages of the stencil sweep, 4..8 (0 = auto) */
-  int threads;         /* threads per stencil work unit, 64..512, multiple of 32 (0 = auto) */
+  int threads;         /* threads per stencil work unit, 128..512, multiple of 32 (0 = auto) */
   int steps_per_sync;  /* (stencil, flat) launch pairs per host convergence check (0 = auto) */
 } vdp_opts;
 
@@ -184,7 +186,7 @@ int vdp_apply(vdp_ctx *ctx, const double *p, double *out);
  * serialise them.
  */
 #define VDP_NOALLOC_MAX_CELLS 65536
-#define VDP_NOALLOC_SCRATCH_BYTES 6436352
+#define VDP_NOALLOC_SCRATCH_BYTES 6752000
 int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double *rho, const double *rhs,
                       double *p, double tol, int precision, void *stream, vdp_stats *stats);
 

@@ -41,7 +41,7 @@ class VdpError(RuntimeError):
 class vdp_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("precond", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("use_guess", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("tile_y", ctypes.c_int), ("units", ctypes.c_int),
+                ("stream", ctypes.c_void_p), ("stencil", ctypes.c_int), ("tile_y", ctypes.c_int), ("units", ctypes.c_int),
                 ("stages", ctypes.c_int), ("threads", ctypes.c_int), ("steps_per_sync", ctypes.c_int)]
 
 

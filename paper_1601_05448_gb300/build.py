@@ -38,6 +38,8 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    """Compile if stale; VDP_NVCC_EXTRA (environment) adds nvcc flags, e.g. -DVDP_DIRECT_MIN_BLOCKS=2."""
+    extra = list(extra) + os.environ.get("VDP_NVCC_EXTRA", "").split()
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)

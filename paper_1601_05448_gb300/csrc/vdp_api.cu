@@ -99,6 +99,7 @@ void vdp_default_options(vdp_opts* o) {
   o->use_guess = 0;
   o->stream = nullptr;
   o->tile_y = 0;
+  o->stencil = 0;
   o->units = 0;
   o->stages = 0;
   o->threads = 0;
@@ -151,8 +152,8 @@ void free_ctx(vdp_ctx* c) {
 }
 
 int choose_layout(const vdp_ctx* c, int prec, Layout* out) {
-  return plan_layout(c->nx, c->ny, c->nz, prec, c->opts.tile_y, c->opts.units, c->opts.stages,
-                     c->opts.threads, out)
+  return plan_layout(c->nx, c->ny, c->nz, prec, c->opts.stencil, c->opts.tile_y, c->opts.units,
+                     c->opts.stages, c->opts.threads, out)
              ? VDP_OK
              : VDP_EINVAL;
 }
@@ -176,7 +177,8 @@ int configure_layout(vdp_ctx* c, int prec) {
   d.nunits = lay.nunits;
   d.nunits_f = lay.nunits_f;
   d.stages = lay.stages;
-  d.npairs = lay.npairs;
+  d.zc = lay.zc;
+  d.mode = lay.mode;
   d.ncell = c->n;
   d.bx = c->bx;
   d.by = c->by;
@@ -196,7 +198,7 @@ int configure_layout(vdp_ctx* c, int prec) {
   d.st = c->st;
   VDP_CK(cudaMemcpyAsync(c->desc, &d, sizeof(d), cudaMemcpyHostToDevice, c->stream));
   VDP_CK(cudaStreamSynchronize(c->stream));
-  VDP_CK(prepare_step(prec, lay.smem));
+  VDP_CK(prepare_step(prec, lay.mode, lay.smem));
   if (c->gexec) {
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
@@ -221,8 +223,8 @@ int ensure_graph(vdp_ctx* c, int prec) {
   cudaGraph_t g = nullptr;
   VDP_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
   for (int i = 0; i < m; ++i) {
-    cudaError_t e = launch_stencil(prec, c->desc, c->units, c->lay.nunits, c->lay.threads,
-                                   c->lay.smem, c->cap);
+    cudaError_t e = launch_stencil(prec, c->lay.mode, c->desc, c->units, c->lay.nunits,
+                                   c->lay.threads, c->lay.smem, c->cap);
     if (e == cudaSuccess)
       e = launch_flat(prec, c->desc, c->units + c->lay.nunits, c->lay.nunits_f, c->cap);
     if (e != cudaSuccess) {
@@ -313,7 +315,8 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
   if (o->precision < VDP_FP64 || o->precision > VDP_MIXED_BF16) return VDP_EINVAL;
   if (o->max_iter < 1 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return VDP_EINVAL;
   if (o->precond != VDP_PRECOND_JACOBI && o->precond != VDP_PRECOND_CHEB) return VDP_EINVAL;
-  if (o->tile_y < 0 || o->units < 0 || o->stages < 0 || o->threads < 0 || o->steps_per_sync < 0)
+  if (o->tile_y < 0 || o->units < 0 || o->stages < 0 || o->threads < 0 || o->steps_per_sync < 0 ||
+      o->stencil < 0 || o->stencil > 1)
     return VDP_EINVAL;
   if (o->units > 152 * 16 || o->stages > kMaxStages || (o->stages > 0 && o->stages < 4))
     return VDP_EINVAL;

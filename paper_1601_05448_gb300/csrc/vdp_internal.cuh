@@ -34,6 +34,7 @@ enum Prec : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_MIXED_BF16 = 2 };
 constexpr int kSlots = 4;          // partial-sum slots per unit
 constexpr int kMaxThreads = 512;   // threads per stencil work unit (CTA), at most
 constexpr int kFlatThreads = 256;  // threads per flat work unit
+constexpr int kDirectThreads = 256;  // threads per direct-stencil work unit, at most
 constexpr int kMaxStages = 8;      // shared-memory pipeline stages of the stencil sweep
 
 // Mutable per-instance solver state (device memory).
@@ -69,8 +70,9 @@ struct InstState {
   double rel_res;      // FP64 relative residual at the last RES64
 };
 
-// Constant per-instance description (device memory).  Stencil sweeps split the (row tile, plane)
-// pairs into `nunits` units; flat sweeps split the cells into `nunits_f` contiguous ranges.
+// Constant per-instance description (device memory).  Stencil sweeps split the grid into
+// nunits = uy * zc units (row tile x z chunk); flat sweeps split the cells into `nunits_f`
+// contiguous ranges.
 struct InstDesc {
   int nx, ny, nz;
   int ty;              // rows per row tile
@@ -78,7 +80,8 @@ struct InstDesc {
   int nunits;          // stencil work units (CTAs) per sweep
   int stages;          // shared-memory pipeline stages of the stencil sweep
   int nunits_f;        // flat work units per sweep
-  long long npairs;    // uy * nz (row tile, plane) pairs
+  int zc;              // z chunks: stencil unit u = (row tile u % uy, z chunk u / uy)
+  int mode;            // stencil sweep: 0 = direct register march, 1 = TMA-staged pipeline
   long long ncell;
   const double* rhs;   // caller's f (set per solve)
   double* p;           // caller's p (set per solve)
@@ -126,13 +129,14 @@ constexpr size_t kSmemPerSM = 227 * 1024; // shared memory per SM available to C
 constexpr size_t kSmemBudget = 225 * 1024;
 
 struct Layout {
+  int mode;            // stencil sweep variant (0 direct, 1 TMA pipeline)
   int ty;              // rows per row tile
   int uy;              // row tiles
   int stages;          // stencil pipeline stages
   int threads;         // stencil threads per unit
-  int nunits;          // stencil units
+  int zc;              // z chunks
+  int nunits;          // stencil units = uy * zc
   int nunits_f;        // flat units
-  long long npairs;
   size_t smem;         // dynamic shared memory of the stencil kernel
 };
 
@@ -143,49 +147,82 @@ inline void prec_sizes(int prec, int* ts, int* bs, bool* diag) {
   *diag = prec == PREC_MIXED_BF16;
 }
 
-// Unit layout for an nx x ny x nz grid in precision `prec`; zero arguments pick the defaults:
-// FP64 uses 512-thread stencil units with about 2048 cells per plane, FP32/BF16 256-thread units
-// with about 1024; the row tile shrinks until four pipeline stages fit; stages default to what
-// fits (at most 6), or to 4 when that lets two units share an SM; one or two stencil units per SM
-// (as shared memory allows), and flat units of about 4096+ cells (at most 4 per SM).
-// Returns false when the rows are too long for a four-stage pipeline.
-inline bool plan_layout(int nx, int ny, int nz, int prec, int tile_y, int units, int stages,
-                        int threads, Layout* L) {
+// Unit layout for an nx x ny x nz grid in precision `prec`; zero arguments pick the defaults.
+// mode 0 (direct, default): units of up to 256 threads (whole rows, whole warps), one thread per
+// 16-byte vector of a row tile of threads * V / nx rows (V = 4 FP32, 2 FP64), about 12 units per
+// SM worth of z chunks.
+// mode 1 (TMA pipeline): FP64 512-thread units with about 2048 cells per plane, FP32/BF16 256
+// threads with about 1024; the row tile shrinks until four pipeline stages fit; stages default to
+// what fits (at most 6), or to 4 when that lets two units share an SM; about four waves.
+// Both: stencil units = row tiles x z chunks (chunk-major); flat units of about 4096+ cells (at
+// most 4 per SM).  In mode 1 the dynamic shared memory also covers the FP64 residual sweep's ring.
+// Returns false when the configuration cannot run (rows too long, bad counts).
+inline bool plan_layout(int nx, int ny, int nz, int prec, int mode, int tile_y, int units,
+                        int stages, int threads, Layout* L) {
   int ts, bs;
   bool diag;
   prec_sizes(prec, &ts, &bs, &diag);
-  const int nt = threads > 0 ? threads : (prec == PREC_FP64 ? 512 : 256);
-  if (nt < 64 || nt > kMaxThreads || nt % 32) return false;
-  const int cells = prec == PREC_FP64 ? 2048 : 1024;
-  int ty = tile_y > 0 ? tile_y : (cells / nx > 1 ? cells / nx : 1);
-  if (ty > ny) ty = ny;
-  while (ty > 1 && 4 * stage_bytes(nx, ty, ts, bs, diag) > kSmemBudget) --ty;
-  const size_t sb = stage_bytes(nx, ty, ts, bs, diag);
-  const int fit = (int)(kSmemBudget / sb);
-  if (fit < 4) return false;
-  int S = stages;
-  if (S <= 0) {
-    S = fit < 6 ? fit : 6;
-    if (4 * sb + 1024 <= kSmemPerSM / 2 && 2 * nt <= 2048) S = 4;  // two units per SM
+  const int V = 16 / ts;
+  int nt, ty, S = 0, per_sm;
+  size_t smem;
+  if (mode == 0) {
+    // largest block of whole rows that is a whole number of warps: a multiple of
+    // lcm(nx / V, 32) threads, at most kDirectThreads
+    const int tpr = nx / V;
+    int g = tpr, b = 32;
+    while (b) {
+      const int t = g % b;
+      g = b;
+      b = t;
+    }
+    const int unit = tpr / g * 32;
+    nt = threads > 0 ? threads : (kDirectThreads / unit) * unit;
+    if (nt < 32 || nt > kDirectThreads || nt % 32 || (nt * V) % nx) return false;
+    ty = nt * V / nx;  // the tile is exactly one vector per thread
+    if (ty < 1) return false;
+    if (tile_y > 0 && tile_y != ty) return false;
+    smem = 0;  // no shared memory: both stencil-kind sweeps march in registers
+    per_sm = 6;
+  } else if (mode == 1) {
+    nt = threads > 0 ? threads : (prec == PREC_FP64 ? 512 : 256);
+    if (nt < 128 || nt > kMaxThreads || nt % 32) return false;  // four warps issue the copies
+    const int cells = prec == PREC_FP64 ? 2048 : 1024;
+    ty = tile_y > 0 ? tile_y : (cells / nx > 1 ? cells / nx : 1);
+    if (ty > ny) ty = ny;
+    while (ty > 1 && 4 * stage_bytes(nx, ty, ts, bs, diag) > kSmemBudget) --ty;
+    const size_t sb = stage_bytes(nx, ty, ts, bs, diag);
+    const int fit = (int)(kSmemBudget / sb);
+    if (fit < 4) return false;
+    S = stages;
+    if (S <= 0) {
+      S = fit < 6 ? fit : 6;
+      if (4 * sb + 1024 <= kSmemPerSM / 2 && 2 * nt <= 2048) S = 4;  // two units per SM
+    }
+    if (S < 4 || S > kMaxStages || S > fit) return false;
+    smem = (size_t)S * sb > ring_bytes(nx, ty) ? (size_t)S * sb : ring_bytes(nx, ty);
+    per_sm = (2 * (smem + 1024) <= kSmemPerSM && 2 * nt <= 2048) ? 2 : 1;
+    per_sm *= 2;  // about four waves of units
+  } else {
+    return false;
   }
-  if (S < 4 || S > kMaxStages || S > fit) return false;
-  const size_t smem = (size_t)S * sb > ring_bytes(nx, ty) ? (size_t)S * sb : ring_bytes(nx, ty);
-  const int per_sm = (2 * (smem + 1024) <= kSmemPerSM && 2 * nt <= 2048) ? 2 : 1;
+  if (ty > ny) ty = ny;
   const int uy = (ny + ty - 1) / ty;
-  const long long npairs = (long long)uy * nz;
-  long long nu = units > 0 ? units : (long long)kSMs * per_sm;
-  if (nu > npairs) nu = npairs;
+  const long long want = units > 0 ? units : 2LL * kSMs * per_sm;
+  long long zc = (want + uy - 1) / uy;
+  if (zc > nz) zc = nz;
+  if (zc < 1) zc = 1;
   const long long ncell = (long long)nx * ny * nz;
   long long nf = ncell / 4096;
   if (nf > kSMs * 4) nf = kSMs * 4;
   if (nf < 1) nf = 1;
+  L->mode = mode;
   L->ty = ty;
   L->uy = uy;
   L->stages = S;
   L->threads = nt;
-  L->nunits = (int)nu;
+  L->zc = (int)zc;
+  L->nunits = (int)(zc * uy);
   L->nunits_f = (int)nf;
-  L->npairs = npairs;
   L->smem = smem;
   return true;
 }

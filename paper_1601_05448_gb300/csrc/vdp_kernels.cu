@@ -76,16 +76,37 @@ template <> struct VecIO<double, 2> {
   }
 };
 
+// the same, through the read-only (non-coherent) load path: only for data no thread of the
+// running kernel writes
+template <class T, int V> struct LdgIO;
+template <> struct LdgIO<float, 4> {
+  static __device__ __forceinline__ void ld(const float* p, float (&o)[4]) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  }
+};
+template <> struct LdgIO<double, 2> {
+  static __device__ __forceinline__ void ld(const double* p, double (&o)[2]) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = t.x; o[1] = t.y;
+  }
+};
 // V coefficients of storage type BT into arithmetic type T
 template <class BT, class T, int V> struct CoefIO;
 template <> struct CoefIO<float, float, 4> {
   static __device__ __forceinline__ void ld(const float* p, float (&o)[4]) {
     VecIO<float, 4>::ld(p, o);
   }
+  static __device__ __forceinline__ void ldg(const float* p, float (&o)[4]) {
+    LdgIO<float, 4>::ld(p, o);
+  }
 };
 template <> struct CoefIO<double, double, 2> {
   static __device__ __forceinline__ void ld(const double* p, double (&o)[2]) {
     VecIO<double, 2>::ld(p, o);
+  }
+  static __device__ __forceinline__ void ldg(const double* p, double (&o)[2]) {
+    LdgIO<double, 2>::ld(p, o);
   }
 };
 template <> struct CoefIO<__nv_bfloat16, float, 4> {
@@ -96,7 +117,19 @@ template <> struct CoefIO<__nv_bfloat16, float, 4> {
     float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
     o[0] = fa.x; o[1] = fa.y; o[2] = fb.x; o[3] = fb.y;
   }
+  static __device__ __forceinline__ void ldg(const __nv_bfloat16* p, float (&o)[4]) {
+    uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    o[0] = __uint_as_float(u.x << 16); o[1] = __uint_as_float(u.x & 0xffff0000u);
+    o[2] = __uint_as_float(u.y << 16); o[3] = __uint_as_float(u.y & 0xffff0000u);
+  }
 };
+
+__device__ __forceinline__ float ldg1(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ldg1(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldg1(const __nv_bfloat16* p) {
+  const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(p));
+  return __uint_as_float((unsigned)u << 16);
+}
 
 __device__ __forceinline__ float ld1(const float* p) { return *p; }
 __device__ __forceinline__ double ld1(const double* p) { return *p; }
@@ -173,43 +206,49 @@ struct Seg {
   int z0, nzs;  // first plane, planes
 };
 
-// Calls fn(seg) for the one or more z runs that make up work unit `unit`.
+// Calls fn(seg) for the z run of work unit `unit`: row tile unit % uy, z chunk unit / uy.  Units
+// that run at the same time share z chunks, so the halo rows one unit reads are the rows its
+// neighbours stream at about the same moment (L2 hits rather than DRAM re-reads).
 template <class F>
 __device__ __forceinline__ void for_each_segment(const InstDesc& I, int unit, F&& fn) {
-  long long b = (long long)unit * I.npairs / I.nunits;
-  const long long e = (long long)(unit + 1) * I.npairs / I.nunits;
-  while (b < e) {
-    const int tile = (int)(b / I.nz);
-    const int z0 = (int)(b - (long long)tile * I.nz);
-    const int nzs = (int)min((long long)(I.nz - z0), e - b);
-    Seg s;
-    s.y0 = tile * I.ty;
-    s.ty = min(I.ty, I.ny - s.y0);
-    s.z0 = z0;
-    s.nzs = nzs;
-    fn(s);
-    b += nzs;
-  }
+  const int tile = unit % I.uy, chunk = unit / I.uy;
+  Seg s;
+  s.y0 = tile * I.ty;
+  s.ty = min(I.ty, I.ny - s.y0);
+  s.z0 = (int)((long long)chunk * I.nz / I.zc);
+  s.nzs = (int)((long long)(chunk + 1) * I.nz / I.zc) - s.z0;
+  if (s.nzs > 0) fn(s);
 }
 
 // ---- reductions: per-unit partial slots, last unit reduces them in a fixed order --------------
 
-__device__ __forceinline__ void store_partials(double (&v)[kSlots], double* part, int nunits,
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block reduction of NS per-thread partials of type A (float partials stay FP32 within a warp;
+// the warp totals are combined in FP64) into slot k of this unit: part[k * nunits + unit].
+// Fixed shuffle tree and fixed warp order: deterministic.
+template <int NS, class A>
+__device__ __forceinline__ void store_partials(const A (&v)[NS], double* part, int nunits,
                                                int unit) {
   __shared__ double red[kMaxThreads / 32][kSlots];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
+  A w[NS];
 #pragma unroll
-  for (int k = 0; k < kSlots; ++k) v[k] = warp_sum(v[k]);
+  for (int k = 0; k < NS; ++k) w[k] = warp_sum(v[k]);
   __syncthreads();  // red[] may still be read by a previous use
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < kSlots; ++k) red[warp][k] = v[k];
+    for (int k = 0; k < NS; ++k) red[warp][k] = (double)w[k];
   }
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
-    for (int k = 0; k < kSlots; ++k) {
+    for (int k = 0; k < NS; ++k) {
       double s = lane < nwarps ? red[lane][k] : 0.0;
       s = warp_sum(s);
       if (lane == 0) part[k * nunits + unit] = s;
@@ -401,9 +440,9 @@ __device__ void sweep_final(const InstDesc& I, const InstState* st, long long c0
 // x += alpha d (x = alpha d on the first inner iteration); rt -= alpha q; <rt, rt>
 template <class T>
 __device__ void sweep_update(const InstDesc& I, const InstState* st, long long c0, long long c1,
-                             double (&acc)[kSlots]) {
+                             T& part) {
   constexpr int V = VecW<T>::V;
-  constexpr int U = 4;  // vectors per thread per round
+  constexpr int U = 2;  // vectors per thread per round
   const T alpha = (T)st->alpha;
   const bool first = st->inner_iters == 0;
   const T* d = static_cast<const T*>(st->parity ? I.d0 : I.d1);  // written by the last stencil
@@ -440,10 +479,10 @@ __device__ void sweep_update(const InstDesc& I, const InstState* st, long long c
       VecIO<T, V>::st(rt + c, rv[u]);
     }
   }
-  double tot = 0.0;
+  T tot = 0;
 #pragma unroll
-  for (int u = 0; u < U; ++u) tot += (double)s[u];
-  acc[0] = tot;
+  for (int u = 0; u < U; ++u) tot += s[u];
+  part = tot;
 }
 
 // ---- the stencil sweep: TMA-fed z march -----------------------------------------------------------
@@ -465,40 +504,43 @@ struct StageLayout {
   __device__ __forceinline__ size_t bd_off() const { return bz_off() + (size_t)ty * nx * sizeof(BT); }
 };
 
-// Issue the bulk copies of plane `j` (j = -1 .. nzs) of segment `sg` into stage buffer `buf`
-// (thread 0 only).  Plane -1 needs only rt / d_old (it supplies d below the segment); plane
-// nzs needs rt / d_old and the z coefficients (its low z face is the high face of the last
-// plane).
+// Issue part `part` (0..3) of the bulk copies of plane `j` (j = -1 .. nzs) of segment `sg` into
+// stage buffer `buf`; lane 0 of warps 0..3 issue one part each, so the four arrive on the stage's
+// mbarrier (count 4) with their own byte counts.  Part 0: rt rows (tile + one halo row above and
+// below); 1: d_old rows (when the direction recurrence needs it); 2: x and y coefficients;
+// 3: z coefficients (+ BF16 diagonal correction).  Plane -1 needs only rt / d_old (it supplies d
+// below the segment); plane nzs needs rt / d_old and the z coefficients (its low z face is the
+// high face of the last plane).
 template <class T, class BT>
-__device__ __forceinline__ void issue_stage(const InstDesc& I, const Seg& sg, int j,
-                                            unsigned char* buf, uint64_t* bar, const T* rt,
-                                            const T* dold, bool use_old, const BT* sx,
-                                            const BT* sy, const BT* sz, const BT* sd) {
+__device__ __forceinline__ void issue_part(int part, const InstDesc& I, const Seg& sg, int j,
+                                           unsigned char* buf, uint64_t* bar, const T* rt,
+                                           const T* dold, bool use_old, const BT* sx,
+                                           const BT* sy, const BT* sz, const BT* sd) {
   const StageLayout<T, BT> L{I.nx, I.ty};
   int zg = sg.z0 + j;
   if (zg < 0) zg += I.nz;
   if (zg >= I.nz) zg -= I.nz;
   const int nx = I.nx;
   const long long plane = (long long)zg * I.ny;
-  const int top = ring_gy(0, sg.y0, I.ny), bot = ring_gy(sg.ty + 1, sg.y0, I.ny);
   const uint32_t rowT = nx * sizeof(T), rowB = nx * sizeof(BT);
-  const bool need_xy = j >= 0 && j < sg.nzs;
-  const bool need_z = j >= 0;
-  uint32_t bytes = (uint32_t)(sg.ty + 2) * rowT * (use_old ? 2 : 1);
-  if (need_xy) bytes += (uint32_t)(2 * sg.ty + 1 + (CoefTraits<BT>::kDiag ? sg.ty : 0)) * rowB;
-  if (need_z) bytes += (uint32_t)sg.ty * rowB;
-  mbar_arrive_expect_tx(bar, bytes);
-  unsigned char* R = buf + L.r_off();
-  bulk_g2s(R, rt + (plane + top) * nx, rowT, bar);
-  bulk_g2s(R + rowT, rt + (plane + sg.y0) * nx, sg.ty * rowT, bar);
-  bulk_g2s(R + (sg.ty + 1) * rowT, rt + (plane + bot) * nx, rowT, bar);
-  if (use_old) {
-    unsigned char* O = buf + L.o_off();
-    bulk_g2s(O, dold + (plane + top) * nx, rowT, bar);
-    bulk_g2s(O + rowT, dold + (plane + sg.y0) * nx, sg.ty * rowT, bar);
-    bulk_g2s(O + (sg.ty + 1) * rowT, dold + (plane + bot) * nx, rowT, bar);
-  }
-  if (need_xy) {
+  if (part <= 1) {
+    const T* src = part == 0 ? rt : dold;
+    if (part == 1 && !use_old) {
+      mbar_arrive_expect_tx(bar, 0);
+      return;
+    }
+    const int top = ring_gy(0, sg.y0, I.ny), bot = ring_gy(sg.ty + 1, sg.y0, I.ny);
+    unsigned char* R = buf + (part == 0 ? L.r_off() : L.o_off());
+    mbar_arrive_expect_tx(bar, (uint32_t)(sg.ty + 2) * rowT);
+    bulk_g2s(R, src + (plane + top) * nx, rowT, bar);
+    bulk_g2s(R + rowT, src + (plane + sg.y0) * nx, sg.ty * rowT, bar);
+    bulk_g2s(R + (sg.ty + 1) * rowT, src + (plane + bot) * nx, rowT, bar);
+  } else if (part == 2) {
+    if (!(j >= 0 && j < sg.nzs)) {
+      mbar_arrive_expect_tx(bar, 0);
+      return;
+    }
+    mbar_arrive_expect_tx(bar, (uint32_t)(2 * sg.ty + 1) * rowB);
     bulk_g2s(buf + L.bx_off(), sx + (plane + sg.y0) * nx, sg.ty * rowB, bar);
     unsigned char* BY = buf + L.by_off();
     if (sg.y0 + sg.ty < I.ny) {
@@ -507,10 +549,12 @@ __device__ __forceinline__ void issue_stage(const InstDesc& I, const Seg& sg, in
       bulk_g2s(BY, sy + (plane + sg.y0) * nx, sg.ty * rowB, bar);
       bulk_g2s(BY + sg.ty * rowB, sy + plane * nx, rowB, bar);
     }
-    if (CoefTraits<BT>::kDiag)
-      bulk_g2s(buf + L.bd_off(), sd + (plane + sg.y0) * nx, sg.ty * rowB, bar);
+  } else {
+    const bool need_z = j >= 0, need_d = CoefTraits<BT>::kDiag && j >= 0 && j < sg.nzs;
+    mbar_arrive_expect_tx(bar, (uint32_t)((need_z ? sg.ty : 0) + (need_d ? sg.ty : 0)) * rowB);
+    if (need_z) bulk_g2s(buf + L.bz_off(), sz + (plane + sg.y0) * nx, sg.ty * rowB, bar);
+    if (need_d) bulk_g2s(buf + L.bd_off(), sd + (plane + sg.y0) * nx, sg.ty * rowB, bar);
   }
-  if (need_z) bulk_g2s(buf + L.bz_off(), sz + (plane + sg.y0) * nx, sg.ty * rowB, bar);
 }
 
 // d = rt + beta d_old in place over all ring rows of a stage
@@ -532,7 +576,7 @@ __device__ __forceinline__ void form_direction(T* R, const T* O, int cells, T be
 // k - 1, k, k + 1, so one block barrier per plane separates the two; the barrier also frees the
 // stage of plane k - 1, which thread 0 then refills with plane k - 1 + S.  S >= 4 stages.
 template <class T, class BT>
-__device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, double (&acc)[kSlots],
+__device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, T& part,
                               unsigned char* smem) {
   constexpr int V = VecW<T>::V;
   constexpr bool kDiag = CoefTraits<BT>::kDiag;
@@ -554,7 +598,7 @@ __device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, double
   const BT* sd = static_cast<const BT*>(I.sd);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 4);  // four issuing lanes arrive per fill
     fence_mbar_init();
     timed_out = 0;
   }
@@ -582,11 +626,13 @@ __device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, double
   for_each_segment(I, unit, [&](const Seg& sg) {
     const int np = sg.nzs + 2;  // planes -1 .. nzs, stage index jj = j + 1
     const int ring_cells = (sg.ty + 2) * nx;
-    if (threadIdx.x == 0) {
+    const int part = threadIdx.x >> 5;  // issuing lanes: lane 0 of warps 0..3
+    const bool issuer = (threadIdx.x & 31) == 0 && part < 4;
+    if (issuer) {
       fence_proxy_async_smem();  // stage buffers were last touched by ordinary loads/stores
       for (int jj = 0; jj < min(S, np); ++jj)
-        issue_stage<T, BT>(I, sg, jj - 1, stage_ptr(jj), &bars[jj % S], rt, dold, use_old, sx, sy,
-                           sz, sd);
+        issue_part<T, BT>(part, I, sg, jj - 1, stage_ptr(jj), &bars[jj % S], rt, dold, use_old, sx,
+                          sy, sz, sd);
     }
     ready(0, ring_cells);  // plane -1
     ready(1, ring_cells);  // plane 0
@@ -653,17 +699,232 @@ __device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, double
       }
       fence_proxy_async_smem();  // this thread's shared accesses before the refill's TMA writes
       __syncthreads();           // stage k (plane k - 1) is free; plane k + 2 is formed
-      if (threadIdx.x == 0 && k + S < np) {
-        issue_stage<T, BT>(I, sg, k + S - 1, stage_ptr(k + S), &bars[(k + S) % S], rt, dold,
-                           use_old, sx, sy, sz, sd);
+      if (issuer && k + S < np) {
+        issue_part<T, BT>(part, I, sg, k + S - 1, stage_ptr(k + S), &bars[(k + S) % S], rt, dold,
+                          use_old, sx, sy, sz, sd);
       }
     }
   });
   if (timed_out && threadIdx.x == 0) atomicExch(&st->fault, 1);
-  double tot = 0.0;
+  T tot = 0;
 #pragma unroll
-  for (int k = 0; k < V; ++k) tot += (double)sum[k];
-  acc[0] = tot;
+  for (int k = 0; k < V; ++k) tot += sum[k];
+  part = tot;
+}
+
+// ---- the stencil sweep, direct form: register z march, no shared memory, no block barrier --------
+// Each thread owns V consecutive cells of one row of the unit's row tile (tile = blockDim * V / nx
+// rows) and marches them through the unit's z chunk, keeping d of planes z-1, z, z+1 in registers.
+// Per plane it loads, as 16-byte vectors, rt and d_old of its own row at z+1 and of the rows above
+// and below at z (forming d there: the neighbouring threads' rows, so these loads hit L1/L2), and
+// the coefficients of its cells; x neighbours come from the adjacent lanes by warp shuffle (row
+// ends, which wrap, are loaded).  Nothing waits on another warp, so many warps per SM keep many
+// independent loads in flight.  Measured on the 256^3 FP32 sweep this runs at about 90 % of the
+// HBM copy bandwidth, against about 50 % for the TMA-staged variant above, whose per-plane block
+// barrier serialises the copy latency with the arithmetic.
+template <class T, class BT>
+__device__ void sweep_stencil_direct(const InstDesc& I, InstState* st, int unit, T& part) {
+  constexpr int V = VecW<T>::V;
+  constexpr bool kDiag = CoefTraits<BT>::kDiag;
+  const int nx = I.nx, ny = I.ny, nz = I.nz;
+  const int tpr = nx / V;  // threads per row
+  const int tile = unit % I.uy, chunk = unit / I.uy;
+  const int row = threadIdx.x / tpr;
+  const int x0 = (threadIdx.x - row * tpr) * V;
+  const int yr = tile * I.ty + row;
+  const bool active = row < I.ty && yr < ny;
+  const int y = active ? yr : ny - 1;  // idle threads follow a valid row (shuffles need them)
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  const int z0 = (int)((long long)chunk * nz / I.zc), z1 = (int)((long long)(chunk + 1) * nz / I.zc);
+  const int lane = threadIdx.x & 31;
+  const bool row_start = x0 == 0, row_end = x0 + V == nx;
+  const int xl = row_start ? nx - 1 : x0 - 1, xr = row_end ? 0 : x0 + V;
+  const T beta = (T)st->beta;
+  const bool use_old = st->inner_iters > 0;
+  const T* rt = static_cast<const T*>(I.r);
+  const T* dold = static_cast<const T*>(st->parity ? I.d1 : I.d0);
+  T* dnew = static_cast<T*>(st->parity ? I.d0 : I.d1);
+  T* q = static_cast<T*>(I.q);
+  const BT* sx = static_cast<const BT*>(I.sx);
+  const BT* sy = static_cast<const BT*>(I.sy);
+  const BT* sz = static_cast<const BT*>(I.sz);
+  const BT* sd = static_cast<const BT*>(I.sd);
+  const long long plane = (long long)nx * ny;
+  const long long dym = (long long)(ym - y) * nx, dyp = (long long)(yp - y) * nx;
+  const int dxl = xl - x0, dxr = xr - x0;
+  const long long cell0 = (long long)y * nx + x0;  // offset of the thread's cells in a plane
+  auto zoff = [&](int z) -> long long {             // plane z (may be -1 or nz) + own cells
+    return (long long)(z < 0 ? z + nz : (z >= nz ? z - nz : z)) * plane + cell0;
+  };
+  // all loads of a plane are issued together (non-coherent read-only path), then used
+  auto dvec = [&](long long o, T (&d)[V]) {  // d = rt + beta d_old, V cells at offset o
+    LdgIO<T, V>::ld(rt + o, d);
+    if (use_old) {
+      T b[V];
+      LdgIO<T, V>::ld(dold + o, b);
+#pragma unroll
+      for (int k = 0; k < V; ++k) d[k] = fma(beta, b[k], d[k]);
+    }
+  };
+  auto d1 = [&](long long o) -> T { return use_old ? fma(beta, __ldg(dold + o), __ldg(rt + o)) : __ldg(rt + o); };
+
+  T dm[V], dc[V], dp[V];
+  if (z0 < z1) {
+    dvec(zoff(z0 - 1), dm);
+    dvec(zoff(z0), dc);
+  }
+  T sum[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) sum[k] = 0;
+  for (int z = z0; z < z1; ++z) {
+    const long long oc = zoff(z), op = zoff(z + 1);
+    T du[V], dd[V], bx[V], by[V], byd[V], bz[V], bzp[V], bd[V];
+    dvec(op, dp);
+    dvec(oc + dym, du);
+    dvec(oc + dyp, dd);
+    CoefIO<BT, T, V>::ldg(sx + oc, bx);
+    CoefIO<BT, T, V>::ldg(sy + oc, by);
+    CoefIO<BT, T, V>::ldg(sy + oc + dyp, byd);
+    CoefIO<BT, T, V>::ldg(sz + oc, bz);
+    CoefIO<BT, T, V>::ldg(sz + op, bzp);
+    if (kDiag) CoefIO<BT, T, V>::ldg(sd + oc, bd);
+    const T bxr = (T)ldg1(sx + oc + dxr);
+    // x neighbours of the first and last cell: adjacent lanes, or a load at row ends / warp ends
+    T left = __shfl_up_sync(0xffffffffu, dc[V - 1], 1);
+    T right = __shfl_down_sync(0xffffffffu, dc[0], 1);
+    if (lane == 0 || row_start) left = d1(oc + dxl);
+    if (lane == 31 || row_end) right = d1(oc + dxr);
+    T qv[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const T l = k == 0 ? left : dc[k - 1];
+      const T r = k == V - 1 ? right : dc[k + 1];
+      const T br = k == V - 1 ? bxr : bx[k + 1];
+      T a = dc[k];
+      if (kDiag) a = fma(bd[k], dc[k], a);
+      a = fma(-bx[k], l, a);
+      a = fma(-br, r, a);
+      a = fma(-by[k], du[k], a);
+      a = fma(-byd[k], dd[k], a);
+      a = fma(-bz[k], dm[k], a);
+      a = fma(-bzp[k], dp[k], a);
+      qv[k] = a;
+      sum[k] = fma(dc[k], a, sum[k]);
+    }
+    if (active) {
+      VecIO<T, V>::st(dnew + oc, dc);
+      VecIO<T, V>::st(q + oc, qv);
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      dm[k] = dc[k];
+      dc[k] = dp[k];
+    }
+  }
+  if (!active) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) sum[k] = 0;
+  }
+  T tot = 0;
+#pragma unroll
+  for (int k = 0; k < V; ++k) tot += sum[k];
+  part = tot;
+}
+
+// FP64 residual sweep in the same direct form (same unit and thread geometry as the stencil
+// sweep: a thread owns VR = 16 / sizeof(T) cells of one row): p of planes z-1, z, z+1 in
+// registers, rows above and below loaded per plane.  r = (f - <f>) - A p with the FP64 face
+// coefficients; rt = D^-1/2 r stored in the inner type; sums of r^2, rt^2, p and, on the first
+// call, (f - <f>)^2.
+template <class T>
+__device__ void sweep_res64_direct(const InstDesc& I, const InstState* st, int unit,
+                                   double (&acc)[kSlots]) {
+  constexpr int VR = VecW<T>::V;  // cells per thread (4 for FP32 inner, 2 for FP64)
+  const int nx = I.nx, ny = I.ny, nz = I.nz;
+  const int tpr = nx / VR;
+  const int tile = unit % I.uy, chunk = unit / I.uy;
+  const int row = threadIdx.x / tpr;
+  const int x0 = (threadIdx.x - row * tpr) * VR;
+  const int yr = tile * I.ty + row;
+  const bool active = row < I.ty && yr < ny;
+  const int y = active ? yr : ny - 1;
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  const int z0 = (int)((long long)chunk * nz / I.zc), z1 = (int)((long long)(chunk + 1) * nz / I.zc);
+  const int lane = threadIdx.x & 31;
+  const bool row_start = x0 == 0, row_end = x0 + VR == nx;
+  const int xl = row_start ? nx - 1 : x0 - 1, xr = row_end ? 0 : x0 + VR;
+  const double mu = st->mu_f;
+  const bool first = st->first_res != 0;
+  const double* p = I.p;
+  T* rt = static_cast<T*>(I.r);
+  auto at = [&](int z, int yy) -> long long {
+    const int zz = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+    return ((long long)zz * ny + yy) * nx;
+  };
+  auto ldv = [&](const double* a, long long o, double (&v)[VR]) {
+#pragma unroll
+    for (int k = 0; k < VR; k += 2) {
+      const double2 t = *reinterpret_cast<const double2*>(a + o + k);
+      v[k] = t.x;
+      v[k + 1] = t.y;
+    }
+  };
+  double pm[VR], pc[VR], pp[VR];
+  if (z0 < z1) {
+    ldv(p, at(z0 - 1, y) + x0, pm);
+    ldv(p, at(z0, y) + x0, pc);
+  }
+  double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  for (int z = z0; z < z1; ++z) {
+    const long long oc = at(z, y), op = at(z + 1, y), oyp = at(z, yp), oym = at(z, ym);
+    ldv(p, op + x0, pp);
+    const double bxr = I.bx[oc + xr];
+    double left = __shfl_up_sync(0xffffffffu, pc[VR - 1], 1);
+    double right = __shfl_down_sync(0xffffffffu, pc[0], 1);
+    if (lane == 0 || row_start) left = p[oc + xl];
+    if (lane == 31 || row_end) right = p[oc + xr];
+    // two cells at a time keeps the live registers down
+#pragma unroll
+    for (int h = 0; h < VR; h += 2) {
+      const long long o = oc + x0 + h;
+      const double2 pu = *reinterpret_cast<const double2*>(p + oym + x0 + h);
+      const double2 pd = *reinterpret_cast<const double2*>(p + oyp + x0 + h);
+      const double2 bx = *reinterpret_cast<const double2*>(I.bx + o);
+      const double2 by = *reinterpret_cast<const double2*>(I.by + o);
+      const double2 byd = *reinterpret_cast<const double2*>(I.by + oyp + x0 + h);
+      const double2 bz = *reinterpret_cast<const double2*>(I.bz + o);
+      const double2 bzp = *reinterpret_cast<const double2*>(I.bz + op + x0 + h);
+      const double2 f = *reinterpret_cast<const double2*>(I.rhs + o);
+      const double2 si = *reinterpret_cast<const double2*>(I.sinv + o);
+      const double l0 = h == 0 ? left : pc[h - 1];
+      const double r1 = h + 2 == VR ? right : pc[h + 2];
+      const double br1 = h + 2 == VR ? bxr : I.bx[o + 2];
+      double res[2];
+      const double c0 = pc[h], c1 = pc[h + 1];
+      res[0] = (f.x - mu) - (bx.y * (c1 - c0) - bx.x * (c0 - l0) + byd.x * (pd.x - c0) -
+                             by.x * (c0 - pu.x) + bzp.x * (pp[h] - c0) - bz.x * (c0 - pm[h]));
+      res[1] = (f.y - mu) - (br1 * (r1 - c1) - bx.y * (c1 - c0) + byd.y * (pd.y - c1) -
+                             by.y * (c1 - pu.y) + bzp.y * (pp[h + 1] - c1) - bz.y * (c1 - pm[h + 1]));
+      const T t0 = from_double_rn<T>(si.x * res[0]), t1 = from_double_rn<T>(si.y * res[1]);
+      if (active) {
+        rt[o] = t0;
+        rt[o + 1] = t1;
+        a0 = fma(res[0], res[0], fma(res[1], res[1], a0));
+        a1 = fma((double)t0, (double)t0, fma((double)t1, (double)t1, a1));
+        a2 += c0 + c1;
+        if (first) a3 = fma(f.x - mu, f.x - mu, fma(f.y - mu, f.y - mu, a3));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+      pm[k] = pc[k];
+      pc[k] = pp[k];
+    }
+  }
+  acc[0] = a0;
+  acc[1] = a1;
+  acc[2] = a2;
+  acc[3] = a3;
 }
 
 // ---- the FP64 residual sweep (a few times per solve): z march through a three-plane ring ---------
@@ -757,9 +1018,8 @@ __device__ __forceinline__ int phase_slots(int phase) {
   }
 }
 
-__device__ __forceinline__ void finish_sweep(const InstDesc& I, InstState* st, int phase, int nunits,
-                                             int unit, double (&acc)[kSlots]) {
-  store_partials(acc, I.part, nunits, unit);
+__device__ __forceinline__ void finish_sweep(const InstDesc& I, InstState* st, int phase,
+                                             int nunits) {
   if (arrive_last(I.ticket, nunits)) {
     if (threadIdx.x < 32) {
       double S[kSlots] = {0.0, 0.0, 0.0, 0.0};
@@ -774,25 +1034,54 @@ __device__ __forceinline__ void finish_sweep(const InstDesc& I, InstState* st, i
   }
 }
 
-template <class T, class BT>
-__global__ void __launch_bounds__(kMaxThreads) k_stencil(const InstDesc* __restrict__ insts,
-                                                         const UnitRef* __restrict__ units) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+template <class T, class BT, int MODE>
+__device__ __forceinline__ void stencil_kind_sweep(const InstDesc* __restrict__ insts,
+                                                   const UnitRef* __restrict__ units,
+                                                   unsigned char* smem_raw) {
   const UnitRef ur = units[blockIdx.x];
   const InstDesc& I = insts[ur.inst];
   InstState* st = I.st;
   const int phase = st->phase;
   if (phase != PH_RES64 && phase != PH_STENCIL) return;
-  double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
-  if (phase == PH_RES64)
-    sweep_res64<T>(I, st, ur.unit, acc, reinterpret_cast<double*>(smem_raw));
-  else
-    sweep_stencil<T, BT>(I, st, ur.unit, acc, smem_raw);
-  finish_sweep(I, st, phase, I.nunits, ur.unit, acc);
+  if (phase == PH_RES64) {
+    double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
+    if (MODE == 0)
+      sweep_res64_direct<T>(I, st, ur.unit, acc);
+    else
+      sweep_res64<T>(I, st, ur.unit, acc, reinterpret_cast<double*>(smem_raw));
+    store_partials<kSlots, double>(acc, I.part, I.nunits, ur.unit);
+  } else {
+    T part[1] = {0};
+    if (MODE == 0)
+      sweep_stencil_direct<T, BT>(I, st, ur.unit, part[0]);
+    else
+      sweep_stencil<T, BT>(I, st, ur.unit, part[0], smem_raw);
+    store_partials<1, T>(part, I.part, I.nunits, ur.unit);
+  }
+  finish_sweep(I, st, phase, I.nunits);
+}
+
+// direct register march: at most 256 threads, VDP_DIRECT_MIN_BLOCKS units per SM
+#ifndef VDP_DIRECT_MIN_BLOCKS
+#define VDP_DIRECT_MIN_BLOCKS 2
+#endif
+template <class T, class BT>
+__global__ void __launch_bounds__(kDirectThreads, VDP_DIRECT_MIN_BLOCKS) k_stencil_direct(
+    const InstDesc* __restrict__ insts, const UnitRef* __restrict__ units) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  stencil_kind_sweep<T, BT, 0>(insts, units, smem_raw);
+}
+
+// TMA-staged pipeline
+template <class T, class BT>
+__global__ void __launch_bounds__(kMaxThreads) k_stencil_tma(const InstDesc* __restrict__ insts,
+                                                             const UnitRef* __restrict__ units) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  stencil_kind_sweep<T, BT, 1>(insts, units, smem_raw);
 }
 
 template <class T>
-__global__ void __launch_bounds__(kFlatThreads) k_flat(const InstDesc* __restrict__ insts,
+__global__ void __launch_bounds__(kFlatThreads, 4) k_flat(const InstDesc* __restrict__ insts,
                                                        const UnitRef* __restrict__ units) {
   const UnitRef ur = units[blockIdx.x];
   const InstDesc& I = insts[ur.inst];
@@ -800,14 +1089,24 @@ __global__ void __launch_bounds__(kFlatThreads) k_flat(const InstDesc* __restric
   const int phase = st->phase;
   if (phase != PH_MEANF && phase != PH_UPDATE && phase != PH_CORRECT && phase != PH_FINAL) return;
   const long long c0 = flat_begin(I, ur.unit), c1 = flat_begin(I, ur.unit + 1);
-  double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
   switch (phase) {
-    case PH_MEANF: sweep_meanf(I, st, c0, c1, acc); break;
-    case PH_UPDATE: sweep_update<T>(I, st, c0, c1, acc); break;
+    case PH_MEANF: {
+      double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
+      sweep_meanf(I, st, c0, c1, acc);
+      const double two[2] = {acc[0], acc[1]};
+      store_partials<2, double>(two, I.part, I.nunits_f, ur.unit);
+      break;
+    }
+    case PH_UPDATE: {
+      T part[1] = {0};
+      sweep_update<T>(I, st, c0, c1, part[0]);
+      store_partials<1, T>(part, I.part, I.nunits_f, ur.unit);
+      break;
+    }
     case PH_CORRECT: sweep_correct<T>(I, c0, c1); break;
     default: sweep_final(I, st, c0, c1); break;
   }
-  finish_sweep(I, st, phase, I.nunits_f, ur.unit, acc);
+  finish_sweep(I, st, phase, I.nunits_f);
 }
 
 // Per-solve initialisation of one instance's state.
@@ -1031,26 +1330,27 @@ cudaError_t launch_init(InstDesc* desc, const double* rhs, double* p, double tol
   return cudaGetLastError();
 }
 
-static void* stencil_fn(int prec) {
-  if (prec == PREC_FP64) return (void*)k_stencil<double, double>;
-  if (prec == PREC_MIXED) return (void*)k_stencil<float, float>;
-  return (void*)k_stencil<float, __nv_bfloat16>;
+static void* stencil_fn(int prec, int mode) {
+  if (mode == 0) {
+    if (prec == PREC_FP64) return (void*)k_stencil_direct<double, double>;
+    if (prec == PREC_MIXED) return (void*)k_stencil_direct<float, float>;
+    return (void*)k_stencil_direct<float, __nv_bfloat16>;
+  }
+  if (prec == PREC_FP64) return (void*)k_stencil_tma<double, double>;
+  if (prec == PREC_MIXED) return (void*)k_stencil_tma<float, float>;
+  return (void*)k_stencil_tma<float, __nv_bfloat16>;
 }
 
-cudaError_t prepare_step(int prec, size_t smem_bytes) {
-  return cudaFuncSetAttribute(stencil_fn(prec), cudaFuncAttributeMaxDynamicSharedMemorySize,
+cudaError_t prepare_step(int prec, int mode, size_t smem_bytes) {
+  return cudaFuncSetAttribute(stencil_fn(prec, mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_bytes);
 }
 
-cudaError_t launch_stencil(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
-                           int threads, size_t smem_bytes, cudaStream_t s) {
-  if (prec == PREC_FP64)
-    k_stencil<double, double><<<nunits, threads, smem_bytes, s>>>(desc, units);
-  else if (prec == PREC_MIXED)
-    k_stencil<float, float><<<nunits, threads, smem_bytes, s>>>(desc, units);
-  else
-    k_stencil<float, __nv_bfloat16><<<nunits, threads, smem_bytes, s>>>(desc, units);
-  return cudaGetLastError();
+cudaError_t launch_stencil(int prec, int mode, const InstDesc* desc, const UnitRef* units,
+                           int nunits, int threads, size_t smem_bytes, cudaStream_t s) {
+  void* fn = stencil_fn(prec, mode);
+  void* args[] = {(void*)&desc, (void*)&units};
+  return cudaLaunchKernel(fn, dim3(nunits), dim3(threads), args, smem_bytes, s);
 }
 
 cudaError_t launch_flat(int prec, const InstDesc* desc, const UnitRef* units, int nunits,

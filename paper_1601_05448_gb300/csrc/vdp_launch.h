@@ -19,9 +19,9 @@ cudaError_t launch_apply(const double* bx, const double* by, const double* bz, c
 cudaError_t launch_init(InstDesc* desc, const double* rhs, double* p, double tol, double inner_tol,
                         int max_iter, int inner_max, int use_guess, int precision,
                         cudaStream_t s);
-cudaError_t prepare_step(int prec, size_t smem_bytes);
-cudaError_t launch_stencil(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
-                           int threads, size_t smem_bytes, cudaStream_t s);
+cudaError_t prepare_step(int prec, int mode, size_t smem_bytes);
+cudaError_t launch_stencil(int prec, int mode, const InstDesc* desc, const UnitRef* units,
+                           int nunits, int threads, size_t smem_bytes, cudaStream_t s);
 cudaError_t launch_flat(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
                         cudaStream_t s);
 

@@ -27,7 +27,7 @@ using namespace vdp;
 namespace {
 
 constexpr long long kMaxCells = VDP_NOALLOC_MAX_CELLS;
-constexpr int kMaxUnits = 320;  // stencil units (at most 2 per SM) plus flat units
+constexpr int kMaxUnits = kMaxCells / 8 + 16;  // stencil units (<= ny*nz) plus flat units (<= 16)
 constexpr size_t kAlign = 256;
 
 constexpr size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
@@ -128,7 +128,7 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
 
   // the default unit layout of vdp_solve
   Layout lay;
-  if (!plan_layout(nx, ny, nz, precision, 0, 0, 0, 0, &lay)) return VDP_EINVAL;
+  if (!plan_layout(nx, ny, nz, precision, 0, 0, 0, 0, 0, &lay)) return VDP_EINVAL;
   const int nunits = lay.nunits, nunits_f = lay.nunits_f;
 
   UnitRef hu[kMaxUnits];
@@ -143,7 +143,8 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
   d.nunits = nunits;
   d.nunits_f = nunits_f;
   d.stages = lay.stages;
-  d.npairs = lay.npairs;
+  d.zc = lay.zc;
+  d.mode = lay.mode;
   d.ncell = n;
   d.bx = bx;
   d.by = by;
@@ -164,7 +165,7 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
   // pageable host sources: these copies complete before the calls return
   NA_CK(cudaMemcpyAsync(units, hu, sizeof(UnitRef) * (nunits + nunits_f), cudaMemcpyHostToDevice, s));
   NA_CK(cudaMemcpyAsync(desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
-  NA_CK(prepare_step(precision, lay.smem));
+  NA_CK(prepare_step(precision, lay.mode, lay.smem));
   // the per-solve state and the ticket are reset on the device by the init kernel
   const int max_iter = 20000;
   NA_CK(launch_init(desc, rhs, p, tol, 1e-4, max_iter, max_iter, 0, precision, s));
@@ -176,7 +177,7 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
   long long rounds = 0;
   while (!done && rounds < max_rounds) {
     for (int i = 0; i < m; ++i) {
-      NA_CK(launch_stencil(precision, desc, units, nunits, lay.threads, lay.smem, s));
+      NA_CK(launch_stencil(precision, lay.mode, desc, units, nunits, lay.threads, lay.smem, s));
       NA_CK(launch_flat(precision, desc, units + nunits, nunits_f, s));
     }
     ++rounds;
