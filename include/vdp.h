@@ -150,6 +150,47 @@ int vdp_version(void);
 int vdp_apply(vdp_ctx *ctx, const double *p, double *out);
 
 /* ------------------------------------------------------------------------------------------ */
+/* Batches: many independent solves advanced together (continuous batching).                   */
+/* ------------------------------------------------------------------------------------------ */
+
+/*
+ * A batch advances the solves of several contexts (any grid sizes, density fields and
+ * tolerances; one precision, the default direct stencil sweep) in the same device launches.
+ * Each member keeps its own context, so its iterations and its result are exactly those of
+ * vdp_solve on that context alone.  persistent = 1 runs each vdp_batch_run as one cooperative
+ * persistent kernel looping over all members with grid-wide barriers (bounded waits);
+ * persistent = 0 as the equivalent sequence of ordinary launches; either is captured into a
+ * CUDA graph that is re-captured only when membership changes.  Work is ordered on `stream`
+ * (NULL = legacy default stream).  A batch does not own its contexts.
+ */
+typedef struct vdp_batch vdp_batch;
+int vdp_batch_create(int precision, int persistent, void *stream, vdp_batch **out);
+void vdp_batch_destroy(vdp_batch *batch);   /* NULL-safe */
+
+/*
+ * Queue a solve of ctx (after vdp_set_density; options precision equal to the batch's):
+ * A p = rhs - <rhs> to relative residual tol, as vdp_solve.  rhs and p: device pointers, 16-byte
+ * aligned, valid until the member is done.  VDP_EINVAL if ctx is already a member.
+ */
+int vdp_batch_add(vdp_batch *batch, vdp_ctx *ctx, const double *rhs, double *p, double tol);
+
+/*
+ * Advance every unfinished member by up to max_pairs sweep pairs (about one Krylov iteration
+ * each) and wait for it; *active = members still unfinished.  Finished members' statistics are
+ * available through vdp_get_stats on their contexts.  VDP_ETIMEOUT if a grid barrier wait expired.
+ */
+int vdp_batch_run(vdp_batch *batch, int max_pairs, int *active);
+
+/* 1 if ctx's queued solve has finished, 0 if not, -VDP_EINVAL if ctx is not a member. */
+int vdp_batch_done(vdp_batch *batch, vdp_ctx *ctx);
+
+/* Remove ctx from the batch (finished or not); the context itself is untouched. */
+int vdp_batch_remove(vdp_batch *batch, vdp_ctx *ctx);
+
+/* Number of members (finished ones included until removed). */
+int vdp_batch_size(const vdp_batch *batch);
+
+/* ------------------------------------------------------------------------------------------ */
 /* A solve that allocates no device memory.                                                    */
 /* ------------------------------------------------------------------------------------------ */
 

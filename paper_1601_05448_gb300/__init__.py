@@ -70,6 +70,13 @@ _SIGS = {
     "vdp_last_cuda_error": (ctypes.c_char_p, []),
     "vdp_version": (ctypes.c_int, []),
     "vdp_apply": (ctypes.c_int, [_P, _P, _P]),
+    "vdp_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_void_p)]),
+    "vdp_batch_destroy": (None, [_P]),
+    "vdp_batch_add": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double]),
+    "vdp_batch_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "vdp_batch_done": (ctypes.c_int, [_P, _P]),
+    "vdp_batch_remove": (ctypes.c_int, [_P, _P]),
+    "vdp_batch_size": (ctypes.c_int, [_P]),
     "vdp_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                          ctypes.c_double, ctypes.c_int, _P, ctypes.POINTER(vdp_stats)]),
 }
@@ -175,6 +182,47 @@ def vdp_solve_noalloc(nx: int, ny: int, nz: int, L: float, rho, rhs, p, tol: flo
     return st, s
 
 
+def vdp_batch_create(precision: int = VDP_MIXED, persistent: int = 1, stream=None) -> int:
+    h = ctypes.c_void_p()
+    st = load().vdp_batch_create(int(precision), int(persistent), _stream(stream), ctypes.byref(h))
+    if st != VDP_OK:
+        raise VdpError(st, "vdp_batch_create")
+    return h.value
+
+
+def vdp_batch_destroy(batch) -> None:
+    if batch:
+        load().vdp_batch_destroy(batch)
+
+
+def vdp_batch_add(batch: int, ctx: int, rhs, p, tol: float) -> int:
+    return load().vdp_batch_add(batch, ctx, _ptr(rhs), _ptr(p, writable=True), float(tol))
+
+
+def vdp_batch_run(batch: int, max_pairs: int):
+    active = ctypes.c_int(0)
+    st = load().vdp_batch_run(batch, int(max_pairs), ctypes.byref(active))
+    return st, active.value
+
+
+def vdp_batch_done(batch: int, ctx: int) -> int:
+    return load().vdp_batch_done(batch, ctx)
+
+
+def vdp_batch_remove(batch: int, ctx: int) -> int:
+    return load().vdp_batch_remove(batch, ctx)
+
+
+def vdp_batch_size(batch: int) -> int:
+    return load().vdp_batch_size(batch)
+
+
+def _stream(stream):
+    if stream is None or isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
 # ---- marshalling ------------------------------------------------------------------------------
 
 def _ptr(a, writable: bool = False) -> int:
@@ -261,6 +309,10 @@ class Solver:
         if st != VDP_OK:
             raise VdpError(st, "vdp_set_density")
 
+    def stats(self) -> Stats:
+        s = vdp_get_stats(self.ctx)
+        return Stats(s.status, s.iters, s.outer_iters, s.rel_res, s.rhs_mean, s.ms, s.sweeps, s.launches)
+
     def solve(self, rhs, p, tol: float, check: bool = True) -> Stats:
         self._check(rhs, "rhs")
         self._check(p, "p")
@@ -282,6 +334,69 @@ class Solver:
         if getattr(self, "ctx", None):
             vdp_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Continuous batch of solves: ``add(solver, rhs, p, tol)``; ``run(max_pairs) -> active``;
+    ``done(solver)``; ``remove(solver)``.  All member solvers must use the batch's precision."""
+
+    def __init__(self, precision: str = "mixed", persistent: bool = True, stream=None):
+        self.precision = PRECISIONS[precision]
+        self.handle = vdp_batch_create(self.precision, 1 if persistent else 0, stream)
+        self._keep = {}
+
+    def add(self, solver: "Solver", rhs, p, tol: float) -> None:
+        solver._check(rhs, "rhs")
+        solver._check(p, "p")
+        st = vdp_batch_add(self.handle, solver.ctx, rhs, p, tol)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_batch_add")
+        self._keep[solver.ctx] = (solver, rhs, p)
+
+    def run(self, max_pairs: int = 64) -> int:
+        st, active = vdp_batch_run(self.handle, max_pairs)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_batch_run")
+        return active
+
+    def done(self, solver: "Solver") -> bool:
+        r = vdp_batch_done(self.handle, solver.ctx)
+        if r < 0:
+            raise VdpError(-r, "vdp_batch_done")
+        return r == 1
+
+    def remove(self, solver: "Solver") -> None:
+        st = vdp_batch_remove(self.handle, solver.ctx)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_batch_remove")
+        self._keep.pop(solver.ctx, None)
+
+    def __len__(self):
+        return vdp_batch_size(self.handle)
+
+    def run_to_completion(self, max_pairs: int = 64, max_runs: int = 100000) -> None:
+        for _ in range(max_runs):
+            if self.run(max_pairs) == 0:
+                return
+        raise VdpError(VDP_ENOTCONV, "Batch.run_to_completion")
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            vdp_batch_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
 
     def __enter__(self):
         return self

@@ -20,13 +20,16 @@
 #include "vdp.h"
 #include "vdp_internal.cuh"
 #include "vdp_launch.h"
+#include "vdp_ctx.h"
 
 using namespace vdp;
 
 namespace {
-
 std::mutex g_err_mu;
 std::string g_last_cuda_error;
+}  // namespace
+
+namespace vdp {
 
 int cuda_fail(cudaError_t e, const char* where) {
   std::lock_guard<std::mutex> lk(g_err_mu);
@@ -34,11 +37,6 @@ int cuda_fail(cudaError_t e, const char* where) {
   return e == cudaErrorMemoryAllocation ? VDP_ENOMEM : VDP_ECUDA;
 }
 
-#define VDP_CK(call)                                   \
-  do {                                                 \
-    cudaError_t _e = (call);                           \
-    if (_e != cudaSuccess) return cuda_fail(_e, #call); \
-  } while (0)
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -49,42 +47,7 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-}  // namespace
-
-struct vdp_ctx {
-  int nx = 0, ny = 0, nz = 0;
-  double L = 0;
-  long long n = 0;
-  int device = 0;
-  vdp_opts opts{};
-  cudaStream_t stream = nullptr;   // work stream (opts.stream)
-  cudaStream_t cap = nullptr;      // private stream used only to capture graphs
-  // FP64 operator data
-  double *bx = nullptr, *by = nullptr, *bz = nullptr, *sinv = nullptr;
-  // inner-precision data (sized for FP64, reinterpreted for FP32 / BF16)
-  void *sx = nullptr, *sy = nullptr, *sz = nullptr, *sd = nullptr;
-  void *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr, *q = nullptr;
-  int scaled_prec = -1;            // precision the scaled coefficients were built for
-  bool has_density = false;
-  // bookkeeping
-  double* part = nullptr;
-  unsigned int* ticket = nullptr;
-  InstState* st = nullptr;
-  InstDesc* desc = nullptr;
-  UnitRef* units = nullptr;
-  int* flag = nullptr;
-  double *stage_a = nullptr, *stage_b = nullptr;  // staging for host pointers
-  InstState* hstate = nullptr;     // pinned, 2 entries
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs[2] = {nullptr, nullptr};
-  // layout
-  Layout lay{};
-  int layout_prec = -1;
-  bool layout_dirty = true;
-  // graph cache
-  cudaGraphExec_t gexec = nullptr;
-  int g_prec = -1, g_steps = 0;
-  vdp_stats stats{};
-};
+}  // namespace vdp
 
 extern "C" {
 
@@ -129,7 +92,7 @@ int vdp_version(void) { return 1; }
 
 }  // extern "C"
 
-namespace {
+namespace vdp {
 
 void free_ctx(vdp_ctx* c) {
   if (!c) return;
@@ -163,6 +126,7 @@ int configure_layout(vdp_ctx* c, int prec) {
   int s = choose_layout(c, prec, &lay);
   if (s != VDP_OK) return s;
   c->lay = lay;
+  c->hdesc_valid = false;
   std::vector<UnitRef> u(lay.nunits + lay.nunits_f);
   for (int i = 0; i < lay.nunits; ++i) u[i] = UnitRef{0, i};
   for (int i = 0; i < lay.nunits_f; ++i) u[lay.nunits + i] = UnitRef{0, i};
@@ -196,6 +160,8 @@ int configure_layout(vdp_ctx* c, int prec) {
   d.part = c->part;
   d.ticket = c->ticket;
   d.st = c->st;
+  c->hdesc = d;
+  c->hdesc_valid = true;
   VDP_CK(cudaMemcpyAsync(c->desc, &d, sizeof(d), cudaMemcpyHostToDevice, c->stream));
   VDP_CK(cudaStreamSynchronize(c->stream));
   VDP_CK(prepare_step(prec, lay.mode, lay.smem));
@@ -251,7 +217,7 @@ int ensure_scaled(vdp_ctx* c, int prec) {
   return VDP_OK;
 }
 
-}  // namespace
+}  // namespace vdp
 
 extern "C" {
 

@@ -1,0 +1,69 @@
+// vdp_ctx.h -- the solver context behind the opaque vdp_ctx handle of include/vdp.h, and the
+// host helpers shared by the single-solve driver (vdp_api.cu) and the batch engine
+// (vdp_batch.cu).  Internal to libvdp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "vdp.h"
+#include "vdp_internal.cuh"
+
+namespace vdp {
+
+int cuda_fail(cudaError_t e, const char* where);  // records the message, maps to a vdp_status
+bool is_device_ptr(const void* p);
+
+}  // namespace vdp
+
+#define VDP_CK(call)                                         \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return vdp::cuda_fail(_e, #call); \
+  } while (0)
+
+struct vdp_ctx {
+  int nx = 0, ny = 0, nz = 0;
+  double L = 0;
+  long long n = 0;
+  int device = 0;
+  vdp_opts opts{};
+  cudaStream_t stream = nullptr;   // work stream (opts.stream)
+  cudaStream_t cap = nullptr;      // private stream used only to capture graphs
+  // FP64 operator data
+  double *bx = nullptr, *by = nullptr, *bz = nullptr, *sinv = nullptr;
+  // inner-precision data (sized for FP64, reinterpreted for FP32 / BF16)
+  void *sx = nullptr, *sy = nullptr, *sz = nullptr, *sd = nullptr;
+  void *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr, *q = nullptr;
+  int scaled_prec = -1;            // precision the scaled coefficients were built for
+  bool has_density = false;
+  // bookkeeping
+  double* part = nullptr;
+  unsigned int* ticket = nullptr;
+  vdp::InstState* st = nullptr;
+  vdp::InstDesc* desc = nullptr;
+  vdp::UnitRef* units = nullptr;
+  int* flag = nullptr;
+  double *stage_a = nullptr, *stage_b = nullptr;  // staging for host pointers
+  vdp::InstState* hstate = nullptr;     // pinned, 2 entries
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs[2] = {nullptr, nullptr};
+  // layout
+  vdp::Layout lay{};
+  vdp::InstDesc hdesc{};           // host copy of the device description (after layout)
+  bool hdesc_valid = false;
+  int layout_prec = -1;
+  bool layout_dirty = true;
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  int g_prec = -1, g_steps = 0;
+  vdp_stats stats{};
+};
+
+
+namespace vdp {
+
+// Make the context ready to run in precision `prec`: scaled coefficients built and the unit
+// layout (and its device description) configured.
+int configure_layout(vdp_ctx* c, int prec);
+int ensure_scaled(vdp_ctx* c, int prec);
+
+}  // namespace vdp

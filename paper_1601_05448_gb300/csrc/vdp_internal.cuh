@@ -101,6 +101,15 @@ struct InstDesc {
   double* part;        // kSlots x nunits partial sums
   unsigned int* ticket;
   InstState* st;
+  int* remaining;      // batch: count of unfinished instances (decremented at DONE), or null
+};
+
+// Control words of a batch's persistent kernel (device memory).
+struct BatchCtl {
+  unsigned int count;  // grid barrier arrivals
+  unsigned int gen;    // grid barrier generation
+  int remaining;       // unfinished instances
+  int fault;           // a grid barrier wait expired
 };
 
 struct UnitRef {

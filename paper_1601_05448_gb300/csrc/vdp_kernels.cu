@@ -278,7 +278,8 @@ __device__ __forceinline__ double sum_slot(const double* part, int nunits) {
 
 // ---- phase transitions (run by thread 0 of the last unit) -------------------------------------
 
-__device__ void transition(const InstDesc& I, InstState* st, int phase, const double (&S)[kSlots]) {
+__device__ void transition(const InstDesc& I, volatile InstState* st, int phase,
+                           const double (&S)[kSlots]) {
   st->sweeps += 1;
   if (st->fault && phase != PH_FINAL) {  // a bounded wait expired: stop with what p holds
     st->status = 6;                      // VDP_ETIMEOUT
@@ -380,6 +381,7 @@ __device__ void transition(const InstDesc& I, InstState* st, int phase, const do
       break;
     case PH_FINAL:
       st->phase = PH_DONE;
+      if (I.remaining) atomicSub(I.remaining, 1);
       break;
     default:
       break;
@@ -723,7 +725,7 @@ __device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, T& par
 // HBM copy bandwidth, against about 50 % for the TMA-staged variant above, whose per-plane block
 // barrier serialises the copy latency with the arithmetic.
 template <class T, class BT>
-__device__ void sweep_stencil_direct(const InstDesc& I, InstState* st, int unit, T& part) {
+__device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int unit, T& part) {
   constexpr int V = VecW<T>::V;
   constexpr bool kDiag = CoefTraits<BT>::kDiag;
   const int nx = I.nx, ny = I.ny, nz = I.nz;
@@ -1034,31 +1036,77 @@ __device__ __forceinline__ void finish_sweep(const InstDesc& I, InstState* st, i
   }
 }
 
+// Snapshot of the state fields the sweeps read, taken through volatile loads: in the persistent
+// kernel the previous phase's transition may have been written by another SM moments ago, so a
+// cached (L1) copy must not be used.
+__device__ __forceinline__ InstState snapshot(const InstState* st) {
+  const volatile InstState* v = st;
+  InstState s;
+  s.phase = v->phase;
+  s.inner_iters = v->inner_iters;
+  s.parity = v->parity;
+  s.first_res = v->first_res;
+  s.zero_sol = v->zero_sol;
+  s.use_guess = v->use_guess;
+  s.mu_f = v->mu_f;
+  s.alpha = v->alpha;
+  s.beta = v->beta;
+  s.sum_p = v->sum_p;
+  return s;
+}
+
+// One stencil-kind unit (RES64 or STENCIL phase) of instance I; no-op for other phases.
 template <class T, class BT, int MODE>
-__device__ __forceinline__ void stencil_kind_sweep(const InstDesc* __restrict__ insts,
-                                                   const UnitRef* __restrict__ units,
-                                                   unsigned char* smem_raw) {
-  const UnitRef ur = units[blockIdx.x];
-  const InstDesc& I = insts[ur.inst];
+__device__ __forceinline__ void stencil_kind_unit(const InstDesc& I, int unit,
+                                                  unsigned char* smem_raw) {
   InstState* st = I.st;
-  const int phase = st->phase;
+  const InstState sn = snapshot(st);
+  const int phase = sn.phase;
   if (phase != PH_RES64 && phase != PH_STENCIL) return;
   if (phase == PH_RES64) {
     double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
     if (MODE == 0)
-      sweep_res64_direct<T>(I, st, ur.unit, acc);
+      sweep_res64_direct<T>(I, &sn, unit, acc);
     else
-      sweep_res64<T>(I, st, ur.unit, acc, reinterpret_cast<double*>(smem_raw));
-    store_partials<kSlots, double>(acc, I.part, I.nunits, ur.unit);
+      sweep_res64<T>(I, &sn, unit, acc, reinterpret_cast<double*>(smem_raw));
+    store_partials<kSlots, double>(acc, I.part, I.nunits, unit);
   } else {
     T part[1] = {0};
     if (MODE == 0)
-      sweep_stencil_direct<T, BT>(I, st, ur.unit, part[0]);
+      sweep_stencil_direct<T, BT>(I, &sn, unit, part[0]);
     else
-      sweep_stencil<T, BT>(I, st, ur.unit, part[0], smem_raw);
-    store_partials<1, T>(part, I.part, I.nunits, ur.unit);
+      sweep_stencil<T, BT>(I, st, unit, part[0], smem_raw);
+    store_partials<1, T>(part, I.part, I.nunits, unit);
   }
   finish_sweep(I, st, phase, I.nunits);
+}
+
+// One flat-kind unit (MEANF, UPDATE, CORRECT or FINAL phase) of instance I.
+template <class T>
+__device__ __forceinline__ void flat_kind_unit(const InstDesc& I, int unit) {
+  InstState* st = I.st;
+  const InstState sn = snapshot(st);
+  const int phase = sn.phase;
+  if (phase != PH_MEANF && phase != PH_UPDATE && phase != PH_CORRECT && phase != PH_FINAL) return;
+  const long long c0 = flat_begin(I, unit), c1 = flat_begin(I, unit + 1);
+  switch (phase) {
+    case PH_MEANF: {
+      double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
+      sweep_meanf(I, &sn, c0, c1, acc);
+      const double two[2] = {acc[0], acc[1]};
+      store_partials<2, double>(two, I.part, I.nunits_f, unit);
+      break;
+    }
+    case PH_UPDATE: {
+      T part[1] = {0};
+      sweep_update<T>(I, &sn, c0, c1, part[0]);
+      store_partials<1, T>(part, I.part, I.nunits_f, unit);
+      break;
+    }
+    case PH_CORRECT: sweep_correct<T>(I, c0, c1); break;
+    default: sweep_final(I, &sn, c0, c1); break;
+  }
+  finish_sweep(I, st, phase, I.nunits_f);
 }
 
 // direct register march: at most 256 threads, VDP_DIRECT_MIN_BLOCKS units per SM
@@ -1068,8 +1116,8 @@ __device__ __forceinline__ void stencil_kind_sweep(const InstDesc* __restrict__ 
 template <class T, class BT>
 __global__ void __launch_bounds__(kDirectThreads, VDP_DIRECT_MIN_BLOCKS) k_stencil_direct(
     const InstDesc* __restrict__ insts, const UnitRef* __restrict__ units) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  stencil_kind_sweep<T, BT, 0>(insts, units, smem_raw);
+  const UnitRef ur = units[blockIdx.x];
+  stencil_kind_unit<T, BT, 0>(insts[ur.inst], ur.unit, nullptr);
 }
 
 // TMA-staged pipeline
@@ -1077,36 +1125,76 @@ template <class T, class BT>
 __global__ void __launch_bounds__(kMaxThreads) k_stencil_tma(const InstDesc* __restrict__ insts,
                                                              const UnitRef* __restrict__ units) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  stencil_kind_sweep<T, BT, 1>(insts, units, smem_raw);
+  const UnitRef ur = units[blockIdx.x];
+  stencil_kind_unit<T, BT, 1>(insts[ur.inst], ur.unit, smem_raw);
 }
 
 template <class T>
 __global__ void __launch_bounds__(kFlatThreads, 4) k_flat(const InstDesc* __restrict__ insts,
-                                                       const UnitRef* __restrict__ units) {
+                                                          const UnitRef* __restrict__ units) {
   const UnitRef ur = units[blockIdx.x];
-  const InstDesc& I = insts[ur.inst];
-  InstState* st = I.st;
-  const int phase = st->phase;
-  if (phase != PH_MEANF && phase != PH_UPDATE && phase != PH_CORRECT && phase != PH_FINAL) return;
-  const long long c0 = flat_begin(I, ur.unit), c1 = flat_begin(I, ur.unit + 1);
-  switch (phase) {
-    case PH_MEANF: {
-      double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
-      sweep_meanf(I, st, c0, c1, acc);
-      const double two[2] = {acc[0], acc[1]};
-      store_partials<2, double>(two, I.part, I.nunits_f, ur.unit);
-      break;
+  flat_kind_unit<T>(insts[ur.inst], ur.unit);
+}
+
+// Grid-wide barrier of the persistent kernel (all CTAs co-resident: cooperative launch).  Bounded:
+// after ~2 s it gives up, sets the fault word and returns false, so a lost arrival ends the
+// launch with an error status instead of a hang.
+__device__ bool grid_sync(BatchCtl* ctl) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &ctl->gen;
+    const unsigned int gen = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&ctl->count, 1u) + 1u;
+    ok = 1;
+    if (arrived == gridDim.x) {
+      ctl->count = 0u;
+      __threadfence();
+      atomicAdd(&ctl->gen, 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      while (*vgen == gen) {
+        if (global_ns() - t0 > 2000000000ull) {
+          atomicExch(&ctl->fault, 1);
+          ok = 0;
+          break;
+        }
+      }
     }
-    case PH_UPDATE: {
-      T part[1] = {0};
-      sweep_update<T>(I, st, c0, c1, part[0]);
-      store_partials<1, T>(part, I.part, I.nunits_f, ur.unit);
-      break;
-    }
-    case PH_CORRECT: sweep_correct<T>(I, c0, c1); break;
-    default: sweep_final(I, st, c0, c1); break;
+    __threadfence();
   }
-  finish_sweep(I, st, phase, I.nunits_f);
+  __syncthreads();
+  return ok != 0;
+}
+
+// The batch engine's persistent kernel: `pairs` rounds of (stencil-kind sweep of every
+// instance, grid barrier, flat-kind sweep of every instance, grid barrier), units distributed
+// over the resident CTAs; stops early once every instance is done.
+template <class T, class BT>
+__global__ void __launch_bounds__(kDirectThreads, VDP_DIRECT_MIN_BLOCKS)
+    k_persistent(const InstDesc* __restrict__ insts, const UnitRef* __restrict__ sunits, int ns,
+                 const UnitRef* __restrict__ funits, int nf, int pairs, BatchCtl* ctl) {
+  for (int it = 0; it < pairs; ++it) {
+    // uniform: `remaining` only changes in flat sweeps, and every CTA reads it after a barrier
+    if (*(volatile int*)&ctl->remaining <= 0) break;
+    for (int u = blockIdx.x; u < ns; u += gridDim.x) {
+      const UnitRef ur = sunits[u];
+      stencil_kind_unit<T, BT, 0>(insts[ur.inst], ur.unit, nullptr);
+    }
+    if (!grid_sync(ctl)) return;
+    for (int u = blockIdx.x; u < nf; u += gridDim.x) {
+      const UnitRef ur = funits[u];
+      flat_kind_unit<T>(insts[ur.inst], ur.unit);
+    }
+    if (!grid_sync(ctl)) return;
+  }
+}
+
+// Copies the state of n instances into a contiguous array (one D2H copy for the host).
+__global__ void k_gather_states(const InstDesc* __restrict__ insts, int n, InstState* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = *insts[i].st;  // a separate launch: the solver kernels have finished
 }
 
 // Per-solve initialisation of one instance's state.
@@ -1351,6 +1439,47 @@ cudaError_t launch_stencil(int prec, int mode, const InstDesc* desc, const UnitR
   void* fn = stencil_fn(prec, mode);
   void* args[] = {(void*)&desc, (void*)&units};
   return cudaLaunchKernel(fn, dim3(nunits), dim3(threads), args, smem_bytes, s);
+}
+
+static void* persistent_fn(int prec) {
+  if (prec == PREC_FP64) return (void*)k_persistent<double, double>;
+  if (prec == PREC_MIXED) return (void*)k_persistent<float, float>;
+  return (void*)k_persistent<float, __nv_bfloat16>;
+}
+
+cudaError_t persistent_grid(int prec, int* grid) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_fn(prec),
+                                                                kDirectThreads, 0);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *grid = per_sm * sms;
+  return cudaSuccess;
+}
+
+cudaError_t launch_persistent(int prec, const InstDesc* desc, const UnitRef* sunits, int ns,
+                              const UnitRef* funits, int nf, int pairs, BatchCtl* ctl, int grid,
+                              cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kDirectThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident: the grid barrier is safe
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {(void*)&desc, (void*)&sunits, (void*)&ns, (void*)&funits, (void*)&nf,
+                  (void*)&pairs, (void*)&ctl};
+  return cudaLaunchKernelExC(&cfg, persistent_fn(prec), args);
+}
+
+cudaError_t launch_gather(const InstDesc* desc, int n, InstState* out, cudaStream_t s) {
+  k_gather_states<<<(n + 127) / 128, 128, 0, s>>>(desc, n, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_flat(int prec, const InstDesc* desc, const UnitRef* units, int nunits,

@@ -25,4 +25,10 @@ cudaError_t launch_stencil(int prec, int mode, const InstDesc* desc, const UnitR
 cudaError_t launch_flat(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
                         cudaStream_t s);
 
+cudaError_t persistent_grid(int prec, int* grid);
+cudaError_t launch_persistent(int prec, const InstDesc* desc, const UnitRef* sunits, int ns,
+                              const UnitRef* funits, int nf, int pairs, BatchCtl* ctl, int grid,
+                              cudaStream_t s);
+cudaError_t launch_gather(const InstDesc* desc, int n, InstState* out, cudaStream_t s);
+
 }  // namespace vdp
