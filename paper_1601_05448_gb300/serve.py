@@ -1,0 +1,191 @@
+"""Continuous-batching server for Poisson solves.
+
+Requests (a grid, a density, a right-hand side, a tolerance) arrive over time.  The server
+keeps a pool of solver contexts resident on the device (face coefficients, Jacobi scaling and
+Krylov vectors stay in HBM; a context is reused by later requests of the same grid size) and one
+batch engine.  Between batch runs it
+
+  * moves arrived requests to the waiting queue,
+  * admits waiting requests (first come, first served) while a context slot and the HBM budget
+    allow -- a new context costs about 96 bytes per cell -- uploading their inputs and adding
+    them to the running batch, so new work overlaps with requests already on the GPU,
+  * retires finished members, records their latency (arrival to result ready) and returns their
+    contexts to the pool (idle contexts are freed, oldest first, when the budget needs room).
+
+Every member is solved exactly as it would be alone (the batch engine guarantees bitwise
+identical results), so serving changes latency and throughput, never answers.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import PRECISIONS, Batch, Solver, VdpError
+
+BYTES_PER_CELL = 96 + 2  # device memory of one context per cell (FP64-sized buffers + BF16 diag)
+
+
+@dataclass
+class ServeRequest:
+    rid: int
+    arrival_s: float          # offset from the start of the run
+    shape: tuple              # (nz, ny, nx)
+    L: float
+    rho: object               # host numpy array or torch tensor (float64)
+    f: object
+    tol: float
+    # filled in by the server
+    t_admit: float = float("nan")
+    t_done: float = float("nan")
+    status: int = -1
+    iters: int = 0
+    p: object = None          # device tensor with the result
+
+    @property
+    def latency_s(self) -> float:
+        return self.t_done - self.arrival_s
+
+    @property
+    def queue_s(self) -> float:
+        return self.t_admit - self.arrival_s
+
+
+@dataclass
+class ServeStats:
+    completed: int = 0
+    elapsed_s: float = 0.0
+    latencies_s: list = field(default_factory=list)
+    queue_s: list = field(default_factory=list)
+    peak_bytes: int = 0
+    contexts_created: int = 0
+    runs: int = 0
+
+    def summary(self) -> dict:
+        lat = np.array(self.latencies_s) if self.latencies_s else np.array([np.nan])
+        q = np.array(self.queue_s) if self.queue_s else np.array([np.nan])
+        return {"completed": self.completed, "elapsed_s": self.elapsed_s,
+                "solves_per_s": self.completed / self.elapsed_s if self.elapsed_s > 0 else None,
+                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                "mean_queue_s": float(np.mean(q)), "peak_context_bytes": self.peak_bytes,
+                "contexts_created": self.contexts_created, "batch_runs": self.runs}
+
+
+class Server:
+    """``Server(precision="mixed", hbm_budget=64 GB, max_active=64).run(requests)``."""
+
+    def __init__(self, precision: str = "mixed", hbm_budget: int = 64 << 30, max_active: int = 64,
+                 pairs_per_run: int = 8, persistent: bool = True, tuned: bool = False, device: str = "cuda:0"):
+        import torch
+        self.torch = torch
+        self.precision = precision
+        self.budget = int(hbm_budget)
+        self.max_active = int(max_active)
+        self.pairs = int(pairs_per_run)
+        self.tuned = tuned
+        self.device = torch.device(device)
+        self.batch = Batch(precision, persistent=persistent)
+        self.idle = collections.OrderedDict()   # ctx id -> (Solver, shape) available for reuse
+        self.bytes_in_use = 0                    # contexts alive (idle or busy)
+        self.stats = ServeStats()
+
+    # ---- context pool -----------------------------------------------------------------------
+
+    def _ctx_bytes(self, shape) -> int:
+        nz, ny, nx = shape
+        return BYTES_PER_CELL * nx * ny * nz
+
+    def _acquire(self, shape, L):
+        for k, (s, shp) in list(self.idle.items()):
+            if shp == shape and abs(s.L - L) == 0.0:
+                del self.idle[k]
+                return s
+        need = self._ctx_bytes(shape)
+        while self.bytes_in_use + need > self.budget and self.idle:
+            _, (s, shp) = self.idle.popitem(last=False)   # free the oldest idle context
+            s.close()
+            self.bytes_in_use -= self._ctx_bytes(shp)
+        if self.bytes_in_use + need > self.budget:
+            return None
+        nz, ny, nx = shape
+        opts = {}
+        if self.tuned:
+            from .tune import cached_options
+            opts = cached_options(nx, ny, nz, self.precision) or {}
+        try:
+            s = Solver(nx, ny, nz, L, precision=self.precision, **opts)
+        except VdpError:
+            return None
+        self.bytes_in_use += need
+        self.stats.contexts_created += 1
+        self.stats.peak_bytes = max(self.stats.peak_bytes, self.bytes_in_use)
+        return s
+
+    def _release(self, s, shape):
+        self.idle[id(s)] = (s, shape)
+
+    # ---- the loop ---------------------------------------------------------------------------
+
+    def run(self, requests, time_scale: float = 1.0, on_done=None) -> ServeStats:
+        """Serve `requests` (sorted by arrival), arrivals replayed in real time scaled by
+        `time_scale`; returns the statistics.  Results are left in req.p (device tensors)."""
+        torch = self.torch
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
+        waiting = collections.deque()
+        active = {}   # ctx id -> (req, solver)
+        t0 = time.perf_counter()
+        now = lambda: (time.perf_counter() - t0) / time_scale
+        while pending or waiting or active:
+            t = now()
+            while pending and pending[0].arrival_s <= t:
+                waiting.append(pending.popleft())
+            # admission: FCFS while a slot and memory allow
+            while waiting and len(active) < self.max_active:
+                req = waiting[0]
+                s = self._acquire(req.shape, req.L)
+                if s is None:
+                    break
+                waiting.popleft()
+                rho = torch.as_tensor(req.rho, dtype=torch.float64).to(self.device).contiguous()
+                f = torch.as_tensor(req.f, dtype=torch.float64).to(self.device).contiguous()
+                s.set_density(rho)
+                req.p = torch.empty_like(f)
+                req._f = f
+                self.batch.add(s, f, req.p, req.tol)
+                req.t_admit = now()
+                active[id(s)] = (req, s)
+            if active:
+                self.batch.run(self.pairs)
+                self.stats.runs += 1
+                for k, (req, s) in list(active.items()):
+                    if self.batch.done(s):
+                        st = s.stats()
+                        req.t_done = now()
+                        req.status, req.iters = st.status, st.iters
+                        self.batch.remove(s)
+                        del active[k]
+                        req._f = None
+                        self._release(s, req.shape)
+                        self.stats.completed += 1
+                        self.stats.latencies_s.append(req.latency_s)
+                        self.stats.queue_s.append(req.queue_s)
+                        if on_done:
+                            on_done(req)
+            elif pending:
+                time.sleep(max(0.0, min(0.01, (pending[0].arrival_s - now()) * time_scale)))
+        self.stats.elapsed_s = now()
+        return self.stats
+
+    def close(self) -> None:
+        for _, (s, _) in list(self.idle.items()):
+            s.close()
+        self.idle.clear()
+        self.batch.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

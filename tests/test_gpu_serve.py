@@ -1,0 +1,83 @@
+"""Serving loop (continuous batching with HBM-budget admission) and the layout autotuner.
+
+Every served result must equal the same request solved alone (bitwise: the batch engine keeps
+each member's arithmetic), requests that arrive while others run must join them, and the memory
+held by resident contexts must stay within the budget."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import paper_1601_05448_gb300 as vdp  # noqa: E402
+import vdp_inputs as V  # noqa: E402
+from paper_1601_05448_gb300 import serve, tune  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def request_stream(count=12, seed=7):
+    rng = np.random.default_rng(seed)
+    shapes = [(16, 16, 16), (24, 32, 32), (40, 40, 40), (48, 48, 48), (32, 32, 64)]
+    t = np.cumsum(rng.exponential(0.004, size=count))
+    reqs = []
+    for j in range(count):
+        shape = shapes[rng.integers(0, len(shapes))]
+        prob = V.smooth_problem(shape, seed=300 + j, amplitude=float(rng.uniform(0.3, 0.8)))
+        tol = float(10.0 ** rng.uniform(-10, -7))
+        reqs.append(serve.ServeRequest(j, float(t[j]), prob.shape, prob.L, prob.rho, prob.f, tol))
+    return reqs
+
+
+def solve_alone(req, precision):
+    nz, ny, nx = req.shape
+    with vdp.Solver(nx, ny, nz, req.L, precision=precision) as s:
+        s.set_density(torch.from_numpy(req.rho).to(DEV))
+        p = torch.empty(req.shape, dtype=torch.float64, device=DEV)
+        st = s.solve(torch.from_numpy(req.f).to(DEV), p, req.tol)
+    return p, st
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+def test_served_results_equal_alone(persistent):
+    reqs = request_stream()
+    seen_overlap = []
+
+    with serve.Server("mixed", max_active=8, pairs_per_run=4, persistent=persistent) as srv:
+        stats = srv.run(reqs, on_done=lambda r: seen_overlap.append(r.t_admit))
+    s = stats.summary()
+    assert s["completed"] == len(reqs) and s["p99_latency_s"] >= s["p50_latency_s"] > 0
+    # continuous batching: some request was admitted before an earlier one finished
+    assert any(b.t_admit < a.t_done for a in reqs for b in reqs if b.arrival_s > a.arrival_s)
+    for r in reqs:
+        assert r.status == vdp.VDP_OK
+        p, st = solve_alone(r, "mixed")
+        assert st.iters == r.iters
+        assert torch.equal(p, r.p), r.rid
+
+
+def test_hbm_budget_admission():
+    reqs = request_stream(count=8, seed=11)
+    budget = 2 * serve.BYTES_PER_CELL * 48 ** 3  # room for about two of the larger contexts
+    with serve.Server("mixed", hbm_budget=budget, max_active=8, pairs_per_run=4) as srv:
+        stats = srv.run(reqs)
+    assert stats.completed == len(reqs) and stats.peak_bytes <= budget
+    ref, _ = oracle.solve_cg(reqs[0].rho, reqs[0].f, reqs[0].L, tol=1e-13)
+    assert np.linalg.norm(reqs[0].p.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-7
+
+
+def test_autotuner_picks_a_valid_layout(tmp_path, monkeypatch):
+    monkeypatch.setenv("VDP_TUNE_CACHE", str(tmp_path / "tune.json"))
+    prob = V.smooth_problem((32, 32, 64), seed=12)
+    nz, ny, nx = prob.shape
+    rho = torch.from_numpy(prob.rho).to(DEV)
+    f = torch.from_numpy(prob.f).to(DEV)
+    best = tune.tune(nx, ny, nz, prob.L, rho, f, "mixed", iters=20)
+    assert tune.cached_options(nx, ny, nz, "mixed") == best
+    with vdp.Solver(nx, ny, nz, prob.L, precision="mixed", **best) as s:
+        s.set_density(rho)
+        p = torch.empty_like(f)
+        st = s.solve(f, p, 1e-9)
+    ref, _ = oracle.solve_cg(prob.rho, prob.f, prob.L, tol=1e-13)
+    assert st.ok and np.linalg.norm(p.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-8
