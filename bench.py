@@ -23,10 +23,14 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Poisson solves/s and % HBM roofline to 1e-8 rel. residual, mixed vs FP64"
+WORKLOAD = ("256^3 periodic box L=2pi, rho=T0/T (20k hot spots, density ratio 4), rhs=div of random "
+            "|k|<=4 velocity; FP64, relative residual 1e-10")
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # FP64 vector peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -158,13 +162,104 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": prob.name, "grid": "256^3", "tol": prob.tol, "density_ratio": prob.info["ratio"],
-                       "l2": "inputs larger than L2"},
+            "config": {"workload": WORKLOAD, "grid": [256, 256, 256], "tol": prob.tol,
+                       "density_ratio": round(prob.info["ratio"], 4), "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"] + f"; median of {args.steps} samples"},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _config3_all(count: int = 64):
+    """The 64 batch instances, generated in a spawn pool (no fork after CUDA initialisation)."""
+    import multiprocessing as mp
+    import vdp_inputs as V
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(V.config3_instance, range(count))
+
+
+def _serve_pool():
+    """Two seeded problems per served grid size (the request stream draws from this pool)."""
+    import multiprocessing as mp
+    import vdp_inputs as V
+    jobs = []
+    for n in V.SERVE_SIZES:
+        for k in range(2):
+            jobs.append((n, 200000 + 10 * n + k))
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return dict(zip(jobs, pool.starmap(_serve_problem, jobs)))
+
+
+def _serve_problem(n, seed):
+    import vdp_inputs as V
+    import numpy as np
+    R = float(np.random.default_rng(seed).uniform(2.0, 10.0))
+    return V.hotspot_problem(n, seed=seed, nspots=int(round(20000 * n ** 3 / 256 ** 3)), target_ratio=R,
+                             precision="mixed", tol=1e-8)
+
+
+def run_batch(torch, vdp, dev, probs, persistent=True):
+    """Config 3: all instances in one batch, mixed precision to 1e-8, autotuned layouts."""
+    from paper_1601_05448_gb300 import tune
+    sizes = {}
+    for pr in probs:
+        sizes.setdefault(pr.shape, pr)
+    for shape, pr in sizes.items():  # tune each distinct grid once (cached)
+        nz, ny, nx = shape
+        tune.tune(nx, ny, nz, pr.L, torch.from_numpy(pr.rho).to(dev), torch.from_numpy(pr.f).to(dev), "mixed",
+                  iters=30)
+    solvers, fs, ps = [], [], []
+    for pr in probs:
+        nz, ny, nx = pr.shape
+        opts = tune.cached_options(nx, ny, nz, "mixed") or {}
+        s = vdp.Solver(nx, ny, nz, pr.L, precision="mixed", **opts)
+        s.set_density(torch.from_numpy(pr.rho).to(dev))
+        solvers.append(s)
+        fs.append(torch.from_numpy(pr.f).to(dev))
+        ps.append(torch.empty_like(fs[-1]))
+    out = {}
+    with vdp.Batch("mixed", persistent=persistent) as b:
+        for rep in range(2):  # the first pass warms up (graph capture, caches)
+            for s, f, p, pr in zip(solvers, fs, ps, probs):
+                b.add(s, f, p, pr.tol)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            runs = 0
+            while b.run(64) > 0:
+                runs += 1
+            torch.cuda.synchronize(dev)
+            el = time.perf_counter() - t0
+            stats = [s.stats() for s in solvers]
+            for s in solvers:
+                b.remove(s)
+        ncell = sum(int(np.prod(pr.shape)) for pr in probs)
+        dofit = sum(int(np.prod(pr.shape)) * st.iters for pr, st in zip(probs, stats))
+        out = {"instances": len(probs), "total_cells": ncell, "seconds": el, "solves_per_s": len(probs) / el,
+               "gdof_iter_per_s": dofit / el / 1e9, "persistent_launch": bool(persistent), "runs": runs + 1,
+               "all_ok": all(st.ok for st in stats), "max_rel_res": max(st.rel_res for st in stats),
+               "sizes": sorted({pr.shape[0] for pr in probs}), "tuned_layouts": {str(k[0]): tune.cached_options(
+                   k[2], k[1], k[0], "mixed") for k in sizes}}
+    for s in solvers:
+        s.close()
+    return out
+
+
+def run_serving(torch, vdp, dev, pool, count=200):
+    """Config 4 (first `count` requests of the Poisson stream, lambda = 200/s)."""
+    import vdp_inputs as V
+    from paper_1601_05448_gb300 import serve
+    reqs = []
+    for rq in V.config4_requests(count):
+        pr = pool[(rq.n, 200000 + 10 * rq.n + (rq.j % 2))]
+        reqs.append(serve.ServeRequest(rq.j, rq.arrival_s, pr.shape, pr.L, pr.rho, pr.f, rq.tol))
+    with serve.Server("mixed", hbm_budget=96 << 30, max_active=64, pairs_per_run=16, tuned=True) as srv:
+        stats = srv.run(reqs)
+    s = stats.summary()
+    s.update({"requests": count, "offered_rate_per_s": 200.0,
+              "statuses_ok": all(r.status == vdp.VDP_OK for r in reqs),
+              "inputs": "14 seeded hot-spot problems (2 per grid size), per-request tolerance"})
+    return s
 
 
 def main():
@@ -174,17 +269,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-iters", type=int, default=10, help="oracle iterations per reference-arm sample")
-    ap.add_argument("--no-extras", action="store_true", help="skip mixed paths, e2e and CPU baseline")
+    ap.add_argument("--no-extras", action="store_true", help="skip mixed paths, e2e, batch, serving, CPU baseline")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests of the serving stream")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
 
-    import numpy as np
     import torch
     import paper_1601_05448_gb300 as vdp
     import vdp_inputs as V
 
+    batch_probs = serve_pool = None
+    if not args.no_extras and rank == 0:
+        batch_probs = _config3_all()
+        serve_pool = _serve_pool()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
@@ -252,9 +351,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "256^3 periodic box L=2pi, rho=T0/T (20k hot spots, density ratio 4), "
-                               "rhs=div of random |k|<=4 velocity; FP64 Jacobi-scaled CG + FP64 refinement, "
-                               "tol 1e-10", "grid": [nx, ny, nz], "tol": prob.tol,
+        "config": {"workload": WORKLOAD, "grid": [nx, ny, nz], "tol": prob.tol,
                    "density_ratio": round(prob.info["ratio"], 4), "l2": "inputs larger than L2 (~1.6 GB working set)",
                    "replicas": world},
         "iterations": iters, "outer_iterations": outer, "rel_res": stats[-1].rel_res,
@@ -300,6 +397,13 @@ def main():
                                "oracle_rel_res": oracle.relative_residual(prob.rho, prob.L, prob.f,
                                                                           pp.cpu().numpy())}
         line["mixed_vs_fp64_at_1e-8"] = paths
+        if batch_probs is not None:
+            line["batch"] = run_batch(torch, vdp, dev, batch_probs)
+            line["batch_nonpersistent"] = {k: v for k, v in run_batch(torch, vdp, dev, batch_probs,
+                                                                       persistent=False).items()
+                                           if k in ("seconds", "solves_per_s", "gdof_iter_per_s", "all_ok")}
+        if serve_pool is not None:
+            line["serving"] = run_serving(torch, vdp, dev, serve_pool, args.serve_requests)
         if rank == 0:
             try:
                 line["cpu_baseline"] = cpu_baseline(prob)
