@@ -189,8 +189,12 @@ int ensure_graph(vdp_ctx* c, int prec) {
   cudaGraph_t g = nullptr;
   VDP_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
   for (int i = 0; i < m; ++i) {
-    cudaError_t e = launch_stencil(prec, c->lay.mode, c->desc, c->units, c->lay.nunits,
-                                   c->lay.threads, c->lay.smem, c->cap);
+    cudaError_t e = cudaSuccess;
+    if (c->lay.mode == 0)  // the residual sweep has its own kernel in the direct mode
+      e = launch_res64(prec, c->desc, c->units, c->lay.nunits, c->lay.threads, c->cap);
+    if (e == cudaSuccess)
+      e = launch_stencil(prec, c->lay.mode, c->desc, c->units, c->lay.nunits, c->lay.threads,
+                         c->lay.smem, c->cap);
     if (e == cudaSuccess)
       e = launch_flat(prec, c->desc, c->units + c->lay.nunits, c->lay.nunits_f, c->cap);
     if (e != cudaSuccess) {
@@ -393,7 +397,7 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   c->stats.rhs_mean = hs.mu_f;
   c->stats.ms = ms;
   c->stats.sweeps = hs.sweeps;
-  c->stats.launches = (int)(1 + issued * 2 * m);
+  c->stats.launches = (int)(1 + issued * (c->lay.mode == 0 ? 3 : 2) * m);
   return c->stats.status;
 }
 

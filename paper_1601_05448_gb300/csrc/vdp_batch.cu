@@ -141,7 +141,9 @@ int capture(vdp_batch* b, int pairs) {
                           b->d_ctl, b->grid, b->cap);
   } else {
     for (int i = 0; i < pairs && e == cudaSuccess; ++i) {
-      e = launch_stencil(b->prec, 0, b->d_desc, b->d_units, b->ns, kDirectThreads, 0, b->cap);
+      e = launch_res64(b->prec, b->d_desc, b->d_units, b->ns, kDirectThreads, b->cap);
+      if (e == cudaSuccess)
+        e = launch_stencil(b->prec, 0, b->d_desc, b->d_units, b->ns, kDirectThreads, 0, b->cap);
       if (e == cudaSuccess) e = launch_flat(b->prec, b->d_desc, b->d_units + b->ns, b->nf, b->cap);
     }
   }

@@ -164,7 +164,7 @@ inline void prec_sizes(int prec, int* ts, int* bs, bool* diag) {
 // threads with about 1024; the row tile shrinks until four pipeline stages fit; stages default to
 // what fits (at most 6), or to 4 when that lets two units share an SM; about four waves.
 // Both: stencil units = row tiles x z chunks (chunk-major); flat units of about 4096+ cells (at
-// most 4 per SM).  In mode 1 the dynamic shared memory also covers the FP64 residual sweep's ring.
+// most 8 per SM).  In mode 1 the dynamic shared memory also covers the FP64 residual sweep's ring.
 // Returns false when the configuration cannot run (rows too long, bad counts).
 inline bool plan_layout(int nx, int ny, int nz, int prec, int mode, int tile_y, int units,
                         int stages, int threads, Layout* L) {
@@ -222,7 +222,7 @@ inline bool plan_layout(int nx, int ny, int nz, int prec, int mode, int tile_y, 
   if (zc < 1) zc = 1;
   const long long ncell = (long long)nx * ny * nz;
   long long nf = ncell / 4096;
-  if (nf > kSMs * 4) nf = kSMs * 4;
+  if (nf > kSMs * 8) nf = kSMs * 8;
   if (nf < 1) nf = 1;
   L->mode = mode;
   L->ty = ty;

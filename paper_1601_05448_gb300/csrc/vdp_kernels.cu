@@ -270,10 +270,32 @@ __device__ __forceinline__ bool arrive_last(unsigned int* ticket, int nunits) {
 }
 
 // Fixed-order sum of one slot over all units (warp 0; identical result in every lane).
-__device__ __forceinline__ double sum_slot(const double* part, int nunits) {
+// Fixed-order sum of one slot over all units by the last unit: 64 lanes (warps 0 and 1) each
+// add the slots lane, lane + 64, ... in index order with eight loads in flight, then a fixed
+// shuffle tree per warp, warp 0's total plus warp 1's.  The order does not depend on the block
+// size, so an instance sums identically whatever launch it runs in.  Every thread returns it.
+__device__ __noinline__ double block_sum_slot(const double* part, int nunits) {
+  __shared__ double wsum[2];
+  constexpr int U = 8, LANES = 64;
+  const int t = threadIdx.x;
   double s = 0.0;
-  for (int i = threadIdx.x & 31; i < nunits; i += 32) s += __ldcg(part + i);
-  return warp_sum(s);
+  if (t < LANES) {
+    for (int i0 = t; i0 < nunits; i0 += U * LANES) {
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * LANES;
+        v[u] = i < nunits ? __ldcg(part + i) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) s += v[u];
+    }
+    s = warp_sum(s);
+  }
+  __syncthreads();  // wsum may be in use by a previous call
+  if (t == 0 || t == 32) wsum[t >> 5] = s;
+  __syncthreads();
+  return wsum[0] + wsum[1];
 }
 
 // ---- phase transitions (run by thread 0 of the last unit) -------------------------------------
@@ -1022,55 +1044,54 @@ __device__ __forceinline__ int phase_slots(int phase) {
 
 __device__ __forceinline__ void finish_sweep(const InstDesc& I, InstState* st, int phase,
                                              int nunits) {
-  if (arrive_last(I.ticket, nunits)) {
-    if (threadIdx.x < 32) {
-      double S[kSlots] = {0.0, 0.0, 0.0, 0.0};
-      const int ns = phase_slots(phase);
-      for (int k = 0; k < ns; ++k) S[k] = sum_slot(I.part + k * nunits, nunits);
-      if (threadIdx.x == 0) {
-        transition(I, st, phase, S);
-        *I.ticket = 0u;
-        __threadfence();
-      }
+  if (arrive_last(I.ticket, nunits)) {  // uniform in the block
+    double S[kSlots] = {0.0, 0.0, 0.0, 0.0};
+    const int ns = phase_slots(phase);
+    for (int k = 0; k < ns; ++k) S[k] = block_sum_slot(I.part + k * nunits, nunits);
+    if (threadIdx.x == 0) {
+      transition(I, st, phase, S);
+      *I.ticket = 0u;
+      __threadfence();
     }
   }
 }
 
-// Snapshot of the state fields the sweeps read, taken through volatile loads: in the persistent
-// kernel the previous phase's transition may have been written by another SM moments ago, so a
-// cached (L1) copy must not be used.
+// Snapshot of the state fields the sweeps read.  Loaded with ld.global.cg (L2, not L1): in the
+// persistent kernel the previous phase's transition may have been written by another SM moments
+// ago, so an L1 copy must not be used; the loads are independent, so they overlap.
 __device__ __forceinline__ InstState snapshot(const InstState* st) {
-  const volatile InstState* v = st;
   InstState s;
-  s.phase = v->phase;
-  s.inner_iters = v->inner_iters;
-  s.parity = v->parity;
-  s.first_res = v->first_res;
-  s.zero_sol = v->zero_sol;
-  s.use_guess = v->use_guess;
-  s.mu_f = v->mu_f;
-  s.alpha = v->alpha;
-  s.beta = v->beta;
-  s.sum_p = v->sum_p;
+  s.phase = __ldcg(&st->phase);
+  s.inner_iters = __ldcg(&st->inner_iters);
+  s.parity = __ldcg(&st->parity);
+  s.first_res = __ldcg(&st->first_res);
+  s.zero_sol = __ldcg(&st->zero_sol);
+  s.use_guess = __ldcg(&st->use_guess);
+  s.mu_f = __ldcg(&st->mu_f);
+  s.alpha = __ldcg(&st->alpha);
+  s.beta = __ldcg(&st->beta);
+  s.sum_p = __ldcg(&st->sum_p);
   return s;
 }
 
-// One stencil-kind unit (RES64 or STENCIL phase) of instance I; no-op for other phases.
-template <class T, class BT, int MODE>
+// One stencil-kind unit of instance I: WHICH = 0 handles the RES64 and STENCIL phases, 1 only
+// STENCIL, 2 only RES64; a no-op for other phases.
+template <class T, class BT, int MODE, int WHICH = 0>
 __device__ __forceinline__ void stencil_kind_unit(const InstDesc& I, int unit,
                                                   unsigned char* smem_raw) {
   InstState* st = I.st;
-  const InstState sn = snapshot(st);
-  const int phase = sn.phase;
+  const int phase = __ldcg(&st->phase);  // one load decides whether this unit has work
   if (phase != PH_RES64 && phase != PH_STENCIL) return;
-  if (phase == PH_RES64) {
+  if ((WHICH == 1 && phase != PH_STENCIL) || (WHICH == 2 && phase != PH_RES64)) return;
+  const InstState sn = snapshot(st);
+  if (WHICH != 1 && phase == PH_RES64) {
     double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
     if (MODE == 0)
       sweep_res64_direct<T>(I, &sn, unit, acc);
     else
       sweep_res64<T>(I, &sn, unit, acc, reinterpret_cast<double*>(smem_raw));
     store_partials<kSlots, double>(acc, I.part, I.nunits, unit);
-  } else {
+  } else if (WHICH != 2) {
     T part[1] = {0};
     if (MODE == 0)
       sweep_stencil_direct<T, BT>(I, &sn, unit, part[0]);
@@ -1085,9 +1106,9 @@ __device__ __forceinline__ void stencil_kind_unit(const InstDesc& I, int unit,
 template <class T>
 __device__ __forceinline__ void flat_kind_unit(const InstDesc& I, int unit) {
   InstState* st = I.st;
-  const InstState sn = snapshot(st);
-  const int phase = sn.phase;
+  const int phase = __ldcg(&st->phase);
   if (phase != PH_MEANF && phase != PH_UPDATE && phase != PH_CORRECT && phase != PH_FINAL) return;
+  const InstState sn = snapshot(st);
   const long long c0 = flat_begin(I, unit), c1 = flat_begin(I, unit + 1);
   switch (phase) {
     case PH_MEANF: {
@@ -1109,15 +1130,28 @@ __device__ __forceinline__ void flat_kind_unit(const InstDesc& I, int unit) {
   finish_sweep(I, st, phase, I.nunits_f);
 }
 
-// direct register march: at most 256 threads, VDP_DIRECT_MIN_BLOCKS units per SM
+// Direct register march, STENCIL phase only: at most 256 threads; three units per SM in FP32
+// (24 warps keep enough loads in flight), two in FP64 (already FP64-pipe bound).
 #ifndef VDP_DIRECT_MIN_BLOCKS
 #define VDP_DIRECT_MIN_BLOCKS 2
 #endif
+template <class T> struct DirectOcc { static constexpr int kMinBlocks = VDP_DIRECT_MIN_BLOCKS; };
+template <> struct DirectOcc<float> { static constexpr int kMinBlocks = VDP_DIRECT_MIN_BLOCKS + 1; };
+
 template <class T, class BT>
-__global__ void __launch_bounds__(kDirectThreads, VDP_DIRECT_MIN_BLOCKS) k_stencil_direct(
+__global__ void __launch_bounds__(kDirectThreads, DirectOcc<T>::kMinBlocks) k_stencil_direct(
     const InstDesc* __restrict__ insts, const UnitRef* __restrict__ units) {
   const UnitRef ur = units[blockIdx.x];
-  stencil_kind_unit<T, BT, 0>(insts[ur.inst], ur.unit, nullptr);
+  stencil_kind_unit<T, BT, 0, 1>(insts[ur.inst], ur.unit, nullptr);
+}
+
+// Direct register march, RES64 phase only (a few launches per solve do work; the kernel has its
+// own register allocation so that the FP64 residual does not limit the stencil's occupancy).
+template <class T>
+__global__ void __launch_bounds__(kDirectThreads, 2) k_res64_direct(
+    const InstDesc* __restrict__ insts, const UnitRef* __restrict__ units) {
+  const UnitRef ur = units[blockIdx.x];
+  stencil_kind_unit<T, T, 0, 2>(insts[ur.inst], ur.unit, nullptr);
 }
 
 // TMA-staged pipeline
@@ -1432,6 +1466,15 @@ static void* stencil_fn(int prec, int mode) {
 cudaError_t prepare_step(int prec, int mode, size_t smem_bytes) {
   return cudaFuncSetAttribute(stencil_fn(prec, mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_bytes);
+}
+
+cudaError_t launch_res64(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
+                         int threads, cudaStream_t s) {
+  if (prec == PREC_FP64)
+    k_res64_direct<double><<<nunits, threads, 0, s>>>(desc, units);
+  else
+    k_res64_direct<float><<<nunits, threads, 0, s>>>(desc, units);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_stencil(int prec, int mode, const InstDesc* desc, const UnitRef* units,

@@ -20,6 +20,9 @@ cudaError_t launch_init(InstDesc* desc, const double* rhs, double* p, double tol
                         int max_iter, int inner_max, int use_guess, int precision,
                         cudaStream_t s);
 cudaError_t prepare_step(int prec, int mode, size_t smem_bytes);
+// mode 0 only: the FP64 residual sweep (its own kernel, launched before each stencil launch)
+cudaError_t launch_res64(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
+                         int threads, cudaStream_t s);
 cudaError_t launch_stencil(int prec, int mode, const InstDesc* desc, const UnitRef* units,
                            int nunits, int threads, size_t smem_bytes, cudaStream_t s);
 cudaError_t launch_flat(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
