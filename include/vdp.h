@@ -61,7 +61,10 @@ typedef enum {
 
 typedef enum {
   VDP_PRECOND_JACOBI = 0, /* diagonal (Jacobi) scaling, folded into the operator */
-  VDP_PRECOND_CHEB = 1    /* Jacobi + fixed-degree Chebyshev polynomial sweep */
+  VDP_PRECOND_CHEB = 1    /* Jacobi + fixed polynomial: cheb_degree terms of the Chebyshev
+                             iteration for the unit-diagonal operator on [0.1, 2] (degree - 1
+                             stencil sweeps per Krylov iteration; symmetric positive definite,
+                             so plain preconditioned CG applies); direct stencil sweep only */
 } vdp_precond;
 
 typedef struct {
@@ -70,7 +73,7 @@ typedef struct {
   double inner_tol;    /* mixed precision: relative residual reduction per inner solve
                           (default 1e-4); FP64 derives its inner target from tol */
   int precond;         /* vdp_precond (default VDP_PRECOND_JACOBI) */
-  int cheb_degree;     /* polynomial degree for VDP_PRECOND_CHEB (default 4) */
+  int cheb_degree;     /* polynomial terms for VDP_PRECOND_CHEB, 1..16 (default 4) */
   int use_guess;       /* 1: p on entry to vdp_solve is the initial guess; 0: start from p = 0 */
   void *stream;        /* cudaStream_t for all work of this context (default NULL) */
   int stencil;         /* stencil sweep: 0 = direct register march (default), 1 = TMA-staged

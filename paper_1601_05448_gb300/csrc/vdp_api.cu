@@ -101,6 +101,7 @@ void free_ctx(vdp_ctx* c) {
   cudaSetDevice(c->device);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   void* bufs[] = {c->bx, c->by, c->bz, c->sinv, c->sx, c->sy, c->sz, c->sd, c->x, c->r, c->d0, c->d1,
+                  c->za, c->zb, c->dch,
                   c->q, c->part, c->ticket, c->st, c->desc, c->units, c->flag, c->stage_a,
                   c->stage_b};
   for (void* b : bufs)
@@ -157,6 +158,17 @@ int configure_layout(vdp_ctx* c, int prec) {
   d.d0 = c->d0;
   d.d1 = c->d1;
   d.q = c->q;
+  d.za = c->za;
+  d.zb = c->zb;
+  d.dch = c->dch;
+  // polynomial preconditioner: Chebyshev on [b / kChebRange, b], b = 2 >= the largest
+  // eigenvalue of the unit-diagonal operator
+  d.cheb_k = c->opts.precond == VDP_PRECOND_CHEB ? c->opts.cheb_degree : 1;
+  {
+    const double b = 2.0, a = b / kChebRange;
+    d.cheb_theta = 0.5 * (b + a);
+    d.cheb_delta = 0.5 * (b - a);
+  }
   d.part = c->part;
   d.ticket = c->ticket;
   d.st = c->st;
@@ -246,7 +258,7 @@ int vdp_create(int nx, int ny, int nz, double L, vdp_ctx** out) {
   double** f64[] = {&c->bx, &c->by, &c->bz, &c->sinv};
   for (double** b : f64)
     if (e == cudaSuccess) e = cudaMalloc((void**)b, bytes);
-  void** vv[] = {&c->sx, &c->sy, &c->sz, &c->x, &c->r, &c->d0, &c->d1, &c->q};
+  void** vv[] = {&c->sx, &c->sy, &c->sz, &c->x, &c->r, &c->d0, &c->d1, &c->q, &c->za, &c->zb, &c->dch};
   if (e == cudaSuccess) e = cudaMalloc(&c->sd, sizeof(uint16_t) * (size_t)c->n);
   for (void** b : vv)
     if (e == cudaSuccess) e = cudaMalloc(b, bytes);
@@ -285,6 +297,8 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
   if (o->precision < VDP_FP64 || o->precision > VDP_MIXED_BF16) return VDP_EINVAL;
   if (o->max_iter < 1 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return VDP_EINVAL;
   if (o->precond != VDP_PRECOND_JACOBI && o->precond != VDP_PRECOND_CHEB) return VDP_EINVAL;
+  if (o->precond == VDP_PRECOND_CHEB && (o->cheb_degree < 1 || o->cheb_degree > 16 || o->stencil != 0))
+    return VDP_EINVAL;
   if (o->tile_y < 0 || o->units < 0 || o->stages < 0 || o->threads < 0 || o->steps_per_sync < 0 ||
       o->stencil < 0 || o->stencil > 1)
     return VDP_EINVAL;

@@ -10,6 +10,8 @@
 
 namespace vdp {
 
+constexpr double kChebRange = 20.0;  // Chebyshev interval [2 / kChebRange, 2]
+
 int cuda_fail(cudaError_t e, const char* where);  // records the message, maps to a vdp_status
 bool is_device_ptr(const void* p);
 
@@ -34,6 +36,7 @@ struct vdp_ctx {
   // inner-precision data (sized for FP64, reinterpreted for FP32 / BF16)
   void *sx = nullptr, *sy = nullptr, *sz = nullptr, *sd = nullptr;
   void *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr, *q = nullptr;
+  void *za = nullptr, *zb = nullptr, *dch = nullptr;  // Chebyshev preconditioner
   int scaled_prec = -1;            // precision the scaled coefficients were built for
   bool has_density = false;
   // bookkeeping

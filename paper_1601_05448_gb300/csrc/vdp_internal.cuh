@@ -26,7 +26,8 @@ enum Phase : int {
   PH_UPDATE = 3,   // x += alpha d; rt -= alpha q; <rt, rt>
   PH_CORRECT = 4,  // p -= D^-1/2 x   (refinement step of the outer FP64 loop)
   PH_FINAL = 5,    // p -= <p>  (gauge)
-  PH_DONE = 6
+  PH_CHEB = 6,     // one Chebyshev sweep of the polynomial preconditioner z = P(At) rt
+  PH_DONE = 7
 };
 
 enum Prec : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_MIXED_BF16 = 2 };
@@ -53,6 +54,9 @@ struct InstState {
   int use_guess;
   int precision;
   int fault;           // a unit's bounded wait expired (reported as VDP_ETIMEOUT)
+  int cheb_j;          // Chebyshev sweep index (1 .. cheb_k - 1)
+  int pad1;
+  double rz;           // <rt, z> (preconditioned inner product; = <rt, rt> for Jacobi)
   double tol;          // requested relative residual
   double inner_tol;    // mixed: minimum relative reduction per inner solve
   double mu_f;         // <f>
@@ -98,6 +102,13 @@ struct InstDesc {
   void* d0;            // search direction, double buffered
   void* d1;
   void* q;             // At d
+  void* za;            // Chebyshev: z iterates (double buffered; the final z is in za) and
+  void* zb;            //   the Chebyshev correction d_j (null without the polynomial)
+  void* dch;
+  int cheb_k;          // polynomial preconditioner: number of terms (1 = Jacobi only)
+  int pad2;
+  double cheb_theta;   // Chebyshev interval [a, b]: theta = (b + a) / 2, delta = (b - a) / 2
+  double cheb_delta;
   double* part;        // kSlots x nunits partial sums
   unsigned int* ticket;
   InstState* st;

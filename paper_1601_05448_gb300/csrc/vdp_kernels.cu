@@ -357,9 +357,11 @@ __device__ void transition(const InstDesc& I, volatile InstState* st, int phase,
         st->rr64_prev = rr64;
         st->rr = rrt;
         st->rr0 = rrt;
+        st->rz = rrt;
         st->beta = 0.0;
         st->inner_iters = 0;
-        st->phase = PH_STENCIL;
+        st->cheb_j = 1;
+        st->phase = I.cheb_k > 1 ? PH_CHEB : PH_STENCIL;
       }
       st->rr64 = rr64;
       break;
@@ -367,7 +369,7 @@ __device__ void transition(const InstDesc& I, volatile InstState* st, int phase,
     case PH_STENCIL: {
       const double dq = S[0];
       if (dq > 0.0 && isfinite(dq)) {
-        st->alpha = st->rr / dq;
+        st->alpha = (I.cheb_k > 1 ? st->rz : st->rr) / dq;
         st->phase = PH_UPDATE;
       } else if (st->inner_iters > 0) {
         // loss of curvature at the end of an inner solve: hand the iterate to the refinement
@@ -390,12 +392,43 @@ __device__ void transition(const InstDesc& I, volatile InstState* st, int phase,
                  st->inner_iters >= st->inner_max) {
         st->inner_ratio = sqrt(rn / st->rr0);
         st->phase = PH_CORRECT;
+      } else if (I.cheb_k > 1) {  // preconditioned: z = P(At) rt first, then beta from <rt, z>
+        st->rr = rn;
+        st->cheb_j = 1;
+        st->phase = PH_CHEB;
       } else {
         st->beta = rn / st->rr;
         st->rr = rn;
+        st->rz = rn;
         st->parity ^= 1;
         st->phase = PH_STENCIL;
       }
+      break;
+    }
+    case PH_CHEB: {
+      if (st->cheb_j < I.cheb_k - 1) {
+        st->cheb_j += 1;
+        break;
+      }
+      const double rz = S[0];
+      if (!(rz > 0.0) || !isfinite(rz)) {  // the polynomial must keep the preconditioner SPD
+        if (st->inner_iters > 0) {
+          st->inner_ratio = sqrt(st->rr / st->rr0);
+          st->phase = PH_CORRECT;
+        } else {
+          st->status = 5;
+          st->phase = PH_FINAL;
+        }
+        break;
+      }
+      if (st->inner_iters == 0) {
+        st->beta = 0.0;
+      } else {
+        st->beta = rz / st->rz;
+        st->parity ^= 1;
+      }
+      st->rz = rz;
+      st->phase = PH_STENCIL;
       break;
     }
     case PH_CORRECT:
@@ -746,7 +779,13 @@ __device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, T& par
 // independent loads in flight.  Measured on the 256^3 FP32 sweep this runs at about 90 % of the
 // HBM copy bandwidth, against about 50 % for the TMA-staged variant above, whose per-plane block
 // barrier serialises the copy latency with the arithmetic.
-template <class T, class BT>
+//
+// CHEB = true: one sweep j of the Chebyshev polynomial preconditioner instead (same march, the
+// marched field is the Chebyshev iterate z_j, z_1 = rt / theta formed on the fly):
+//   d_j = rho_j rho_{j-1} d_{j-1} + (2 rho_j / delta) (rt - At z_j),  z_{j+1} = z_j + d_j,
+// with rho_0 = 1 / sigma, rho_j = 1 / (2 sigma - rho_{j-1}), sigma = theta / delta, d_0 = z_1;
+// the last sweep also sums <rt, z>.
+template <class T, class BT, bool CHEB>
 __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int unit, T& part) {
   constexpr int V = VecW<T>::V;
   constexpr bool kDiag = CoefTraits<BT>::kDiag;
@@ -763,12 +802,37 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
   const int lane = threadIdx.x & 31;
   const bool row_start = x0 == 0, row_end = x0 + V == nx;
   const int xl = row_start ? nx - 1 : x0 - 1, xr = row_end ? 0 : x0 + V;
-  const T beta = (T)st->beta;
-  const bool use_old = st->inner_iters > 0;
+  // STENCIL: marched field d = src + beta d_old, src = rt (Jacobi) or the final Chebyshev z
+  // CHEB:    marched field z_j = src * scale, src = rt / z buffer, scale = 1 / theta or 1
+  const int cj = CHEB ? st->cheb_j : 0;
+  const bool last = CHEB && cj == I.cheb_k - 1;
+  T beta = (T)st->beta, scale = 1, c1 = 0, c2 = 0;
+  bool use_old = st->inner_iters > 0;
   const T* rt = static_cast<const T*>(I.r);
+  const T* src = I.cheb_k > 1 ? static_cast<const T*>(I.za) : rt;
   const T* dold = static_cast<const T*>(st->parity ? I.d1 : I.d0);
   T* dnew = static_cast<T*>(st->parity ? I.d0 : I.d1);
   T* q = static_cast<T*>(I.q);
+  T* zout = nullptr;
+  T* dch = static_cast<T*>(I.dch);
+  if (CHEB) {
+    // sweep j reads z_j from buffer (k - j) % 2 and writes z_{j+1} to (k - 1 - j) % 2, so the
+    // last sweep (j = k - 1) leaves z in za
+    const int k = I.cheb_k;
+    src = cj == 1 ? rt : static_cast<const T*>(((k - cj) & 1) ? I.zb : I.za);
+    zout = static_cast<T*>(((k - 1 - cj) & 1) ? I.zb : I.za);
+    scale = cj == 1 ? (T)(1.0 / I.cheb_theta) : (T)1;
+    const double sigma = I.cheb_theta / I.cheb_delta;
+    double rp = 1.0 / sigma, r = rp;
+    for (int i = 1; i <= cj; ++i) {
+      rp = r;
+      r = 1.0 / (2.0 * sigma - rp);
+    }
+    c1 = (T)(r * rp);                  // rho_j rho_{j-1}
+    c2 = (T)(2.0 * r / I.cheb_delta);  // 2 rho_j / delta
+    use_old = false;
+    beta = 0;
+  }
   const BT* sx = static_cast<const BT*>(I.sx);
   const BT* sy = static_cast<const BT*>(I.sy);
   const BT* sz = static_cast<const BT*>(I.sz);
@@ -781,16 +845,22 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
     return (long long)(z < 0 ? z + nz : (z >= nz ? z - nz : z)) * plane + cell0;
   };
   // all loads of a plane are issued together (non-coherent read-only path), then used
-  auto dvec = [&](long long o, T (&d)[V]) {  // d = rt + beta d_old, V cells at offset o
-    LdgIO<T, V>::ld(rt + o, d);
-    if (use_old) {
+  auto dvec = [&](long long o, T (&d)[V]) {  // marched field, V cells at offset o
+    LdgIO<T, V>::ld(src + o, d);
+    if (CHEB) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) d[k] *= scale;
+    } else if (use_old) {
       T b[V];
       LdgIO<T, V>::ld(dold + o, b);
 #pragma unroll
       for (int k = 0; k < V; ++k) d[k] = fma(beta, b[k], d[k]);
     }
   };
-  auto d1 = [&](long long o) -> T { return use_old ? fma(beta, __ldg(dold + o), __ldg(rt + o)) : __ldg(rt + o); };
+  auto d1 = [&](long long o) -> T {
+    if (CHEB) return __ldg(src + o) * scale;
+    return use_old ? fma(beta, __ldg(dold + o), __ldg(src + o)) : __ldg(src + o);
+  };
 
   T dm[V], dc[V], dp[V];
   if (z0 < z1) {
@@ -833,9 +903,28 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
       a = fma(-bz[k], dm[k], a);
       a = fma(-bzp[k], dp[k], a);
       qv[k] = a;
-      sum[k] = fma(dc[k], a, sum[k]);
+      if (!CHEB) sum[k] = fma(dc[k], a, sum[k]);
     }
-    if (active) {
+    if (CHEB) {
+      T r[V], dprev[V], zn[V], dn[V];
+      LdgIO<T, V>::ld(rt + oc, r);
+      if (cj == 1) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) dprev[k] = dc[k];  // d_0 = z_1
+      } else {
+        LdgIO<T, V>::ld(dch + oc, dprev);
+      }
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        dn[k] = fma(c1, dprev[k], c2 * (r[k] - qv[k]));
+        zn[k] = dc[k] + dn[k];
+        if (last) sum[k] = fma(r[k], zn[k], sum[k]);
+      }
+      if (active) {
+        VecIO<T, V>::st(zout + oc, zn);
+        if (!last) VecIO<T, V>::st(dch + oc, dn);
+      }
+    } else if (active) {
       VecIO<T, V>::st(dnew + oc, dc);
       VecIO<T, V>::st(q + oc, qv);
     }
@@ -1037,7 +1126,8 @@ __device__ __forceinline__ int phase_slots(int phase) {
     case PH_MEANF: return 2;
     case PH_RES64: return 4;
     case PH_STENCIL:
-    case PH_UPDATE: return 1;
+    case PH_UPDATE:
+    case PH_CHEB: return 1;
     default: return 0;
   }
 }
@@ -1071,6 +1161,7 @@ __device__ __forceinline__ InstState snapshot(const InstState* st) {
   s.alpha = __ldcg(&st->alpha);
   s.beta = __ldcg(&st->beta);
   s.sum_p = __ldcg(&st->sum_p);
+  s.cheb_j = __ldcg(&st->cheb_j);
   return s;
 }
 
@@ -1081,8 +1172,9 @@ __device__ __forceinline__ void stencil_kind_unit(const InstDesc& I, int unit,
                                                   unsigned char* smem_raw) {
   InstState* st = I.st;
   const int phase = __ldcg(&st->phase);  // one load decides whether this unit has work
-  if (phase != PH_RES64 && phase != PH_STENCIL) return;
-  if ((WHICH == 1 && phase != PH_STENCIL) || (WHICH == 2 && phase != PH_RES64)) return;
+  if (phase != PH_RES64 && phase != PH_STENCIL && phase != PH_CHEB) return;
+  if ((WHICH == 1 && phase == PH_RES64) || (WHICH == 2 && phase != PH_RES64)) return;
+  if (MODE != 0 && phase == PH_CHEB) return;  // the polynomial runs in the direct form only
   const InstState sn = snapshot(st);
   if (WHICH != 1 && phase == PH_RES64) {
     double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
@@ -1093,8 +1185,10 @@ __device__ __forceinline__ void stencil_kind_unit(const InstDesc& I, int unit,
     store_partials<kSlots, double>(acc, I.part, I.nunits, unit);
   } else if (WHICH != 2) {
     T part[1] = {0};
-    if (MODE == 0)
-      sweep_stencil_direct<T, BT>(I, &sn, unit, part[0]);
+    if (MODE == 0 && phase == PH_CHEB)
+      sweep_stencil_direct<T, BT, true>(I, &sn, unit, part[0]);
+    else if (MODE == 0)
+      sweep_stencil_direct<T, BT, false>(I, &sn, unit, part[0]);
     else
       sweep_stencil<T, BT>(I, st, unit, part[0], smem_raw);
     store_partials<1, T>(part, I.part, I.nunits, unit);

@@ -179,3 +179,24 @@ def test_iteration_cap_reports_notconv():
     assert st.status == vdp.VDP_ENOTCONV and st.iters == 5
     pc = p.cpu().numpy()
     assert np.isfinite(pc).all() and abs(float(pc.mean())) < 1e-12 * float(np.abs(pc).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_bf16"])
+@pytest.mark.parametrize("degree", [2, 4, 8])
+def test_chebyshev_preconditioner_matches_oracle(precision, degree):
+    prob = V.hotspot_problem(48, seed=61, nspots=int(round(20000 * 48 ** 3 / 256 ** 3)), target_ratio=6.0)
+    tol = 1e-10 if precision == "fp64" else 1e-9
+    p_j, st_j = gpu_solve(prob, precision, tol=tol)
+    p_c, st_c = gpu_solve(prob, precision, tol=tol, precond=vdp.VDP_PRECOND_CHEB, cheb_degree=degree)
+    ref = oracle_solution(prob, "hot48")
+    print(f"cheb {precision} k={degree}: iters {st_j.iters} -> {st_c.iters}, sweeps {st_j.sweeps} -> {st_c.sweeps}")
+    assert st_c.ok and st_c.rel_res <= tol
+    assert rel(p_c, ref) <= (1e-9 if precision == "fp64" else 1e-8)
+    assert st_c.iters < st_j.iters  # a polynomial preconditioner cuts the Krylov iterations
+
+
+def test_chebyshev_degree_one_is_jacobi():
+    prob = V.smooth_problem((24, 24, 32), seed=62)
+    p_j, st_j = gpu_solve(prob, "fp64", tol=1e-10)
+    p_c, st_c = gpu_solve(prob, "fp64", tol=1e-10, precond=vdp.VDP_PRECOND_CHEB, cheb_degree=1)
+    assert st_c.iters == st_j.iters and rel(p_c, p_j) < 1e-12
