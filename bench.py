@@ -35,22 +35,96 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # FP64 vector peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
-# Algorithmic bytes and flops per cell of one sweep (inner type T bytes, coefficient bytes B):
-#   stencil: read rt, d_old, 3 coefficients; write d, q          -> 4T + 3B + (BF16: diag B)
-#   update : read x, d, q, rt; write x, rt  (x not read on the first inner iteration)  -> 6T
-#   res64  : read p, f, sinv, 3 FP64 coefficients; write rt        -> 6*8 + T
-#   correct: read p, sinv, x; write p                              -> 24 + T
-#   meanf  : read f, write p                                        -> 16;  final: 16
-# flops per cell and inner iteration: 8 FMA in the stencil sweep (d, six faces, <d,q>) and 3 FMA
-# in the update sweep (x, rt, <rt,rt>): 22 flop.
+# Algorithmic bytes and flops per cell of one launch of each sweep kind (inner type T bytes,
+# coefficient type B bytes; the BF16 ablation also reads a per-cell diagonal correction):
+#   stencil: read rt (or z), d_old, 3 coefficients; write d, q           -> 4T + 3B (+B)
+#            d = z + beta d_old (1 FMA), q = d - sum_6 b d_nb (6 FMA), <d,q> (1 FMA) -> 16 flop
+#   update : read x, d, q, rt; write x, rt                                -> 6T;  3 FMA -> 6 flop
+#   res64  : read p, f, sinv, 3 FP64 coefficients; write rt                -> 48 + T
+#            6 x (difference + FMA), f - Ap, scaling, |r|^2                -> 22 flop
+#   cheb   : sweep 1 reads rt and 3 coefficients, writes z, dz           -> 3T + 3B (+B)
+#            later sweeps also read z and dz                              -> 5T + 3B (+B); 18 flop
+#   other  : rhs mean removal, refinement correction, gauge: not in the roofline
 SIZES = {"fp64": (8, 8, False), "mixed": (4, 4, False), "mixed_bf16": (4, 2, True)}
+KERNEL_NAMES = {"res64": "k_res64_direct", "stencil": "k_stencil_direct", "cheb": "k_stencil_direct",
+                "update": "k_flat", "other": "k_flat"}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
+# kernel at this precision and grid (profiles/k_stencil_direct_fp64_192.md and
+# profiles/k_stencil_direct_mixed_192.md: 192^3, third solve; 256^3 entries scaled by the cell
+# count 256^3 / 192^3).  A changed kernel drops its entries until it is re-captured.
+_SCALE_256 = (256 / 192) ** 3
+_TRAFFIC_192 = {("fp64", "stencil"): 284.913664e6 + 92.214784e6, ("fp64", "update"): 227.577344e6 + 70.953472e6,
+                ("mixed", "stencil"): 142.582016e6 + 36.517376e6, ("mixed", "update"): 113.334272e6 + 15.742720e6}
+TRAFFIC = {(p, k, 192): v for (p, k), v in _TRAFFIC_192.items()}
+TRAFFIC.update({(p, k, 256): v * _SCALE_256 for (p, k), v in _TRAFFIC_192.items()})
+
+
+def sweep_cost(prec: str, kind: str, cheb_k: int = 1):
+    """(bytes, flops) per cell of one launch of sweep `kind`, or None."""
+    T, B, diag = SIZES[prec]
+    Bd = B if diag else 0
+    if kind == "stencil":
+        return 4 * T + 3 * B + Bd, 16.0 + (2.0 if diag else 0.0)
+    if kind == "update":
+        return 6 * T, 6.0
+    if kind == "res64":
+        return 48 + T, 22.0
+    if kind == "cheb":
+        k = max(cheb_k - 1, 1)
+        return ((3 * T + 3 * B + Bd) + (k - 1) * (5 * T + 3 * B + Bd)) / k, 18.0
+    return None
 
 
 def algorithmic(prec: str, ncell: int, iters: int, outer: int):
+    """Algorithmic bytes and flops of a whole Jacobi-preconditioned solve."""
     T, B, diag = SIZES[prec]
-    per_iter = (4 * T + 3 * B + (B if diag else 0)) + 6 * T
+    per_iter = sweep_cost(prec, "stencil")[0] + sweep_cost(prec, "update")[0]
     total = iters * per_iter + outer * (48 + T) + max(outer - 1, 0) * (24 + T) + 32
     return total * ncell, 22.0 * iters * ncell
+
+
+def kernel_table(prec: str, ncell: int, kinds: dict, peaks: dict, grid: int, cheb_k: int = 1):
+    """Per sweep kind: launches, mean/min duration (CUDA events around each launch), share of the
+    summed kernel time, algorithmic GB/s and TFLOP/s and their fractions of the roofs."""
+    total = sum(k["ms"] for k in kinds.values()) or 1.0
+    out = {}
+    for name, k in kinds.items():
+        if not k["launches"]:
+            continue
+        row = {"kernel": KERNEL_NAMES[name], "launches": k["launches"], "mean_us": 1e3 * k["ms_mean"],
+               "min_us": 1e3 * k["ms_min"], "share": k["ms"] / total}
+        cost = sweep_cost(prec, name, cheb_k)
+        if cost is not None:
+            t = k["ms_mean"] / 1e3
+            row["alg_bytes_per_launch"] = cost[0] * ncell
+            row["gbs"] = cost[0] * ncell / t / 1e9
+            row["hbm_frac"] = row["gbs"] / peaks["hbm_gbs"]
+            row["tflops"] = cost[1] * ncell / t / 1e12
+            if prec == "fp64":
+                row["fp64_alu_frac"] = row["tflops"] / FP64_PEAK_TFLOPS
+            row["traffic"] = TRAFFIC.get((prec, name, grid))
+        out[name] = row
+    return out
+
+
+def roofline(prec: str, table: dict, peaks: dict):
+    """The roofline object of the dominant sweep kind (largest share of kernel time)."""
+    name = max((n for n in table if "gbs" in table[n]), key=lambda n: table[n]["share"])
+    row = table[name]
+    t_hbm = row["alg_bytes_per_launch"] / (peaks["hbm_gbs"] * 1e9)
+    t_alu = row["tflops"] * row["mean_us"] * 1e-6 / FP64_PEAK_TFLOPS if prec == "fp64" else 0.0
+    if t_alu > t_hbm:  # FP64 arithmetic needs more time than the bytes: the FP64 pipe bounds it
+        roof = {"bound": "alu", "achieved": row["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": row["tflops"] / FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": row["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": row["gbs"] / peaks["hbm_gbs"], "peak_source": peaks["source"]}
+    roof.update({"traffic": row["traffic"], "kernel": row["kernel"], "sweep": name, "precision": prec,
+                 "launches": row["launches"], "mean_us": row["mean_us"], "share": row["share"],
+                 "timing": "CUDA events around each launch of an instrumented solve of the same workload "
+                           "on the same stream and solver, after the timed region"})
+    return roof
 
 
 def load_peaks():
@@ -208,11 +282,11 @@ def run_batch(torch, vdp, dev, probs, persistent=True):
     for shape, pr in sizes.items():  # tune each distinct grid once (cached)
         nz, ny, nx = shape
         tune.tune(nx, ny, nz, pr.L, torch.from_numpy(pr.rho).to(dev), torch.from_numpy(pr.f).to(dev), "mixed",
-                  iters=30)
+                  iters=30, batchable=True)
     solvers, fs, ps = [], [], []
     for pr in probs:
         nz, ny, nx = pr.shape
-        opts = tune.cached_options(nx, ny, nz, "mixed") or {}
+        opts = tune.cached_options(nx, ny, nz, "mixed", batchable=True) or {}
         s = vdp.Solver(nx, ny, nz, pr.L, precision="mixed", **opts)
         s.set_density(torch.from_numpy(pr.rho).to(dev))
         solvers.append(s)
@@ -239,7 +313,7 @@ def run_batch(torch, vdp, dev, probs, persistent=True):
                "gdof_iter_per_s": dofit / el / 1e9, "persistent_launch": bool(persistent), "runs": runs + 1,
                "all_ok": all(st.ok for st in stats), "max_rel_res": max(st.rel_res for st in stats),
                "sizes": sorted({pr.shape[0] for pr in probs}), "tuned_layouts": {str(k[0]): tune.cached_options(
-                   k[2], k[1], k[0], "mixed") for k in sizes}}
+                   k[2], k[1], k[0], "mixed", batchable=True) for k in sizes}}
     for s in solvers:
         s.close()
     return out
@@ -271,6 +345,11 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=10, help="oracle iterations per reference-arm sample")
     ap.add_argument("--no-extras", action="store_true", help="skip mixed paths, e2e, batch, serving, CPU baseline")
     ap.add_argument("--serve-requests", type=int, default=200, help="requests of the serving stream")
+    ap.add_argument("--grid", type=int, default=256,
+                    help="grid size of the main workload (256 = the benchmark; smaller grids keep the same "
+                         "recipe with hot spots scaled by volume, for profiling small cases)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_bf16"],
+                    help="precision of the main workload (fp64 = the benchmark)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -294,14 +373,24 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
 
-    prob = V.config1()
+    if args.grid == 256:
+        prob = V.config1()
+    else:
+        n = args.grid
+        prob = V.hotspot_problem(n, seed=2, nspots=int(round(20000 * n ** 3 / 256 ** 3)), tol=1e-10,
+                                 target_ratio=4.0)
+    if args.precision != "fp64":
+        prob.tol = 1e-8
+    workload = WORKLOAD if (args.grid, args.precision) == (256, "fp64") else (
+        f"{args.grid}^3 periodic box L=2pi, rho=T0/T (hot spots scaled by volume, density ratio 4), rhs=div of "
+        f"random |k|<=4 velocity; {args.precision}, relative residual {prob.tol:g} (profiling case)")
     nz, ny, nx = prob.shape
     ncell = nx * ny * nz
     rho = torch.from_numpy(prob.rho).to(dev)
     f = torch.from_numpy(prob.f).to(dev)
     p = torch.empty_like(f)
     stream = torch.cuda.current_stream(dev)
-    solver = vdp.Solver(nx, ny, nz, prob.L, precision="fp64", stream=stream)
+    solver = vdp.Solver(nx, ny, nz, prob.L, precision=args.precision, stream=stream)
     solver.set_density(rho)
 
     def barrier():
@@ -331,33 +420,30 @@ def main():
     iters = stats[-1].iters
     outer = stats[-1].outer_iters
 
-    # roofline of the step kernel (it is every launch in the timed region but the per-solve init)
+    # per-kernel durations: one instrumented solve of the same workload on the same solver and
+    # stream, every launch bracketed by CUDA events
     peaks = load_peaks()
-    b_per_solve, fl_per_solve = algorithmic("fp64", ncell, iters, outer)
-    t_launch = elapsed / launches
-    b_launch = b_per_solve * args.steps / launches
-    f_launch = fl_per_solve * args.steps / launches
-    hbm = {"bound": "hbm", "achieved": b_launch / t_launch / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
-    hbm["frac"] = hbm["achieved"] / hbm["peak"]
-    alu = {"bound": "alu", "achieved": f_launch / t_launch / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
-    alu["frac"] = alu["achieved"] / alu["peak"]
-    # the binding roof is the one that needs more time for the algorithmic work
-    roof = alu if fl_per_solve / (FP64_PEAK_TFLOPS * 1e12) > b_per_solve / (peaks["hbm_gbs"] * 1e9) else hbm
-    roof = dict(roof, traffic=None, kernel="k_step<double,double>", peak_source=peaks["source"] if roof is hbm
-                else "nominal: 152 SM x 2 DFMA/clk x 2.07 GHz")
-    other = hbm if roof["bound"] == "alu" else alu
+    pt = torch.empty_like(f)
+    st_t, kinds = solver.solve_timed(f, pt, prob.tol)
+    assert st_t.iters == iters and torch.equal(pt, p), "instrumented solve differs from the timed solves"
+    table = kernel_table(args.precision, ncell, kinds, peaks, args.grid)
+    roof = roofline(args.precision, table, peaks)
+    b_solve, fl_solve = algorithmic(args.precision, ncell, iters, outer)
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [nx, ny, nz], "tol": prob.tol,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32 inner, f64 outer",
+                                                          "mixed_bf16": "f32 inner (bf16 coefficients), f64 outer"}[
+            args.precision], "data": "synthetic",
+        "config": {"workload": workload, "grid": [nx, ny, nz], "tol": prob.tol,
                    "density_ratio": round(prob.info["ratio"], 4), "l2": "inputs larger than L2 (~1.6 GB working set)",
                    "replicas": world},
         "iterations": iters, "outer_iterations": outer, "rel_res": stats[-1].rel_res,
         "gdof_iter_per_s": ncell * iters * args.steps * world / elapsed / 1e9,
-        "gpu_launches": launches + args.steps,
-        "roofline": roof, "roofline_other": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")},
+        "gpu_launches": launches,
+        "roofline": roof, "kernels": table,
+        "solve_hbm_frac": b_solve * args.steps * world / elapsed / 1e9 / peaks["hbm_gbs"],
         "clocks": clk.summary(),
     }
 
@@ -382,20 +468,25 @@ def main():
         # mixed vs FP64 at equal final accuracy (relative residual 1e-8), same input
         import oracle
         paths = {}
-        for prec in ("fp64", "mixed", "mixed_bf16"):
-            with vdp.Solver(nx, ny, nz, prob.L, precision=prec, stream=stream) as s2:
+        variants = {"fp64": ("fp64", 1), "fp64_cheb2": ("fp64", 2), "mixed": ("mixed", 1),
+                    "mixed_cheb3": ("mixed", 3), "mixed_bf16": ("mixed_bf16", 1), "mixed_bf16_cheb2": ("mixed_bf16", 2)}
+        for label, (prec, k) in variants.items():
+            opts = dict(precond=vdp.VDP_PRECOND_CHEB, cheb_degree=k) if k > 1 else {}
+            with vdp.Solver(nx, ny, nz, prob.L, precision=prec, stream=stream, **opts) as s2:
                 s2.set_density(rho)
                 pp = torch.empty_like(f)
                 s2.solve(f, pp, 1e-8, check=False)
                 ts = [s2.solve(f, pp, 1e-8, check=False) for _ in range(3)]
                 best = min(ts, key=lambda s: s.ms)
-                b, fl = algorithmic(prec, ncell, best.iters, best.outer_iters)
-                paths[prec] = {"solves_per_s": 1e3 / best.ms, "ms": best.ms, "iters": best.iters,
-                               "outer": best.outer_iters, "status": vdp.vdp_strerror(best.status),
-                               "rel_res": best.rel_res,
-                               "hbm_frac": b / (best.ms / 1e3) / 1e9 / peaks["hbm_gbs"],
-                               "oracle_rel_res": oracle.relative_residual(prob.rho, prob.L, prob.f,
-                                                                          pp.cpu().numpy())}
+                _, kk = s2.solve_timed(f, pp, 1e-8, check=False)
+                tab = kernel_table(prec, ncell, kk, peaks, args.grid, cheb_k=k)
+                paths[label] = {"precision": prec, "cheb_degree": k, "solves_per_s": 1e3 / best.ms, "ms": best.ms,
+                                "iters": best.iters, "outer": best.outer_iters, "sweeps": best.sweeps,
+                                "status": vdp.vdp_strerror(best.status), "rel_res": best.rel_res,
+                                "oracle_rel_res": oracle.relative_residual(prob.rho, prob.L, prob.f,
+                                                                           pp.cpu().numpy()),
+                                "kernels": {n: {x: r[x] for x in ("mean_us", "share", "gbs", "hbm_frac")
+                                                if x in r} for n, r in tab.items()}}
         line["mixed_vs_fp64_at_1e-8"] = paths
         if batch_probs is not None:
             line["batch"] = run_batch(torch, vdp, dev, batch_probs)
@@ -404,7 +495,7 @@ def main():
                                            if k in ("seconds", "solves_per_s", "gdof_iter_per_s", "all_ok")}
         if serve_pool is not None:
             line["serving"] = run_serving(torch, vdp, dev, serve_pool, args.serve_requests)
-        if rank == 0:
+        if rank == 0 and (args.grid, args.precision) == (256, "fp64"):
             try:
                 line["cpu_baseline"] = cpu_baseline(prob)
             except Exception as e:  # the stored iteration count is missing

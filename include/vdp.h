@@ -153,6 +153,37 @@ int vdp_version(void);
 int vdp_apply(vdp_ctx *ctx, const double *p, double *out);
 
 /* ------------------------------------------------------------------------------------------ */
+/* Per-kernel timing (instrumentation; the paper has no counterpart).                          */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Sweep kinds timed by vdp_solve_timed, by the phase of the method the launch advances. */
+enum {
+  VDP_SWEEP_RES64 = 0,   /* FP64 residual r = f - A p (refinement step, Eq. Pois operator)    */
+  VDP_SWEEP_STENCIL = 1, /* search direction + stencil apply + <d, q> (one per Krylov iter.)  */
+  VDP_SWEEP_CHEB = 2,    /* one Chebyshev preconditioner sweep (precond = VDP_PRECOND_CHEB)   */
+  VDP_SWEEP_UPDATE = 3,  /* x, r updates + <r, r> (one per Krylov iteration)                  */
+  VDP_SWEEP_OTHER = 4,   /* rhs mean removal, refinement correction p -= ..., final gauge     */
+  VDP_SWEEP_KINDS = 5
+};
+
+typedef struct {
+  int launches[VDP_SWEEP_KINDS];  /* kernel launches of each kind in the solve               */
+  double ms[VDP_SWEEP_KINDS];     /* their summed durations (CUDA events around each launch) */
+  double ms_min[VDP_SWEEP_KINDS]; /* shortest single launch (0 when there was none)          */
+} vdp_sweep_times;
+
+/*
+ * vdp_solve with every kernel launch timed on its own.  Instead of replaying a CUDA graph the
+ * host reads the solve's state before each launch and launches only the kernel the current
+ * phase needs, with a CUDA event recorded on the context's stream before and after it.  The
+ * kernels, their launch configuration and the order of all arithmetic are those of vdp_solve,
+ * so p, the statistics (except ms, which here includes the host round trips) and the iteration
+ * counts are bitwise the same; only the gaps between launches grow.  rhs and p: device
+ * pointers (VDP_EINVAL otherwise); times: output, required.  Meant for measurement, not speed.
+ */
+int vdp_solve_timed(vdp_ctx *ctx, const double *rhs, double *p, double tol, vdp_sweep_times *times);
+
+/* ------------------------------------------------------------------------------------------ */
 /* Batches: many independent solves advanced together (continuous batching).                   */
 /* ------------------------------------------------------------------------------------------ */
 

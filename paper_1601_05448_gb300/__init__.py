@@ -51,6 +51,15 @@ class vdp_stats(ctypes.Structure):
                 ("sweeps", ctypes.c_int), ("launches", ctypes.c_int)]
 
 
+VDP_SWEEP_RES64, VDP_SWEEP_STENCIL, VDP_SWEEP_CHEB, VDP_SWEEP_UPDATE, VDP_SWEEP_OTHER, VDP_SWEEP_KINDS = range(6)
+SWEEP_NAMES = ("res64", "stencil", "cheb", "update", "other")
+
+
+class vdp_sweep_times(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int * VDP_SWEEP_KINDS), ("ms", ctypes.c_double * VDP_SWEEP_KINDS),
+                ("ms_min", ctypes.c_double * VDP_SWEEP_KINDS)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -77,6 +86,7 @@ _SIGS = {
     "vdp_batch_done": (ctypes.c_int, [_P, _P]),
     "vdp_batch_remove": (ctypes.c_int, [_P, _P]),
     "vdp_batch_size": (ctypes.c_int, [_P]),
+    "vdp_solve_timed": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.POINTER(vdp_sweep_times)]),
     "vdp_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                          ctypes.c_double, ctypes.c_int, _P, ctypes.POINTER(vdp_stats)]),
 }
@@ -165,6 +175,13 @@ def vdp_version() -> int:
 
 def vdp_apply(ctx: int, p, out) -> int:
     return load().vdp_apply(ctx, _ptr(p), _ptr(out, writable=True))
+
+
+def vdp_solve_timed(ctx: int, rhs, p, tol: float):
+    """vdp_solve with each kernel launch timed alone; returns (status, vdp_sweep_times)."""
+    t = vdp_sweep_times()
+    st = load().vdp_solve_timed(ctx, _ptr(rhs), _ptr(p, writable=True), float(tol), ctypes.byref(t))
+    return st, t
 
 
 def vdp_solve_noalloc(nx: int, ny: int, nz: int, L: float, rho, rhs, p, tol: float, precision: int = VDP_FP64,
@@ -322,6 +339,23 @@ class Solver:
         if st != VDP_OK and (check or st not in (VDP_ENOTCONV, VDP_EBREAKDOWN)):
             raise VdpError(st, "vdp_solve")
         return out
+
+    def solve_timed(self, rhs, p, tol: float, check: bool = True):
+        """The solve with every kernel launch timed on its own (device tensors).  Returns
+        (Stats, {kind: {"launches", "ms", "ms_min", "ms_mean"}}) with kind in SWEEP_NAMES."""
+        self._check(rhs, "rhs")
+        self._check(p, "p")
+        st, t = vdp_solve_timed(self.ctx, rhs, p, tol)
+        s = vdp_get_stats(self.ctx)
+        out = Stats(s.status, s.iters, s.outer_iters, s.rel_res, s.rhs_mean, s.ms, s.sweeps, s.launches)
+        if st != VDP_OK and (check or st not in (VDP_ENOTCONV, VDP_EBREAKDOWN)):
+            raise VdpError(st, "vdp_solve_timed")
+        kinds = {}
+        for i, name in enumerate(SWEEP_NAMES):
+            n = t.launches[i]
+            kinds[name] = {"launches": n, "ms": t.ms[i], "ms_min": t.ms_min[i],
+                           "ms_mean": t.ms[i] / n if n else 0.0}
+        return out, kinds
 
     def apply(self, p, out) -> None:
         self._check(p, "p")

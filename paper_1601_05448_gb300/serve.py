@@ -113,7 +113,7 @@ class Server:
         opts = {}
         if self.tuned:
             from .tune import cached_options
-            opts = cached_options(nx, ny, nz, self.precision) or {}
+            opts = cached_options(nx, ny, nz, self.precision, batchable=True) or {}
         try:
             s = Solver(nx, ny, nz, L, precision=self.precision, **opts)
         except VdpError:

@@ -37,8 +37,8 @@ def _device_name() -> str:
         return "unknown"
 
 
-def _key(nx, ny, nz, precision) -> str:
-    return f"{_device_name()}|{nx}x{ny}x{nz}|{precision}"
+def _key(nx, ny, nz, precision, batchable=False) -> str:
+    return f"{_device_name()}|{nx}x{ny}x{nz}|{precision}" + ("|batch" if batchable else "")
 
 
 def _load_cache() -> dict:
@@ -61,9 +61,9 @@ def _store(key: str, entry: dict) -> None:
         os.replace(tmp, path)
 
 
-def cached_options(nx: int, ny: int, nz: int, precision: str):
-    """Tuned options for this grid and precision, or None."""
-    e = _load_cache().get(_key(nx, ny, nz, precision))
+def cached_options(nx: int, ny: int, nz: int, precision: str, batchable: bool = False):
+    """Tuned options for this grid and precision (batchable: for batch members), or None."""
+    e = _load_cache().get(_key(nx, ny, nz, precision, batchable))
     return dict(e["options"]) if e else None
 
 
@@ -78,12 +78,16 @@ def _direct_threads(nx: int, precision: str):
     return out[:2]
 
 
-def candidates(nx: int, ny: int, nz: int, precision: str):
-    """Candidate option sets (zero = the library's automatic choice)."""
+def candidates(nx: int, ny: int, nz: int, precision: str, batchable: bool = False):
+    """Candidate option sets (zero = the library's automatic choice).  Batch members run the
+    direct stencil sweep and the batch's own launch schedule, so `batchable` keeps only the
+    direct-sweep splits."""
     cands = []
     for t in _direct_threads(nx, precision):
         for units in (0, 608, 1216, 2432):
             cands.append({"stencil": 0, "threads": t, "units": units})
+    if batchable:
+        return cands
     for stages in (4, 6):
         cands.append({"stencil": 1, "stages": stages})
     for sps in (8, 32):
@@ -109,16 +113,17 @@ def time_options(nx, ny, nz, L, rho, f, precision, options, iters=40, reps=2) ->
 
 
 def tune(nx: int, ny: int, nz: int, L: float, rho, f, precision: str = "mixed", iters: int = 40,
-         use_cache: bool = True, verbose: bool = False) -> dict:
-    """Pick the fastest layout for this grid/precision; returns the options (cached)."""
+         use_cache: bool = True, verbose: bool = False, batchable: bool = False) -> dict:
+    """Pick the fastest layout for this grid/precision; returns the options (cached).
+    batchable: only layouts a batch member can use (vdp_batch_add accepts them)."""
     assert precision in PRECISIONS
-    key = _key(nx, ny, nz, precision)
+    key = _key(nx, ny, nz, precision, batchable)
     if use_cache:
         e = _load_cache().get(key)
         if e:
             return dict(e["options"])
     results = []
-    for opt in candidates(nx, ny, nz, precision):
+    for opt in candidates(nx, ny, nz, precision, batchable):
         ms = time_options(nx, ny, nz, L, rho, f, precision, opt, iters=iters)
         results.append((ms, opt))
         if verbose:

@@ -73,3 +73,13 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(vdp, "_lib", None)
     with pytest.raises(vdp.VdpUnavailable):
         vdp.load(str(tmp_path / "nope.so"))
+
+
+def test_batch_tuning_keeps_to_batchable_layouts():
+    from paper_1601_05448_gb300 import tune
+    for n, prec in ((64, "mixed"), (96, "fp64"), (192, "mixed_bf16")):
+        allc = tune.candidates(n, n, n, prec)
+        bc = tune.candidates(n, n, n, prec, batchable=True)
+        assert bc and all(c["stencil"] == 0 and "steps_per_sync" not in c for c in bc)
+        assert any(c["stencil"] == 1 for c in allc)
+        assert tune._key(n, n, n, prec) != tune._key(n, n, n, prec, batchable=True)

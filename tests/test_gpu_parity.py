@@ -200,3 +200,72 @@ def test_chebyshev_degree_one_is_jacobi():
     p_j, st_j = gpu_solve(prob, "fp64", tol=1e-10)
     p_c, st_c = gpu_solve(prob, "fp64", tol=1e-10, precond=vdp.VDP_PRECOND_CHEB, cheb_degree=1)
     assert st_c.iters == st_j.iters and rel(p_c, p_j) < 1e-12
+
+
+@pytest.mark.parametrize("precision,cheb", [("fp64", 0), ("mixed", 0), ("mixed", 3), ("mixed_bf16", 0)])
+def test_timed_solve_is_the_solve(precision, cheb):
+    prob = V.smooth_problem((24, 32, 40), seed=63)
+    nz, ny, nx = prob.shape
+    opts = dict(precond=vdp.VDP_PRECOND_CHEB, cheb_degree=cheb) if cheb else {}
+    rho = torch.from_numpy(prob.rho).to(DEV)
+    f = torch.from_numpy(prob.f).to(DEV)
+    with vdp.Solver(nx, ny, nz, prob.L, precision=precision, **opts) as s:
+        s.set_density(rho)
+        p1, p2 = torch.empty_like(f), torch.empty_like(f)
+        st1 = s.solve(f, p1, 1e-9)
+        st2, kinds = s.solve_timed(f, p2, 1e-9)
+    assert torch.equal(p1, p2)
+    assert (st1.iters, st1.outer_iters, st1.sweeps) == (st2.iters, st2.outer_iters, st2.sweeps)
+    # one stencil and one update launch per Krylov iteration, one residual launch per refinement step
+    assert kinds["stencil"]["launches"] == st2.iters == kinds["update"]["launches"]
+    assert kinds["res64"]["launches"] == st2.outer_iters
+    assert (kinds["cheb"]["launches"] > 0) == bool(cheb)
+    assert sum(k["launches"] for k in kinds.values()) == st2.sweeps
+    for k in kinds.values():
+        assert (k["ms"] > 0) == (k["launches"] > 0) and k["ms_min"] <= k["ms_mean"] + 1e-12
+
+
+_C1 = {}
+
+
+def config1_problem():
+    if "p" not in _C1:
+        _C1["p"] = V.config1()
+    return _C1["p"]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8), ("mixed_bf16", 1e-8)])
+def test_full_size_256_residual_in_oracle_operator(precision, tol):
+    """The 256^3 hot-spot workload in the benchmark's launch configuration: the oracle's own
+    operator must confirm the relative residual of the returned pressure, on every cell; a
+    sample of cells is also checked against the flux form evaluated one cell at a time."""
+    prob = config1_problem()
+    nz, ny, nx = prob.shape
+    stream = torch.cuda.current_stream()
+    rho = torch.from_numpy(prob.rho).to(DEV)
+    f = torch.from_numpy(prob.f).to(DEV)
+    p = torch.empty_like(f)
+    with vdp.Solver(nx, ny, nz, prob.L, precision=precision, stream=stream) as s:
+        s.set_density(rho)
+        st = s.solve(f, p, tol)
+    ph = p.cpu().numpy()
+    rr = oracle.relative_residual(prob.rho, prob.L, prob.f, ph)
+    print(f"256^3 {precision}: iters={st.iters} outer={st.outer_iters} rel_res={st.rel_res:.3e} oracle={rr:.3e}")
+    assert st.ok and st.rel_res <= tol and rr <= 1.01 * tol
+    assert abs(float(ph.mean())) <= 1e-13 * float(np.abs(ph).max())
+    # sampled cells, flux form written out per cell (Eq. Pois with face 1/rho from the
+    # averaged face density): no cell's residual can exceed the L2 norm of the whole residual
+    rng = np.random.default_rng(64)
+    h = prob.L / nx
+    fm = prob.f - prob.f.mean()
+    bound = 1.01 * tol * np.linalg.norm(fm)
+    for _ in range(200):
+        k, j, i = (int(rng.integers(0, n)) for n in prob.shape)
+        acc = 0.0
+        for dk, dj, di in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+            kp, jp, ip = (k + dk) % nz, (j + dj) % ny, (i + di) % nx
+            km, jm, im = (k - dk) % nz, (j - dj) % ny, (i - di) % nx
+            bp = 2.0 / (prob.rho[k, j, i] + prob.rho[kp, jp, ip])
+            bm = 2.0 / (prob.rho[k, j, i] + prob.rho[km, jm, im])
+            acc += (bp * (ph[kp, jp, ip] - ph[k, j, i]) - bm * (ph[k, j, i] - ph[km, jm, im])) / (h * h)
+        assert abs(acc - fm[k, j, i]) <= bound
