@@ -258,7 +258,9 @@ int vdp_create(int nx, int ny, int nz, double L, vdp_ctx** out) {
   double** f64[] = {&c->bx, &c->by, &c->bz, &c->sinv};
   for (double** b : f64)
     if (e == cudaSuccess) e = cudaMalloc((void**)b, bytes);
-  void** vv[] = {&c->sx, &c->sy, &c->sz, &c->x, &c->r, &c->d0, &c->d1, &c->q, &c->za, &c->zb, &c->dch};
+  // (the Chebyshev buffers za, zb, dch are allocated by vdp_set_options when that
+  // preconditioner is first selected)
+  void** vv[] = {&c->sx, &c->sy, &c->sz, &c->x, &c->r, &c->d0, &c->d1, &c->q};
   if (e == cudaSuccess) e = cudaMalloc(&c->sd, sizeof(uint16_t) * (size_t)c->n);
   for (void** b : vv)
     if (e == cudaSuccess) e = cudaMalloc(b, bytes);
@@ -310,6 +312,20 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
   if (choose_layout(c, o->precision, &lay) != VDP_OK) {
     c->opts = old;
     return VDP_EINVAL;
+  }
+  if (o->precond == VDP_PRECOND_CHEB && o->cheb_degree > 1 && !c->za) {
+    const size_t bytes = sizeof(double) * (size_t)c->n;
+    cudaError_t e = cudaMalloc(&c->za, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->zb, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->dch, bytes);
+    if (e != cudaSuccess) {
+      for (void** b : {&c->za, &c->zb, &c->dch}) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+      }
+      c->opts = old;
+      return cuda_fail(e, "vdp_set_options (Chebyshev buffers)");
+    }
   }
   c->stream = (cudaStream_t)o->stream;
   c->layout_dirty = true;
