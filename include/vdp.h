@@ -61,10 +61,18 @@ typedef enum {
 
 typedef enum {
   VDP_PRECOND_JACOBI = 0, /* diagonal (Jacobi) scaling, folded into the operator */
-  VDP_PRECOND_CHEB = 1    /* Jacobi + fixed polynomial: cheb_degree terms of the Chebyshev
+  VDP_PRECOND_CHEB = 1,   /* Jacobi + fixed polynomial: cheb_degree terms of the Chebyshev
                              iteration for the unit-diagonal operator on [0.1, 2] (degree - 1
                              stencil sweeps per Krylov iteration; symmetric positive definite,
                              so plain preconditioned CG applies); direct stencil sweep only */
+  VDP_PRECOND_SPECTRAL = 2 /* the constant-coefficient inverse of the paper's Poisson iteration
+                             (Sec. 3.4): z = (-L_h)^-1 r in unscaled variables, L_h the 7-point
+                             Laplacian with 1/h^2 faces, applied by FP32 FFTs (five passes per
+                             Krylov iteration).  The preconditioned condition number is at most
+                             max(rho)/min(rho) for any grid size.  Each of nx, ny, nz must be one
+                             of 32, 48, 64, 96, 128, 192, 256, 512; direct stencil sweep only;
+                             single solves (not batch members).  Extra memory: about 16 bytes
+                             per cell */
 } vdp_precond;
 
 typedef struct {
@@ -152,6 +160,16 @@ int vdp_version(void);
  */
 int vdp_apply(vdp_ctx *ctx, const double *p, double *out);
 
+/*
+ * out = L_h^-1 g: the constant-coefficient periodic Poisson solve of the paper's iteration
+ * (Sec. 3.4) with the context's grid (L_h: 7-point Laplacian, faces 1/h_d^2; the zero Fourier
+ * mode of g is dropped, so out has zero mean).  Computed with the FP32 FFT passes of the
+ * spectral preconditioner (relative error about 1e-6); g and out are nx*ny*nz doubles, device
+ * pointers, 16-byte aligned, out must not alias g.  Needs no density.  VDP_EINVAL for grid
+ * sizes the spectral passes do not support (see VDP_PRECOND_SPECTRAL).
+ */
+int vdp_inverse_laplacian(vdp_ctx *ctx, const double *g, double *out);
+
 /* ------------------------------------------------------------------------------------------ */
 /* Per-kernel timing (instrumentation; the paper has no counterpart).                          */
 /* ------------------------------------------------------------------------------------------ */
@@ -163,7 +181,10 @@ enum {
   VDP_SWEEP_CHEB = 2,    /* one Chebyshev preconditioner sweep (precond = VDP_PRECOND_CHEB)   */
   VDP_SWEEP_UPDATE = 3,  /* x, r updates + <r, r> (one per Krylov iteration)                  */
   VDP_SWEEP_OTHER = 4,   /* rhs mean removal, refinement correction p -= ..., final gauge     */
-  VDP_SWEEP_KINDS = 5
+  VDP_SWEEP_SPEC_X = 5,  /* spectral preconditioner: forward and inverse real FFTs along x     */
+  VDP_SWEEP_SPEC_Y = 6,  /* ... forward and inverse FFTs along y                               */
+  VDP_SWEEP_SPEC_Z = 7,  /* ... FFT along z, division by the eigenvalues, inverse FFT along z   */
+  VDP_SWEEP_KINDS = 8
 };
 
 typedef struct {

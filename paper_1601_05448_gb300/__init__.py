@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libvdp.so")
 
 VDP_OK, VDP_EINVAL, VDP_ENOMEM, VDP_EDENSITY, VDP_ENOTCONV, VDP_EBREAKDOWN, VDP_ETIMEOUT, VDP_ECUDA = range(8)
 VDP_FP64, VDP_MIXED, VDP_MIXED_BF16 = 0, 1, 2
-VDP_PRECOND_JACOBI, VDP_PRECOND_CHEB = 0, 1
+VDP_PRECOND_JACOBI, VDP_PRECOND_CHEB, VDP_PRECOND_SPECTRAL = 0, 1, 2
 PRECISIONS = {"fp64": VDP_FP64, "mixed": VDP_MIXED, "mixed_bf16": VDP_MIXED_BF16}
 
 
@@ -51,8 +51,9 @@ class vdp_stats(ctypes.Structure):
                 ("sweeps", ctypes.c_int), ("launches", ctypes.c_int)]
 
 
-VDP_SWEEP_RES64, VDP_SWEEP_STENCIL, VDP_SWEEP_CHEB, VDP_SWEEP_UPDATE, VDP_SWEEP_OTHER, VDP_SWEEP_KINDS = range(6)
-SWEEP_NAMES = ("res64", "stencil", "cheb", "update", "other")
+(VDP_SWEEP_RES64, VDP_SWEEP_STENCIL, VDP_SWEEP_CHEB, VDP_SWEEP_UPDATE, VDP_SWEEP_OTHER, VDP_SWEEP_SPEC_X,
+ VDP_SWEEP_SPEC_Y, VDP_SWEEP_SPEC_Z, VDP_SWEEP_KINDS) = range(9)
+SWEEP_NAMES = ("res64", "stencil", "cheb", "update", "other", "spec_x", "spec_y", "spec_z")
 
 
 class vdp_sweep_times(ctypes.Structure):
@@ -79,6 +80,7 @@ _SIGS = {
     "vdp_last_cuda_error": (ctypes.c_char_p, []),
     "vdp_version": (ctypes.c_int, []),
     "vdp_apply": (ctypes.c_int, [_P, _P, _P]),
+    "vdp_inverse_laplacian": (ctypes.c_int, [_P, _P, _P]),
     "vdp_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_void_p)]),
     "vdp_batch_destroy": (None, [_P]),
     "vdp_batch_add": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double]),
@@ -175,6 +177,10 @@ def vdp_version() -> int:
 
 def vdp_apply(ctx: int, p, out) -> int:
     return load().vdp_apply(ctx, _ptr(p), _ptr(out, writable=True))
+
+
+def vdp_inverse_laplacian(ctx: int, g, out) -> int:
+    return load().vdp_inverse_laplacian(ctx, _ptr(g), _ptr(out, writable=True))
 
 
 def vdp_solve_timed(ctx: int, rhs, p, tol: float):
@@ -356,6 +362,14 @@ class Solver:
             kinds[name] = {"launches": n, "ms": t.ms[i], "ms_min": t.ms_min[i],
                            "ms_mean": t.ms[i] / n if n else 0.0}
         return out, kinds
+
+    def inverse_laplacian(self, g, out) -> None:
+        """out = L_h^-1 g, the constant-coefficient periodic solve (device tensors)."""
+        self._check(g, "g")
+        self._check(out, "out")
+        st = vdp_inverse_laplacian(self.ctx, g, out)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_inverse_laplacian")
 
     def apply(self, p, out) -> None:
         self._check(p, "p")

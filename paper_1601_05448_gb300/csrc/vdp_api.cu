@@ -21,6 +21,7 @@
 #include "vdp_internal.cuh"
 #include "vdp_launch.h"
 #include "vdp_ctx.h"
+#include "vdp_spectral.h"
 
 using namespace vdp;
 
@@ -101,7 +102,7 @@ void free_ctx(vdp_ctx* c) {
   cudaSetDevice(c->device);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   void* bufs[] = {c->bx, c->by, c->bz, c->sinv, c->sx, c->sy, c->sz, c->sd, c->x, c->r, c->d0, c->d1,
-                  c->za, c->zb, c->dch,
+                  c->za, c->zb, c->dch, c->spec, c->omega, c->sptab,
                   c->q, c->part, c->ticket, c->st, c->desc, c->units, c->flag, c->stage_a,
                   c->stage_b};
   for (void* b : bufs)
@@ -164,6 +165,7 @@ int configure_layout(vdp_ctx* c, int prec) {
   // polynomial preconditioner: Chebyshev on [b / kChebRange, b], b = 2 >= the largest
   // eigenvalue of the unit-diagonal operator
   d.cheb_k = c->opts.precond == VDP_PRECOND_CHEB ? c->opts.cheb_degree : 1;
+  d.pc = c->opts.precond == VDP_PRECOND_SPECTRAL ? PC_SPECTRAL : (d.cheb_k > 1 ? PC_CHEB : PC_JACOBI);
   {
     const double b = 2.0, a = b / kChebRange;
     d.cheb_theta = 0.5 * (b + a);
@@ -204,6 +206,12 @@ int ensure_graph(vdp_ctx* c, int prec) {
     cudaError_t e = cudaSuccess;
     if (c->lay.mode == 0)  // the residual sweep has its own kernel in the direct mode
       e = launch_res64(prec, c->desc, c->units, c->lay.nunits, c->lay.threads, c->cap);
+    if (e == cudaSuccess && c->hdesc.pc == PC_SPECTRAL) {  // z = M^-1 rt before the stencil sweep
+      SpecArgs a;
+      solve_spec_args(c, prec, &a);
+      for (int pass = 0; pass < SPEC_PASSES && e == cudaSuccess; ++pass)
+        e = launch_spectral_pass(prec, pass, a, c->cap);
+    }
     if (e == cudaSuccess)
       e = launch_stencil(prec, c->lay.mode, c->desc, c->units, c->lay.nunits, c->lay.threads,
                          c->lay.smem, c->cap);
@@ -231,6 +239,58 @@ int ensure_scaled(vdp_ctx* c, int prec) {
                        c->sz, c->sd, c->stream));
   c->scaled_prec = prec;
   return VDP_OK;
+}
+
+int ensure_spectral(vdp_ctx* c) {
+  if (!spectral_supported(c->nx, c->ny, c->nz)) return VDP_EINVAL;
+  if (c->spec && c->sptab && c->za) return VDP_OK;
+  static std::mutex mu;
+  static std::vector<int> uploaded;  // devices whose register-DFT roots are in place
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(uploaded.begin(), uploaded.end(), c->device) == uploaded.end()) {
+      VDP_CK(spectral_upload_roots());
+      uploaded.push_back(c->device);
+    }
+  }
+  std::vector<float> tab;
+  spectral_tables(c->nx, c->ny, c->nz, c->L, tab);
+  const size_t spec_bytes = sizeof(float2) * (size_t)spectral_pitch(c->nx) * c->ny * c->nz;
+  cudaError_t e = cudaSuccess;
+  if (!c->za) e = cudaMalloc(&c->za, sizeof(double) * (size_t)c->n);
+  if (e == cudaSuccess && !c->spec) e = cudaMalloc((void**)&c->spec, spec_bytes);
+  if (e == cudaSuccess && !c->omega) e = cudaMalloc((void**)&c->omega, sizeof(float) * (size_t)c->n);
+  if (e == cudaSuccess && !c->sptab) e = cudaMalloc((void**)&c->sptab, sizeof(float) * tab.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->sptab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    for (void** b : {(void**)&c->spec, (void**)&c->omega, (void**)&c->sptab}) {
+      if (*b) cudaFree(*b);
+      *b = nullptr;
+    }
+    return cuda_fail(e, "spectral buffers");
+  }
+  c->omega_valid = false;
+  return VDP_OK;
+}
+
+void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a) {
+  const int m = c->nx / 2;
+  a->in = c->r;
+  a->out = c->za;
+  a->dot_with = c->r;
+  a->omega = c->omega;
+  a->spec = c->spec;
+  a->tw = reinterpret_cast<const float2*>(c->sptab);
+  a->lam = c->sptab + 2 * (2 * m + 1 + c->ny + c->nz);
+  a->nx = c->nx;
+  a->ny = c->ny;
+  a->nz = c->nz;
+  a->nxp = spectral_pitch(c->nx);
+  a->scale = (float)(1.0 / (double)c->n);
+  a->st = c->st;
+  a->I = c->desc;
+  (void)prec;
 }
 
 }  // namespace vdp
@@ -298,7 +358,12 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
   if (!c || !o) return VDP_EINVAL;
   if (o->precision < VDP_FP64 || o->precision > VDP_MIXED_BF16) return VDP_EINVAL;
   if (o->max_iter < 1 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return VDP_EINVAL;
-  if (o->precond != VDP_PRECOND_JACOBI && o->precond != VDP_PRECOND_CHEB) return VDP_EINVAL;
+  if (o->precond != VDP_PRECOND_JACOBI && o->precond != VDP_PRECOND_CHEB &&
+      o->precond != VDP_PRECOND_SPECTRAL)
+    return VDP_EINVAL;
+  if (o->precond == VDP_PRECOND_SPECTRAL &&
+      (o->stencil != 0 || !spectral_supported(c->nx, c->ny, c->nz)))
+    return VDP_EINVAL;
   if (o->precond == VDP_PRECOND_CHEB && (o->cheb_degree < 1 || o->cheb_degree > 16 || o->stencil != 0))
     return VDP_EINVAL;
   if (o->tile_y < 0 || o->units < 0 || o->stages < 0 || o->threads < 0 || o->steps_per_sync < 0 ||
@@ -313,18 +378,25 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
     c->opts = old;
     return VDP_EINVAL;
   }
-  if (o->precond == VDP_PRECOND_CHEB && o->cheb_degree > 1 && !c->za) {
+  if (o->precond == VDP_PRECOND_CHEB && o->cheb_degree > 1 && !(c->za && c->zb && c->dch)) {
     const size_t bytes = sizeof(double) * (size_t)c->n;
-    cudaError_t e = cudaMalloc(&c->za, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&c->zb, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&c->dch, bytes);
-    if (e != cudaSuccess) {
-      for (void** b : {&c->za, &c->zb, &c->dch}) {
+    cudaError_t e = cudaSuccess;
+    for (void** b : {&c->za, &c->zb, &c->dch})
+      if (e == cudaSuccess && !*b) e = cudaMalloc(b, bytes);
+    if (e != cudaSuccess) {  // keep what other options use; za is shared with the spectral path
+      for (void** b : {&c->zb, &c->dch}) {
         if (*b) cudaFree(*b);
         *b = nullptr;
       }
       c->opts = old;
       return cuda_fail(e, "vdp_set_options (Chebyshev buffers)");
+    }
+  }
+  if (o->precond == VDP_PRECOND_SPECTRAL) {
+    const int sres = ensure_spectral(c);
+    if (sres != VDP_OK) {
+      c->opts = old;
+      return sres;
     }
   }
   c->stream = (cudaStream_t)o->stream;
@@ -356,6 +428,7 @@ int vdp_set_density(vdp_ctx* c, const double* rho) {
   VDP_CK(launch_build_coefficients(src, c->nx, c->ny, c->nz, c->L, c->bx, c->by, c->bz, c->sinv,
                                    c->stream));
   c->scaled_prec = -1;
+  c->omega_valid = false;
   int s = ensure_scaled(c, c->opts.precision);
   if (s != VDP_OK) return s;
   VDP_CK(cudaStreamSynchronize(c->stream));
@@ -375,6 +448,10 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   if ((c->layout_dirty || c->layout_prec != prec) && (s = configure_layout(c, prec)) != VDP_OK)
     return s;
   if ((s = ensure_graph(c, prec)) != VDP_OK) return s;
+  if (c->hdesc.pc == PC_SPECTRAL && !c->omega_valid) {
+    VDP_CK(launch_omega(c->sinv, c->n, c->omega, c->stream));
+    c->omega_valid = true;
+  }
   const double* drhs = rhs;
   double* dp = p;
   if (host_rhs) {
@@ -427,13 +504,35 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   c->stats.rhs_mean = hs.mu_f;
   c->stats.ms = ms;
   c->stats.sweeps = hs.sweeps;
-  c->stats.launches = (int)(1 + issued * (c->lay.mode == 0 ? 3 : 2) * m);
+  const int per_round = (c->lay.mode == 0 ? 3 : 2) + (c->hdesc.pc == PC_SPECTRAL ? SPEC_PASSES : 0);
+  c->stats.launches = (int)(1 + issued * per_round * m);
   return c->stats.status;
 }
 
 int vdp_get_stats(const vdp_ctx* c, vdp_stats* s) {
   if (!c || !s) return VDP_EINVAL;
   *s = c->stats;
+  return VDP_OK;
+}
+
+int vdp_inverse_laplacian(vdp_ctx* c, const double* g, double* out) {
+  if (!c || !g || !out || g == out) return VDP_EINVAL;
+  if (!is_device_ptr(g) || !is_device_ptr(out) || ((uintptr_t)g & 15) || ((uintptr_t)out & 15))
+    return VDP_EINVAL;
+  int s;
+  if ((s = ensure_spectral(c)) != VDP_OK) return s;
+  SpecArgs a;
+  solve_spec_args(c, PREC_FP64, &a);
+  a.in = g;
+  a.out = out;
+  a.dot_with = nullptr;
+  a.omega = nullptr;
+  a.scale = (float)(-1.0 / (double)c->n);  // L_h^-1 (negative definite), not (-L_h)^-1
+  a.st = nullptr;
+  a.I = nullptr;
+  for (int pass = 0; pass < SPEC_PASSES; ++pass)
+    VDP_CK(launch_spectral_pass(PREC_FP64, pass, a, c->stream));
+  VDP_CK(cudaStreamSynchronize(c->stream));
   return VDP_OK;
 }
 

@@ -214,6 +214,7 @@ void vdp_batch_destroy(vdp_batch* b) {
 int vdp_batch_add(vdp_batch* b, vdp_ctx* c, const double* rhs, double* p, double tol) {
   if (!b || !c || !rhs || !p || !(tol > 0.0)) return VDP_EINVAL;
   if (!c->has_density || c->opts.precision != b->prec || c->opts.stencil != 0) return VDP_EINVAL;
+  if (c->opts.precond == VDP_PRECOND_SPECTRAL) return VDP_EINVAL;  // single solves only
   if (!is_device_ptr(rhs) || !is_device_ptr(p) || ((uintptr_t)rhs & 15) || ((uintptr_t)p & 15))
     return VDP_EINVAL;
   if (find(b, c, nullptr)) return VDP_EINVAL;  // already a member

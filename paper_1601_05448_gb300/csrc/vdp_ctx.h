@@ -36,7 +36,12 @@ struct vdp_ctx {
   // inner-precision data (sized for FP64, reinterpreted for FP32 / BF16)
   void *sx = nullptr, *sy = nullptr, *sz = nullptr, *sd = nullptr;
   void *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr, *q = nullptr;
-  void *za = nullptr, *zb = nullptr, *dch = nullptr;  // Chebyshev preconditioner
+  void *za = nullptr, *zb = nullptr, *dch = nullptr;  // preconditioned z; Chebyshev iterates
+  // spectral preconditioner / constant-coefficient inverse
+  float2* spec = nullptr;          // half spectrum
+  float* omega = nullptr;          // D^1/2 per cell (FP32)
+  float* sptab = nullptr;          // twiddle and eigenvalue tables
+  bool omega_valid = false;        // omega matches the current density
   int scaled_prec = -1;            // precision the scaled coefficients were built for
   bool has_density = false;
   // bookkeeping
@@ -68,5 +73,10 @@ namespace vdp {
 // layout (and its device description) configured.
 int configure_layout(vdp_ctx* c, int prec);
 int ensure_scaled(vdp_ctx* c, int prec);
+// allocate the spectral buffers and tables (no-op when present); VDP_EINVAL for unsupported grids
+int ensure_spectral(vdp_ctx* c);
+// the arguments of the five spectral passes of a solve on this context (gated on its state)
+struct SpecArgs;
+void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a);
 
 }  // namespace vdp

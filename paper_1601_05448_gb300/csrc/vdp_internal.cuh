@@ -27,8 +27,12 @@ enum Phase : int {
   PH_CORRECT = 4,  // p -= D^-1/2 x   (refinement step of the outer FP64 loop)
   PH_FINAL = 5,    // p -= <p>  (gauge)
   PH_CHEB = 6,     // one Chebyshev sweep of the polynomial preconditioner z = P(At) rt
-  PH_DONE = 7
+  PH_SPEC = 7,     // spectral preconditioner z = W (-L_h)^-1 W rt (five FFT passes)
+  PH_DONE = 8
 };
+
+// Preconditioner applied to the Jacobi-scaled inner system (InstDesc::pc).
+enum PrecondKind : int { PC_JACOBI = 0, PC_CHEB = 1, PC_SPECTRAL = 2 };
 
 enum Prec : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_MIXED_BF16 = 2 };
 
@@ -106,7 +110,7 @@ struct InstDesc {
   void* zb;            //   the Chebyshev correction d_j (null without the polynomial)
   void* dch;
   int cheb_k;          // polynomial preconditioner: number of terms (1 = Jacobi only)
-  int pad2;
+  int pc;              // PrecondKind (PC_CHEB only with cheb_k > 1)
   double cheb_theta;   // Chebyshev interval [a, b]: theta = (b + a) / 2, delta = (b - a) / 2
   double cheb_delta;
   double* part;        // kSlots x nunits partial sums

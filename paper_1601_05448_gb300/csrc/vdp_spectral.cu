@@ -1,0 +1,584 @@
+// vdp_spectral.cu -- the constant-coefficient spectral inverse (Sec. 3.4) on sm_103a, used as a
+// preconditioner of the inner conjugate-gradient solve and exposed as vdp_inverse_laplacian.
+//
+// The paper solves the variable-density equation by repeated constant-coefficient Poisson
+// solves done with FFTs.  Here the same operator, the inverse of the 7-point Laplacian L_h on
+// the periodic grid (eigenvalues -sum_d 4 sin^2(pi k_d / n_d) / h_d^2, zero mode removed), is
+// applied to the Jacobi-scaled inner residual as
+//     z = W (-L_h)^-1 W rt,   W = D^1/2 (D: diagonal of the variable-coefficient operator),
+// which is the constant-coefficient inverse in unscaled variables.  Between the smallest and the
+// largest face value of 1/rho the variable operator is bounded by multiples of -L_h, so the
+// preconditioned condition number is at most the density ratio, whatever the grid size.
+//
+// Five passes over a half spectrum S[kz][ky][kx] (kx = 0 .. nx/2, complex FP32, row pitch nxp):
+//   X+  each row of nx reals is read as nx/2 complex pairs, weighted by W, transformed by a
+//       complex FFT of length nx/2 and unpacked into the nx/2 + 1 bins of the real transform;
+//   Y+  complex FFTs along y of tiles of 8 consecutive kx columns;
+//   Z   FFT along z, division by the eigenvalue (and by nx ny nz), inverse FFT along z: the
+//       whole z line is in the block, so the solve costs one pass;
+//   Y-  inverse FFTs along y;
+//   X-  the real inverse transform of each row, weighted by W, stored as z; in the solve this
+//       pass also sums <rt, z> and, as the last unit to finish, moves the solve to its next
+//       phase (the same fixed-order reduction as every other sweep).
+// Every line FFT is a four-step factorisation n = M1 x M2 (both products of 2 and 3, at most
+// 32): M2-point DFTs in registers, twiddles W_n^(j1 k2), an exchange through shared memory,
+// M1-point DFTs in registers.  Global accesses are coalesced: rows are contiguous in the X
+// passes and the Y/Z tiles read 8 consecutive complex values (64 bytes) per line element.
+// The passes are HBM bound: about 52 bytes per cell for the FP32 inner solve.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "vdp.h"
+#include "vdp_device.cuh"
+#include "vdp_internal.cuh"
+#include "vdp_spectral.h"
+
+namespace vdp {
+
+// ---- complex arithmetic and small DFTs in registers ---------------------------------------------
+
+// exp(-2 pi i k / 96): the roots of unity of every register DFT size used here (all divide 96).
+__constant__ float2 c_w96[96];
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+
+// v * W_M^k with W = exp(-2 pi i / M) (INV: the conjugate root).  k and M are constants after
+// unrolling, so the trivial roots cost nothing and the others are constant-bank operands.
+template <bool INV>
+__device__ __forceinline__ float2 rot(float2 v, int k, int M) {
+  k %= M;
+  if (k == 0) return v;
+  if (2 * k == M) return make_float2(-v.x, -v.y);
+  if (4 * k == M) return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+  if (4 * k == 3 * M) return INV ? make_float2(v.y, -v.x) : make_float2(-v.y, v.x);
+  const float2 w = c_w96[(96 / M) * k];
+  return cmul(v, INV ? cconj(w) : w);
+}
+
+// y[k] = sum_j x[O + S j] W_M^(j k), k < M: recursive decimation in time (radix 2, then 3).
+template <int M, int O, int S, bool INV, int N>
+__device__ __forceinline__ void dft(const float2 (&x)[N], float2 (&y)[M]) {
+  static_assert(O + S * (M - 1) < N, "dft reads outside its input");
+  if constexpr (M == 1) {
+    y[0] = x[O];
+  } else if constexpr (M % 2 == 0) {
+    constexpr int H = M / 2;
+    float2 e[H], o[H];
+    dft<H, O, 2 * S, INV>(x, e);
+    dft<H, O + S, 2 * S, INV>(x, o);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float2 t = rot<INV>(o[k], k, M);
+      y[k] = cadd(e[k], t);
+      y[k + H] = csub(e[k], t);
+    }
+  } else {
+    static_assert(M % 3 == 0, "register DFT sizes are products of 2 and 3");
+    constexpr int T = M / 3;
+    constexpr float kS3 = 0.86602540378443864676f;  // sin(pi / 3)
+    float2 a[T], b[T], c[T];
+    dft<T, O, 3 * S, INV>(x, a);
+    dft<T, O + S, 3 * S, INV>(x, b);
+    dft<T, O + 2 * S, 3 * S, INV>(x, c);
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+      const float2 tb = rot<INV>(b[k], k, M), tc = rot<INV>(c[k], 2 * k, M);
+      const float2 s = cadd(tb, tc), d = csub(tb, tc);
+      const float2 m = make_float2(a[k].x - 0.5f * s.x, a[k].y - 0.5f * s.y);
+      // forward: W_3 = -1/2 - i sin(pi/3); (tb - tc) times -i sin(pi/3) (+i for the inverse)
+      const float2 j = INV ? make_float2(-kS3 * d.y, kS3 * d.x) : make_float2(kS3 * d.y, -kS3 * d.x);
+      y[k] = cadd(a[k], s);
+      y[k + T] = cadd(m, j);
+      y[k + 2 * T] = csub(m, j);
+    }
+  }
+}
+
+// ---- table layout ---------------------------------------------------------------------------------
+
+struct Tables {
+  const float2* wm;  // W_m^k, m = nx / 2
+  const float2* wr;  // W_nx^k, k = 0 .. m
+  const float2* wy;  // W_ny^k
+  const float2* wz;  // W_nz^k
+  const float* lx;   // 4 sin^2(pi k / nx) / hx^2, k = 0 .. m
+  const float* ly;
+  const float* lz;
+};
+
+__device__ __forceinline__ Tables tables(const SpecArgs& a) {
+  const int m = a.nx / 2;
+  Tables t;
+  t.wm = a.tw;
+  t.wr = a.tw + m;
+  t.wy = a.tw + 2 * m + 1;
+  t.wz = a.tw + 2 * m + 1 + a.ny;
+  t.lx = a.lam;
+  t.ly = a.lam + m + 1;
+  t.lz = a.lam + m + 1 + a.ny;
+  return t;
+}
+
+// In the solve every pass first checks that the instance is in the spectral phase (one L2
+// load); the stand-alone inverse passes st = nullptr and always runs.
+__device__ __forceinline__ bool spec_active(const SpecArgs& a) {
+  return a.st == nullptr || __ldcg(&a.st->phase) == PH_SPEC;
+}
+
+template <class T> struct Pair;
+template <> struct Pair<float> {
+  static __device__ __forceinline__ float2 ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
+  static __device__ __forceinline__ void st(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+  static __device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    a = v.x;
+    b = v.y;
+  }
+};
+template <> struct Pair<double> {
+  static __device__ __forceinline__ float2 ld(const double* p) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    return make_float2((float)v.x, (float)v.y);
+  }
+  static __device__ __forceinline__ void st(double* p, float2 v) {
+    *reinterpret_cast<double2*>(p) = make_double2((double)v.x, (double)v.y);
+  }
+  static __device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a = v.x;
+    b = v.y;
+  }
+};
+
+// Rows per block of the X passes: at most 256 threads and 32 KB of shared memory, and a
+// multiple of 32 threads (the block reduction works on whole warps).
+template <int M1, int M2>
+constexpr int rows_per_block() {
+  for (int ry = 256 / M1; ry > 1; --ry)
+    if ((M1 * ry) % 32 == 0 && 16 * M1 * M2 * ry <= 32768) return ry;
+  return 32;  // not reached for the supported sizes
+}
+
+// ---- X+ : real rows -> half spectrum -----------------------------------------------------------
+
+template <class T, int M1, int M2>
+__global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
+    k_spec_x_fwd(SpecArgs a) {
+  constexpr int m = M1 * M2, RY = rows_per_block<M1, M2>();
+  __shared__ float2 sa[RY][m], sb[RY][m];
+  if (!spec_active(a)) return;
+  const Tables tb = tables(a);
+  const int t = threadIdx.x % M1, r = threadIdx.x / M1;
+  const long long rows = (long long)a.ny * a.nz;
+  const long long row = (long long)blockIdx.x * RY + r;
+  const bool live = row < rows;
+  const T* in = static_cast<const T*>(a.in) + row * a.nx;
+  // step A: M2-point DFTs over j2 of z[t + M1 j2] = (x[2j], x[2j+1]) * W
+  if (live) {
+    float2 v[M2], y[M2];
+#pragma unroll
+    for (int j2 = 0; j2 < M2; ++j2) {
+      const int j = t + M1 * j2;
+      float2 z = Pair<T>::ld(in + 2 * j);
+      if (a.omega) {
+        const float2 w = *reinterpret_cast<const float2*>(a.omega + row * a.nx + 2 * j);
+        z = make_float2(z.x * w.x, z.y * w.y);
+      }
+      v[j2] = z;
+    }
+    dft<M2, 0, 1, false>(v, y);
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) sa[r][k2 * M1 + t] = k2 == 0 || t == 0 ? y[k2] : cmul(y[k2], tb.wm[t * k2]);
+  }
+  __syncthreads();
+  // step B: M1-point DFTs over j1 -> Z[k2 + M2 k1]
+  if (live) {
+#pragma unroll
+    for (int k2 = t; k2 < M2; k2 += M1) {
+      float2 u[M1], o[M1];
+#pragma unroll
+      for (int j1 = 0; j1 < M1; ++j1) u[j1] = sa[r][k2 * M1 + j1];
+      dft<M1, 0, 1, false>(u, o);
+#pragma unroll
+      for (int k1 = 0; k1 < M1; ++k1) sb[r][k2 + M2 * k1] = o[k1];
+    }
+  }
+  __syncthreads();
+  // unpack: X[k] = E[k] + W_nx^k O[k], E = (Z[k] + conj Z[m-k]) / 2, O = (Z[k] - conj Z[m-k]) / 2i
+  if (live) {
+    float2* out = a.spec + row * a.nxp;
+    for (int k = t; k < a.nxp; k += M1) {
+      float2 X = make_float2(0.f, 0.f);
+      if (k <= m) {
+        const float2 p = sb[r][k == m ? 0 : k], q = cconj(sb[r][k == 0 ? 0 : m - k]);
+        const float2 e = cscale(cadd(p, q), 0.5f);
+        const float2 d = csub(p, q);
+        const float2 o = make_float2(0.5f * d.y, -0.5f * d.x);
+        X = cadd(e, cmul(tb.wr[k], o));
+      }
+      out[k] = X;
+    }
+  }
+}
+
+// ---- X- : half spectrum -> real rows (z = W x), <rt, z> ------------------------------------------
+
+template <class T, int M1, int M2>
+__global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
+    k_spec_x_inv(SpecArgs a) {
+  constexpr int m = M1 * M2, RY = rows_per_block<M1, M2>();
+  __shared__ float2 sa[RY][m + 1], sb[RY][m];
+  if (!spec_active(a)) return;
+  const Tables tb = tables(a);
+  const int t = threadIdx.x % M1, r = threadIdx.x / M1;
+  const long long rows = (long long)a.ny * a.nz;
+  const long long row = (long long)blockIdx.x * RY + r;
+  const bool live = row < rows;
+  if (live) {
+    const float2* src = a.spec + row * a.nxp;
+    for (int k = t; k <= m; k += M1) sa[r][k] = src[k];
+  }
+  __syncthreads();
+  // Z'[k] = (X[k] + conj X[m-k]) + i conj(W_nx^k) (X[k] - conj X[m-k]); inverse M2-point DFTs
+  if (live) {
+    float2 v[M2], y[M2];
+#pragma unroll
+    for (int j2 = 0; j2 < M2; ++j2) {
+      const int k = t + M1 * j2;
+      const float2 p = sa[r][k], q = cconj(sa[r][m - k]);
+      const float2 e = cadd(p, q);
+      const float2 o = cmulc(csub(p, q), tb.wr[k]);
+      v[j2] = make_float2(e.x - o.y, e.y + o.x);
+    }
+    dft<M2, 0, 1, true>(v, y);
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2)
+      sb[r][k2 * M1 + t] = k2 == 0 || t == 0 ? y[k2] : cmulc(y[k2], tb.wm[t * k2]);
+  }
+  __syncthreads();
+  T acc = 0;
+  if (live) {
+    const T* rt = static_cast<const T*>(a.dot_with);
+    T* out = static_cast<T*>(a.out) + row * a.nx;
+#pragma unroll
+    for (int k2 = t; k2 < M2; k2 += M1) {
+      float2 u[M1], o[M1];
+#pragma unroll
+      for (int j1 = 0; j1 < M1; ++j1) u[j1] = sb[r][k2 * M1 + j1];
+      dft<M1, 0, 1, true>(u, o);
+#pragma unroll
+      for (int k1 = 0; k1 < M1; ++k1) {
+        const int l = k2 + M2 * k1;  // cells 2l, 2l + 1 of the row
+        float2 z = o[k1];
+        if (a.omega) {
+          const float2 w = *reinterpret_cast<const float2*>(a.omega + row * a.nx + 2 * l);
+          z = make_float2(z.x * w.x, z.y * w.y);
+        }
+        Pair<T>::st(out + 2 * l, z);
+        if (rt) {
+          T r0, r1;
+          Pair<T>::ld2(rt + row * a.nx + 2 * l, r0, r1);
+          acc = fma(r0, (T)z.x, acc);
+          acc = fma(r1, (T)z.y, acc);
+        }
+      }
+    }
+  }
+  if (a.st) {  // the solve: this pass completes the preconditioner sweep
+    const InstDesc& I = *a.I;
+    T part[1] = {acc};
+    store_partials<1, T>(part, I.part, gridDim.x, blockIdx.x);
+    finish_sweep(I, I.st, PH_SPEC, gridDim.x);
+  }
+}
+
+// ---- Y and Z: tiles of TX consecutive kx columns, whole lines -----------------------------------
+
+constexpr int kTX = 8;  // columns per tile (64 bytes of each line element)
+
+// Y pass (forward or inverse), in place: block = (column tile, kz).
+template <int M1, int M2, bool INV>
+__global__ void __launch_bounds__(M1 * kTX) k_spec_y(SpecArgs a) {
+  constexpr int n = M1 * M2;
+  __shared__ float2 sm[n * kTX];
+  if (!spec_active(a)) return;
+  const Tables tb = tables(a);
+  const int c = threadIdx.x % kTX, t = threadIdx.x / kTX;
+  const int tiles = a.nxp / kTX;
+  const int kz = blockIdx.x / tiles, kx = (blockIdx.x % tiles) * kTX + c;
+  float2* g = a.spec + (long long)kz * a.ny * a.nxp + kx;
+  const long long es = a.nxp;  // element stride along y
+  {
+    float2 v[M2], y[M2];
+#pragma unroll
+    for (int j2 = 0; j2 < M2; ++j2) v[j2] = g[(t + M1 * j2) * es];
+    dft<M2, 0, 1, INV>(v, y);
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) {
+      const float2 w = tb.wy[t * k2];
+      sm[(k2 * M1 + t) * kTX + c] = k2 == 0 || t == 0 ? y[k2] : (INV ? cmulc(y[k2], w) : cmul(y[k2], w));
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k2 = t; k2 < M2; k2 += M1) {
+    float2 u[M1], o[M1];
+#pragma unroll
+    for (int j1 = 0; j1 < M1; ++j1) u[j1] = sm[(k2 * M1 + j1) * kTX + c];
+    dft<M1, 0, 1, INV>(u, o);
+#pragma unroll
+    for (int k1 = 0; k1 < M1; ++k1) g[(k2 + M2 * k1) * es] = o[k1];
+  }
+}
+
+// Z pass: forward FFT along z, scale by sign / (N lambda), inverse FFT along z; block =
+// (column tile, ky).  Forward: A (M2-point, over j2) and B (M1-point, over j1), leaving owner
+// k2 with X[k2 + M2 k1]; inverse: A' (M1-point over k1 in registers), B' (M2-point over k2).
+template <int M1, int M2>
+__global__ void __launch_bounds__(M1 * kTX) k_spec_z(SpecArgs a) {
+  constexpr int n = M1 * M2, R = (M2 + M1 - 1) / M1;
+  __shared__ float2 sm[n * kTX];
+  if (!spec_active(a)) return;
+  const Tables tb = tables(a);
+  const int c = threadIdx.x % kTX, t = threadIdx.x / kTX;
+  const int tiles = a.nxp / kTX;
+  const int ky = blockIdx.x / tiles, kx = (blockIdx.x % tiles) * kTX + c;
+  float2* g = a.spec + (long long)ky * a.nxp + kx;
+  const long long es = (long long)a.ny * a.nxp;  // element stride along z
+  {
+    float2 v[M2], y[M2];
+#pragma unroll
+    for (int j2 = 0; j2 < M2; ++j2) v[j2] = g[(t + M1 * j2) * es];
+    dft<M2, 0, 1, false>(v, y);
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2)
+      sm[(k2 * M1 + t) * kTX + c] = k2 == 0 || t == 0 ? y[k2] : cmul(y[k2], tb.wz[t * k2]);
+  }
+  __syncthreads();
+  const bool pad = kx > a.nx / 2;  // padding columns of the row pitch: set to 0
+  const float lxy = pad ? 0.f : tb.lx[kx] + tb.ly[ky];
+  float2 X[R][M1];
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int k2 = t + M1 * rr;
+    if (k2 < M2) {
+      float2 u[M1], o[M1];
+#pragma unroll
+      for (int j1 = 0; j1 < M1; ++j1) u[j1] = sm[(k2 * M1 + j1) * kTX + c];
+      dft<M1, 0, 1, false>(u, o);
+#pragma unroll
+      for (int k1 = 0; k1 < M1; ++k1) {
+        const float lam = lxy + tb.lz[k2 + M2 * k1];
+        const float s = (lam > 0.f && !pad) ? a.scale / lam : 0.f;  // zero mode removed
+        X[rr][k1] = cscale(o[k1], s);
+      }
+    }
+  }
+  __syncthreads();  // the forward exchange buffer is reused
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int k2 = t + M1 * rr;
+    if (k2 < M2) {
+      float2 u[M1];
+      dft<M1, 0, 1, true>(X[rr], u);
+#pragma unroll
+      for (int l2 = 0; l2 < M1; ++l2)
+        sm[(l2 * M2 + k2) * kTX + c] = l2 == 0 || k2 == 0 ? u[l2] : cmulc(u[l2], tb.wz[k2 * l2]);
+    }
+  }
+  __syncthreads();
+  {
+    float2 w[M2], o[M2];
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) w[k2] = sm[(t * M2 + k2) * kTX + c];
+    dft<M2, 0, 1, true>(w, o);
+#pragma unroll
+    for (int l1 = 0; l1 < M2; ++l1) g[(t + M1 * l1) * es] = o[l1];
+  }
+}
+
+// ---- host side ----------------------------------------------------------------------------------
+
+namespace {
+
+// n = M1 x M2 for the supported line lengths (0 = unsupported)
+void factor(int n, int* m1, int* m2) {
+  switch (n) {
+    case 16: *m1 = 4; *m2 = 4; return;
+    case 24: *m1 = 4; *m2 = 6; return;
+    case 32: *m1 = 4; *m2 = 8; return;
+    case 48: *m1 = 6; *m2 = 8; return;
+    case 64: *m1 = 8; *m2 = 8; return;
+    case 96: *m1 = 8; *m2 = 12; return;
+    case 128: *m1 = 8; *m2 = 16; return;
+    case 192: *m1 = 12; *m2 = 16; return;
+    case 256: *m1 = 16; *m2 = 16; return;
+    case 512: *m1 = 16; *m2 = 32; return;
+    default: *m1 = 0; *m2 = 0; return;
+  }
+}
+
+using SpecKernel = void (*)(SpecArgs);
+
+template <class T>
+SpecKernel x_kernel(int m, bool inverse, int* threads) {
+  int m1, m2;
+  factor(m, &m1, &m2);
+#define VDP_X(M1, M2)                                                       \
+  if (m1 == M1 && m2 == M2) {                                               \
+    *threads = M1 * rows_per_block<M1, M2>();                               \
+    return inverse ? k_spec_x_inv<T, M1, M2> : k_spec_x_fwd<T, M1, M2>;     \
+  }
+  VDP_X(4, 4) VDP_X(4, 6) VDP_X(4, 8) VDP_X(6, 8) VDP_X(8, 8) VDP_X(8, 12) VDP_X(8, 16)
+  VDP_X(16, 16)
+#undef VDP_X
+  return nullptr;
+}
+
+int x_rows_per_block(int m) {
+  int m1, m2;
+  factor(m, &m1, &m2);
+#define VDP_R(M1, M2) \
+  if (m1 == M1 && m2 == M2) return rows_per_block<M1, M2>();
+  VDP_R(4, 4) VDP_R(4, 6) VDP_R(4, 8) VDP_R(6, 8) VDP_R(8, 8) VDP_R(8, 12) VDP_R(8, 16)
+  VDP_R(16, 16)
+#undef VDP_R
+  return 0;
+}
+
+SpecKernel yz_kernel(int n, int which, int* threads) {  // which: 0 = Y+, 1 = Y-, 2 = Z
+  int m1, m2;
+  factor(n, &m1, &m2);
+#define VDP_YZ(M1, M2)                                                                  \
+  if (m1 == M1 && m2 == M2) {                                                           \
+    *threads = M1 * kTX;                                                                \
+    return which == 0 ? k_spec_y<M1, M2, false> : which == 1 ? k_spec_y<M1, M2, true>   \
+                                                             : k_spec_z<M1, M2>;        \
+  }
+  VDP_YZ(4, 8) VDP_YZ(6, 8) VDP_YZ(8, 8) VDP_YZ(8, 12) VDP_YZ(8, 16) VDP_YZ(12, 16)
+  VDP_YZ(16, 16) VDP_YZ(16, 32)
+#undef VDP_YZ
+  return nullptr;
+}
+
+bool x_supported(int nx) {
+  if (nx % 2) return false;
+  int threads = 0;
+  return x_kernel<float>(nx / 2, false, &threads) != nullptr;
+}
+
+bool yz_supported(int n) {
+  int threads = 0;
+  return n != 16 && n != 24 && yz_kernel(n, 0, &threads) != nullptr;
+}
+
+}  // namespace
+
+bool spectral_supported(int nx, int ny, int nz) {
+  return x_supported(nx) && yz_supported(ny) && yz_supported(nz);
+}
+
+int spectral_pitch(int nx) { return ((nx / 2 + 1 + kTX - 1) / kTX) * kTX; }
+
+size_t spectral_table_floats(int nx, int ny, int nz) {
+  const int m = nx / 2;
+  return 2 * (size_t)(2 * m + 1 + ny + nz) + (size_t)(m + 1 + ny + nz);
+}
+
+void spectral_tables(int nx, int ny, int nz, double L, std::vector<float>& out) {
+  const int m = nx / 2;
+  out.assign(spectral_table_floats(nx, ny, nz), 0.f);
+  size_t i = 0;
+  auto roots = [&](int n, int count) {
+    for (int k = 0; k < count; ++k) {
+      const double ang = -2.0 * M_PI * (double)k / (double)n;
+      out[i++] = (float)std::cos(ang);
+      out[i++] = (float)std::sin(ang);
+    }
+  };
+  roots(m, m);
+  roots(nx, m + 1);
+  roots(ny, ny);
+  roots(nz, nz);
+  auto eig = [&](int n, int count) {
+    const double h = L / n;
+    for (int k = 0; k < count; ++k) {
+      const double s = std::sin(M_PI * (double)k / (double)n);
+      out[i++] = (float)(4.0 * s * s / (h * h));
+    }
+  };
+  eig(nx, m + 1);
+  eig(ny, ny);
+  eig(nz, nz);
+}
+
+cudaError_t spectral_upload_roots() {
+  float2 w[96];
+  for (int k = 0; k < 96; ++k) {
+    const double ang = -2.0 * M_PI * (double)k / 96.0;
+    w[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  return cudaMemcpyToSymbol(c_w96, w, sizeof(w));
+}
+
+cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStream_t s) {
+  int threads = 0;
+  SpecKernel k = nullptr;
+  unsigned grid = 0;
+  const int m = a.nx / 2;
+  const long long rows = (long long)a.ny * a.nz;
+  switch (pass) {
+    case SPEC_X_FWD:
+    case SPEC_X_INV: {
+      const bool inv = pass == SPEC_X_INV;
+      k = prec == PREC_FP64 ? x_kernel<double>(m, inv, &threads) : x_kernel<float>(m, inv, &threads);
+      const int ry = x_rows_per_block(m);
+      grid = ry ? (unsigned)((rows + ry - 1) / ry) : 0;
+      break;
+    }
+    case SPEC_Y_FWD:
+    case SPEC_Y_INV:
+      k = yz_kernel(a.ny, pass == SPEC_Y_FWD ? 0 : 1, &threads);
+      grid = (unsigned)((a.nxp / kTX) * a.nz);
+      break;
+    case SPEC_Z:
+      k = yz_kernel(a.nz, 2, &threads);
+      grid = (unsigned)((a.nxp / kTX) * a.ny);
+      break;
+    default:
+      break;
+  }
+  if (!k || !grid) return cudaErrorInvalidValue;
+  k<<<grid, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int spectral_units(int nx, int ny, int nz) {
+  const int ry = x_rows_per_block(nx / 2);
+  return ry ? (int)(((long long)ny * nz + ry - 1) / ry) : 0;
+}
+
+__global__ void k_omega(const double* __restrict__ sinv, long long n, float* __restrict__ omega) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x)
+    omega[c] = (float)(1.0 / sinv[c]);
+}
+
+cudaError_t launch_omega(const double* sinv, long long n, float* omega, cudaStream_t s) {
+  k_omega<<<152 * 8, 256, 0, s>>>(sinv, n, omega);
+  return cudaGetLastError();
+}
+
+}  // namespace vdp

@@ -1,0 +1,42 @@
+// vdp_spectral.h -- host interface of the spectral passes in vdp_spectral.cu (internal to libvdp).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "vdp_internal.cuh"
+
+namespace vdp {
+
+// The five passes of one application of the constant-coefficient inverse, in launch order.
+enum SpecPass : int { SPEC_X_FWD = 0, SPEC_Y_FWD = 1, SPEC_Z = 2, SPEC_Y_INV = 3, SPEC_X_INV = 4,
+                      SPEC_PASSES = 5 };
+
+// Arguments of every spectral pass (by value).
+struct SpecArgs {
+  const void* in;        // X+: nx*ny*nz values of the inner type (FP64 or FP32)
+  void* out;             // X-: output, same type and layout
+  const void* dot_with;  // X-: sum <dot_with, out> into the solve's partial slots (or null)
+  const float* omega;    // per-cell weight W applied before X+ and after X- (or null: 1)
+  float2* spec;          // half spectrum [nz][ny][nxp]
+  const float2* tw;      // tables built by spectral_tables (twiddles first, then eigenvalues)
+  const float* lam;
+  int nx, ny, nz, nxp;
+  float scale;           // sign / (nx ny nz): +1 applies (-L_h)^-1, -1 applies L_h^-1
+  InstState* st;         // the solve's state: passes run only in PH_SPEC (null: always run)
+  const InstDesc* I;     // the solve's description (X- completes the sweep), with st
+};
+
+bool spectral_supported(int nx, int ny, int nz);
+int spectral_pitch(int nx);                       // nxp
+size_t spectral_table_floats(int nx, int ny, int nz);
+// twiddles (float2 pairs) W_m (m = nx/2), W_nx (m + 1), W_ny, W_nz, then the eigenvalue factors
+// 4 sin^2(pi k / n_d) / h_d^2 for kx = 0..m, ky, kz; computed in double, stored as float
+void spectral_tables(int nx, int ny, int nz, double L, std::vector<float>& out);
+cudaError_t spectral_upload_roots();               // the register-DFT roots, once per device
+cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStream_t s);
+int spectral_units(int nx, int ny, int nz);        // CTAs of the X- pass (partial slots)
+cudaError_t launch_omega(const double* sinv, long long n, float* omega, cudaStream_t s);
+
+}  // namespace vdp

@@ -18,6 +18,7 @@
 #include "vdp_ctx.h"
 #include "vdp_internal.cuh"
 #include "vdp_launch.h"
+#include "vdp_spectral.h"
 
 using namespace vdp;
 
@@ -59,9 +60,14 @@ int launch_shape(int phase) {
   }
 }
 
+// graphs 3 .. 7: the five spectral passes (SPEC_X_FWD .. SPEC_X_INV)
+constexpr int kTimedGraphs = 3 + SPEC_PASSES;
+constexpr int kSpecKind[SPEC_PASSES] = {VDP_SWEEP_SPEC_X, VDP_SWEEP_SPEC_Y, VDP_SWEEP_SPEC_Z,
+                                        VDP_SWEEP_SPEC_Y, VDP_SWEEP_SPEC_X};
+
 struct TimedGraphs {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaGraphExec_t g[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t g[kTimedGraphs] = {};
   ~TimedGraphs() {
     for (auto& x : g)
       if (x) cudaGraphExecDestroy(x);
@@ -70,12 +76,22 @@ struct TimedGraphs {
   }
 };
 
-cudaError_t capture_timed(vdp_ctx* c, int prec, int phase, TimedGraphs& t, cudaGraphExec_t* out) {
+// spec_pass >= 0: that spectral pass instead of the phase's kernel
+cudaError_t capture_timed(vdp_ctx* c, int prec, int phase, int spec_pass, TimedGraphs& t,
+                          cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   cudaError_t e2 = cudaEventRecordWithFlags(t.e0, c->cap, cudaEventRecordExternal);
-  if (e2 == cudaSuccess) e2 = launch_for_phase(c, prec, phase, c->cap);
+  if (e2 == cudaSuccess) {
+    if (spec_pass >= 0) {
+      SpecArgs a;
+      solve_spec_args(c, prec, &a);
+      e2 = launch_spectral_pass(prec, spec_pass, a, c->cap);
+    } else {
+      e2 = launch_for_phase(c, prec, phase, c->cap);
+    }
+  }
   if (e2 == cudaSuccess) e2 = cudaEventRecordWithFlags(t.e1, c->cap, cudaEventRecordExternal);
   e = cudaStreamEndCapture(c->cap, &g);
   if (e2 != cudaSuccess || e != cudaSuccess) {
@@ -105,7 +121,16 @@ extern "C" int vdp_solve_timed(vdp_ctx* c, const double* rhs, double* p, double 
   VDP_CK(cudaEventCreate(&t.e0));
   VDP_CK(cudaEventCreate(&t.e1));
   const int shape_phase[3] = {PH_RES64, PH_STENCIL, PH_UPDATE};
-  for (int i = 0; i < 3; ++i) VDP_CK(capture_timed(c, prec, shape_phase[i], t, &t.g[i]));
+  for (int i = 0; i < 3; ++i) VDP_CK(capture_timed(c, prec, shape_phase[i], -1, t, &t.g[i]));
+  const bool spectral = c->hdesc.pc == PC_SPECTRAL;
+  if (spectral) {
+    if (!c->omega_valid) {
+      VDP_CK(launch_omega(c->sinv, c->n, c->omega, c->stream));
+      c->omega_valid = true;
+    }
+    for (int i = 0; i < SPEC_PASSES; ++i)
+      VDP_CK(capture_timed(c, prec, PH_SPEC, i, t, &t.g[3 + i]));
+  }
   auto fail = [&](cudaError_t e, const char* where) { return cuda_fail(e, where); };
   cudaError_t e;
   if ((e = cudaEventRecord(c->ev0, c->stream)) != cudaSuccess) return fail(e, "cudaEventRecord");
@@ -126,15 +151,21 @@ extern "C" int vdp_solve_timed(vdp_ctx* c, const double* rhs, double* p, double 
       done = true;
       break;
     }
-    const int kind = sweep_kind(hs.phase);
-    if ((e = cudaGraphLaunch(t.g[launch_shape(hs.phase)], c->stream)) != cudaSuccess)
-      return fail(e, "sweep launch");
-    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(e, "cudaStreamSynchronize");
-    float ms = 0.f;
-    if ((e = cudaEventElapsedTime(&ms, t.e0, t.e1)) != cudaSuccess) return fail(e, "cudaEventElapsedTime");
-    times->ms[kind] += ms;
-    if (times->launches[kind] == 0 || ms < times->ms_min[kind]) times->ms_min[kind] = ms;
-    times->launches[kind] += 1;
+    const bool spec = spectral && hs.phase == PH_SPEC;
+    for (int pass = 0; pass < (spec ? SPEC_PASSES : 1); ++pass) {
+      const int kind = spec ? kSpecKind[pass] : sweep_kind(hs.phase);
+      if ((e = cudaGraphLaunch(t.g[spec ? 3 + pass : launch_shape(hs.phase)], c->stream)) !=
+          cudaSuccess)
+        return fail(e, "sweep launch");
+      if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+        return fail(e, "cudaStreamSynchronize");
+      float ms = 0.f;
+      if ((e = cudaEventElapsedTime(&ms, t.e0, t.e1)) != cudaSuccess)
+        return fail(e, "cudaEventElapsedTime");
+      times->ms[kind] += ms;
+      if (times->launches[kind] == 0 || ms < times->ms_min[kind]) times->ms_min[kind] = ms;
+      times->launches[kind] += 1;
+    }
   }
   cudaEventRecord(c->ev1, c->stream);
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(e, "cudaStreamSynchronize");

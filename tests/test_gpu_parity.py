@@ -234,8 +234,9 @@ def config1_problem():
     return _C1["p"]
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8), ("mixed_bf16", 1e-8)])
-def test_full_size_256_residual_in_oracle_operator(precision, tol):
+@pytest.mark.parametrize("precision,tol,precond", [("fp64", 1e-10, 0), ("mixed", 1e-8, 0), ("mixed_bf16", 1e-8, 0),
+                                                   ("fp64", 1e-10, 2), ("mixed", 1e-8, 2)])
+def test_full_size_256_residual_in_oracle_operator(precision, tol, precond):
     """The 256^3 hot-spot workload in the benchmark's launch configuration: the oracle's own
     operator must confirm the relative residual of the returned pressure, on every cell; a
     sample of cells is also checked against the flux form evaluated one cell at a time."""
@@ -245,12 +246,12 @@ def test_full_size_256_residual_in_oracle_operator(precision, tol):
     rho = torch.from_numpy(prob.rho).to(DEV)
     f = torch.from_numpy(prob.f).to(DEV)
     p = torch.empty_like(f)
-    with vdp.Solver(nx, ny, nz, prob.L, precision=precision, stream=stream) as s:
+    with vdp.Solver(nx, ny, nz, prob.L, precision=precision, stream=stream, precond=precond) as s:
         s.set_density(rho)
         st = s.solve(f, p, tol)
     ph = p.cpu().numpy()
     rr = oracle.relative_residual(prob.rho, prob.L, prob.f, ph)
-    print(f"256^3 {precision}: iters={st.iters} outer={st.outer_iters} rel_res={st.rel_res:.3e} oracle={rr:.3e}")
+    print(f"256^3 {precision} precond {precond}: iters={st.iters} outer={st.outer_iters} rel_res={st.rel_res:.3e} oracle={rr:.3e}")
     assert st.ok and st.rel_res <= tol and rr <= 1.01 * tol
     assert abs(float(ph.mean())) <= 1e-13 * float(np.abs(ph).max())
     # sampled cells, flux form written out per cell (Eq. Pois with face 1/rho from the
@@ -269,3 +270,83 @@ def test_full_size_256_residual_in_oracle_operator(precision, tol):
             bm = 2.0 / (prob.rho[k, j, i] + prob.rho[km, jm, im])
             acc += (bp * (ph[kp, jp, ip] - ph[k, j, i]) - bm * (ph[k, j, i] - ph[km, jm, im])) / (h * h)
         assert abs(acc - fm[k, j, i]) <= bound
+
+
+# ---- the spectral preconditioner (the paper's constant-coefficient inverse, Sec. 3.4) -----------
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (48, 64, 32), (64, 48, 96), (32, 32, 512), (96, 32, 48)])
+def test_inverse_laplacian_matches_oracle(shape):
+    nz, ny, nx = shape
+    L = 2.0 * np.pi
+    g = np.random.default_rng(sum(shape)).standard_normal(shape)
+    out = torch.empty(shape, dtype=torch.float64, device=DEV)
+    with vdp.Solver(nx, ny, nz, L) as s:
+        s.inverse_laplacian(torch.from_numpy(g).to(DEV), out)
+    ref = oracle.inverse_laplacian(g, L)
+    err = rel(out.cpu().numpy(), ref)
+    print(f"inverse Laplacian {shape}: rel err {err:.2e}")
+    assert err <= 2e-6
+    assert abs(float(out.mean())) <= 1e-6 * float(out.abs().max())
+
+
+def test_inverse_laplacian_fourier_mode_closed_form():
+    """A single discrete Fourier mode: L_h^-1 u = u / lambda(k) exactly (up to FP32 rounding)."""
+    nz, ny, nx = 32, 48, 64
+    L = 3.0
+    k = (3, -5, 7)
+    z, y, x = np.meshgrid(*[(np.arange(n) + 0.5) * (L / n) for n in (nz, ny, nx)], indexing="ij")
+    u = np.cos(2 * np.pi * (k[0] * x + k[1] * y + k[2] * z) / L + 0.4)
+    lam = -4.0 * sum(np.sin(np.pi * kd / nd) ** 2 / (L / nd) ** 2 for kd, nd in zip(k, (nx, ny, nz)))
+    out = torch.empty(u.shape, dtype=torch.float64, device=DEV)
+    with vdp.Solver(nx, ny, nz, L) as s:
+        s.inverse_laplacian(torch.from_numpy(u).to(DEV), out)
+    assert rel(out.cpu().numpy(), u / lam) <= 2e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_bf16"])
+def test_spectral_preconditioner_matches_oracle(precision):
+    prob = V.hotspot_problem(48, seed=61, nspots=int(round(20000 * 48 ** 3 / 256 ** 3)), target_ratio=6.0)
+    tol = 1e-10 if precision == "fp64" else 1e-9
+    p_j, st_j = gpu_solve(prob, precision, tol=tol)
+    p_s, st_s = gpu_solve(prob, precision, tol=tol, precond=vdp.VDP_PRECOND_SPECTRAL)
+    ref = oracle_solution(prob, "hot48")
+    err = rel(p_s, ref)
+    print(f"spectral {precision}: iters {st_j.iters} -> {st_s.iters} (outer {st_s.outer_iters}), err {err:.2e}")
+    assert st_s.ok and st_s.rel_res <= tol
+    assert err <= (1e-9 if precision == "fp64" else 1e-8)
+    assert oracle.relative_residual(prob.rho, prob.L, prob.f, p_s) <= 1.01 * tol
+    assert 4 * st_s.iters < st_j.iters  # the density ratio (6) bounds the condition number
+
+
+@pytest.mark.parametrize("shape", [(32, 64, 96), (64, 32, 32), (96, 48, 64)])
+def test_spectral_preconditioner_shapes(shape):
+    prob = V.smooth_problem(shape, seed=sum(shape) + 7)
+    p, st = gpu_solve(prob, "fp64", tol=1e-10, precond=vdp.VDP_PRECOND_SPECTRAL)
+    ref = oracle_solution(prob, ("smooth", shape))
+    assert st.ok and rel(p, ref) <= 1e-9, (st, rel(p, ref))
+    pm, stm = gpu_solve(prob, "mixed", tol=1e-9, precond=vdp.VDP_PRECOND_SPECTRAL)
+    assert stm.ok and rel(pm, ref) <= 1e-8
+
+
+def test_spectral_timed_and_limits():
+    prob = V.smooth_problem((32, 48, 64), seed=65)
+    nz, ny, nx = prob.shape
+    rho = torch.from_numpy(prob.rho).to(DEV)
+    f = torch.from_numpy(prob.f).to(DEV)
+    with vdp.Solver(nx, ny, nz, prob.L, precision="mixed", precond=vdp.VDP_PRECOND_SPECTRAL) as s:
+        s.set_density(rho)
+        p1, p2 = torch.empty_like(f), torch.empty_like(f)
+        st1 = s.solve(f, p1, 1e-9)
+        st2, kinds = s.solve_timed(f, p2, 1e-9)
+        assert torch.equal(p1, p2) and st1.iters == st2.iters
+        # one preconditioner application per Krylov iteration
+        napp = kinds["spec_z"]["launches"]
+        assert napp == st2.iters
+        assert kinds["spec_x"]["launches"] == 2 * napp == kinds["spec_y"]["launches"]
+        assert kinds["stencil"]["launches"] == st2.iters
+        with vdp.Batch("mixed") as b:  # spectral contexts are single solves
+            with pytest.raises(vdp.VdpError):
+                b.add(s, f, p1, 1e-9)
+    with pytest.raises(vdp.VdpError) as e:  # 40 is not a supported FFT length
+        vdp.Solver(40, 32, 32, 1.0, precond=vdp.VDP_PRECOND_SPECTRAL)
+    assert e.value.status == vdp.VDP_EINVAL
