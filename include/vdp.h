@@ -71,8 +71,8 @@ typedef enum {
                              Krylov iteration).  The preconditioned condition number is at most
                              max(rho)/min(rho) for any grid size.  Each of nx, ny, nz must be one
                              of 32, 48, 64, 96, 128, 192, 256, 512; direct stencil sweep only;
-                             single solves (not batch members).  Extra memory: about 16 bytes
-                             per cell */
+                             batch members only in batches of ordinary launches (persistent =
+                             0).  Extra memory: about 16 bytes per cell */
 } vdp_precond;
 
 typedef struct {

@@ -23,6 +23,19 @@ VDP_OK, VDP_EINVAL, VDP_ENOMEM, VDP_EDENSITY, VDP_ENOTCONV, VDP_EBREAKDOWN, VDP_
 VDP_FP64, VDP_MIXED, VDP_MIXED_BF16 = 0, 1, 2
 VDP_PRECOND_JACOBI, VDP_PRECOND_CHEB, VDP_PRECOND_SPECTRAL = 0, 1, 2
 PRECISIONS = {"fp64": VDP_FP64, "mixed": VDP_MIXED, "mixed_bf16": VDP_MIXED_BF16}
+# grid sizes (per direction) the spectral preconditioner's FFT passes support
+SPECTRAL_SIZES = (32, 48, 64, 96, 128, 192, 256, 512)
+
+
+def spectral_supported(nx: int, ny: int, nz: int) -> bool:
+    return all(n in SPECTRAL_SIZES for n in (nx, ny, nz))
+
+
+def spectral_extra_bytes(nx: int, ny: int, nz: int) -> int:
+    """Device memory the spectral preconditioner adds to a context: z (8 B/cell), the weights
+    (4 B/cell) and the half spectrum (8 B per complex value, rows padded to 8 values)."""
+    nxp = ((nx // 2 + 1 + 7) // 8) * 8
+    return 12 * nx * ny * nz + 8 * nxp * ny * nz
 
 
 class VdpUnavailable(RuntimeError):

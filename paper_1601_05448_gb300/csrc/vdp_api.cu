@@ -213,7 +213,8 @@ int ensure_graph(vdp_ctx* c, int prec) {
         e = launch_spectral_pass(prec, pass, a, c->cap);
     }
     if (e == cudaSuccess)
-      e = launch_stencil(prec, c->lay.mode, c->desc, c->units, c->lay.nunits, c->lay.threads,
+      e = launch_stencil(prec, c->lay.mode, c->hdesc.pc == PC_CHEB, c->desc, c->units,
+                         c->lay.nunits, c->lay.threads,
                          c->lay.smem, c->cap);
     if (e == cudaSuccess)
       e = launch_flat(prec, c->desc, c->units + c->lay.nunits, c->lay.nunits_f, c->cap);

@@ -19,6 +19,7 @@
 #include "vdp_ctx.h"
 #include "vdp_internal.cuh"
 #include "vdp_launch.h"
+#include "vdp_spectral.h"
 
 using namespace vdp;
 
@@ -140,10 +141,23 @@ int capture(vdp_batch* b, int pairs) {
     e = launch_persistent(b->prec, b->d_desc, b->d_units, b->ns, b->d_units + b->ns, b->nf, pairs,
                           b->d_ctl, b->grid, b->cap);
   } else {
+    int cheb = 0;  // the stencil kernel variant with Chebyshev sweeps if any member needs it
+    for (int k : b->active) cheb |= b->members[k].ctx->hdesc.pc == PC_CHEB;
     for (int i = 0; i < pairs && e == cudaSuccess; ++i) {
       e = launch_res64(b->prec, b->d_desc, b->d_units, b->ns, kDirectThreads, b->cap);
+      // members with the spectral preconditioner: their five FFT passes (each gated on its own
+      // member's phase), between the residual and the stencil sweeps as in a solve alone
+      for (size_t k = 0; k < b->active.size() && e == cudaSuccess; ++k) {
+        const vdp_ctx* c = b->members[b->active[k]].ctx;
+        if (c->hdesc.pc != PC_SPECTRAL) continue;
+        SpecArgs a;
+        solve_spec_args(c, b->prec, &a);
+        for (int pass = 0; pass < SPEC_PASSES && e == cudaSuccess; ++pass)
+          e = launch_spectral_pass(b->prec, pass, a, b->cap);
+      }
       if (e == cudaSuccess)
-        e = launch_stencil(b->prec, 0, b->d_desc, b->d_units, b->ns, kDirectThreads, 0, b->cap);
+        e = launch_stencil(b->prec, 0, cheb, b->d_desc, b->d_units, b->ns, kDirectThreads, 0,
+                           b->cap);
       if (e == cudaSuccess) e = launch_flat(b->prec, b->d_desc, b->d_units + b->ns, b->nf, b->cap);
     }
   }
@@ -214,7 +228,9 @@ void vdp_batch_destroy(vdp_batch* b) {
 int vdp_batch_add(vdp_batch* b, vdp_ctx* c, const double* rhs, double* p, double tol) {
   if (!b || !c || !rhs || !p || !(tol > 0.0)) return VDP_EINVAL;
   if (!c->has_density || c->opts.precision != b->prec || c->opts.stencil != 0) return VDP_EINVAL;
-  if (c->opts.precond == VDP_PRECOND_SPECTRAL) return VDP_EINVAL;  // single solves only
+  // the spectral passes are separate kernels: members with that preconditioner need the batch
+  // of ordinary launches, not the persistent kernel
+  if (c->opts.precond == VDP_PRECOND_SPECTRAL && b->persistent) return VDP_EINVAL;
   if (!is_device_ptr(rhs) || !is_device_ptr(p) || ((uintptr_t)rhs & 15) || ((uintptr_t)p & 15))
     return VDP_EINVAL;
   if (find(b, c, nullptr)) return VDP_EINVAL;  // already a member
@@ -223,6 +239,10 @@ int vdp_batch_add(vdp_batch* b, vdp_ctx* c, const double* rhs, double* p, double
   if ((c->layout_dirty || c->layout_prec != b->prec || !c->hdesc_valid) &&
       (s = configure_layout(c, b->prec)) != VDP_OK)
     return s;
+  if (c->hdesc.pc == PC_SPECTRAL && !c->omega_valid) {
+    VDP_CK(launch_omega(c->sinv, c->n, c->omega, c->stream));
+    c->omega_valid = true;
+  }
   VDP_CK(cudaStreamSynchronize(c->stream));
   VDP_CK(launch_init(c->desc, rhs, p, tol, c->opts.inner_tol, c->opts.max_iter, c->opts.max_iter,
                      c->opts.use_guess ? 1 : 0, b->prec, b->stream));

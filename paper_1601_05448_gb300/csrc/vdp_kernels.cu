@@ -557,10 +557,19 @@ __device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, T& par
 //   d_j = rho_j rho_{j-1} d_{j-1} + (2 rho_j / delta) (rt - At z_j),  z_{j+1} = z_j + d_j,
 // with rho_0 = 1 / sigma, rho_j = 1 / (2 sigma - rho_{j-1}), sigma = theta / delta, d_0 = z_1;
 // the last sweep also sums <rt, z>.
+template <class T> struct IsF64 { static constexpr bool value = false; };
+template <> struct IsF64<double> { static constexpr bool value = true; };
+
 template <class T, class BT, bool CHEB>
 __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int unit, T& part) {
   constexpr int V = VecW<T>::V;
   constexpr bool kDiag = CoefTraits<BT>::kDiag;
+  // FP64 sweeps are bound by the FP64 pipe, not by HBM: there the stencil is applied to the
+  // preconditioned residual z itself, and q = At d follows from q = At z + beta q_old, with
+  // d = z + beta d_old formed for the thread's own cells only (9 FP64 operations per cell
+  // instead of also forming d for the rows above and below and the row ends).  FP32 sweeps are
+  // HBM bound and keep forming d, which reads one vector (q_old) less.
+  constexpr bool QREC = !CHEB && IsF64<T>::value;
   const int nx = I.nx, ny = I.ny, nz = I.nz;
   const int tpr = nx / V;  // threads per row
   const int tile = unit % I.uy, chunk = unit / I.uy;
@@ -580,6 +589,7 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
   const bool last = CHEB && cj == I.cheb_k - 1;
   T beta = (T)st->beta, scale = 1, c1 = 0, c2 = 0;
   bool use_old = st->inner_iters > 0;
+  bool form = use_old && !QREC;  // form d = src + beta d_old for every marched value
   const T* rt = static_cast<const T*>(I.r);
   const T* src = I.pc != PC_JACOBI ? static_cast<const T*>(I.za) : rt;
   const T* dold = static_cast<const T*>(st->parity ? I.d1 : I.d0);
@@ -603,6 +613,7 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
     c1 = (T)(r * rp);                  // rho_j rho_{j-1}
     c2 = (T)(2.0 * r / I.cheb_delta);  // 2 rho_j / delta
     use_old = false;
+    form = false;
     beta = 0;
   }
   const BT* sx = static_cast<const BT*>(I.sx);
@@ -622,7 +633,7 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
     if (CHEB) {
 #pragma unroll
       for (int k = 0; k < V; ++k) d[k] *= scale;
-    } else if (use_old) {
+    } else if (form) {
       T b[V];
       LdgIO<T, V>::ld(dold + o, b);
 #pragma unroll
@@ -631,7 +642,7 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
   };
   auto d1 = [&](long long o) -> T {
     if (CHEB) return __ldg(src + o) * scale;
-    return use_old ? fma(beta, __ldg(dold + o), __ldg(src + o)) : __ldg(src + o);
+    return form ? fma(beta, __ldg(dold + o), __ldg(src + o)) : __ldg(src + o);
   };
 
   T dm[V], dc[V], dp[V];
@@ -654,6 +665,11 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
     CoefIO<BT, T, V>::ldg(sz + oc, bz);
     CoefIO<BT, T, V>::ldg(sz + op, bzp);
     if (kDiag) CoefIO<BT, T, V>::ldg(sd + oc, bd);
+    T qo[V], dol[V];  // QREC: q_old and d_old of the own cells
+    if (QREC && use_old) {
+      VecIO<T, V>::ld(q + oc, qo);  // q is rewritten below by this thread only
+      LdgIO<T, V>::ld(dold + oc, dol);
+    }
     const T bxr = (T)ldg1(sx + oc + dxr);
     // x neighbours of the first and last cell: adjacent lanes, or a load at row ends / warp ends
     T left = __shfl_up_sync(0xffffffffu, dc[V - 1], 1);
@@ -675,7 +691,16 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
       a = fma(-bz[k], dm[k], a);
       a = fma(-bzp[k], dp[k], a);
       qv[k] = a;
-      if (!CHEB) sum[k] = fma(dc[k], a, sum[k]);
+      if (!CHEB && !QREC) sum[k] = fma(dc[k], a, sum[k]);
+    }
+    T dn[V];
+    if (QREC) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        dn[k] = use_old ? fma(beta, dol[k], dc[k]) : dc[k];
+        qv[k] = use_old ? fma(beta, qo[k], qv[k]) : qv[k];
+        sum[k] = fma(dn[k], qv[k], sum[k]);
+      }
     }
     if (CHEB) {
       T r[V], dprev[V], zn[V], dn[V];
@@ -697,7 +722,10 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
         if (!last) VecIO<T, V>::st(dch + oc, dn);
       }
     } else if (active) {
-      VecIO<T, V>::st(dnew + oc, dc);
+      if (QREC)
+        VecIO<T, V>::st(dnew + oc, dn);
+      else
+        VecIO<T, V>::st(dnew + oc, dc);
       VecIO<T, V>::st(q + oc, qv);
     }
 #pragma unroll
@@ -894,14 +922,16 @@ __device__ void sweep_res64(const InstDesc& I, const InstState* st, int unit,
 
 // One stencil-kind unit of instance I: WHICH = 0 handles the RES64 and STENCIL phases, 1 only
 // STENCIL, 2 only RES64; a no-op for other phases.
-template <class T, class BT, int MODE, int WHICH = 0>
+// CHEBOK = false compiles the Chebyshev sweep out (instances without that preconditioner): the
+// kernel then keeps the register budget of the plain stencil sweep.
+template <class T, class BT, int MODE, int WHICH = 0, bool CHEBOK = true>
 __device__ __forceinline__ void stencil_kind_unit(const InstDesc& I, int unit,
                                                   unsigned char* smem_raw) {
   InstState* st = I.st;
   const int phase = __ldcg(&st->phase);  // one load decides whether this unit has work
   if (phase != PH_RES64 && phase != PH_STENCIL && phase != PH_CHEB) return;
   if ((WHICH == 1 && phase == PH_RES64) || (WHICH == 2 && phase != PH_RES64)) return;
-  if (MODE != 0 && phase == PH_CHEB) return;  // the polynomial runs in the direct form only
+  if ((MODE != 0 || !CHEBOK) && phase == PH_CHEB) return;  // direct form with CHEBOK only
   const InstState sn = snapshot(st);
   if (WHICH != 1 && phase == PH_RES64) {
     double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
@@ -912,9 +942,12 @@ __device__ __forceinline__ void stencil_kind_unit(const InstDesc& I, int unit,
     store_partials<kSlots, double>(acc, I.part, I.nunits, unit);
   } else if (WHICH != 2) {
     T part[1] = {0};
-    if (MODE == 0 && phase == PH_CHEB)
-      sweep_stencil_direct<T, BT, true>(I, &sn, unit, part[0]);
-    else if (MODE == 0)
+    if constexpr (MODE == 0 && CHEBOK) {
+      if (phase == PH_CHEB)
+        sweep_stencil_direct<T, BT, true>(I, &sn, unit, part[0]);
+      else
+        sweep_stencil_direct<T, BT, false>(I, &sn, unit, part[0]);
+    } else if (MODE == 0)
       sweep_stencil_direct<T, BT, false>(I, &sn, unit, part[0]);
     else
       sweep_stencil<T, BT>(I, st, unit, part[0], smem_raw);
@@ -959,11 +992,11 @@ __device__ __forceinline__ void flat_kind_unit(const InstDesc& I, int unit) {
 template <class T> struct DirectOcc { static constexpr int kMinBlocks = VDP_DIRECT_MIN_BLOCKS; };
 template <> struct DirectOcc<float> { static constexpr int kMinBlocks = VDP_DIRECT_MIN_BLOCKS + 1; };
 
-template <class T, class BT>
+template <class T, class BT, bool CHEBOK>
 __global__ void __launch_bounds__(kDirectThreads, DirectOcc<T>::kMinBlocks) k_stencil_direct(
     const InstDesc* __restrict__ insts, const UnitRef* __restrict__ units) {
   const UnitRef ur = units[blockIdx.x];
-  stencil_kind_unit<T, BT, 0, 1>(insts[ur.inst], ur.unit, nullptr);
+  stencil_kind_unit<T, BT, 0, 1, CHEBOK>(insts[ur.inst], ur.unit, nullptr);
 }
 
 // Direct register march, RES64 phase only (a few launches per solve do work; the kernel has its
@@ -1273,11 +1306,16 @@ cudaError_t launch_init(InstDesc* desc, const double* rhs, double* p, double tol
   return cudaGetLastError();
 }
 
-static void* stencil_fn(int prec, int mode) {
+static void* stencil_fn(int prec, int mode, int cheb) {
+  if (mode == 0 && cheb) {
+    if (prec == PREC_FP64) return (void*)k_stencil_direct<double, double, true>;
+    if (prec == PREC_MIXED) return (void*)k_stencil_direct<float, float, true>;
+    return (void*)k_stencil_direct<float, __nv_bfloat16, true>;
+  }
   if (mode == 0) {
-    if (prec == PREC_FP64) return (void*)k_stencil_direct<double, double>;
-    if (prec == PREC_MIXED) return (void*)k_stencil_direct<float, float>;
-    return (void*)k_stencil_direct<float, __nv_bfloat16>;
+    if (prec == PREC_FP64) return (void*)k_stencil_direct<double, double, false>;
+    if (prec == PREC_MIXED) return (void*)k_stencil_direct<float, float, false>;
+    return (void*)k_stencil_direct<float, __nv_bfloat16, false>;
   }
   if (prec == PREC_FP64) return (void*)k_stencil_tma<double, double>;
   if (prec == PREC_MIXED) return (void*)k_stencil_tma<float, float>;
@@ -1285,8 +1323,9 @@ static void* stencil_fn(int prec, int mode) {
 }
 
 cudaError_t prepare_step(int prec, int mode, size_t smem_bytes) {
-  return cudaFuncSetAttribute(stencil_fn(prec, mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes);
+  if (mode == 0) return cudaSuccess;  // the direct sweeps use no dynamic shared memory
+  return cudaFuncSetAttribute(stencil_fn(prec, mode, 0),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 cudaError_t launch_res64(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
@@ -1298,9 +1337,10 @@ cudaError_t launch_res64(int prec, const InstDesc* desc, const UnitRef* units, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_stencil(int prec, int mode, const InstDesc* desc, const UnitRef* units,
-                           int nunits, int threads, size_t smem_bytes, cudaStream_t s) {
-  void* fn = stencil_fn(prec, mode);
+cudaError_t launch_stencil(int prec, int mode, int cheb, const InstDesc* desc,
+                           const UnitRef* units, int nunits, int threads, size_t smem_bytes,
+                           cudaStream_t s) {
+  void* fn = stencil_fn(prec, mode, cheb);
   void* args[] = {(void*)&desc, (void*)&units};
   return cudaLaunchKernel(fn, dim3(nunits), dim3(threads), args, smem_bytes, s);
 }

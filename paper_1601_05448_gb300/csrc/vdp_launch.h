@@ -23,8 +23,10 @@ cudaError_t prepare_step(int prec, int mode, size_t smem_bytes);
 // mode 0 only: the FP64 residual sweep (its own kernel, launched before each stencil launch)
 cudaError_t launch_res64(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
                          int threads, cudaStream_t s);
-cudaError_t launch_stencil(int prec, int mode, const InstDesc* desc, const UnitRef* units,
-                           int nunits, int threads, size_t smem_bytes, cudaStream_t s);
+// cheb = 1: the variant that also runs Chebyshev preconditioner sweeps (PH_CHEB)
+cudaError_t launch_stencil(int prec, int mode, int cheb, const InstDesc* desc,
+                           const UnitRef* units, int nunits, int threads, size_t smem_bytes,
+                           cudaStream_t s);
 cudaError_t launch_flat(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
                         cudaStream_t s);
 

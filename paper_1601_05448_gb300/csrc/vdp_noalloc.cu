@@ -178,7 +178,7 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
   while (!done && rounds < max_rounds) {
     for (int i = 0; i < m; ++i) {
       NA_CK(launch_res64(precision, desc, units, nunits, lay.threads, s));
-      NA_CK(launch_stencil(precision, lay.mode, desc, units, nunits, lay.threads, lay.smem, s));
+      NA_CK(launch_stencil(precision, lay.mode, 0, desc, units, nunits, lay.threads, lay.smem, s));
       NA_CK(launch_flat(precision, desc, units + nunits, nunits_f, s));
     }
     ++rounds;

@@ -41,10 +41,11 @@ cudaError_t launch_for_phase(vdp_ctx* c, int prec, int phase, cudaStream_t s) {
   switch (phase) {
     case PH_RES64:
       if (l.mode == 0) return launch_res64(prec, c->desc, c->units, l.nunits, l.threads, s);
-      return launch_stencil(prec, l.mode, c->desc, c->units, l.nunits, l.threads, l.smem, s);
+      return launch_stencil(prec, l.mode, 0, c->desc, c->units, l.nunits, l.threads, l.smem, s);
     case PH_STENCIL:
     case PH_CHEB:
-      return launch_stencil(prec, l.mode, c->desc, c->units, l.nunits, l.threads, l.smem, s);
+      return launch_stencil(prec, l.mode, c->hdesc.pc == PC_CHEB, c->desc, c->units, l.nunits,
+                            l.threads, l.smem, s);
     default:
       return launch_flat(prec, c->desc, c->units + l.nunits, l.nunits_f, s);
   }

@@ -7,8 +7,9 @@ batch engine.  Between batch runs it
 
   * moves arrived requests to the waiting queue,
   * admits waiting requests (first come, first served) while a context slot and the HBM budget
-    allow -- a new context costs about 96 bytes per cell -- uploading their inputs and adding
-    them to the running batch, so new work overlaps with requests already on the GPU,
+    allow -- a new context costs 98 bytes per cell, plus about 16 with the spectral
+    preconditioner -- uploading their inputs and adding them to the running batch, so new work
+    overlaps with requests already on the GPU,
   * retires finished members, records their latency (arrival to result ready) and returns their
     contexts to the pool (idle contexts are freed, oldest first, when the budget needs room).
 
@@ -23,7 +24,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import PRECISIONS, Batch, Solver, VdpError
+from . import PRECISIONS, VDP_PRECOND_JACOBI, VDP_PRECOND_SPECTRAL, Batch, Solver, VdpError, \
+    spectral_extra_bytes, spectral_supported
 
 BYTES_PER_CELL = 96 + 2  # device memory of one context per cell (FP64-sized buffers + BF16 diag)
 
@@ -74,10 +76,15 @@ class ServeStats:
 
 
 class Server:
-    """``Server(precision="mixed", hbm_budget=64 GB, max_active=64).run(requests)``."""
+    """``Server(precision="mixed", hbm_budget=64 GB, max_active=64).run(requests)``.
+
+    precond="spectral" gives every request whose grid the FFT passes support the spectral
+    preconditioner (the others get Jacobi); it needs the batch of ordinary launches
+    (persistent=False).  precond="jacobi" uses Jacobi everywhere."""
 
     def __init__(self, precision: str = "mixed", hbm_budget: int = 64 << 30, max_active: int = 64,
-                 pairs_per_run: int = 8, persistent: bool = True, tuned: bool = False, device: str = "cuda:0"):
+                 pairs_per_run: int = 8, persistent: bool = False, tuned: bool = False, device: str = "cuda:0",
+                 precond: str = "spectral"):
         import torch
         self.torch = torch
         self.precision = precision
@@ -85,6 +92,9 @@ class Server:
         self.max_active = int(max_active)
         self.pairs = int(pairs_per_run)
         self.tuned = tuned
+        if precond not in ("spectral", "jacobi") or (precond == "spectral" and persistent):
+            raise ValueError("precond must be 'jacobi', or 'spectral' with persistent=False")
+        self.precond = precond
         self.device = torch.device(device)
         self.batch = Batch(precision, persistent=persistent)
         self.idle = collections.OrderedDict()   # ctx id -> (Solver, shape) available for reuse
@@ -93,9 +103,14 @@ class Server:
 
     # ---- context pool -----------------------------------------------------------------------
 
+    def _spectral(self, shape) -> bool:
+        nz, ny, nx = shape
+        return self.precond == "spectral" and spectral_supported(nx, ny, nz)
+
     def _ctx_bytes(self, shape) -> int:
         nz, ny, nx = shape
-        return BYTES_PER_CELL * nx * ny * nz
+        extra = spectral_extra_bytes(nx, ny, nz) if self._spectral(shape) else 0
+        return BYTES_PER_CELL * nx * ny * nz + extra
 
     def _acquire(self, shape, L):
         for k, (s, shp) in list(self.idle.items()):
@@ -114,6 +129,7 @@ class Server:
         if self.tuned:
             from .tune import cached_options
             opts = cached_options(nx, ny, nz, self.precision, batchable=True) or {}
+        opts["precond"] = VDP_PRECOND_SPECTRAL if self._spectral(shape) else VDP_PRECOND_JACOBI
         try:
             s = Solver(nx, ny, nz, L, precision=self.precision, **opts)
         except VdpError:

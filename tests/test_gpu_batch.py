@@ -102,3 +102,37 @@ def test_continuous_admission_and_retirement():
         assert torch.equal(p, q), items[i][0].name
     for s, _ in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_spectral_members_equal_alone(precision):
+    """Batch of ordinary launches with spectrally preconditioned members (FFT-supported sizes),
+    mixed with a Jacobi member: every result equals its solve alone, bit for bit."""
+    probs = [(V.hotspot_problem(32, seed=57, nspots=40, target_ratio=5.0), 1e-9, vdp.VDP_PRECOND_SPECTRAL),
+             (V.smooth_problem((48, 32, 64), seed=58), 1e-10, vdp.VDP_PRECOND_SPECTRAL),
+             (V.smooth_problem((16, 16, 24), seed=51), 1e-9, vdp.VDP_PRECOND_JACOBI),
+             (V.hotspot_problem(64, seed=59, nspots=312, target_ratio=8.0), 1e-8, vdp.VDP_PRECOND_SPECTRAL)]
+    members = []
+    for prob, tol, pc in probs:
+        nz, ny, nx = prob.shape
+        s = vdp.Solver(nx, ny, nz, prob.L, precision=precision, precond=pc)
+        s.set_density(torch.from_numpy(prob.rho).to(DEV))
+        f = torch.from_numpy(prob.f).to(DEV)
+        p_alone = torch.empty_like(f)
+        st_alone = s.solve(f, p_alone, tol)
+        members.append((prob, tol, s, f, p_alone, st_alone))
+    with vdp.Batch(precision, persistent=False) as b:
+        outs = []
+        for prob, tol, s, f, *_ in members:
+            p = torch.full_like(f, -1.0)
+            b.add(s, f, p, tol)
+            outs.append(p)
+        b.run_to_completion(max_pairs=8)
+        for (prob, tol, s, f, p_alone, st_alone), p in zip(members, outs):
+            st = s.stats()
+            assert st.ok and st.iters == st_alone.iters and st.rel_res <= tol
+            assert torch.equal(p, p_alone), prob.name
+    ref, _ = oracle.solve_cg(probs[3][0].rho, probs[3][0].f, probs[3][0].L, tol=1e-13)
+    assert np.linalg.norm(outs[3].cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-7
+    for _, _, s, *_ in members:
+        s.close()

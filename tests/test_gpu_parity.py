@@ -344,7 +344,7 @@ def test_spectral_timed_and_limits():
         assert napp == st2.iters
         assert kinds["spec_x"]["launches"] == 2 * napp == kinds["spec_y"]["launches"]
         assert kinds["stencil"]["launches"] == st2.iters
-        with vdp.Batch("mixed") as b:  # spectral contexts are single solves
+        with vdp.Batch("mixed", persistent=True) as b:  # the persistent kernel has no FFT passes
             with pytest.raises(vdp.VdpError):
                 b.add(s, f, p1, 1e-9)
     with pytest.raises(vdp.VdpError) as e:  # 40 is not a supported FFT length

@@ -30,21 +30,22 @@ def request_stream(count=12, seed=7):
     return reqs
 
 
-def solve_alone(req, precision):
+def solve_alone(req, precision, precond="jacobi"):
     nz, ny, nx = req.shape
-    with vdp.Solver(nx, ny, nz, req.L, precision=precision) as s:
+    pc = vdp.VDP_PRECOND_SPECTRAL if precond == "spectral" and vdp.spectral_supported(nx, ny, nz) else 0
+    with vdp.Solver(nx, ny, nz, req.L, precision=precision, precond=pc) as s:
         s.set_density(torch.from_numpy(req.rho).to(DEV))
         p = torch.empty(req.shape, dtype=torch.float64, device=DEV)
         st = s.solve(torch.from_numpy(req.f).to(DEV), p, req.tol)
     return p, st
 
 
-@pytest.mark.parametrize("persistent", [True, False])
-def test_served_results_equal_alone(persistent):
+@pytest.mark.parametrize("persistent,precond", [(True, "jacobi"), (False, "jacobi"), (False, "spectral")])
+def test_served_results_equal_alone(persistent, precond):
     reqs = request_stream()
     seen_overlap = []
 
-    with serve.Server("mixed", max_active=8, pairs_per_run=4, persistent=persistent) as srv:
+    with serve.Server("mixed", max_active=8, pairs_per_run=4, persistent=persistent, precond=precond) as srv:
         stats = srv.run(reqs, on_done=lambda r: seen_overlap.append(r.t_admit))
     s = stats.summary()
     assert s["completed"] == len(reqs) and s["p99_latency_s"] >= s["p50_latency_s"] > 0
@@ -52,7 +53,7 @@ def test_served_results_equal_alone(persistent):
     assert any(b.t_admit < a.t_done for a in reqs for b in reqs if b.arrival_s > a.arrival_s)
     for r in reqs:
         assert r.status == vdp.VDP_OK
-        p, st = solve_alone(r, "mixed")
+        p, st = solve_alone(r, "mixed", precond)
         assert st.iters == r.iters
         assert torch.equal(p, r.p), r.rid
 
@@ -60,7 +61,7 @@ def test_served_results_equal_alone(persistent):
 def test_hbm_budget_admission():
     reqs = request_stream(count=8, seed=11)
     budget = 2 * serve.BYTES_PER_CELL * 48 ** 3  # room for about two of the larger contexts
-    with serve.Server("mixed", hbm_budget=budget, max_active=8, pairs_per_run=4) as srv:
+    with serve.Server("mixed", hbm_budget=budget, max_active=8, pairs_per_run=4, precond="jacobi") as srv:
         stats = srv.run(reqs)
     assert stats.completed == len(reqs) and stats.peak_bytes <= budget
     ref, _ = oracle.solve_cg(reqs[0].rho, reqs[0].f, reqs[0].L, tol=1e-13)
