@@ -75,6 +75,22 @@ typedef enum {
                              0).  Extra memory: about 16 bytes per cell */
 } vdp_precond;
 
+typedef enum {
+  VDP_METHOD_CG = 0,          /* preconditioned conjugate gradients (precond), FP64 refinement */
+  VDP_METHOD_FIXED_POINT = 1  /* the paper's own iteration (Sec. 3.4, Eq. (Pois)): with p = p_g
+                                 + dp it drops the term rho grad(1/rho) . grad(dp) and solves the
+                                 constant-coefficient equation L_h dp = rho (f - A p_g) with the
+                                 spectral inverse (FP32 FFTs), then p_g += damping * dp, until
+                                 the FP64 residual meets tol.  Each iteration costs one FP64
+                                 residual and one spectral inverse.  Converges when the density
+                                 varies moderately (the paper: the rate depends on the density
+                                 variation); a residual growing past 1e4 x ||f - <f>|| ends the
+                                 solve with VDP_ENOTCONV.  Grid sizes as VDP_PRECOND_SPECTRAL;
+                                 the density weight is taken at vdp_set_density, so select the
+                                 method before setting the density (VDP_EINVAL otherwise);
+                                 precond is ignored; iters counts fixed-point updates */
+} vdp_method;
+
 typedef struct {
   int precision;       /* vdp_precision (default VDP_FP64) */
   int max_iter;        /* cap on the total number of inner Krylov iterations (default 20000) */
@@ -91,6 +107,9 @@ typedef struct {
   int stages;          /* shared-memory pipeline stages of the stencil sweep, 4..8 (0 = auto) */
   int threads;         /* threads per stencil work unit, 128..512, multiple of 32 (0 = auto) */
   int steps_per_sync;  /* (stencil, flat) launch pairs per host convergence check (0 = auto) */
+  int method;          /* vdp_method (default VDP_METHOD_CG) */
+  double damping;      /* VDP_METHOD_FIXED_POINT: scale of each update, 0 < damping <= 2
+                          (default 1, the paper's update) */
 } vdp_opts;
 
 typedef struct {

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libvdp.so")
 VDP_OK, VDP_EINVAL, VDP_ENOMEM, VDP_EDENSITY, VDP_ENOTCONV, VDP_EBREAKDOWN, VDP_ETIMEOUT, VDP_ECUDA = range(8)
 VDP_FP64, VDP_MIXED, VDP_MIXED_BF16 = 0, 1, 2
 VDP_PRECOND_JACOBI, VDP_PRECOND_CHEB, VDP_PRECOND_SPECTRAL = 0, 1, 2
+VDP_METHOD_CG, VDP_METHOD_FIXED_POINT = 0, 1
 PRECISIONS = {"fp64": VDP_FP64, "mixed": VDP_MIXED, "mixed_bf16": VDP_MIXED_BF16}
 # grid sizes (per direction) the spectral preconditioner's FFT passes support
 SPECTRAL_SIZES = (32, 48, 64, 96, 128, 192, 256, 512)
@@ -55,7 +56,8 @@ class vdp_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("precond", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("use_guess", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("stencil", ctypes.c_int), ("tile_y", ctypes.c_int), ("units", ctypes.c_int),
-                ("stages", ctypes.c_int), ("threads", ctypes.c_int), ("steps_per_sync", ctypes.c_int)]
+                ("stages", ctypes.c_int), ("threads", ctypes.c_int), ("steps_per_sync", ctypes.c_int),
+                ("method", ctypes.c_int), ("damping", ctypes.c_double)]
 
 
 class vdp_stats(ctypes.Structure):

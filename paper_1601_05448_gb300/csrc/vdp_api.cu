@@ -68,6 +68,8 @@ void vdp_default_options(vdp_opts* o) {
   o->stages = 0;
   o->threads = 0;
   o->steps_per_sync = 0;
+  o->method = VDP_METHOD_CG;
+  o->damping = 1.0;
 }
 
 const char* vdp_strerror(int s) {
@@ -102,7 +104,7 @@ void free_ctx(vdp_ctx* c) {
   cudaSetDevice(c->device);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   void* bufs[] = {c->bx, c->by, c->bz, c->sinv, c->sx, c->sy, c->sz, c->sd, c->x, c->r, c->d0, c->d1,
-                  c->za, c->zb, c->dch, c->spec, c->omega, c->sptab,
+                  c->za, c->zb, c->dch, c->spec, c->omega, c->sptab, c->rho_w,
                   c->q, c->part, c->ticket, c->st, c->desc, c->units, c->flag, c->stage_a,
                   c->stage_b};
   for (void* b : bufs)
@@ -165,7 +167,9 @@ int configure_layout(vdp_ctx* c, int prec) {
   // polynomial preconditioner: Chebyshev on [b / kChebRange, b], b = 2 >= the largest
   // eigenvalue of the unit-diagonal operator
   d.cheb_k = c->opts.precond == VDP_PRECOND_CHEB ? c->opts.cheb_degree : 1;
-  d.pc = c->opts.precond == VDP_PRECOND_SPECTRAL ? PC_SPECTRAL : (d.cheb_k > 1 ? PC_CHEB : PC_JACOBI);
+  d.pc = c->opts.method == VDP_METHOD_FIXED_POINT ? PC_FIXED
+         : c->opts.precond == VDP_PRECOND_SPECTRAL ? PC_SPECTRAL
+                                                   : (d.cheb_k > 1 ? PC_CHEB : PC_JACOBI);
   {
     const double b = 2.0, a = b / kChebRange;
     d.cheb_theta = 0.5 * (b + a);
@@ -206,7 +210,7 @@ int ensure_graph(vdp_ctx* c, int prec) {
     cudaError_t e = cudaSuccess;
     if (c->lay.mode == 0)  // the residual sweep has its own kernel in the direct mode
       e = launch_res64(prec, c->desc, c->units, c->lay.nunits, c->lay.threads, c->cap);
-    if (e == cudaSuccess && c->hdesc.pc == PC_SPECTRAL) {  // z = M^-1 rt before the stencil sweep
+    if (e == cudaSuccess && c->hdesc.pc >= PC_SPECTRAL) {  // z = M^-1 rt before the stencil sweep
       SpecArgs a;
       solve_spec_args(c, prec, &a);
       for (int pass = 0; pass < SPEC_PASSES && e == cudaSuccess; ++pass)
@@ -277,10 +281,13 @@ int ensure_spectral(vdp_ctx* c) {
 
 void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a) {
   const int m = c->nx / 2;
+  const bool fixed = c->opts.method == VDP_METHOD_FIXED_POINT;
   a->in = c->r;
-  a->out = c->za;
-  a->dot_with = c->r;
-  a->omega = c->omega;
+  // CG: z = W (-L_h)^-1 W rt.  Fixed point: x = W (-L_h)^-1 (rho W rt) * damping, applied as
+  // p -= D^-1/2 x, i.e. p += damping * L_h^-1 (rho r)
+  a->out = fixed ? c->x : c->za;
+  a->omega_in = fixed ? c->rho_w : c->omega;
+  a->omega_out = c->omega;
   a->spec = c->spec;
   a->tw = reinterpret_cast<const float2*>(c->sptab);
   a->lam = c->sptab + 2 * (2 * m + 1 + c->ny + c->nz);
@@ -288,10 +295,21 @@ void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a) {
   a->ny = c->ny;
   a->nz = c->nz;
   a->nxp = spectral_pitch(c->nx);
-  a->scale = (float)(1.0 / (double)c->n);
+  a->scale = (float)((fixed ? c->opts.damping : 1.0) / (double)c->n);
   a->st = c->st;
   a->I = c->desc;
+  a->zunits = spectral_units(c->nx, c->ny, c->nz);
   (void)prec;
+}
+
+int prepare_spectral_solve(vdp_ctx* c) {
+  if (c->hdesc.pc < PC_SPECTRAL) return VDP_OK;
+  if (c->hdesc.pc == PC_FIXED && !c->rho_w_valid) return VDP_EINVAL;
+  if (!c->omega_valid) {
+    VDP_CK(launch_omega(c->sinv, c->n, c->omega, c->stream));
+    c->omega_valid = true;
+  }
+  return VDP_OK;
 }
 
 }  // namespace vdp
@@ -365,6 +383,11 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
   if (o->precond == VDP_PRECOND_SPECTRAL &&
       (o->stencil != 0 || !spectral_supported(c->nx, c->ny, c->nz)))
     return VDP_EINVAL;
+  if (o->method != VDP_METHOD_CG && o->method != VDP_METHOD_FIXED_POINT) return VDP_EINVAL;
+  if (o->method == VDP_METHOD_FIXED_POINT &&
+      (o->stencil != 0 || !spectral_supported(c->nx, c->ny, c->nz) || !(o->damping > 0.0) ||
+       o->damping > 2.0))
+    return VDP_EINVAL;
   if (o->precond == VDP_PRECOND_CHEB && (o->cheb_degree < 1 || o->cheb_degree > 16 || o->stencil != 0))
     return VDP_EINVAL;
   if (o->tile_y < 0 || o->units < 0 || o->stages < 0 || o->threads < 0 || o->steps_per_sync < 0 ||
@@ -393,12 +416,21 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
       return cuda_fail(e, "vdp_set_options (Chebyshev buffers)");
     }
   }
-  if (o->precond == VDP_PRECOND_SPECTRAL) {
+  if (o->precond == VDP_PRECOND_SPECTRAL || o->method == VDP_METHOD_FIXED_POINT) {
     const int sres = ensure_spectral(c);
     if (sres != VDP_OK) {
       c->opts = old;
       return sres;
     }
+  }
+  if (o->method == VDP_METHOD_FIXED_POINT && !c->rho_w) {
+    cudaError_t e = cudaMalloc((void**)&c->rho_w, sizeof(float) * (size_t)c->n);
+    if (e != cudaSuccess) {
+      c->rho_w = nullptr;
+      c->opts = old;
+      return cuda_fail(e, "vdp_set_options (density weight)");
+    }
+    c->rho_w_valid = false;
   }
   c->stream = (cudaStream_t)o->stream;
   c->layout_dirty = true;
@@ -430,6 +462,11 @@ int vdp_set_density(vdp_ctx* c, const double* rho) {
                                    c->stream));
   c->scaled_prec = -1;
   c->omega_valid = false;
+  c->rho_w_valid = false;
+  if (c->rho_w) {  // the fixed-point iteration's weight needs rho itself
+    VDP_CK(launch_rho_weight(src, c->sinv, c->n, c->rho_w, c->stream));
+    c->rho_w_valid = true;
+  }
   int s = ensure_scaled(c, c->opts.precision);
   if (s != VDP_OK) return s;
   VDP_CK(cudaStreamSynchronize(c->stream));
@@ -449,10 +486,7 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   if ((c->layout_dirty || c->layout_prec != prec) && (s = configure_layout(c, prec)) != VDP_OK)
     return s;
   if ((s = ensure_graph(c, prec)) != VDP_OK) return s;
-  if (c->hdesc.pc == PC_SPECTRAL && !c->omega_valid) {
-    VDP_CK(launch_omega(c->sinv, c->n, c->omega, c->stream));
-    c->omega_valid = true;
-  }
+  if ((s = prepare_spectral_solve(c)) != VDP_OK) return s;
   const double* drhs = rhs;
   double* dp = p;
   if (host_rhs) {
@@ -505,7 +539,7 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   c->stats.rhs_mean = hs.mu_f;
   c->stats.ms = ms;
   c->stats.sweeps = hs.sweeps;
-  const int per_round = (c->lay.mode == 0 ? 3 : 2) + (c->hdesc.pc == PC_SPECTRAL ? SPEC_PASSES : 0);
+  const int per_round = (c->lay.mode == 0 ? 3 : 2) + (c->hdesc.pc >= PC_SPECTRAL ? SPEC_PASSES : 0);
   c->stats.launches = (int)(1 + issued * per_round * m);
   return c->stats.status;
 }
@@ -526,8 +560,8 @@ int vdp_inverse_laplacian(vdp_ctx* c, const double* g, double* out) {
   solve_spec_args(c, PREC_FP64, &a);
   a.in = g;
   a.out = out;
-  a.dot_with = nullptr;
-  a.omega = nullptr;
+  a.omega_in = nullptr;
+  a.omega_out = nullptr;
   a.scale = (float)(-1.0 / (double)c->n);  // L_h^-1 (negative definite), not (-L_h)^-1
   a.st = nullptr;
   a.I = nullptr;

@@ -149,7 +149,7 @@ int capture(vdp_batch* b, int pairs) {
       // member's phase), between the residual and the stencil sweeps as in a solve alone
       for (size_t k = 0; k < b->active.size() && e == cudaSuccess; ++k) {
         const vdp_ctx* c = b->members[b->active[k]].ctx;
-        if (c->hdesc.pc != PC_SPECTRAL) continue;
+        if (c->hdesc.pc < PC_SPECTRAL) continue;
         SpecArgs a;
         solve_spec_args(c, b->prec, &a);
         for (int pass = 0; pass < SPEC_PASSES && e == cudaSuccess; ++pass)
@@ -230,7 +230,9 @@ int vdp_batch_add(vdp_batch* b, vdp_ctx* c, const double* rhs, double* p, double
   if (!c->has_density || c->opts.precision != b->prec || c->opts.stencil != 0) return VDP_EINVAL;
   // the spectral passes are separate kernels: members with that preconditioner need the batch
   // of ordinary launches, not the persistent kernel
-  if (c->opts.precond == VDP_PRECOND_SPECTRAL && b->persistent) return VDP_EINVAL;
+  if ((c->opts.precond == VDP_PRECOND_SPECTRAL || c->opts.method == VDP_METHOD_FIXED_POINT) &&
+      b->persistent)
+    return VDP_EINVAL;
   if (!is_device_ptr(rhs) || !is_device_ptr(p) || ((uintptr_t)rhs & 15) || ((uintptr_t)p & 15))
     return VDP_EINVAL;
   if (find(b, c, nullptr)) return VDP_EINVAL;  // already a member
@@ -239,10 +241,7 @@ int vdp_batch_add(vdp_batch* b, vdp_ctx* c, const double* rhs, double* p, double
   if ((c->layout_dirty || c->layout_prec != b->prec || !c->hdesc_valid) &&
       (s = configure_layout(c, b->prec)) != VDP_OK)
     return s;
-  if (c->hdesc.pc == PC_SPECTRAL && !c->omega_valid) {
-    VDP_CK(launch_omega(c->sinv, c->n, c->omega, c->stream));
-    c->omega_valid = true;
-  }
+  if ((s = prepare_spectral_solve(c)) != VDP_OK) return s;
   VDP_CK(cudaStreamSynchronize(c->stream));
   VDP_CK(launch_init(c->desc, rhs, p, tol, c->opts.inner_tol, c->opts.max_iter, c->opts.max_iter,
                      c->opts.use_guess ? 1 : 0, b->prec, b->stream));

@@ -42,6 +42,8 @@ struct vdp_ctx {
   float* omega = nullptr;          // D^1/2 per cell (FP32)
   float* sptab = nullptr;          // twiddle and eigenvalue tables
   bool omega_valid = false;        // omega matches the current density
+  float* rho_w = nullptr;          // fixed-point iteration: rho D^1/2 per cell (FP32)
+  bool rho_w_valid = false;        // rho_w was computed from the current density
   int scaled_prec = -1;            // precision the scaled coefficients were built for
   bool has_density = false;
   // bookkeeping
@@ -78,5 +80,8 @@ int ensure_spectral(vdp_ctx* c);
 // the arguments of the five spectral passes of a solve on this context (gated on its state)
 struct SpecArgs;
 void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a);
+// before a solve that uses the spectral passes: the weights for the current density
+// (VDP_EINVAL when the fixed-point method's density weight is missing)
+int prepare_spectral_solve(vdp_ctx* c);
 
 }  // namespace vdp

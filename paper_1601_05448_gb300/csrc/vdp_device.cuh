@@ -136,6 +136,14 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
       } else if (rrt == 0.0) {  // residual below the inner type's range: cannot refine further
         st->status = 4;
         st->phase = PH_FINAL;
+      } else if (I.pc == PC_FIXED) {  // the paper's iteration: dp from the spectral passes
+        if (rel > 1e4) {              // diverging (the density varies too much for it)
+          st->status = 4;
+          st->phase = PH_FINAL;
+        } else {
+          st->inner_iters = 0;
+          st->phase = PH_SPEC;
+        }
       } else {
         // How far the FP64 residual fell during the last inner solve compared with the scaled
         // inner residual; the next inner target is tightened by it (at least 1).
@@ -200,6 +208,11 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
     }
     case PH_CHEB:
     case PH_SPEC: {
+      if (I.pc == PC_FIXED) {  // x holds the scaled update; apply it and measure again
+        st->iters += 1;
+        st->phase = PH_CORRECT;
+        break;
+      }
       if (phase == PH_CHEB && st->cheb_j < I.cheb_k - 1) {
         st->cheb_j += 1;
         break;
@@ -250,12 +263,15 @@ __device__ __forceinline__ int phase_slots(int phase) {
   }
 }
 
+// nunits units arrive; their partial slots were written by nparts units (default: the same),
+// which lets a sweep of several kernels reduce what an earlier kernel of the sweep stored.
 __device__ __forceinline__ void finish_sweep(const InstDesc& I, InstState* st, int phase,
-                                             int nunits) {
+                                             int nunits, int nparts = 0) {
+  if (nparts <= 0) nparts = nunits;
   if (arrive_last(I.ticket, nunits)) {  // uniform in the block
     double S[kSlots] = {0.0, 0.0, 0.0, 0.0};
     const int ns = phase_slots(phase);
-    for (int k = 0; k < ns; ++k) S[k] = block_sum_slot(I.part + k * nunits, nunits);
+    for (int k = 0; k < ns; ++k) S[k] = block_sum_slot(I.part + k * nparts, nparts);
     if (threadIdx.x == 0) {
       transition(I, st, phase, S);
       *I.ticket = 0u;

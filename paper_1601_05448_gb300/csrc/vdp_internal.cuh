@@ -32,7 +32,9 @@ enum Phase : int {
 };
 
 // Preconditioner applied to the Jacobi-scaled inner system (InstDesc::pc).
-enum PrecondKind : int { PC_JACOBI = 0, PC_CHEB = 1, PC_SPECTRAL = 2 };
+// PC_FIXED: not a preconditioner but the paper's fixed-point iteration, which applies the
+// spectral passes (with a density-weighted input) between FP64 residuals instead of running CG.
+enum PrecondKind : int { PC_JACOBI = 0, PC_CHEB = 1, PC_SPECTRAL = 2, PC_FIXED = 3 };
 
 enum Prec : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_MIXED_BF16 = 2 };
 

@@ -162,14 +162,26 @@ template <> struct Pair<double> {
   }
 };
 
-// Rows per block of the X passes: at most 256 threads and 32 KB of shared memory, and a
+// Shared-memory row strides (in complex values) congruent to 8 modulo 16: the four rows (or
+// line groups) a warp touches then fall on alternating halves of the 32 banks.
+__host__ __device__ constexpr int pad_stride(int len) { return ((len + 7) / 16) * 16 + 8; }
+
+// Rows per block of the X passes: at most 256 threads and about 40 KB of shared memory, and a
 // multiple of 32 threads (the block reduction works on whole warps).
 template <int M1, int M2>
 constexpr int rows_per_block() {
   for (int ry = 256 / M1; ry > 1; --ry)
-    if ((M1 * ry) % 32 == 0 && 16 * M1 * M2 * ry <= 32768) return ry;
+    if ((M1 * ry) % 32 == 0 &&
+        8 * ry * (pad_stride(M2 * (M1 + 1)) + pad_stride(M1 * M2 + 1)) <= 40960)
+      return ry;
   return 32;  // not reached for the supported sizes
 }
+
+// The four-step exchange of one line through shared memory: step A's thread j1 writes its
+// M2 outputs to [k2][j1], step B's thread k2 reads them back; rows of M1 + 1 values keep the
+// step B reads (stride M1 + 1) free of bank conflicts.
+template <int M1>
+__device__ __forceinline__ int ex(int k2, int j1) { return k2 * (M1 + 1) + j1; }
 
 // ---- X+ : real rows -> half spectrum -----------------------------------------------------------
 
@@ -177,42 +189,46 @@ template <class T, int M1, int M2>
 __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
     k_spec_x_fwd(SpecArgs a) {
   constexpr int m = M1 * M2, RY = rows_per_block<M1, M2>();
-  __shared__ float2 sa[RY][m], sb[RY][m];
+  constexpr int SA = pad_stride(M2 * (M1 + 1)), SB = pad_stride(m + 1);
+  __shared__ float2 sa[RY * SA], sb[RY * SB];
   if (!spec_active(a)) return;
   const Tables tb = tables(a);
   const int t = threadIdx.x % M1, r = threadIdx.x / M1;
   const long long rows = (long long)a.ny * a.nz;
   const long long row = (long long)blockIdx.x * RY + r;
   const bool live = row < rows;
-  const T* in = static_cast<const T*>(a.in) + row * a.nx;
+  float2* ra = sa + r * SA;
+  float2* rb = sb + r * SB;
   // step A: M2-point DFTs over j2 of z[t + M1 j2] = (x[2j], x[2j+1]) * W
   if (live) {
+    const T* in = static_cast<const T*>(a.in) + row * a.nx;
+    const float* om = a.omega_in ? a.omega_in + row * a.nx : nullptr;
     float2 v[M2], y[M2];
 #pragma unroll
     for (int j2 = 0; j2 < M2; ++j2) {
       const int j = t + M1 * j2;
       float2 z = Pair<T>::ld(in + 2 * j);
-      if (a.omega) {
-        const float2 w = *reinterpret_cast<const float2*>(a.omega + row * a.nx + 2 * j);
+      if (om) {
+        const float2 w = *reinterpret_cast<const float2*>(om + 2 * j);
         z = make_float2(z.x * w.x, z.y * w.y);
       }
       v[j2] = z;
     }
     dft<M2, 0, 1, false>(v, y);
 #pragma unroll
-    for (int k2 = 0; k2 < M2; ++k2) sa[r][k2 * M1 + t] = k2 == 0 || t == 0 ? y[k2] : cmul(y[k2], tb.wm[t * k2]);
+    for (int k2 = 0; k2 < M2; ++k2)
+      ra[ex<M1>(k2, t)] = k2 == 0 || t == 0 ? y[k2] : cmul(y[k2], tb.wm[t * k2]);
   }
   __syncthreads();
   // step B: M1-point DFTs over j1 -> Z[k2 + M2 k1]
   if (live) {
-#pragma unroll
     for (int k2 = t; k2 < M2; k2 += M1) {
       float2 u[M1], o[M1];
 #pragma unroll
-      for (int j1 = 0; j1 < M1; ++j1) u[j1] = sa[r][k2 * M1 + j1];
+      for (int j1 = 0; j1 < M1; ++j1) u[j1] = ra[ex<M1>(k2, j1)];
       dft<M1, 0, 1, false>(u, o);
 #pragma unroll
-      for (int k1 = 0; k1 < M1; ++k1) sb[r][k2 + M2 * k1] = o[k1];
+      for (int k1 = 0; k1 < M1; ++k1) rb[k2 + M2 * k1] = o[k1];
     }
   }
   __syncthreads();
@@ -222,7 +238,7 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
     for (int k = t; k < a.nxp; k += M1) {
       float2 X = make_float2(0.f, 0.f);
       if (k <= m) {
-        const float2 p = sb[r][k == m ? 0 : k], q = cconj(sb[r][k == 0 ? 0 : m - k]);
+        const float2 p = rb[k == m ? 0 : k], q = cconj(rb[k == 0 ? 0 : m - k]);
         const float2 e = cscale(cadd(p, q), 0.5f);
         const float2 d = csub(p, q);
         const float2 o = make_float2(0.5f * d.y, -0.5f * d.x);
@@ -233,22 +249,25 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
   }
 }
 
-// ---- X- : half spectrum -> real rows (z = W x), <rt, z> ------------------------------------------
+// ---- X- : half spectrum -> real rows, z = W x ----------------------------------------------------
 
 template <class T, int M1, int M2>
 __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
     k_spec_x_inv(SpecArgs a) {
   constexpr int m = M1 * M2, RY = rows_per_block<M1, M2>();
-  __shared__ float2 sa[RY][m + 1], sb[RY][m];
+  constexpr int SA = pad_stride(m + 1), SB = pad_stride(M2 * (M1 + 1));
+  __shared__ float2 sa[RY * SA], sb[RY * SB];
   if (!spec_active(a)) return;
   const Tables tb = tables(a);
   const int t = threadIdx.x % M1, r = threadIdx.x / M1;
   const long long rows = (long long)a.ny * a.nz;
   const long long row = (long long)blockIdx.x * RY + r;
   const bool live = row < rows;
+  float2* ra = sa + r * SA;
+  float2* rb = sb + r * SB;
   if (live) {
     const float2* src = a.spec + row * a.nxp;
-    for (int k = t; k <= m; k += M1) sa[r][k] = src[k];
+    for (int k = t; k <= m; k += M1) ra[k] = src[k];
   }
   __syncthreads();
   // Z'[k] = (X[k] + conj X[m-k]) + i conj(W_nx^k) (X[k] - conj X[m-k]); inverse M2-point DFTs
@@ -257,7 +276,7 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
 #pragma unroll
     for (int j2 = 0; j2 < M2; ++j2) {
       const int k = t + M1 * j2;
-      const float2 p = sa[r][k], q = cconj(sa[r][m - k]);
+      const float2 p = ra[k], q = cconj(ra[m - k]);
       const float2 e = cadd(p, q);
       const float2 o = cmulc(csub(p, q), tb.wr[k]);
       v[j2] = make_float2(e.x - o.y, e.y + o.x);
@@ -265,42 +284,33 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
     dft<M2, 0, 1, true>(v, y);
 #pragma unroll
     for (int k2 = 0; k2 < M2; ++k2)
-      sb[r][k2 * M1 + t] = k2 == 0 || t == 0 ? y[k2] : cmulc(y[k2], tb.wm[t * k2]);
+      rb[ex<M1>(k2, t)] = k2 == 0 || t == 0 ? y[k2] : cmulc(y[k2], tb.wm[t * k2]);
   }
   __syncthreads();
-  T acc = 0;
   if (live) {
-    const T* rt = static_cast<const T*>(a.dot_with);
     T* out = static_cast<T*>(a.out) + row * a.nx;
-#pragma unroll
+    const float* om = a.omega_out ? a.omega_out + row * a.nx : nullptr;
     for (int k2 = t; k2 < M2; k2 += M1) {
       float2 u[M1], o[M1];
 #pragma unroll
-      for (int j1 = 0; j1 < M1; ++j1) u[j1] = sb[r][k2 * M1 + j1];
+      for (int j1 = 0; j1 < M1; ++j1) u[j1] = rb[ex<M1>(k2, j1)];
       dft<M1, 0, 1, true>(u, o);
 #pragma unroll
       for (int k1 = 0; k1 < M1; ++k1) {
         const int l = k2 + M2 * k1;  // cells 2l, 2l + 1 of the row
         float2 z = o[k1];
-        if (a.omega) {
-          const float2 w = *reinterpret_cast<const float2*>(a.omega + row * a.nx + 2 * l);
+        if (om) {
+          const float2 w = *reinterpret_cast<const float2*>(om + 2 * l);
           z = make_float2(z.x * w.x, z.y * w.y);
         }
         Pair<T>::st(out + 2 * l, z);
-        if (rt) {
-          T r0, r1;
-          Pair<T>::ld2(rt + row * a.nx + 2 * l, r0, r1);
-          acc = fma(r0, (T)z.x, acc);
-          acc = fma(r1, (T)z.y, acc);
-        }
       }
     }
   }
-  if (a.st) {  // the solve: this pass completes the preconditioner sweep
+  if (a.st) {  // the solve: the last block of this pass completes the preconditioner sweep, with
+               // <rt, z> from the partial sums the Z pass stored
     const InstDesc& I = *a.I;
-    T part[1] = {acc};
-    store_partials<1, T>(part, I.part, gridDim.x, blockIdx.x);
-    finish_sweep(I, I.st, PH_SPEC, gridDim.x);
+    finish_sweep(I, I.st, PH_SPEC, gridDim.x, a.zunits);
   }
 }
 
@@ -308,11 +318,17 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
 
 constexpr int kTX = 8;  // columns per tile (64 bytes of each line element)
 
+// shared-memory index of line element e (of a tile column c) when lines are grouped by g
+// elements: groups of g * kTX values padded to a stride = 8 (mod 16)
+template <int G>
+__device__ __forceinline__ int tx(int group, int e, int c) {
+  return group * pad_stride(G * kTX) + e * kTX + c;
+}
+
 // Y pass (forward or inverse), in place: block = (column tile, kz).
 template <int M1, int M2, bool INV>
 __global__ void __launch_bounds__(M1 * kTX) k_spec_y(SpecArgs a) {
-  constexpr int n = M1 * M2;
-  __shared__ float2 sm[n * kTX];
+  __shared__ float2 sm[M2 * pad_stride(M1 * kTX)];
   if (!spec_active(a)) return;
   const Tables tb = tables(a);
   const int c = threadIdx.x % kTX, t = threadIdx.x / kTX;
@@ -328,15 +344,14 @@ __global__ void __launch_bounds__(M1 * kTX) k_spec_y(SpecArgs a) {
 #pragma unroll
     for (int k2 = 0; k2 < M2; ++k2) {
       const float2 w = tb.wy[t * k2];
-      sm[(k2 * M1 + t) * kTX + c] = k2 == 0 || t == 0 ? y[k2] : (INV ? cmulc(y[k2], w) : cmul(y[k2], w));
+      sm[tx<M1>(k2, t, c)] = k2 == 0 || t == 0 ? y[k2] : (INV ? cmulc(y[k2], w) : cmul(y[k2], w));
     }
   }
   __syncthreads();
-#pragma unroll
   for (int k2 = t; k2 < M2; k2 += M1) {
     float2 u[M1], o[M1];
 #pragma unroll
-    for (int j1 = 0; j1 < M1; ++j1) u[j1] = sm[(k2 * M1 + j1) * kTX + c];
+    for (int j1 = 0; j1 < M1; ++j1) u[j1] = sm[tx<M1>(k2, j1, c)];
     dft<M1, 0, 1, INV>(u, o);
 #pragma unroll
     for (int k1 = 0; k1 < M1; ++k1) g[(k2 + M2 * k1) * es] = o[k1];
@@ -346,10 +361,14 @@ __global__ void __launch_bounds__(M1 * kTX) k_spec_y(SpecArgs a) {
 // Z pass: forward FFT along z, scale by sign / (N lambda), inverse FFT along z; block =
 // (column tile, ky).  Forward: A (M2-point, over j2) and B (M1-point, over j1), leaving owner
 // k2 with X[k2 + M2 k1]; inverse: A' (M1-point over k1 in registers), B' (M2-point over k2).
+// In the solve it also stores this tile's part of <y, (-L_h)^-1 y> = sum_k |Y(k)|^2 s(k)
+// (Parseval; y = W rt, the half spectrum counting kx = 1 .. nx/2 - 1 twice), which is <rt, z>.
 template <int M1, int M2>
 __global__ void __launch_bounds__(M1 * kTX) k_spec_z(SpecArgs a) {
-  constexpr int n = M1 * M2, R = (M2 + M1 - 1) / M1;
-  __shared__ float2 sm[n * kTX];
+  constexpr int R = (M2 + M1 - 1) / M1;
+  constexpr int SZ = M2 * pad_stride(M1 * kTX) > M1 * pad_stride(M2 * kTX) ? M2 * pad_stride(M1 * kTX)
+                                                                             : M1 * pad_stride(M2 * kTX);
+  __shared__ float2 sm[SZ];
   if (!spec_active(a)) return;
   const Tables tb = tables(a);
   const int c = threadIdx.x % kTX, t = threadIdx.x / kTX;
@@ -364,11 +383,14 @@ __global__ void __launch_bounds__(M1 * kTX) k_spec_z(SpecArgs a) {
     dft<M2, 0, 1, false>(v, y);
 #pragma unroll
     for (int k2 = 0; k2 < M2; ++k2)
-      sm[(k2 * M1 + t) * kTX + c] = k2 == 0 || t == 0 ? y[k2] : cmul(y[k2], tb.wz[t * k2]);
+      sm[tx<M1>(k2, t, c)] = k2 == 0 || t == 0 ? y[k2] : cmul(y[k2], tb.wz[t * k2]);
   }
   __syncthreads();
-  const bool pad = kx > a.nx / 2;  // padding columns of the row pitch: set to 0
+  const int m = a.nx / 2;
+  const bool pad = kx > m;  // padding columns of the row pitch: set to 0
   const float lxy = pad ? 0.f : tb.lx[kx] + tb.ly[ky];
+  const float wkx = (kx == 0 || kx == m) ? 1.f : 2.f;  // conjugate partners of the half spectrum
+  float energy = 0.f;
   float2 X[R][M1];
 #pragma unroll
   for (int rr = 0; rr < R; ++rr) {
@@ -376,12 +398,13 @@ __global__ void __launch_bounds__(M1 * kTX) k_spec_z(SpecArgs a) {
     if (k2 < M2) {
       float2 u[M1], o[M1];
 #pragma unroll
-      for (int j1 = 0; j1 < M1; ++j1) u[j1] = sm[(k2 * M1 + j1) * kTX + c];
+      for (int j1 = 0; j1 < M1; ++j1) u[j1] = sm[tx<M1>(k2, j1, c)];
       dft<M1, 0, 1, false>(u, o);
 #pragma unroll
       for (int k1 = 0; k1 < M1; ++k1) {
         const float lam = lxy + tb.lz[k2 + M2 * k1];
         const float s = (lam > 0.f && !pad) ? a.scale / lam : 0.f;  // zero mode removed
+        energy = fmaf(wkx * s, fmaf(o[k1].x, o[k1].x, o[k1].y * o[k1].y), energy);
         X[rr][k1] = cscale(o[k1], s);
       }
     }
@@ -395,17 +418,21 @@ __global__ void __launch_bounds__(M1 * kTX) k_spec_z(SpecArgs a) {
       dft<M1, 0, 1, true>(X[rr], u);
 #pragma unroll
       for (int l2 = 0; l2 < M1; ++l2)
-        sm[(l2 * M2 + k2) * kTX + c] = l2 == 0 || k2 == 0 ? u[l2] : cmulc(u[l2], tb.wz[k2 * l2]);
+        sm[tx<M2>(l2, k2, c)] = l2 == 0 || k2 == 0 ? u[l2] : cmulc(u[l2], tb.wz[k2 * l2]);
     }
   }
   __syncthreads();
   {
     float2 w[M2], o[M2];
 #pragma unroll
-    for (int k2 = 0; k2 < M2; ++k2) w[k2] = sm[(t * M2 + k2) * kTX + c];
+    for (int k2 = 0; k2 < M2; ++k2) w[k2] = sm[tx<M2>(t, k2, c)];
     dft<M2, 0, 1, true>(w, o);
 #pragma unroll
     for (int l1 = 0; l1 < M2; ++l1) g[(t + M1 * l1) * es] = o[l1];
+  }
+  if (a.st) {
+    const float part[1] = {energy};
+    store_partials<1, float>(part, a.I->part, gridDim.x, blockIdx.x);
   }
 }
 
@@ -419,7 +446,7 @@ void factor(int n, int* m1, int* m2) {
     case 16: *m1 = 4; *m2 = 4; return;
     case 24: *m1 = 4; *m2 = 6; return;
     case 32: *m1 = 4; *m2 = 8; return;
-    case 48: *m1 = 6; *m2 = 8; return;
+    case 48: *m1 = 6; *m2 = 8; return;  // x rows; y and z lines use 4 x 12 (warp-sized blocks)
     case 64: *m1 = 8; *m2 = 8; return;
     case 96: *m1 = 8; *m2 = 12; return;
     case 128: *m1 = 8; *m2 = 16; return;
@@ -461,13 +488,17 @@ int x_rows_per_block(int m) {
 SpecKernel yz_kernel(int n, int which, int* threads) {  // which: 0 = Y+, 1 = Y-, 2 = Z
   int m1, m2;
   factor(n, &m1, &m2);
+  if (n == 48) {  // blocks of M1 * 8 threads: a whole number of warps for the block reduction
+    m1 = 4;
+    m2 = 12;
+  }
 #define VDP_YZ(M1, M2)                                                                  \
   if (m1 == M1 && m2 == M2) {                                                           \
     *threads = M1 * kTX;                                                                \
     return which == 0 ? k_spec_y<M1, M2, false> : which == 1 ? k_spec_y<M1, M2, true>   \
                                                              : k_spec_z<M1, M2>;        \
   }
-  VDP_YZ(4, 8) VDP_YZ(6, 8) VDP_YZ(8, 8) VDP_YZ(8, 12) VDP_YZ(8, 16) VDP_YZ(12, 16)
+  VDP_YZ(4, 8) VDP_YZ(4, 12) VDP_YZ(8, 8) VDP_YZ(8, 12) VDP_YZ(8, 16) VDP_YZ(12, 16)
   VDP_YZ(16, 16) VDP_YZ(16, 32)
 #undef VDP_YZ
   return nullptr;
@@ -565,9 +596,9 @@ cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStre
   return cudaGetLastError();
 }
 
-int spectral_units(int nx, int ny, int nz) {
-  const int ry = x_rows_per_block(nx / 2);
-  return ry ? (int)(((long long)ny * nz + ry - 1) / ry) : 0;
+int spectral_units(int nx, int ny, int nz) {  // CTAs of the Z pass (they store <rt, z> parts)
+  (void)nz;
+  return (spectral_pitch(nx) / kTX) * ny;
 }
 
 __global__ void k_omega(const double* __restrict__ sinv, long long n, float* __restrict__ omega) {
@@ -578,6 +609,19 @@ __global__ void k_omega(const double* __restrict__ sinv, long long n, float* __r
 
 cudaError_t launch_omega(const double* sinv, long long n, float* omega, cudaStream_t s) {
   k_omega<<<152 * 8, 256, 0, s>>>(sinv, n, omega);
+  return cudaGetLastError();
+}
+
+__global__ void k_rho_weight(const double* __restrict__ rho, const double* __restrict__ sinv,
+                             long long n, float* __restrict__ out) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x)
+    out[c] = (float)(rho[c] / sinv[c]);
+}
+
+cudaError_t launch_rho_weight(const double* rho, const double* sinv, long long n, float* out,
+                              cudaStream_t s) {
+  k_rho_weight<<<152 * 8, 256, 0, s>>>(rho, sinv, n, out);
   return cudaGetLastError();
 }
 

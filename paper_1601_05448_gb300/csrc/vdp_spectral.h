@@ -17,15 +17,17 @@ enum SpecPass : int { SPEC_X_FWD = 0, SPEC_Y_FWD = 1, SPEC_Z = 2, SPEC_Y_INV = 3
 struct SpecArgs {
   const void* in;        // X+: nx*ny*nz values of the inner type (FP64 or FP32)
   void* out;             // X-: output, same type and layout
-  const void* dot_with;  // X-: sum <dot_with, out> into the solve's partial slots (or null)
-  const float* omega;    // per-cell weight W applied before X+ and after X- (or null: 1)
+  const float* omega_in;   // per-cell weight applied before X+ (or null: 1)
+  const float* omega_out;  // per-cell weight applied after X- (or null: 1)
   float2* spec;          // half spectrum [nz][ny][nxp]
   const float2* tw;      // tables built by spectral_tables (twiddles first, then eigenvalues)
   const float* lam;
   int nx, ny, nz, nxp;
   float scale;           // sign / (nx ny nz): +1 applies (-L_h)^-1, -1 applies L_h^-1
   InstState* st;         // the solve's state: passes run only in PH_SPEC (null: always run)
-  const InstDesc* I;     // the solve's description (X- completes the sweep), with st
+  const InstDesc* I;     // the solve's description, with st: Z stores the partial sums of
+                         // <rt, z>, X- completes the sweep
+  int zunits;            // CTAs of the Z pass (partial slots), with st
 };
 
 bool spectral_supported(int nx, int ny, int nz);
@@ -36,7 +38,10 @@ size_t spectral_table_floats(int nx, int ny, int nz);
 void spectral_tables(int nx, int ny, int nz, double L, std::vector<float>& out);
 cudaError_t spectral_upload_roots();               // the register-DFT roots, once per device
 cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStream_t s);
-int spectral_units(int nx, int ny, int nz);        // CTAs of the X- pass (partial slots)
+int spectral_units(int nx, int ny, int nz);        // CTAs of the Z pass (partial slots)
 cudaError_t launch_omega(const double* sinv, long long n, float* omega, cudaStream_t s);
+// out = rho / sinv (the fixed-point iteration's input weight)
+cudaError_t launch_rho_weight(const double* rho, const double* sinv, long long n, float* out,
+                              cudaStream_t s);
 
 }  // namespace vdp

@@ -123,12 +123,9 @@ extern "C" int vdp_solve_timed(vdp_ctx* c, const double* rhs, double* p, double 
   VDP_CK(cudaEventCreate(&t.e1));
   const int shape_phase[3] = {PH_RES64, PH_STENCIL, PH_UPDATE};
   for (int i = 0; i < 3; ++i) VDP_CK(capture_timed(c, prec, shape_phase[i], -1, t, &t.g[i]));
-  const bool spectral = c->hdesc.pc == PC_SPECTRAL;
+  const bool spectral = c->hdesc.pc >= PC_SPECTRAL;
   if (spectral) {
-    if (!c->omega_valid) {
-      VDP_CK(launch_omega(c->sinv, c->n, c->omega, c->stream));
-      c->omega_valid = true;
-    }
+    if ((s = prepare_spectral_solve(c)) != VDP_OK) return s;
     for (int i = 0; i < SPEC_PASSES; ++i)
       VDP_CK(capture_timed(c, prec, PH_SPEC, i, t, &t.g[3 + i]));
   }

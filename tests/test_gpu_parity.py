@@ -22,14 +22,14 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def gpu_solve(prob, precision="fp64", tol=None, **opts):
+def gpu_solve(prob, precision="fp64", tol=None, check=True, **opts):
     nz, ny, nx = prob.shape
     rho = torch.from_numpy(prob.rho).to(DEV)
     f = torch.from_numpy(prob.f).to(DEV)
     p = torch.empty_like(f)
     with vdp.Solver(nx, ny, nz, prob.L, precision=precision, **opts) as s:
         s.set_density(rho)
-        st = s.solve(f, p, prob.tol if tol is None else tol)
+        st = s.solve(f, p, prob.tol if tol is None else tol, check=check)
     return p.cpu().numpy(), st
 
 
@@ -350,3 +350,51 @@ def test_spectral_timed_and_limits():
     with pytest.raises(vdp.VdpError) as e:  # 40 is not a supported FFT length
         vdp.Solver(40, 32, 32, 1.0, precond=vdp.VDP_PRECOND_SPECTRAL)
     assert e.value.status == vdp.VDP_EINVAL
+
+
+# ---- the paper's own fixed-point iteration (Sec. 3.4, Eq. (Pois)) on the GPU ------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("damping", [1.0, 0.8])
+def test_fixed_point_matches_oracle_iteration(precision, damping):
+    """Same algorithm as the oracle's second solver: the same iteration count (the FP32 spectral
+    inverse may move the crossing of the tolerance by one iteration) and the oracle's answer."""
+    prob = V.config0()
+    _, info = oracle.solve_fixed_point(prob.rho, prob.f, prob.L, tol=1e-10, maxit=500, omega=damping)
+    assert info["status"] == "ok"
+    p, st = gpu_solve(prob, precision, tol=1e-10, method=vdp.VDP_METHOD_FIXED_POINT, damping=damping)
+    ref = oracle_solution(prob, "c0")
+    err = rel(p, ref)
+    print(f"fixed point {precision} damping {damping}: gpu {st.iters} iters, oracle {info['iters']}, err {err:.2e}")
+    assert st.ok and st.rel_res <= 1e-10 and st.outer_iters == st.iters + 1
+    assert abs(st.iters - info["iters"]) <= 1
+    assert err <= 1e-9
+    assert oracle.relative_residual(prob.rho, prob.L, prob.f, p) <= 1.01e-10
+
+
+def test_fixed_point_on_hot_spots_and_its_limits():
+    prob = V.hotspot_problem(64, seed=66, nspots=312, target_ratio=3.0)
+    _, info = oracle.solve_fixed_point(prob.rho, prob.f, prob.L, tol=1e-9, maxit=2000)
+    p, st = gpu_solve(prob, "fp64", tol=1e-9, method=vdp.VDP_METHOD_FIXED_POINT, check=False)
+    print(f"fixed point hot spots ratio 3: gpu {st.iters} ({vdp.vdp_strerror(st.status)}), oracle {info['iters']} "
+          f"({info['status']})")
+    if info["status"] == "ok":
+        assert st.ok and abs(st.iters - info["iters"]) <= 1
+        assert rel(p, oracle_solution(prob, "hot64r3")) <= 1e-8
+    else:
+        assert st.status == vdp.VDP_ENOTCONV and np.isfinite(p).all()
+    nz, ny, nx = prob.shape
+    with vdp.Solver(nx, ny, nz, prob.L) as s:  # the density weight is taken at vdp_set_density
+        s.set_density(torch.from_numpy(prob.rho).to(DEV))
+        s.set_options(method=vdp.VDP_METHOD_FIXED_POINT)
+        f = torch.from_numpy(prob.f).to(DEV)
+        with pytest.raises(vdp.VdpError) as e:
+            s.solve(f, torch.empty_like(f), 1e-9)
+        assert e.value.status == vdp.VDP_EINVAL
+        s.set_density(torch.from_numpy(prob.rho).to(DEV))
+        st2 = s.solve(f, torch.empty_like(f), 1e-9, check=False)
+        assert st2.iters == st.iters
+    with pytest.raises(vdp.VdpError):
+        vdp.Solver(40, 32, 32, 1.0, method=vdp.VDP_METHOD_FIXED_POINT)
+    with pytest.raises(vdp.VdpError):
+        vdp.Solver(32, 32, 32, 1.0, method=vdp.VDP_METHOD_FIXED_POINT, damping=2.5)
