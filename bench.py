@@ -379,7 +379,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_bf16"],
                     help="precision of the main workload (fp64 = the benchmark)")
     ap.add_argument("--precond", default="spectral", choices=list(PRECONDS),
-                    help="preconditioner of the main workload (spectral = the benchmark)")
+                    help="preconditioner of the main workload's CG (spectral = the benchmark)")
+    ap.add_argument("--method", default="cg", choices=["cg", "fixed_point"],
+                    help="cg: preconditioned conjugate gradients; fixed_point: the paper's iteration")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -417,6 +419,9 @@ def main():
     method = {"spectral": "CG preconditioned by the constant-coefficient FFT inverse (Sec. 3.4)",
               "cheb": "CG preconditioned by a degree-3 Chebyshev polynomial", "jacobi": "Jacobi-preconditioned CG"}[
         args.precond]
+    if args.method == "fixed_point":
+        method = ("the paper's fixed-point iteration (Sec. 3.4, Eq. (Pois)): FP64 residual, constant-coefficient "
+                  "FFT inverse of rho * residual, update")
     nz, ny, nx = prob.shape
     ncell = nx * ny * nz
     rho = torch.from_numpy(prob.rho).to(dev)
@@ -426,6 +431,8 @@ def main():
     popts = {"precond": PRECONDS[args.precond]}
     if args.precond == "cheb":
         popts["cheb_degree"] = 3
+    if args.method == "fixed_point":
+        popts = {"method": vdp.VDP_METHOD_FIXED_POINT}
     solver = vdp.Solver(nx, ny, nz, prob.L, precision=args.precision, stream=stream, **popts)
     solver.set_density(rho)
 
@@ -465,6 +472,11 @@ def main():
     table = kernel_table(args.precision, ncell, kinds, peaks, args.grid, nx=nx)
     roof = roofline(args.precision, table, peaks)
     b_solve, fl_solve = algorithmic(args.precision, ncell, iters, outer, args.precond == "spectral", nx)
+    if args.method == "fixed_point":  # per update: residual, five spectral passes, correction
+        T = SIZES[args.precision][0]
+        per = (48 + T) + sum(c * sweep_cost(args.precision, k, nx=nx)[0]
+                             for k, c in (("spec_x", 2), ("spec_y", 2), ("spec_z", 1))) + (24 + T)
+        b_solve = (iters * per + (48 + T) + 32) * ncell
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -506,11 +518,12 @@ def main():
         paths = {}
         # (precision, preconditioner, Chebyshev degree)
         variants = {"fp64_spectral": ("fp64", "spectral", 1), "mixed_spectral": ("mixed", "spectral", 1),
+                    "fp64_fixed_point": ("fp64", "fixed_point", 1), "mixed_fixed_point": ("mixed", "fixed_point", 1),
                     "mixed_bf16_spectral": ("mixed_bf16", "spectral", 1), "fp64_jacobi": ("fp64", "jacobi", 1),
                     "mixed_jacobi": ("mixed", "jacobi", 1), "mixed_cheb3": ("mixed", "cheb", 3),
                     "mixed_bf16_jacobi": ("mixed_bf16", "jacobi", 1)}
         for label, (prec, pc, k) in variants.items():
-            opts = {"precond": PRECONDS[pc]}
+            opts = {"method": vdp.VDP_METHOD_FIXED_POINT} if pc == "fixed_point" else {"precond": PRECONDS[pc]}
             if pc == "cheb":
                 opts["cheb_degree"] = k
             with vdp.Solver(nx, ny, nz, prob.L, precision=prec, stream=stream, **opts) as s2:

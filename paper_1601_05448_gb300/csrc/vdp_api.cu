@@ -283,9 +283,10 @@ void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a) {
   const int m = c->nx / 2;
   const bool fixed = c->opts.method == VDP_METHOD_FIXED_POINT;
   a->in = c->r;
-  // CG: z = W (-L_h)^-1 W rt.  Fixed point: x = W (-L_h)^-1 (rho W rt) * damping, applied as
-  // p -= D^-1/2 x, i.e. p += damping * L_h^-1 (rho r)
-  a->out = fixed ? c->x : c->za;
+  // CG: z = W (-L_h)^-1 W rt, W = D^1/2.  Fixed point: with rt = D^-1/2 r the input weight
+  // rho D^1/2 gives rho r, and z = damping D^1/2 (-L_h)^-1 (rho r) is the scaled form of the
+  // paper's update p += damping L_h^-1 (rho r) (applied as p -= D^-1/2 x, x the sum of the z)
+  a->out = c->za;
   a->omega_in = fixed ? c->rho_w : c->omega;
   a->omega_out = c->omega;
   a->spec = c->spec;

@@ -136,14 +136,9 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
       } else if (rrt == 0.0) {  // residual below the inner type's range: cannot refine further
         st->status = 4;
         st->phase = PH_FINAL;
-      } else if (I.pc == PC_FIXED) {  // the paper's iteration: dp from the spectral passes
-        if (rel > 1e4) {              // diverging (the density varies too much for it)
-          st->status = 4;
-          st->phase = PH_FINAL;
-        } else {
-          st->inner_iters = 0;
-          st->phase = PH_SPEC;
-        }
+      } else if (I.pc == PC_FIXED && rel > 1e4) {  // the paper's iteration is diverging (the
+        st->status = 4;                              // density varies too much for it)
+        st->phase = PH_FINAL;
       } else {
         // How far the FP64 residual fell during the last inner solve compared with the scaled
         // inner residual; the next inner target is tightened by it (at least 1).
@@ -162,14 +157,17 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
         st->beta = 0.0;
         st->inner_iters = 0;
         st->cheb_j = 1;
-        st->phase = I.pc == PC_CHEB ? PH_CHEB : (I.pc == PC_SPECTRAL ? PH_SPEC : PH_STENCIL);
+        st->phase = I.pc == PC_CHEB ? PH_CHEB : (I.pc >= PC_SPECTRAL ? PH_SPEC : PH_STENCIL);
       }
       st->rr64 = rr64;
       break;
     }
     case PH_STENCIL: {
       const double dq = S[0];
-      if (dq > 0.0 && isfinite(dq)) {
+      if (I.pc == PC_FIXED) {  // the paper's iteration: the full update, x += z, rt -= At z
+        st->alpha = 1.0;
+        st->phase = PH_UPDATE;
+      } else if (dq > 0.0 && isfinite(dq)) {
         st->alpha = (I.pc != PC_JACOBI ? st->rz : st->rr) / dq;
         st->phase = PH_UPDATE;
       } else if (st->inner_iters > 0) {
@@ -190,7 +188,8 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
         st->status = 5;
         st->phase = PH_FINAL;
       } else if (rn <= st->tau2 * st->rr0 || st->iters >= st->max_iter ||
-                 st->inner_iters >= st->inner_max) {
+                 st->inner_iters >= st->inner_max ||
+                 (I.pc == PC_FIXED && rn > 1e8 * st->rr0)) {  // a diverging iteration stops
         st->inner_ratio = sqrt(rn / st->rr0);
         st->phase = PH_CORRECT;
       } else if (I.pc != PC_JACOBI) {  // preconditioned: z = M^-1 rt first, then beta from <rt, z>
@@ -208,9 +207,9 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
     }
     case PH_CHEB:
     case PH_SPEC: {
-      if (I.pc == PC_FIXED) {  // x holds the scaled update; apply it and measure again
-        st->iters += 1;
-        st->phase = PH_CORRECT;
+      if (I.pc == PC_FIXED) {  // z = the scaled update of the paper's iteration
+        st->beta = 0.0;
+        st->phase = PH_STENCIL;
         break;
       }
       if (phase == PH_CHEB && st->cheb_j < I.cheb_k - 1) {

@@ -588,7 +588,8 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
   const int cj = CHEB ? st->cheb_j : 0;
   const bool last = CHEB && cj == I.cheb_k - 1;
   T beta = (T)st->beta, scale = 1, c1 = 0, c2 = 0;
-  bool use_old = st->inner_iters > 0;
+  // the paper's fixed-point iteration has no search-direction history (beta = 0)
+  bool use_old = st->inner_iters > 0 && I.pc != PC_FIXED;
   bool form = use_old && !QREC;  // form d = src + beta d_old for every marched value
   const T* rt = static_cast<const T*>(I.r);
   const T* src = I.pc != PC_JACOBI ? static_cast<const T*>(I.za) : rt;
@@ -748,10 +749,13 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
 // sweep: a thread owns VR = 16 / sizeof(T) cells of one row): p of planes z-1, z, z+1 in
 // registers, rows above and below loaded per plane.  r = (f - <f>) - A p with the FP64 face
 // coefficients; rt = D^-1/2 r stored in the inner type; sums of r^2, rt^2, p and, on the first
-// call, (f - <f>)^2.
-template <class T>
-__device__ void sweep_res64_direct(const InstDesc& I, const InstState* st, int unit,
-                                   double (&acc)[kSlots]) {
+// call, (f - <f>)^2.  The sweep is bound by the FP64 pipe: each face flux b (p_hi - p_lo) is
+// one subtraction and one FMA into the cell's residual, which starts from f - <f>; the flux
+// through the face between a thread's own cells is formed once for both; rt^2 is summed in the
+// inner type.
+template <class T, bool FIRST>
+__device__ __forceinline__ void res64_march(const InstDesc& I, const InstState* st, int unit,
+                                            double (&acc)[kSlots]) {
   constexpr int VR = VecW<T>::V;  // cells per thread (4 for FP32 inner, 2 for FP64)
   const int nx = I.nx, ny = I.ny, nz = I.nz;
   const int tpr = nx / VR;
@@ -767,7 +771,6 @@ __device__ void sweep_res64_direct(const InstDesc& I, const InstState* st, int u
   const bool row_start = x0 == 0, row_end = x0 + VR == nx;
   const int xl = row_start ? nx - 1 : x0 - 1, xr = row_end ? 0 : x0 + VR;
   const double mu = st->mu_f;
-  const bool first = st->first_res != 0;
   const double* p = I.p;
   T* rt = static_cast<T*>(I.r);
   auto at = [&](int z, int yy) -> long long {
@@ -787,7 +790,8 @@ __device__ void sweep_res64_direct(const InstDesc& I, const InstState* st, int u
     ldv(p, at(z0 - 1, y) + x0, pm);
     ldv(p, at(z0, y) + x0, pc);
   }
-  double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  double a0 = 0, a2 = 0, a3 = 0;
+  T a1 = 0;
   for (int z = z0; z < z1; ++z) {
     const long long oc = at(z, y), op = at(z + 1, y), oyp = at(z, yp), oym = at(z, ym);
     ldv(p, op + x0, pp);
@@ -812,20 +816,29 @@ __device__ void sweep_res64_direct(const InstDesc& I, const InstState* st, int u
       const double l0 = h == 0 ? left : pc[h - 1];
       const double r1 = h + 2 == VR ? right : pc[h + 2];
       const double br1 = h + 2 == VR ? bxr : I.bx[o + 2];
-      double res[2];
       const double c0 = pc[h], c1 = pc[h + 1];
-      res[0] = (f.x - mu) - (bx.y * (c1 - c0) - bx.x * (c0 - l0) + byd.x * (pd.x - c0) -
-                             by.x * (c0 - pu.x) + bzp.x * (pp[h] - c0) - bz.x * (c0 - pm[h]));
-      res[1] = (f.y - mu) - (br1 * (r1 - c1) - bx.y * (c1 - c0) + byd.y * (pd.y - c1) -
-                             by.y * (c1 - pu.y) + bzp.y * (pp[h + 1] - c1) - bz.y * (c1 - pm[h + 1]));
-      const T t0 = from_double_rn<T>(si.x * res[0]), t1 = from_double_rn<T>(si.y * res[1]);
+      // (A p)_c = sum over the three directions of F_hi - F_lo, F = b (p_hi - p_lo)
+      const double fm = bx.y * (c1 - c0);  // the face between the two cells
+      const double f0 = f.x - mu, f1 = f.y - mu;
+      double res0 = f0 - fm, res1 = f1 + fm;
+      res0 = fma(bx.x, c0 - l0, res0);
+      res1 = fma(-br1, r1 - c1, res1);
+      res0 = fma(-byd.x, pd.x - c0, res0);
+      res1 = fma(-byd.y, pd.y - c1, res1);
+      res0 = fma(by.x, c0 - pu.x, res0);
+      res1 = fma(by.y, c1 - pu.y, res1);
+      res0 = fma(-bzp.x, pp[h] - c0, res0);
+      res1 = fma(-bzp.y, pp[h + 1] - c1, res1);
+      res0 = fma(bz.x, c0 - pm[h], res0);
+      res1 = fma(bz.y, c1 - pm[h + 1], res1);
+      const T t0 = from_double_rn<T>(si.x * res0), t1 = from_double_rn<T>(si.y * res1);
       if (active) {
         rt[o] = t0;
         rt[o + 1] = t1;
-        a0 = fma(res[0], res[0], fma(res[1], res[1], a0));
-        a1 = fma((double)t0, (double)t0, fma((double)t1, (double)t1, a1));
+        a0 = fma(res0, res0, fma(res1, res1, a0));
+        a1 = fma(t0, t0, fma(t1, t1, a1));
         a2 += c0 + c1;
-        if (first) a3 = fma(f.x - mu, f.x - mu, fma(f.y - mu, f.y - mu, a3));
+        if (FIRST) a3 = fma(f0, f0, fma(f1, f1, a3));
       }
     }
 #pragma unroll
@@ -835,9 +848,18 @@ __device__ void sweep_res64_direct(const InstDesc& I, const InstState* st, int u
     }
   }
   acc[0] = a0;
-  acc[1] = a1;
+  acc[1] = (double)a1;
   acc[2] = a2;
   acc[3] = a3;
+}
+
+template <class T>
+__device__ void sweep_res64_direct(const InstDesc& I, const InstState* st, int unit,
+                                   double (&acc)[kSlots]) {
+  if (st->first_res != 0)
+    res64_march<T, true>(I, st, unit, acc);
+  else
+    res64_march<T, false>(I, st, unit, acc);
 }
 
 // ---- the FP64 residual sweep (a few times per solve): z march through a three-plane ring ---------
