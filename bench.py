@@ -3,13 +3,14 @@
 One step = one complete solve (all phases: rhs mean removal, Krylov iterations with FP64
 refinement, gauge) of the 256^3 periodic hot-spot workload: rho = T0/T with 20k Gaussian hot
 spots (density ratio 4), rhs = divergence of a random low-k velocity field, FP64, relative
-residual 1e-10, by conjugate gradients preconditioned with the paper's constant-coefficient FFT
-inverse (Sec. 3.4).  Inputs are resident in HBM when timing starts; the working set (~1.7 GB)
+residual 1e-10, by the paper's own iteration (Sec. 3.4, Eq. (Pois)): the FP64 residual is
+multiplied by rho and inverted with the constant-coefficient FFT Laplacian, p += that update.  Inputs are resident in HBM when timing starts; the working set (~1.7 GB)
 is far larger than L2.  The JSON line also carries the end-to-end number through the C ABI with
 host buffers, per-kernel timings and the roofline of the dominant kernel, the mixed-precision
 paths on the same input (solves/s to 1e-8 for FP64, FP32-inside-FP64 and the BF16-coefficient
-ablation, each with the spectral, Jacobi or Chebyshev preconditioner), the same FP64 solve with
-Jacobi-preconditioned CG, the 64-grid batch, the serving stream and the CPU oracle baseline.
+ablation, each with the spectral, Jacobi or Chebyshev preconditioner), the same FP64 solve by conjugate
+gradients (spectral and Jacobi preconditioners), the 64-grid batch, the serving stream and the
+CPU oracle baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   torchrun --nproc-per-node N bench.py --gpus N ...   (N independent replicas, weak scaling)
@@ -65,21 +66,28 @@ def spectrum_bytes(nx: int) -> float:
     nxp = ((nx // 2 + 1 + 7) // 8) * 8
     return 8.0 * nxp / nx
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# kernel at this precision and grid (profiles/k_stencil_direct_fp64_192.md and
-# profiles/k_stencil_direct_mixed_192.md: 192^3, third solve; 256^3 entries scaled by the cell
-# count 256^3 / 192^3).  A changed kernel drops its entries until it is re-captured.
+# kernel at this precision and grid (profiles/k_stencil_direct_fp64_192.md,
+# profiles/k_stencil_direct_mixed_192.md, profiles/k_spec_passes_192.md: 192^3, fixed-point
+# method), keyed (precision, sweep, grid, fixed-point); 256^3 entries scale by the cell count
+# 256^3 / 192^3.  A changed kernel drops its entries until it is re-captured.
 _SCALE_256 = (256 / 192) ** 3
-_TRAFFIC_192 = {("fp64", "update"): 227.577344e6 + 70.953472e6,
-                ("mixed", "stencil"): 142.582016e6 + 36.517376e6, ("mixed", "update"): 113.334272e6 + 15.742720e6}
-TRAFFIC = {(p, k, 192): v for (p, k), v in _TRAFFIC_192.items()}
-TRAFFIC.update({(p, k, 256): v * _SCALE_256 for (p, k), v in _TRAFFIC_192.items()})
+_TRAFFIC_192 = {("fp64", "stencil", True): 227.5e6 + 87.8e6, ("fp64", "update", True): 227.5e6 + 70.3e6,
+                ("mixed", "stencil", True): 113.8e6 + 31.4e6, ("mixed", "update", True): 113.3e6 + 15.5e6,
+                ("fp64", "spec_x", True): (85.0e6 + 6.7e6 + 59.0e6 + 12.8e6) / 2,
+                ("mixed", "spec_x", True): (56.6e6 + 2.9e6 + 59.0e6 + 2.6e6) / 2}
+TRAFFIC = {(p, k, 192, f): v for (p, k, f), v in _TRAFFIC_192.items()}
+TRAFFIC.update({(p, k, 256, f): v * _SCALE_256 for (p, k, f), v in _TRAFFIC_192.items()})
 
 
-def sweep_cost(prec: str, kind: str, cheb_k: int = 1, nx: int = 256):
-    """(bytes, flops) per cell of one launch of sweep `kind`, or None."""
+def sweep_cost(prec: str, kind: str, cheb_k: int = 1, nx: int = 256, fixed: bool = False):
+    """(bytes, flops) per cell of one launch of sweep `kind`, or None.  fixed: the fixed-point
+    method, whose stencil sweep has no search-direction history (reads z, coefficients; writes
+    d, q: 3T + 3B (+B), 7 FMA)."""
     T, B, diag = SIZES[prec]
     Bd = B if diag else 0
     S = spectrum_bytes(nx)
+    if fixed and kind == "stencil":
+        return 3 * T + 3 * B + Bd, 14.0 + (2.0 if diag else 0.0)
     if kind == "spec_x":
         return (3 * T + 8 + 2 * S) / 2, 0.0
     if kind in ("spec_y", "spec_z"):
@@ -108,7 +116,8 @@ def algorithmic(prec: str, ncell: int, iters: int, outer: int, spectral: bool = 
     return total * ncell, 22.0 * iters * ncell
 
 
-def kernel_table(prec: str, ncell: int, kinds: dict, peaks: dict, grid: int, cheb_k: int = 1, nx: int = 256):
+def kernel_table(prec: str, ncell: int, kinds: dict, peaks: dict, grid: int, cheb_k: int = 1, nx: int = 256,
+                 fixed: bool = False):
     """Per sweep kind: launches, mean/min duration (CUDA events around each launch), share of the
     summed kernel time, algorithmic GB/s and TFLOP/s and their fractions of the roofs."""
     total = sum(k["ms"] for k in kinds.values()) or 1.0
@@ -118,7 +127,7 @@ def kernel_table(prec: str, ncell: int, kinds: dict, peaks: dict, grid: int, che
             continue
         row = {"kernel": KERNEL_NAMES[name], "launches": k["launches"], "mean_us": 1e3 * k["ms_mean"],
                "min_us": 1e3 * k["ms_min"], "share": k["ms"] / total}
-        cost = sweep_cost(prec, name, cheb_k, nx)
+        cost = sweep_cost(prec, name, cheb_k, nx, fixed)
         if cost is not None:
             t = k["ms_mean"] / 1e3
             row["alg_bytes_per_launch"] = cost[0] * ncell
@@ -127,7 +136,7 @@ def kernel_table(prec: str, ncell: int, kinds: dict, peaks: dict, grid: int, che
             row["tflops"] = cost[1] * ncell / t / 1e12
             if prec == "fp64" and cost[1] > 0:
                 row["fp64_alu_frac"] = row["tflops"] / FP64_PEAK_TFLOPS
-            row["traffic"] = TRAFFIC.get((prec, name, grid))
+            row["traffic"] = TRAFFIC.get((prec, name, grid, fixed))
         out[name] = row
     return out
 
@@ -380,8 +389,9 @@ def main():
                     help="precision of the main workload (fp64 = the benchmark)")
     ap.add_argument("--precond", default="spectral", choices=list(PRECONDS),
                     help="preconditioner of the main workload's CG (spectral = the benchmark)")
-    ap.add_argument("--method", default="cg", choices=["cg", "fixed_point"],
-                    help="cg: preconditioned conjugate gradients; fixed_point: the paper's iteration")
+    ap.add_argument("--method", default="fixed_point", choices=["cg", "fixed_point"],
+                    help="fixed_point: the paper's iteration (the benchmark); cg: preconditioned conjugate "
+                         "gradients (--precond)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -420,8 +430,8 @@ def main():
               "cheb": "CG preconditioned by a degree-3 Chebyshev polynomial", "jacobi": "Jacobi-preconditioned CG"}[
         args.precond]
     if args.method == "fixed_point":
-        method = ("the paper's fixed-point iteration (Sec. 3.4, Eq. (Pois)): FP64 residual, constant-coefficient "
-                  "FFT inverse of rho * residual, update")
+        method = ("the paper's fixed-point iteration (Sec. 3.4, Eq. (Pois)): update = constant-coefficient FFT "
+                  "inverse of rho * residual; the residual recurs in the inner precision between FP64 residuals")
     nz, ny, nx = prob.shape
     ncell = nx * ny * nz
     rho = torch.from_numpy(prob.rho).to(dev)
@@ -469,14 +479,15 @@ def main():
     pt = torch.empty_like(f)
     st_t, kinds = solver.solve_timed(f, pt, prob.tol)
     assert st_t.iters == iters and torch.equal(pt, p), "instrumented solve differs from the timed solves"
-    table = kernel_table(args.precision, ncell, kinds, peaks, args.grid, nx=nx)
+    fixed = args.method == "fixed_point"
+    table = kernel_table(args.precision, ncell, kinds, peaks, args.grid, nx=nx, fixed=fixed)
     roof = roofline(args.precision, table, peaks)
     b_solve, fl_solve = algorithmic(args.precision, ncell, iters, outer, args.precond == "spectral", nx)
-    if args.method == "fixed_point":  # per update: residual, five spectral passes, correction
+    if fixed:  # per update: five spectral passes, stencil and update sweeps; FP64 residuals
         T = SIZES[args.precision][0]
-        per = (48 + T) + sum(c * sweep_cost(args.precision, k, nx=nx)[0]
-                             for k, c in (("spec_x", 2), ("spec_y", 2), ("spec_z", 1))) + (24 + T)
-        b_solve = (iters * per + (48 + T) + 32) * ncell
+        per = sum(c * sweep_cost(args.precision, k, nx=nx, fixed=True)[0]
+                  for k, c in (("spec_x", 2), ("spec_y", 2), ("spec_z", 1), ("stencil", 1), ("update", 1)))
+        b_solve = (iters * per + outer * (48 + T) + max(outer - 1, 0) * (24 + T) + 32) * ncell
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -533,7 +544,7 @@ def main():
                 ts = [s2.solve(f, pp, 1e-8, check=False) for _ in range(3)]
                 best = min(ts, key=lambda s: s.ms)
                 _, kk = s2.solve_timed(f, pp, 1e-8, check=False)
-                tab = kernel_table(prec, ncell, kk, peaks, args.grid, cheb_k=k, nx=nx)
+                tab = kernel_table(prec, ncell, kk, peaks, args.grid, cheb_k=k, nx=nx, fixed=pc == "fixed_point")
                 paths[label] = {"precision": prec, "precond": pc, "cheb_degree": k, "solves_per_s": 1e3 / best.ms,
                                 "ms": best.ms,
                                 "iters": best.iters, "outer": best.outer_iters, "sweeps": best.sweeps,
@@ -553,7 +564,16 @@ def main():
         if serve_pool is not None:
             line["serving"] = run_serving(torch, vdp, dev, serve_pool, args.serve_requests)
         if rank == 0 and (args.grid, args.precision) == (256, "fp64"):
-            # the same FP64 workload with Jacobi-preconditioned CG (the oracle's method) on the GPU
+            # the same FP64 workload by CG with the spectral preconditioner
+            with vdp.Solver(nx, ny, nz, prob.L, precision="fp64", stream=stream,
+                            precond=vdp.VDP_PRECOND_SPECTRAL) as sc:
+                sc.set_density(rho)
+                pc_ = torch.empty_like(f)
+                sc.solve(f, pc_, prob.tol)
+                tc = [sc.solve(f, pc_, prob.tol) for _ in range(3)]
+            bc = min(tc, key=lambda x: x.ms)
+            line["fp64_cg_spectral_1e-10"] = {"solves_per_s": 1e3 / bc.ms, "ms": bc.ms, "iters": bc.iters}
+            # ... and with Jacobi-preconditioned CG (the oracle's method)
             with vdp.Solver(nx, ny, nz, prob.L, precision="fp64", stream=stream) as sj:
                 sj.set_density(rho)
                 pj = torch.empty_like(f)
