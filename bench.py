@@ -307,7 +307,7 @@ def _serve_problem(n, seed):
                              precision="mixed", tol=1e-8)
 
 
-def run_batch(torch, vdp, dev, probs, persistent=False, precond="spectral"):
+def run_batch(torch, vdp, dev, probs, persistent=False, precond="fixed_point"):
     """The 64-grid batch: all instances in one batch, mixed precision to 1e-8, autotuned layouts."""
     from paper_1601_05448_gb300 import tune
     sizes = {}
@@ -321,7 +321,10 @@ def run_batch(torch, vdp, dev, probs, persistent=False, precond="spectral"):
     for pr in probs:
         nz, ny, nx = pr.shape
         opts = dict(tune.cached_options(nx, ny, nz, "mixed", batchable=True) or {})
-        opts["precond"] = PRECONDS[precond]
+        if precond == "fixed_point":
+            opts.update(method=vdp.VDP_METHOD_FIXED_POINT, inner_tol=1e-5)
+        else:
+            opts["precond"] = PRECONDS[precond]
         s = vdp.Solver(nx, ny, nz, pr.L, precision="mixed", **opts)
         s.set_density(torch.from_numpy(pr.rho).to(dev))
         solvers.append(s)
@@ -364,10 +367,11 @@ def run_serving(torch, vdp, dev, pool, count=200):
         pr = pool[(rq.n, 200000 + 10 * rq.n + (rq.j % 2))]
         reqs.append(serve.ServeRequest(rq.j, rq.arrival_s, pr.shape, pr.L, pr.rho, pr.f, rq.tol))
     with serve.Server("mixed", hbm_budget=96 << 30, max_active=64, pairs_per_run=16, tuned=True,
-                      precond="spectral", persistent=False) as srv:
+                      precond="fixed_point", persistent=False) as srv:
         stats = srv.run(reqs)
     s = stats.summary()
-    s.update({"requests": count, "offered_rate_per_s": 200.0, "precond": "spectral (Jacobi for other sizes)",
+    s.update({"requests": count, "offered_rate_per_s": 200.0,
+              "method": "the paper's fixed-point iteration (Jacobi-preconditioned CG for other sizes)",
               "statuses_ok": all(r.status == vdp.VDP_OK for r in reqs),
               "inputs": "14 seeded hot-spot problems (2 per grid size), per-request tolerance"})
     return s
@@ -530,11 +534,13 @@ def main():
         # (precision, preconditioner, Chebyshev degree)
         variants = {"fp64_spectral": ("fp64", "spectral", 1), "mixed_spectral": ("mixed", "spectral", 1),
                     "fp64_fixed_point": ("fp64", "fixed_point", 1), "mixed_fixed_point": ("mixed", "fixed_point", 1),
+                    "mixed_bf16_fixed_point": ("mixed_bf16", "fixed_point", 1),
                     "mixed_bf16_spectral": ("mixed_bf16", "spectral", 1), "fp64_jacobi": ("fp64", "jacobi", 1),
                     "mixed_jacobi": ("mixed", "jacobi", 1), "mixed_cheb3": ("mixed", "cheb", 3),
                     "mixed_bf16_jacobi": ("mixed_bf16", "jacobi", 1)}
         for label, (prec, pc, k) in variants.items():
-            opts = {"method": vdp.VDP_METHOD_FIXED_POINT} if pc == "fixed_point" else {"precond": PRECONDS[pc]}
+            opts = ({"method": vdp.VDP_METHOD_FIXED_POINT, "inner_tol": 1e-5} if pc == "fixed_point"
+                    else {"precond": PRECONDS[pc]})
             if pc == "cheb":
                 opts["cheb_degree"] = k
             with vdp.Solver(nx, ny, nz, prob.L, precision=prec, stream=stream, **opts) as s2:
@@ -557,6 +563,8 @@ def main():
         if batch_probs is not None:
             line["batch"] = run_batch(torch, vdp, dev, batch_probs)
             keep = ("seconds", "solves_per_s", "gdof_iter_per_s", "iterations_total", "all_ok")
+            line["batch_cg_spectral"] = {k: v for k, v in run_batch(torch, vdp, dev, batch_probs,
+                                                                    precond="spectral").items() if k in keep}
             line["batch_jacobi"] = {k: v for k, v in run_batch(torch, vdp, dev, batch_probs, precond="jacobi").items()
                                     if k in keep}
             line["batch_jacobi_persistent"] = {k: v for k, v in run_batch(torch, vdp, dev, batch_probs, True,

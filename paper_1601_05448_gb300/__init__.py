@@ -33,10 +33,11 @@ def spectral_supported(nx: int, ny: int, nz: int) -> bool:
 
 
 def spectral_extra_bytes(nx: int, ny: int, nz: int) -> int:
-    """Device memory the spectral preconditioner adds to a context: z (8 B/cell), the weights
-    (4 B/cell) and the half spectrum (8 B per complex value, rows padded to 8 values)."""
+    """Device memory the spectral passes add to a context: z (8 B/cell), the weights (4 B/cell,
+    4 more for the fixed-point iteration's density weight) and the half spectrum (8 B per
+    complex value, rows padded to 8 values)."""
     nxp = ((nx // 2 + 1 + 7) // 8) * 8
-    return 12 * nx * ny * nz + 8 * nxp * ny * nz
+    return 16 * nx * ny * nz + 8 * nxp * ny * nz
 
 
 class VdpUnavailable(RuntimeError):

@@ -1,10 +1,11 @@
 // vdp_api.cu -- the C ABI of libvdp (include/vdp.h): contexts, device buffers, the solve driver.
 //
-// A solve is one instance of the per-instance state machine in vdp_kernels.cu, advanced by the
-// two sweep kernels (stencil kind, flat kind).  The driver launches a captured CUDA graph of
-// `steps_per_sync` (stencil, flat) launch pairs, copies the instance's 200-byte state to pinned
-// host memory after each graph, and keeps two graphs in flight so that the convergence check on
-// the host overlaps with device work.
+// A solve is one instance of the per-instance state machine (vdp_internal.cuh, transitions in
+// vdp_device.cuh), advanced by the sweep kernels of vdp_kernels.cu and vdp_spectral.cu.  The
+// driver launches a captured CUDA graph of `steps_per_sync` rounds -- residual, (five spectral
+// passes,) stencil and flat kernels, each returning at once unless the phase is its own --
+// copies the instance's state to pinned host memory after each graph, and keeps two graphs in
+// flight so that the convergence check on the host overlaps with device work.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -13,17 +13,19 @@
 // outer FP64 loop evaluates the true residual r = (f - <f>) - A p, hands rt = D^-1/2 r to the
 // inner solver (FP64, or FP32 with FP32/BF16 coefficients), and applies p -= D^-1/2 x.
 //
-// Kernels: the coefficient builders (set-up), and one step kernel that performs one sweep of
-// the phase each instance is in (see vdp_internal.cuh).
+// The preconditioned residual z (Chebyshev polynomial or the spectral passes of
+// vdp_spectral.cu) replaces rt as the stencil sweep's source; the paper's fixed-point iteration
+// runs as the same sweeps with beta = 0 and alpha = 1.
 //
-// The stencil sweep (the hot kernel) marches each unit through consecutive z planes.  For every
-// plane, one thread issues TMA bulk copies (cp.async.bulk, global -> shared, completion counted
-// on an mbarrier) of whole contiguous row blocks: rt and d_old with one halo row above and below
-// the tile, and the three coefficient arrays.  `stages` planes are in flight, so HBM streams
-// while the CTA computes.  The search direction d = rt + beta d_old is formed in place in the
-// stage buffer (once per cell, halo rows included), and the 7-point product q = At d reads the
-// z-1, z and z+1 planes of d from three live stages; every value is fetched from global memory
-// once per unit, x neighbours wrap inside the row, and only the halo rows are re-read from L2.
+// Kernels: the coefficient builders (set-up) and three sweep kernels, each advancing every
+// instance whose phase is of its kind (see vdp_internal.cuh): k_res64_direct (FP64 residual),
+// k_stencil_direct (search direction, stencil product and <d, q>; Chebyshev sweeps in its
+// CHEBOK variant) and k_flat (element-wise phases).  The direct sweeps march each work unit
+// through a z chunk with three planes in registers: a thread owns 16 bytes of one row, takes
+// its x neighbours from the adjacent lanes by warp shuffle and the rows above and below from
+// L1/L2, and waits on no other warp.  k_stencil_tma is the TMA-staged variant (cp.async.bulk
+// row blocks into a shared-memory ring, mbarrier completion with bounded waits, one block
+// barrier per plane), kept as an option; k_persistent runs all of them for a batch.
 #include "vdp_device.cuh"
 #include "vdp_internal.cuh"
 #include "vdp_launch.h"
@@ -274,7 +276,8 @@ __device__ void sweep_update(const InstDesc& I, const InstState* st, long long c
   constexpr int U = 2;  // vectors per thread per round
   const T alpha = (T)st->alpha;
   const bool first = st->inner_iters == 0;
-  const T* d = static_cast<const T*>(st->parity ? I.d0 : I.d1);  // written by the last stencil
+  // written by the last stencil sweep (the fixed-point iteration's direction is z itself)
+  const T* d = static_cast<const T*>(I.pc == PC_FIXED ? I.za : (st->parity ? I.d0 : I.d1));
   const T* q = static_cast<const T*>(I.q);
   T* x = static_cast<T*>(I.x);
   T* rt = static_cast<T*>(I.r);
@@ -588,8 +591,10 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
   const int cj = CHEB ? st->cheb_j : 0;
   const bool last = CHEB && cj == I.cheb_k - 1;
   T beta = (T)st->beta, scale = 1, c1 = 0, c2 = 0;
-  // the paper's fixed-point iteration has no search-direction history (beta = 0)
-  bool use_old = st->inner_iters > 0 && I.pc != PC_FIXED;
+  // the paper's fixed-point iteration has no search-direction history (beta = 0) and needs
+  // neither <d, q> nor d itself (the update sweep reads z)
+  const bool fixed = I.pc == PC_FIXED;
+  bool use_old = st->inner_iters > 0 && !fixed;
   bool form = use_old && !QREC;  // form d = src + beta d_old for every marched value
   const T* rt = static_cast<const T*>(I.r);
   const T* src = I.pc != PC_JACOBI ? static_cast<const T*>(I.za) : rt;
@@ -692,7 +697,7 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
       a = fma(-bz[k], dm[k], a);
       a = fma(-bzp[k], dp[k], a);
       qv[k] = a;
-      if (!CHEB && !QREC) sum[k] = fma(dc[k], a, sum[k]);
+      if (!CHEB && !QREC && !fixed) sum[k] = fma(dc[k], a, sum[k]);
     }
     T dn[V];
     if (QREC) {
@@ -700,7 +705,7 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
       for (int k = 0; k < V; ++k) {
         dn[k] = use_old ? fma(beta, dol[k], dc[k]) : dc[k];
         qv[k] = use_old ? fma(beta, qo[k], qv[k]) : qv[k];
-        sum[k] = fma(dn[k], qv[k], sum[k]);
+        if (!fixed) sum[k] = fma(dn[k], qv[k], sum[k]);
       }
     }
     if (CHEB) {
@@ -723,10 +728,12 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
         if (!last) VecIO<T, V>::st(dch + oc, dn);
       }
     } else if (active) {
-      if (QREC)
-        VecIO<T, V>::st(dnew + oc, dn);
-      else
-        VecIO<T, V>::st(dnew + oc, dc);
+      if (!fixed) {
+        if (QREC)
+          VecIO<T, V>::st(dnew + oc, dn);
+        else
+          VecIO<T, V>::st(dnew + oc, dc);
+      }
       VecIO<T, V>::st(q + oc, qv);
     }
 #pragma unroll

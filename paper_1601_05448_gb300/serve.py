@@ -24,7 +24,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import PRECISIONS, VDP_PRECOND_JACOBI, VDP_PRECOND_SPECTRAL, Batch, Solver, VdpError, \
+from . import PRECISIONS, VDP_METHOD_FIXED_POINT, VDP_PRECOND_JACOBI, VDP_PRECOND_SPECTRAL, Batch, Solver, \
+    VdpError, \
     spectral_extra_bytes, spectral_supported
 
 BYTES_PER_CELL = 96 + 2  # device memory of one context per cell (FP64-sized buffers + BF16 diag)
@@ -78,13 +79,15 @@ class ServeStats:
 class Server:
     """``Server(precision="mixed", hbm_budget=64 GB, max_active=64).run(requests)``.
 
-    precond="spectral" gives every request whose grid the FFT passes support the spectral
-    preconditioner (the others get Jacobi); it needs the batch of ordinary launches
-    (persistent=False).  precond="jacobi" uses Jacobi everywhere."""
+    precond="fixed_point" solves every request whose grid the FFT passes support by the paper's
+    fixed-point iteration, "spectral" by CG with the spectral preconditioner (the others by
+    Jacobi-preconditioned CG); both need the batch of ordinary launches (persistent=False).
+    precond="jacobi" uses Jacobi-preconditioned CG everywhere.  inner_tol: the mixed path's
+    reduction per inner solve."""
 
     def __init__(self, precision: str = "mixed", hbm_budget: int = 64 << 30, max_active: int = 64,
                  pairs_per_run: int = 8, persistent: bool = False, tuned: bool = False, device: str = "cuda:0",
-                 precond: str = "spectral"):
+                 precond: str = "fixed_point", inner_tol: float = 1e-5):
         import torch
         self.torch = torch
         self.precision = precision
@@ -92,9 +95,10 @@ class Server:
         self.max_active = int(max_active)
         self.pairs = int(pairs_per_run)
         self.tuned = tuned
-        if precond not in ("spectral", "jacobi") or (precond == "spectral" and persistent):
-            raise ValueError("precond must be 'jacobi', or 'spectral' with persistent=False")
+        if precond not in ("fixed_point", "spectral", "jacobi") or (precond != "jacobi" and persistent):
+            raise ValueError("precond must be 'jacobi', or 'fixed_point' / 'spectral' with persistent=False")
         self.precond = precond
+        self.inner_tol = float(inner_tol)
         self.device = torch.device(device)
         self.batch = Batch(precision, persistent=persistent)
         self.idle = collections.OrderedDict()   # ctx id -> (Solver, shape) available for reuse
@@ -105,7 +109,7 @@ class Server:
 
     def _spectral(self, shape) -> bool:
         nz, ny, nx = shape
-        return self.precond == "spectral" and spectral_supported(nx, ny, nz)
+        return self.precond != "jacobi" and spectral_supported(nx, ny, nz)
 
     def _ctx_bytes(self, shape) -> int:
         nz, ny, nx = shape
@@ -130,6 +134,9 @@ class Server:
             from .tune import cached_options
             opts = cached_options(nx, ny, nz, self.precision, batchable=True) or {}
         opts["precond"] = VDP_PRECOND_SPECTRAL if self._spectral(shape) else VDP_PRECOND_JACOBI
+        if self._spectral(shape) and self.precond == "fixed_point":
+            opts["method"] = VDP_METHOD_FIXED_POINT
+        opts["inner_tol"] = self.inner_tol
         try:
             s = Solver(nx, ny, nz, L, precision=self.precision, **opts)
         except VdpError:

@@ -106,16 +106,20 @@ def test_continuous_admission_and_retirement():
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_spectral_members_equal_alone(precision):
-    """Batch of ordinary launches with spectrally preconditioned members (FFT-supported sizes),
-    mixed with a Jacobi member: every result equals its solve alone, bit for bit."""
-    probs = [(V.hotspot_problem(32, seed=57, nspots=40, target_ratio=5.0), 1e-9, vdp.VDP_PRECOND_SPECTRAL),
-             (V.smooth_problem((48, 32, 64), seed=58), 1e-10, vdp.VDP_PRECOND_SPECTRAL),
-             (V.smooth_problem((16, 16, 24), seed=51), 1e-9, vdp.VDP_PRECOND_JACOBI),
-             (V.hotspot_problem(64, seed=59, nspots=312, target_ratio=8.0), 1e-8, vdp.VDP_PRECOND_SPECTRAL)]
+    """Batch of ordinary launches with spectrally preconditioned and fixed-point members
+    (FFT-supported sizes), mixed with a Jacobi member: every result equals its solve alone, bit
+    for bit."""
+    fp = {"method": vdp.VDP_METHOD_FIXED_POINT}
+    probs = [(V.hotspot_problem(32, seed=57, nspots=40, target_ratio=5.0), 1e-9, {"precond": vdp.VDP_PRECOND_SPECTRAL}),
+             (V.smooth_problem((48, 32, 64), seed=58), 1e-10, {"precond": vdp.VDP_PRECOND_SPECTRAL}),
+             (V.smooth_problem((16, 16, 24), seed=51), 1e-9, {}),
+             (V.hotspot_problem(64, seed=59, nspots=312, target_ratio=8.0), 1e-8, {"precond": vdp.VDP_PRECOND_SPECTRAL}),
+             (V.hotspot_problem(48, seed=60, nspots=130, target_ratio=6.0), 1e-9, fp),
+             (V.smooth_problem((32, 64, 32), seed=61), 1e-10, fp)]
     members = []
-    for prob, tol, pc in probs:
+    for prob, tol, opts in probs:
         nz, ny, nx = prob.shape
-        s = vdp.Solver(nx, ny, nz, prob.L, precision=precision, precond=pc)
+        s = vdp.Solver(nx, ny, nz, prob.L, precision=precision, **opts)
         s.set_density(torch.from_numpy(prob.rho).to(DEV))
         f = torch.from_numpy(prob.f).to(DEV)
         p_alone = torch.empty_like(f)

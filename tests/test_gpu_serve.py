@@ -32,15 +32,19 @@ def request_stream(count=12, seed=7):
 
 def solve_alone(req, precision, precond="jacobi"):
     nz, ny, nx = req.shape
-    pc = vdp.VDP_PRECOND_SPECTRAL if precond == "spectral" and vdp.spectral_supported(nx, ny, nz) else 0
-    with vdp.Solver(nx, ny, nz, req.L, precision=precision, precond=pc) as s:
+    fft = precond != "jacobi" and vdp.spectral_supported(nx, ny, nz)
+    opts = {"precond": vdp.VDP_PRECOND_SPECTRAL if fft else 0, "inner_tol": 1e-5}
+    if fft and precond == "fixed_point":
+        opts["method"] = vdp.VDP_METHOD_FIXED_POINT
+    with vdp.Solver(nx, ny, nz, req.L, precision=precision, **opts) as s:
         s.set_density(torch.from_numpy(req.rho).to(DEV))
         p = torch.empty(req.shape, dtype=torch.float64, device=DEV)
         st = s.solve(torch.from_numpy(req.f).to(DEV), p, req.tol)
     return p, st
 
 
-@pytest.mark.parametrize("persistent,precond", [(True, "jacobi"), (False, "jacobi"), (False, "spectral")])
+@pytest.mark.parametrize("persistent,precond", [(True, "jacobi"), (False, "jacobi"), (False, "spectral"),
+                                               (False, "fixed_point")])
 def test_served_results_equal_alone(persistent, precond):
     reqs = request_stream()
     seen_overlap = []
