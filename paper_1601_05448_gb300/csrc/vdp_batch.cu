@@ -57,6 +57,10 @@ struct vdp_batch {
   cudaGraphExec_t gexec = nullptr;
   int g_pairs = 0;
   int grid = 0;
+  // graph branches for the members' spectral passes (captured from these streams)
+  static constexpr int kBranches = 4;
+  cudaStream_t aux[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {};
 };
 
 namespace {
@@ -145,15 +149,28 @@ int capture(vdp_batch* b, int pairs) {
     for (int k : b->active) cheb |= b->members[k].ctx->hdesc.pc == PC_CHEB;
     for (int i = 0; i < pairs && e == cudaSuccess; ++i) {
       e = launch_res64(b->prec, b->d_desc, b->d_units, b->ns, kDirectThreads, b->cap);
-      // members with the spectral preconditioner: their five FFT passes (each gated on its own
-      // member's phase), between the residual and the stencil sweeps as in a solve alone
+      // members with the spectral passes: their five FFT kernels (each gated on its own
+      // member's phase), between the residual and the stencil sweeps as in a solve alone.  The
+      // members' chains are independent, so they go to up to four graph branches that the GPU
+      // runs concurrently (small grids alone would leave most SMs idle).
+      int nspec = 0;
+      for (int k : b->active) nspec += b->members[k].ctx->hdesc.pc >= PC_SPECTRAL;
+      const int nb = std::min(nspec, (int)vdp_batch::kBranches);
+      if (nb > 0 && e == cudaSuccess) e = cudaEventRecord(b->fork, b->cap);
+      for (int j = 0; j < nb && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(b->aux[j], b->fork, 0);
+      int slot = 0;
       for (size_t k = 0; k < b->active.size() && e == cudaSuccess; ++k) {
         const vdp_ctx* c = b->members[b->active[k]].ctx;
         if (c->hdesc.pc < PC_SPECTRAL) continue;
         SpecArgs a;
         solve_spec_args(c, b->prec, &a);
+        cudaStream_t br = b->aux[slot++ % nb];
         for (int pass = 0; pass < SPEC_PASSES && e == cudaSuccess; ++pass)
-          e = launch_spectral_pass(b->prec, pass, a, b->cap);
+          e = launch_spectral_pass(b->prec, pass, a, br);
+      }
+      for (int j = 0; j < nb && e == cudaSuccess; ++j) {
+        e = cudaEventRecord(b->join[j], b->aux[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[j], 0);
       }
       if (e == cudaSuccess)
         e = launch_stencil(b->prec, 0, cheb, b->d_desc, b->d_units, b->ns, kDirectThreads, 0,
@@ -199,6 +216,11 @@ int vdp_batch_create(int precision, int persistent, void* stream, vdp_batch** ou
   b->stream = (cudaStream_t)stream;
   cudaGetDevice(&b->device);
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  for (int j = 0; j < vdp_batch::kBranches && e == cudaSuccess; ++j) {
+    e = cudaStreamCreateWithFlags(&b->aux[j], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[j], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_ctl, sizeof(BatchCtl));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_ctl, sizeof(BatchCtl));
   if (e == cudaSuccess) e = persistent_grid(precision, &b->grid);
@@ -222,6 +244,11 @@ void vdp_batch_destroy(vdp_batch* b) {
   if (b->d_ctl) cudaFree(b->d_ctl);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int j = 0; j < vdp_batch::kBranches; ++j) {
+    if (b->aux[j]) cudaStreamDestroy(b->aux[j]);
+    if (b->join[j]) cudaEventDestroy(b->join[j]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   delete b;
 }
 
