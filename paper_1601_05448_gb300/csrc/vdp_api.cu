@@ -218,7 +218,7 @@ int ensure_graph(vdp_ctx* c, int prec) {
         e = launch_spectral_pass(prec, pass, a, c->cap);
     }
     if (e == cudaSuccess)
-      e = launch_stencil(prec, c->lay.mode, c->hdesc.pc == PC_CHEB, c->desc, c->units,
+      e = launch_stencil(prec, c->lay.mode, stencil_kind(c->hdesc.pc), c->desc, c->units,
                          c->lay.nunits, c->lay.threads,
                          c->lay.smem, c->cap);
     if (e == cudaSuccess)

@@ -145,8 +145,15 @@ int capture(vdp_batch* b, int pairs) {
     e = launch_persistent(b->prec, b->d_desc, b->d_units, b->ns, b->d_units + b->ns, b->nf, pairs,
                           b->d_ctl, b->grid, b->cap);
   } else {
-    int cheb = 0;  // the stencil kernel variant with Chebyshev sweeps if any member needs it
-    for (int k : b->active) cheb |= b->members[k].ctx->hdesc.pc == PC_CHEB;
+    // one stencil kernel for all members: the fixed-point variant if every member uses that
+    // method, the variant with Chebyshev sweeps if any member needs it (it also runs the
+    // fixed-point sweep), the CG variant otherwise
+    int nfixed = 0, ncheb = 0;
+    for (int k : b->active) {
+      nfixed += b->members[k].ctx->hdesc.pc == PC_FIXED;
+      ncheb += b->members[k].ctx->hdesc.pc == PC_CHEB;
+    }
+    const int kind = nfixed == (int)b->active.size() ? 2 : (ncheb || nfixed) ? 1 : 0;
     for (int i = 0; i < pairs && e == cudaSuccess; ++i) {
       e = launch_res64(b->prec, b->d_desc, b->d_units, b->ns, kDirectThreads, b->cap);
       // members with the spectral passes: their five FFT kernels (each gated on its own
@@ -173,7 +180,7 @@ int capture(vdp_batch* b, int pairs) {
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[j], 0);
       }
       if (e == cudaSuccess)
-        e = launch_stencil(b->prec, 0, cheb, b->d_desc, b->d_units, b->ns, kDirectThreads, 0,
+        e = launch_stencil(b->prec, 0, kind, b->d_desc, b->d_units, b->ns, kDirectThreads, 0,
                            b->cap);
       if (e == cudaSuccess) e = launch_flat(b->prec, b->d_desc, b->d_units + b->ns, b->nf, b->cap);
     }

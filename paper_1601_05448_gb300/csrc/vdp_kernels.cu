@@ -563,7 +563,11 @@ __device__ void sweep_stencil(const InstDesc& I, InstState* st, int unit, T& par
 template <class T> struct IsF64 { static constexpr bool value = false; };
 template <> struct IsF64<double> { static constexpr bool value = true; };
 
-template <class T, class BT, bool CHEB>
+// VAR selects the variant at compile time (a predicated-off FMA still costs FP64-pipe slots):
+//   0  first iteration of an inner CG solve (no search-direction history), or a Chebyshev sweep
+//   1  CG with history (d = z + beta d_old)
+//   2  the paper's fixed-point iteration (no history, no <d, q>, d not stored)
+template <class T, class BT, bool CHEB, int VAR>
 __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int unit, T& part) {
   constexpr int V = VecW<T>::V;
   constexpr bool kDiag = CoefTraits<BT>::kDiag;
@@ -593,9 +597,9 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
   T beta = (T)st->beta, scale = 1, c1 = 0, c2 = 0;
   // the paper's fixed-point iteration has no search-direction history (beta = 0) and needs
   // neither <d, q> nor d itself (the update sweep reads z)
-  const bool fixed = I.pc == PC_FIXED;
-  bool use_old = st->inner_iters > 0 && !fixed;
-  bool form = use_old && !QREC;  // form d = src + beta d_old for every marched value
+  constexpr bool fixed = VAR == 2;
+  constexpr bool use_old = VAR == 1 && !CHEB;
+  constexpr bool form = use_old && !QREC;  // form d = src + beta d_old for every marched value
   const T* rt = static_cast<const T*>(I.r);
   const T* src = I.pc != PC_JACOBI ? static_cast<const T*>(I.za) : rt;
   const T* dold = static_cast<const T*>(st->parity ? I.d1 : I.d0);
@@ -618,8 +622,6 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
     }
     c1 = (T)(r * rp);                  // rho_j rho_{j-1}
     c2 = (T)(2.0 * r / I.cheb_delta);  // 2 rho_j / delta
-    use_old = false;
-    form = false;
     beta = 0;
   }
   const BT* sx = static_cast<const BT*>(I.sx);
@@ -951,16 +953,17 @@ __device__ void sweep_res64(const InstDesc& I, const InstState* st, int unit,
 
 // One stencil-kind unit of instance I: WHICH = 0 handles the RES64 and STENCIL phases, 1 only
 // STENCIL, 2 only RES64; a no-op for other phases.
-// CHEBOK = false compiles the Chebyshev sweep out (instances without that preconditioner): the
-// kernel then keeps the register budget of the plain stencil sweep.
-template <class T, class BT, int MODE, int WHICH = 0, bool CHEBOK = true>
+// KIND (direct form): 0 = CG sweeps only (the Chebyshev sweep compiled out, so the kernel keeps
+// the register budget of the plain stencil sweep), 1 = CG and Chebyshev sweeps, 2 = the
+// fixed-point iteration's sweep only.  The persistent batch kernel uses 1.
+template <class T, class BT, int MODE, int WHICH = 0, int KIND = 1>
 __device__ __forceinline__ void stencil_kind_unit(const InstDesc& I, int unit,
                                                   unsigned char* smem_raw) {
   InstState* st = I.st;
   const int phase = __ldcg(&st->phase);  // one load decides whether this unit has work
   if (phase != PH_RES64 && phase != PH_STENCIL && phase != PH_CHEB) return;
   if ((WHICH == 1 && phase == PH_RES64) || (WHICH == 2 && phase != PH_RES64)) return;
-  if ((MODE != 0 || !CHEBOK) && phase == PH_CHEB) return;  // direct form with CHEBOK only
+  if ((MODE != 0 || KIND != 1) && phase == PH_CHEB) return;  // direct form, KIND 1 only
   const InstState sn = snapshot(st);
   if (WHICH != 1 && phase == PH_RES64) {
     double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
@@ -971,15 +974,20 @@ __device__ __forceinline__ void stencil_kind_unit(const InstDesc& I, int unit,
     store_partials<kSlots, double>(acc, I.part, I.nunits, unit);
   } else if (WHICH != 2) {
     T part[1] = {0};
-    if constexpr (MODE == 0 && CHEBOK) {
-      if (phase == PH_CHEB)
-        sweep_stencil_direct<T, BT, true>(I, &sn, unit, part[0]);
-      else
-        sweep_stencil_direct<T, BT, false>(I, &sn, unit, part[0]);
-    } else if (MODE == 0)
-      sweep_stencil_direct<T, BT, false>(I, &sn, unit, part[0]);
-    else
+    if constexpr (MODE != 0) {
       sweep_stencil<T, BT>(I, st, unit, part[0], smem_raw);
+    } else if constexpr (KIND == 2) {
+      sweep_stencil_direct<T, BT, false, 2>(I, &sn, unit, part[0]);
+    } else {
+      if (KIND == 1 && phase == PH_CHEB)
+        sweep_stencil_direct<T, BT, KIND == 1, 0>(I, &sn, unit, part[0]);
+      else if (I.pc == PC_FIXED)  // the persistent kernel runs every kind of instance
+        sweep_stencil_direct<T, BT, false, 2>(I, &sn, unit, part[0]);
+      else if (sn.inner_iters > 0)
+        sweep_stencil_direct<T, BT, false, 1>(I, &sn, unit, part[0]);
+      else
+        sweep_stencil_direct<T, BT, false, 0>(I, &sn, unit, part[0]);
+    }
     store_partials<1, T>(part, I.part, I.nunits, unit);
   }
   finish_sweep(I, st, phase, I.nunits);
@@ -1021,11 +1029,11 @@ __device__ __forceinline__ void flat_kind_unit(const InstDesc& I, int unit) {
 template <class T> struct DirectOcc { static constexpr int kMinBlocks = VDP_DIRECT_MIN_BLOCKS; };
 template <> struct DirectOcc<float> { static constexpr int kMinBlocks = VDP_DIRECT_MIN_BLOCKS + 1; };
 
-template <class T, class BT, bool CHEBOK>
+template <class T, class BT, int KIND>
 __global__ void __launch_bounds__(kDirectThreads, DirectOcc<T>::kMinBlocks) k_stencil_direct(
     const InstDesc* __restrict__ insts, const UnitRef* __restrict__ units) {
   const UnitRef ur = units[blockIdx.x];
-  stencil_kind_unit<T, BT, 0, 1, CHEBOK>(insts[ur.inst], ur.unit, nullptr);
+  stencil_kind_unit<T, BT, 0, 1, KIND>(insts[ur.inst], ur.unit, nullptr);
 }
 
 // Direct register march, RES64 phase only (a few launches per solve do work; the kernel has its
@@ -1335,17 +1343,15 @@ cudaError_t launch_init(InstDesc* desc, const double* rhs, double* p, double tol
   return cudaGetLastError();
 }
 
-static void* stencil_fn(int prec, int mode, int cheb) {
-  if (mode == 0 && cheb) {
-    if (prec == PREC_FP64) return (void*)k_stencil_direct<double, double, true>;
-    if (prec == PREC_MIXED) return (void*)k_stencil_direct<float, float, true>;
-    return (void*)k_stencil_direct<float, __nv_bfloat16, true>;
-  }
-  if (mode == 0) {
-    if (prec == PREC_FP64) return (void*)k_stencil_direct<double, double, false>;
-    if (prec == PREC_MIXED) return (void*)k_stencil_direct<float, float, false>;
-    return (void*)k_stencil_direct<float, __nv_bfloat16, false>;
-  }
+template <int KIND>
+static void* direct_fn(int prec) {
+  if (prec == PREC_FP64) return (void*)k_stencil_direct<double, double, KIND>;
+  if (prec == PREC_MIXED) return (void*)k_stencil_direct<float, float, KIND>;
+  return (void*)k_stencil_direct<float, __nv_bfloat16, KIND>;
+}
+
+static void* stencil_fn(int prec, int mode, int kind) {
+  if (mode == 0) return kind == 2 ? direct_fn<2>(prec) : kind == 1 ? direct_fn<1>(prec) : direct_fn<0>(prec);
   if (prec == PREC_FP64) return (void*)k_stencil_tma<double, double>;
   if (prec == PREC_MIXED) return (void*)k_stencil_tma<float, float>;
   return (void*)k_stencil_tma<float, __nv_bfloat16>;
@@ -1366,10 +1372,10 @@ cudaError_t launch_res64(int prec, const InstDesc* desc, const UnitRef* units, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_stencil(int prec, int mode, int cheb, const InstDesc* desc,
+cudaError_t launch_stencil(int prec, int mode, int kind, const InstDesc* desc,
                            const UnitRef* units, int nunits, int threads, size_t smem_bytes,
                            cudaStream_t s) {
-  void* fn = stencil_fn(prec, mode, cheb);
+  void* fn = stencil_fn(prec, mode, kind);
   void* args[] = {(void*)&desc, (void*)&units};
   return cudaLaunchKernel(fn, dim3(nunits), dim3(threads), args, smem_bytes, s);
 }

@@ -23,8 +23,10 @@ cudaError_t prepare_step(int prec, int mode, size_t smem_bytes);
 // mode 0 only: the FP64 residual sweep (its own kernel, launched before each stencil launch)
 cudaError_t launch_res64(int prec, const InstDesc* desc, const UnitRef* units, int nunits,
                          int threads, cudaStream_t s);
-// cheb = 1: the variant that also runs Chebyshev preconditioner sweeps (PH_CHEB)
-cudaError_t launch_stencil(int prec, int mode, int cheb, const InstDesc* desc,
+// kind (direct sweep variants): 0 = CG, 1 = CG and Chebyshev preconditioner sweeps (PH_CHEB),
+// 2 = the fixed-point iteration; stencil_kind(pc) picks it for an instance's preconditioner
+inline int stencil_kind(int pc) { return pc == PC_FIXED ? 2 : (pc == PC_CHEB ? 1 : 0); }
+cudaError_t launch_stencil(int prec, int mode, int kind, const InstDesc* desc,
                            const UnitRef* units, int nunits, int threads, size_t smem_bytes,
                            cudaStream_t s);
 cudaError_t launch_flat(int prec, const InstDesc* desc, const UnitRef* units, int nunits,

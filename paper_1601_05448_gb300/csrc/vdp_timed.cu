@@ -44,7 +44,7 @@ cudaError_t launch_for_phase(vdp_ctx* c, int prec, int phase, cudaStream_t s) {
       return launch_stencil(prec, l.mode, 0, c->desc, c->units, l.nunits, l.threads, l.smem, s);
     case PH_STENCIL:
     case PH_CHEB:
-      return launch_stencil(prec, l.mode, c->hdesc.pc == PC_CHEB, c->desc, c->units, l.nunits,
+      return launch_stencil(prec, l.mode, stencil_kind(c->hdesc.pc), c->desc, c->units, l.nunits,
                             l.threads, l.smem, s);
     default:
       return launch_flat(prec, c->desc, c->units + l.nunits, l.nunits_f, s);
