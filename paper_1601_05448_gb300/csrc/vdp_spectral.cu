@@ -147,13 +147,37 @@ template <> struct Pair<float> {
     b = v.y;
   }
 };
+// Conversions between binary64 and binary32 by repacking the IEEE 754 fields with integer
+// operations: on this GPU the conversion instructions run on the FP64 pipe (2 results per clock
+// per SM), which the FP64 passes otherwise spend a third of their time in.
+//   to binary32: exponent rebiased (1023 -> 127), the 23 leading fraction bits kept (rounding
+//                toward zero), magnitudes below the binary32 normal range flushed to zero and
+//                above it (infinities, NaNs) sent to infinity -- adequate for a preconditioner
+//                input, which the FP32 transforms round anyway;
+//   to binary64: exact for every binary32 normal number and zero (subnormals flush to zero).
+__device__ __forceinline__ float narrow(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned bits = e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : (sign | ((unsigned)e << 23) | frac));
+  return __uint_as_float(bits);
+}
+__device__ __forceinline__ double widen(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xffu, frac = b & 0x7fffffu;
+  const unsigned hi = e == 0 ? sign : (sign | ((e + 1023u - 127u) << 20) | (frac >> 3));
+  const unsigned lo = e == 0 ? 0u : (frac << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 template <> struct Pair<double> {
   static __device__ __forceinline__ float2 ld(const double* p) {
     const double2 v = *reinterpret_cast<const double2*>(p);
-    return make_float2((float)v.x, (float)v.y);
+    return make_float2(narrow(v.x), narrow(v.y));
   }
   static __device__ __forceinline__ void st(double* p, float2 v) {
-    *reinterpret_cast<double2*>(p) = make_double2((double)v.x, (double)v.y);
+    *reinterpret_cast<double2*>(p) = make_double2(widen(v.x), widen(v.y));
   }
   static __device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
     const double2 v = *reinterpret_cast<const double2*>(p);
@@ -265,6 +289,19 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
   const bool live = row < rows;
   float2* ra = sa + r * SA;
   float2* rb = sb + r * SB;
+  // the output weights of this thread's cells are loaded first, so that their latency overlaps
+  // the transforms (cells 2l, 2l + 1 with l = k2 + M2 k1, k2 = t, t + M1, ...)
+  constexpr int R = (M2 + M1 - 1) / M1;
+  float2 wv[R][M1];
+  const float* om = a.omega_out ? a.omega_out + row * a.nx : nullptr;
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr)
+#pragma unroll
+    for (int k1 = 0; k1 < M1; ++k1) {
+      const int k2 = t + M1 * rr;
+      wv[rr][k1] = make_float2(1.f, 1.f);
+      if (live && om && k2 < M2) wv[rr][k1] = *reinterpret_cast<const float2*>(om + 2 * (k2 + M2 * k1));
+    }
   if (live) {
     const float2* src = a.spec + row * a.nxp;
     for (int k = t; k <= m; k += M1) ra[k] = src[k];
@@ -289,8 +326,10 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
   __syncthreads();
   if (live) {
     T* out = static_cast<T*>(a.out) + row * a.nx;
-    const float* om = a.omega_out ? a.omega_out + row * a.nx : nullptr;
-    for (int k2 = t; k2 < M2; k2 += M1) {
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int k2 = t + M1 * rr;
+      if (k2 >= M2) break;
       float2 u[M1], o[M1];
 #pragma unroll
       for (int j1 = 0; j1 < M1; ++j1) u[j1] = rb[ex<M1>(k2, j1)];
@@ -298,11 +337,7 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
 #pragma unroll
       for (int k1 = 0; k1 < M1; ++k1) {
         const int l = k2 + M2 * k1;  // cells 2l, 2l + 1 of the row
-        float2 z = o[k1];
-        if (om) {
-          const float2 w = *reinterpret_cast<const float2*>(om + 2 * l);
-          z = make_float2(z.x * w.x, z.y * w.y);
-        }
+        const float2 z = make_float2(o[k1].x * wv[rr][k1].x, o[k1].y * wv[rr][k1].y);
         Pair<T>::st(out + 2 * l, z);
       }
     }
