@@ -71,8 +71,7 @@ def spectrum_bytes(nx: int) -> float:
 # method), keyed (precision, sweep, grid, fixed-point); 256^3 entries scale by the cell count
 # 256^3 / 192^3.  A changed kernel drops its entries until it is re-captured.
 _SCALE_256 = (256 / 192) ** 3
-_TRAFFIC_192 = {("fp64", "stencil", True): 227.5e6 + 87.8e6, ("fp64", "update", True): 227.5e6 + 70.3e6,
-                ("mixed", "stencil", True): 113.8e6 + 31.4e6, ("mixed", "update", True): 113.3e6 + 15.5e6,
+_TRAFFIC_192 = {("fp64", "update", True): 227.5e6 + 70.3e6, ("mixed", "update", True): 113.3e6 + 15.5e6,
                 ("fp64", "spec_x", True): (85.0e6 + 6.7e6 + 59.0e6 + 12.8e6) / 2,
                 ("mixed", "spec_x", True): (56.6e6 + 2.9e6 + 59.0e6 + 2.6e6) / 2}
 TRAFFIC = {(p, k, 192, f): v for (p, k, f), v in _TRAFFIC_192.items()}
@@ -81,13 +80,14 @@ TRAFFIC.update({(p, k, 256, f): v * _SCALE_256 for (p, k, f), v in _TRAFFIC_192.
 
 def sweep_cost(prec: str, kind: str, cheb_k: int = 1, nx: int = 256, fixed: bool = False):
     """(bytes, flops) per cell of one launch of sweep `kind`, or None.  fixed: the fixed-point
-    method, whose stencil sweep has no search-direction history (reads z, coefficients; writes
-    d, q: 3T + 3B (+B), 7 FMA)."""
+    method, whose stencil sweep has no search-direction history and applies the update itself
+    (reads z, coefficients, rt, x; writes rt, x: 5T + 3B (+B); 6 FMA in At z, rt -= At z,
+    x += z, <rt, rt>: 16 flop)."""
     T, B, diag = SIZES[prec]
     Bd = B if diag else 0
     S = spectrum_bytes(nx)
-    if fixed and kind == "stencil":
-        return 3 * T + 3 * B + Bd, 14.0 + (2.0 if diag else 0.0)
+    if fixed and kind == "stencil":  # fused with the update: reads z, 3 coefficients, rt, x; writes rt, x
+        return 5 * T + 3 * B + Bd, 16.0 + (2.0 if diag else 0.0)
     if kind == "spec_x":
         return (3 * T + 8 + 2 * S) / 2, 0.0
     if kind in ("spec_y", "spec_z"):
@@ -490,7 +490,7 @@ def main():
     if fixed:  # per update: five spectral passes, stencil and update sweeps; FP64 residuals
         T = SIZES[args.precision][0]
         per = sum(c * sweep_cost(args.precision, k, nx=nx, fixed=True)[0]
-                  for k, c in (("spec_x", 2), ("spec_y", 2), ("spec_z", 1), ("stencil", 1), ("update", 1)))
+                  for k, c in (("spec_x", 2), ("spec_y", 2), ("spec_z", 1), ("stencil", 1)))
         b_solve = (iters * per + outer * (48 + T) + max(outer - 1, 0) * (24 + T) + 32) * ncell
 
     line = {

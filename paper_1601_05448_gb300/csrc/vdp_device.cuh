@@ -164,9 +164,11 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
     }
     case PH_STENCIL: {
       const double dq = S[0];
-      if (I.pc == PC_FIXED) {  // the paper's iteration: the full update, x += z, rt -= At z
-        st->alpha = 1.0;
-        st->phase = PH_UPDATE;
+      if (I.pc == PC_FIXED) {
+        // the paper's iteration: the stencil sweep has also applied the update x += z,
+        // rt -= At z and summed <rt, rt> (S[0]); continue as after an update sweep
+        phase = PH_UPDATE;
+        goto after_update;
       } else if (dq > 0.0 && isfinite(dq)) {
         st->alpha = (I.pc != PC_JACOBI ? st->rz : st->rr) / dq;
         st->phase = PH_UPDATE;
@@ -180,7 +182,8 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
       }
       break;
     }
-    case PH_UPDATE: {
+    case PH_UPDATE:
+    after_update: {
       const double rn = S[0];
       st->inner_iters += 1;
       st->iters += 1;

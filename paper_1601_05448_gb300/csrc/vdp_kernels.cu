@@ -596,8 +596,12 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
   const bool last = CHEB && cj == I.cheb_k - 1;
   T beta = (T)st->beta, scale = 1, c1 = 0, c2 = 0;
   // the paper's fixed-point iteration has no search-direction history (beta = 0) and needs
-  // neither <d, q> nor d itself (the update sweep reads z)
+  // neither d nor q: the sweep applies the update itself on the thread's own cells,
+  // x += z and rt -= At z, and sums <rt, rt> (one pass instead of a stencil and an update sweep)
   constexpr bool fixed = VAR == 2;
+  const bool first_inner = st->inner_iters == 0;
+  T* xv = static_cast<T*>(I.x);
+  T* rw = static_cast<T*>(I.r);
   constexpr bool use_old = VAR == 1 && !CHEB;
   constexpr bool form = use_old && !QREC;  // form d = src + beta d_old for every marched value
   const T* rt = static_cast<const T*>(I.r);
@@ -678,6 +682,16 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
       VecIO<T, V>::ld(q + oc, qo);  // q is rewritten below by this thread only
       LdgIO<T, V>::ld(dold + oc, dol);
     }
+    T ro[V], xo[V];  // fixed point: rt and x of the own cells (rewritten by this thread only)
+    if (fixed) {
+      VecIO<T, V>::ld(rw + oc, ro);
+      if (first_inner) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) xo[k] = 0;
+      } else {
+        VecIO<T, V>::ld(xv + oc, xo);
+      }
+    }
     const T bxr = (T)ldg1(sx + oc + dxr);
     // x neighbours of the first and last cell: adjacent lanes, or a load at row ends / warp ends
     T left = __shfl_up_sync(0xffffffffu, dc[V - 1], 1);
@@ -701,8 +715,16 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
       qv[k] = a;
       if (!CHEB && !QREC && !fixed) sum[k] = fma(dc[k], a, sum[k]);
     }
+    if (fixed) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        ro[k] -= qv[k];
+        xo[k] += dc[k];
+        sum[k] = fma(ro[k], ro[k], sum[k]);
+      }
+    }
     T dn[V];
-    if (QREC) {
+    if (QREC && !fixed) {
 #pragma unroll
       for (int k = 0; k < V; ++k) {
         dn[k] = use_old ? fma(beta, dol[k], dc[k]) : dc[k];
@@ -729,13 +751,14 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
         VecIO<T, V>::st(zout + oc, zn);
         if (!last) VecIO<T, V>::st(dch + oc, dn);
       }
+    } else if (active && fixed) {
+      VecIO<T, V>::st(rw + oc, ro);
+      VecIO<T, V>::st(xv + oc, xo);
     } else if (active) {
-      if (!fixed) {
-        if (QREC)
-          VecIO<T, V>::st(dnew + oc, dn);
-        else
-          VecIO<T, V>::st(dnew + oc, dc);
-      }
+      if (QREC)
+        VecIO<T, V>::st(dnew + oc, dn);
+      else
+        VecIO<T, V>::st(dnew + oc, dc);
       VecIO<T, V>::st(q + oc, qv);
     }
 #pragma unroll
