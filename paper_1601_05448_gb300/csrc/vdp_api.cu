@@ -288,6 +288,7 @@ void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a) {
   // rho D^1/2 gives rho r, and z = damping D^1/2 (-L_h)^-1 (rho r) is the scaled form of the
   // paper's update p += damping L_h^-1 (rho r) (applied as p -= D^-1/2 x, x the sum of the z)
   a->out = c->za;
+  a->out_f32 = fixed ? 1 : 0;  // the fixed-point sweep reads z as FP32
   a->omega_in = fixed ? c->rho_w : c->omega;
   a->omega_out = c->omega;
   a->spec = c->spec;
@@ -562,6 +563,7 @@ int vdp_inverse_laplacian(vdp_ctx* c, const double* g, double* out) {
   solve_spec_args(c, PREC_FP64, &a);
   a.in = g;
   a.out = out;
+  a.out_f32 = 0;
   a.omega_in = nullptr;
   a.omega_out = nullptr;
   a.scale = (float)(-1.0 / (double)c->n);  // L_h^-1 (negative definite), not (-L_h)^-1

@@ -7,6 +7,31 @@
 
 namespace vdp {
 
+// Conversions between binary64 and binary32 by repacking the IEEE 754 fields with integer
+// operations: on this GPU the conversion instructions run on the FP64 pipe (2 results per clock
+// per SM), which FP64 kernels otherwise spend a large share of their time in.
+//   to binary32: exponent rebiased (1023 -> 127), the 23 leading fraction bits kept (rounding
+//                toward zero), magnitudes below the binary32 normal range flushed to zero and
+//                above it (infinities, NaNs) sent to infinity -- adequate for a preconditioner
+//                input, which the FP32 transforms round anyway;
+//   to binary64: exact for every binary32 normal number and zero (subnormals flush to zero).
+__device__ __forceinline__ float narrow(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned bits = e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : (sign | ((unsigned)e << 23) | frac));
+  return __uint_as_float(bits);
+}
+__device__ __forceinline__ double widen(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xffu, frac = b & 0x7fffffu;
+  const unsigned hi = e == 0 ? sign : (sign | ((e + 1023u - 127u) << 20) | (frac >> 3));
+  const unsigned lo = e == 0 ? 0u : (frac << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

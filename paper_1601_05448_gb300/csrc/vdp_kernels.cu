@@ -606,6 +606,9 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
   constexpr bool form = use_old && !QREC;  // form d = src + beta d_old for every marched value
   const T* rt = static_cast<const T*>(I.r);
   const T* src = I.pc != PC_JACOBI ? static_cast<const T*>(I.za) : rt;
+  // the fixed-point iteration's z comes from the FP32 spectral passes and is stored as FP32
+  // (exactly representable: widening it loses nothing)
+  const float* srcf = static_cast<const float*>(I.za);
   const T* dold = static_cast<const T*>(st->parity ? I.d1 : I.d0);
   T* dnew = static_cast<T*>(st->parity ? I.d0 : I.d1);
   T* q = static_cast<T*>(I.q);
@@ -641,7 +644,16 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
   };
   // all loads of a plane are issued together (non-coherent read-only path), then used
   auto dvec = [&](long long o, T (&d)[V]) {  // marched field, V cells at offset o
-    LdgIO<T, V>::ld(src + o, d);
+    if constexpr (fixed && IsF64<T>::value) {
+#pragma unroll
+      for (int k = 0; k < V; k += 2) {
+        const float2 t = __ldg(reinterpret_cast<const float2*>(srcf + o + k));
+        d[k] = widen(t.x);
+        d[k + 1] = widen(t.y);
+      }
+    } else {
+      LdgIO<T, V>::ld(src + o, d);
+    }
     if (CHEB) {
 #pragma unroll
       for (int k = 0; k < V; ++k) d[k] *= scale;
@@ -653,6 +665,7 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
     }
   };
   auto d1 = [&](long long o) -> T {
+    if constexpr (fixed && IsF64<T>::value) return widen(__ldg(srcf + o));
     if (CHEB) return __ldg(src + o) * scale;
     return form ? fma(beta, __ldg(dold + o), __ldg(src + o)) : __ldg(src + o);
   };
@@ -885,10 +898,50 @@ __device__ __forceinline__ void res64_march(const InstDesc& I, const InstState* 
   acc[3] = a3;
 }
 
+// The first residual of a solve started from p = 0 is r = f - <f>: no stencil, no p reads.
+template <class T>
+__device__ void res64_zero_p(const InstDesc& I, const InstState* st, int unit,
+                             double (&acc)[kSlots]) {
+  constexpr int VR = VecW<T>::V;
+  const int nx = I.nx, ny = I.ny, nz = I.nz;
+  const int tpr = nx / VR;
+  const int tile = unit % I.uy, chunk = unit / I.uy;
+  const int row = threadIdx.x / tpr;
+  const int x0 = (threadIdx.x - row * tpr) * VR;
+  const int yr = tile * I.ty + row;
+  const int z0 = (int)((long long)chunk * nz / I.zc), z1 = (int)((long long)(chunk + 1) * nz / I.zc);
+  const double mu = st->mu_f;
+  T* rt = static_cast<T*>(I.r);
+  double a0 = 0;
+  T a1 = 0;
+  if (row < I.ty && yr < ny) {
+    for (int z = z0; z < z1; ++z) {
+      const long long o = ((long long)z * ny + yr) * nx + x0;
+#pragma unroll
+      for (int h = 0; h < VR; h += 2) {
+        const double2 f = *reinterpret_cast<const double2*>(I.rhs + o + h);
+        const double2 si = *reinterpret_cast<const double2*>(I.sinv + o + h);
+        const double f0 = f.x - mu, f1 = f.y - mu;
+        const T t0 = from_double_rn<T>(si.x * f0), t1 = from_double_rn<T>(si.y * f1);
+        rt[o + h] = t0;
+        rt[o + h + 1] = t1;
+        a0 = fma(f0, f0, fma(f1, f1, a0));
+        a1 = fma(t0, t0, fma(t1, t1, a1));
+      }
+    }
+  }
+  acc[0] = a0;          // ||r||^2
+  acc[1] = (double)a1;  // ||rt||^2
+  acc[2] = 0.0;         // sum of p
+  acc[3] = a0;          // ||f - <f>||^2 (this is the first residual)
+}
+
 template <class T>
 __device__ void sweep_res64_direct(const InstDesc& I, const InstState* st, int unit,
                                    double (&acc)[kSlots]) {
-  if (st->first_res != 0)
+  if (st->first_res != 0 && !st->use_guess)
+    res64_zero_p<T>(I, st, unit, acc);
+  else if (st->first_res != 0)
     res64_march<T, true>(I, st, unit, acc);
   else
     res64_march<T, false>(I, st, unit, acc);

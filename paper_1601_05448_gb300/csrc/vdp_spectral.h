@@ -16,7 +16,8 @@ enum SpecPass : int { SPEC_X_FWD = 0, SPEC_Y_FWD = 1, SPEC_Z = 2, SPEC_Y_INV = 3
 // Arguments of every spectral pass (by value).
 struct SpecArgs {
   const void* in;        // X+: nx*ny*nz values of the inner type (FP64 or FP32)
-  void* out;             // X-: output, same type and layout
+  void* out;             // X-: output, same layout; the inner type, or FP32 with out_f32
+  int out_f32;           // X-: store FP32 (the fixed-point iteration's z)
   const float* omega_in;   // per-cell weight applied before X+ (or null: 1)
   const float* omega_out;  // per-cell weight applied after X- (or null: 1)
   float2* spec;          // half spectrum [nz][ny][nxp]
