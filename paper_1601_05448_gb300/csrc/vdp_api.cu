@@ -104,8 +104,9 @@ void free_ctx(vdp_ctx* c) {
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->wexec) cudaGraphExecDestroy(c->wexec);
   void* bufs[] = {c->bx, c->by, c->bz, c->sinv, c->sx, c->sy, c->sz, c->sd, c->x, c->r, c->d0, c->d1,
-                  c->za, c->zb, c->dch, c->spec, c->omega, c->sptab, c->rho_w,
+                  c->za, c->zb, c->dch, c->spec, c->omega, c->sptab, c->rho_w, c->d_rounds,
                   c->q, c->part, c->ticket, c->st, c->desc, c->units, c->flag, c->stage_a,
                   c->stage_b};
   for (void* b : bufs)
@@ -188,6 +189,10 @@ int configure_layout(vdp_ctx* c, int prec) {
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
   }
+  if (c->wexec) {
+    cudaGraphExecDestroy(c->wexec);
+    c->wexec = nullptr;
+  }
   c->layout_prec = prec;
   c->layout_dirty = false;
   return VDP_OK;
@@ -196,6 +201,26 @@ int configure_layout(vdp_ctx* c, int prec) {
 int steps_per_sync(const vdp_ctx* c) {
   if (c->opts.steps_per_sync > 0) return c->opts.steps_per_sync;
   return 16;
+}
+
+// One round of the solve's launch schedule: residual kernel (direct form), the five spectral
+// passes (spectral preconditioner or fixed-point iteration), stencil kernel, flat kernel; each
+// returns at once unless the instance's phase is its own.
+cudaError_t launch_round(vdp_ctx* c, int prec, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (c->lay.mode == 0)  // the residual sweep has its own kernel in the direct mode
+    e = launch_res64(prec, c->desc, c->units, c->lay.nunits, c->lay.threads, s);
+  if (e == cudaSuccess && c->hdesc.pc >= PC_SPECTRAL) {  // z = M^-1 rt before the stencil sweep
+    SpecArgs a;
+    solve_spec_args(c, prec, &a);
+    for (int pass = 0; pass < SPEC_PASSES && e == cudaSuccess; ++pass)
+      e = launch_spectral_pass(prec, pass, a, s);
+  }
+  if (e == cudaSuccess)
+    e = launch_stencil(prec, c->lay.mode, stencil_kind(c->hdesc.pc), c->desc, c->units,
+                       c->lay.nunits, c->lay.threads, c->lay.smem, s);
+  if (e == cudaSuccess) e = launch_flat(prec, c->desc, c->units + c->lay.nunits, c->lay.nunits_f, s);
+  return e;
 }
 
 int ensure_graph(vdp_ctx* c, int prec) {
@@ -208,21 +233,7 @@ int ensure_graph(vdp_ctx* c, int prec) {
   cudaGraph_t g = nullptr;
   VDP_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
   for (int i = 0; i < m; ++i) {
-    cudaError_t e = cudaSuccess;
-    if (c->lay.mode == 0)  // the residual sweep has its own kernel in the direct mode
-      e = launch_res64(prec, c->desc, c->units, c->lay.nunits, c->lay.threads, c->cap);
-    if (e == cudaSuccess && c->hdesc.pc >= PC_SPECTRAL) {  // z = M^-1 rt before the stencil sweep
-      SpecArgs a;
-      solve_spec_args(c, prec, &a);
-      for (int pass = 0; pass < SPEC_PASSES && e == cudaSuccess; ++pass)
-        e = launch_spectral_pass(prec, pass, a, c->cap);
-    }
-    if (e == cudaSuccess)
-      e = launch_stencil(prec, c->lay.mode, stencil_kind(c->hdesc.pc), c->desc, c->units,
-                         c->lay.nunits, c->lay.threads,
-                         c->lay.smem, c->cap);
-    if (e == cudaSuccess)
-      e = launch_flat(prec, c->desc, c->units + c->lay.nunits, c->lay.nunits_f, c->cap);
+    cudaError_t e = launch_round(c, prec, c->cap);
     if (e != cudaSuccess) {
       cudaGraph_t junk;
       cudaStreamEndCapture(c->cap, &junk);
@@ -237,6 +248,67 @@ int ensure_graph(vdp_ctx* c, int prec) {
   c->g_prec = prec;
   c->g_steps = m;
   return VDP_OK;
+}
+
+// The device-side loop: a graph whose WHILE node repeats kWhileRounds rounds and a condition
+// kernel until the instance is done (or a round bound is reached), so a whole solve is one
+// graph launch -- no host polling between rounds and at most kWhileRounds - 1 idle rounds at
+// the end.  Returns false (and remembers it) if the driver cannot build such a graph; the
+// solve then uses the polling schedule.
+constexpr int kWhileRounds = 2;
+
+bool ensure_while_graph(vdp_ctx* c, int prec) {
+  if (c->w_failed) return false;
+  if (c->wexec && c->w_prec == prec) return true;
+  if (c->wexec) {
+    cudaGraphExecDestroy(c->wexec);
+    c->wexec = nullptr;
+  }
+  if (!c->d_rounds && cudaMalloc((void**)&c->d_rounds, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_rounds = nullptr;
+    c->w_failed = true;
+    return false;
+  }
+  const int k = c->opts.precond == VDP_PRECOND_CHEB ? std::max(1, c->opts.cheb_degree) : 1;
+  const long long bound = (2LL * (k + 1) * c->opts.max_iter + 4096) / kWhileRounds + 1;
+  const unsigned max_loops = (unsigned)std::min<long long>(bound, 0x7fffffffLL);
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+  cudaGraphConditionalHandle h = 0;
+  ok = ok && cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  ok = ok && cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+  if (ok) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      cudaError_t e = cudaSuccess;
+      for (int i = 0; i < kWhileRounds && e == cudaSuccess; ++i) e = launch_round(c, prec, c->cap);
+      if (e == cudaSuccess) e = launch_continue(c->st, h, c->d_rounds, max_loops, c->cap);
+      cudaGraph_t out = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(c->cap, &out);
+      ok = e == cudaSuccess && e2 == cudaSuccess;
+    }
+  }
+  ok = ok && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();  // clear the error: this schedule is optional
+    if (exec) cudaGraphExecDestroy(exec);
+    c->w_failed = true;
+    return false;
+  }
+  c->wexec = exec;
+  c->w_prec = prec;
+  return true;
 }
 
 int ensure_scaled(vdp_ctx* c, int prec) {
@@ -488,7 +560,8 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   if ((s = ensure_scaled(c, prec)) != VDP_OK) return s;
   if ((c->layout_dirty || c->layout_prec != prec) && (s = configure_layout(c, prec)) != VDP_OK)
     return s;
-  if ((s = ensure_graph(c, prec)) != VDP_OK) return s;
+  const bool dev_loop = ensure_while_graph(c, prec);
+  if (!dev_loop && (s = ensure_graph(c, prec)) != VDP_OK) return s;
   if ((s = prepare_spectral_solve(c)) != VDP_OK) return s;
   const double* drhs = rhs;
   double* dp = p;
@@ -506,6 +579,31 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   VDP_CK(cudaEventRecord(c->ev0, c->stream));
   VDP_CK(launch_init(c->desc, drhs, dp, tol, c->opts.inner_tol, c->opts.max_iter,
                      c->opts.max_iter, c->opts.use_guess ? 1 : 0, prec, c->stream));
+  const int per_round = (c->lay.mode == 0 ? 3 : 2) + (c->hdesc.pc >= PC_SPECTRAL ? SPEC_PASSES : 0);
+  if (dev_loop) {  // the whole solve is one graph launch; the device decides when to stop
+    VDP_CK(cudaMemsetAsync(c->d_rounds, 0, sizeof(unsigned), c->stream));
+    VDP_CK(cudaGraphLaunch(c->wexec, c->stream));
+    VDP_CK(cudaMemcpyAsync(&c->hstate[0], c->st, sizeof(InstState), cudaMemcpyDeviceToHost,
+                           c->stream));
+    VDP_CK(cudaEventRecord(c->ev1, c->stream));
+    if (host_p) VDP_CK(cudaMemcpyAsync(p, dp, bytes, cudaMemcpyDeviceToHost, c->stream));
+    VDP_CK(cudaStreamSynchronize(c->stream));
+    unsigned loops = 0;
+    VDP_CK(cudaMemcpy(&loops, c->d_rounds, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    const InstState& hs = c->hstate[0];
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    c->stats.status = hs.phase >= PH_DONE ? hs.status : VDP_ETIMEOUT;
+    c->stats.iters = hs.iters;
+    c->stats.outer_iters = hs.outer;
+    c->stats.rel_res = hs.rel_res;
+    c->stats.rhs_mean = hs.mu_f;
+    c->stats.ms = ms;
+    c->stats.sweeps = hs.sweeps;
+    c->stats.launches = (int)(1 + (long long)loops * (per_round * kWhileRounds + 1));
+    return c->stats.status;
+  }
+  // Polling schedule: graphs of m rounds, two in flight, the host checks the state after each.
   // Upper bound on launch pairs: one per inner iteration plus the outer phases; the state
   // machine itself stops at max_iter, this only guards the host loop.
   const long long max_pairs = 2LL * c->opts.max_iter + 4096;
@@ -542,7 +640,6 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   c->stats.rhs_mean = hs.mu_f;
   c->stats.ms = ms;
   c->stats.sweeps = hs.sweeps;
-  const int per_round = (c->lay.mode == 0 ? 3 : 2) + (c->hdesc.pc >= PC_SPECTRAL ? SPEC_PASSES : 0);
   c->stats.launches = (int)(1 + issued * per_round * m);
   return c->stats.status;
 }

@@ -65,6 +65,11 @@ struct vdp_ctx {
   // graph cache
   cudaGraphExec_t gexec = nullptr;
   int g_prec = -1, g_steps = 0;
+  // device-side loop: one graph per solve whose WHILE node repeats the rounds until done
+  cudaGraphExec_t wexec = nullptr;
+  int w_prec = -1;
+  bool w_failed = false;           // the driver cannot build it: use the polling schedule
+  unsigned* d_rounds = nullptr;
   vdp_stats stats{};
 };
 

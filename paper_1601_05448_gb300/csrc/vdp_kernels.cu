@@ -1495,6 +1495,24 @@ cudaError_t launch_persistent(int prec, const InstDesc* desc, const UnitRef* sun
   return cudaLaunchKernelExC(&cfg, persistent_fn(prec), args);
 }
 
+// The body of a solve's device-side loop ends with this kernel: it keeps the loop going while
+// the solve is unfinished and the round count is below its bound.
+__global__ void k_continue(const InstState* st, cudaGraphConditionalHandle handle, unsigned* rounds,
+                           unsigned max_rounds) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const unsigned r = *rounds + 1u;
+    *rounds = r;
+    const bool more = __ldcg(&st->phase) < PH_DONE && r < max_rounds;
+    cudaGraphSetConditional(handle, more ? 1u : 0u);
+  }
+}
+
+cudaError_t launch_continue(const InstState* st, cudaGraphConditionalHandle handle,
+                            unsigned* rounds, unsigned max_rounds, cudaStream_t s) {
+  k_continue<<<1, 32, 0, s>>>(st, handle, rounds, max_rounds);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const InstDesc* desc, int n, InstState* out, cudaStream_t s) {
   k_gather_states<<<(n + 127) / 128, 128, 0, s>>>(desc, n, out);
   return cudaGetLastError();

@@ -37,5 +37,9 @@ cudaError_t launch_persistent(int prec, const InstDesc* desc, const UnitRef* sun
                               const UnitRef* funits, int nf, int pairs, BatchCtl* ctl, int grid,
                               cudaStream_t s);
 cudaError_t launch_gather(const InstDesc* desc, int n, InstState* out, cudaStream_t s);
+// device-side solve loop: sets the WHILE condition `handle` to continue while the instance is
+// unfinished and fewer than max_rounds loop iterations have run (*rounds counts them)
+cudaError_t launch_continue(const InstState* st, cudaGraphConditionalHandle handle,
+                            unsigned* rounds, unsigned max_rounds, cudaStream_t s);
 
 }  // namespace vdp
