@@ -678,6 +678,7 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
   T sum[V];
 #pragma unroll
   for (int k = 0; k < V; ++k) sum[k] = 0;
+  float sumf = 0.f;  // FP64 fixed-point sweep: <rt, rt> in FP32
   for (int z = z0; z < z1; ++z) {
     const long long oc = zoff(z), op = zoff(z + 1);
     T du[V], dd[V], bx[V], by[V], byd[V], bz[V], bzp[V], bd[V];
@@ -733,7 +734,12 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
       for (int k = 0; k < V; ++k) {
         ro[k] -= qv[k];
         xo[k] += dc[k];
-        sum[k] = fma(ro[k], ro[k], sum[k]);
+        if constexpr (IsF64<T>::value) {  // <rt, rt> only steers the inner stop: FP32 suffices,
+          const float rf = narrow(ro[k]);   // and keeps the FP64 pipe to the update itself
+          sumf = fmaf(rf, rf, sumf);
+        } else {
+          sum[k] = fma(ro[k], ro[k], sum[k]);
+        }
       }
     }
     T dn[V];
@@ -783,10 +789,12 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
   if (!active) {
 #pragma unroll
     for (int k = 0; k < V; ++k) sum[k] = 0;
+    sumf = 0.f;
   }
   T tot = 0;
 #pragma unroll
   for (int k = 0; k < V; ++k) tot += sum[k];
+  if (fixed && IsF64<T>::value) tot = (T)sumf;
   part = tot;
 }
 
