@@ -106,7 +106,9 @@ typedef struct {
   int units;           /* work units (thread blocks) per sweep (0 = automatic) */
   int stages;          /* shared-memory pipeline stages of the stencil sweep, 4..8 (0 = auto) */
   int threads;         /* threads per stencil work unit, 128..512, multiple of 32 (0 = auto) */
-  int steps_per_sync;  /* (stencil, flat) launch pairs per host convergence check (0 = auto) */
+  int steps_per_sync;  /* 0 (default): each solve is one graph launch whose device-side loop
+                          stops when the solve is done; > 0: replay graphs of that many rounds
+                          with a host check of the state after each (same results) */
   int method;          /* vdp_method (default VDP_METHOD_CG) */
   double damping;      /* VDP_METHOD_FIXED_POINT: scale of each update, 0 < damping <= 2
                           (default 1, the paper's update) */

@@ -2,10 +2,11 @@
 //
 // A solve is one instance of the per-instance state machine (vdp_internal.cuh, transitions in
 // vdp_device.cuh), advanced by the sweep kernels of vdp_kernels.cu and vdp_spectral.cu.  The
-// driver launches a captured CUDA graph of `steps_per_sync` rounds -- residual, (five spectral
-// passes,) stencil and flat kernels, each returning at once unless the phase is its own --
-// copies the instance's state to pinned host memory after each graph, and keeps two graphs in
-// flight so that the convergence check on the host overlaps with device work.
+// driver launches one graph per solve whose WHILE node repeats rounds -- residual, (five
+// spectral passes,) stencil and flat kernels, each returning at once unless the phase is its
+// own -- until a condition kernel sees the solve done.  With steps_per_sync > 0 (or a driver
+// without conditional nodes) it instead replays graphs of that many rounds, copies the state to
+// pinned host memory after each, and keeps two in flight so the host check overlaps device work.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -560,7 +561,7 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   if ((s = ensure_scaled(c, prec)) != VDP_OK) return s;
   if ((c->layout_dirty || c->layout_prec != prec) && (s = configure_layout(c, prec)) != VDP_OK)
     return s;
-  const bool dev_loop = ensure_while_graph(c, prec);
+  const bool dev_loop = c->opts.steps_per_sync == 0 && ensure_while_graph(c, prec);
   if (!dev_loop && (s = ensure_graph(c, prec)) != VDP_OK) return s;
   if ((s = prepare_spectral_solve(c)) != VDP_OK) return s;
   const double* drhs = rhs;

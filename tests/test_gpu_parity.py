@@ -401,3 +401,15 @@ def test_fixed_point_on_hot_spots_and_its_limits():
         vdp.Solver(40, 32, 32, 1.0, method=vdp.VDP_METHOD_FIXED_POINT)
     with pytest.raises(vdp.VdpError):
         vdp.Solver(32, 32, 32, 1.0, method=vdp.VDP_METHOD_FIXED_POINT, damping=2.5)
+
+
+@pytest.mark.parametrize("opts", [{}, {"precond": vdp.VDP_PRECOND_SPECTRAL}, {"method": vdp.VDP_METHOD_FIXED_POINT}])
+def test_device_loop_equals_polling_schedule(opts):
+    """The device-side solve loop (one graph launch per solve) and the host-polled schedule run
+    the same kernels in the same order: bitwise the same pressure and iteration counts."""
+    prob = V.smooth_problem((32, 48, 64), seed=67)
+    p_dev, st_dev = gpu_solve(prob, "mixed", tol=1e-9, **opts)
+    p_host, st_host = gpu_solve(prob, "mixed", tol=1e-9, steps_per_sync=16, **opts)
+    print(f"device loop {st_dev.launches} launches, polling {st_host.launches}")
+    assert np.array_equal(p_dev, p_host)
+    assert (st_dev.iters, st_dev.outer_iters, st_dev.sweeps) == (st_host.iters, st_host.outer_iters, st_host.sweeps)
