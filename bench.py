@@ -393,6 +393,10 @@ def main():
                     help="precision of the main workload (fp64 = the benchmark)")
     ap.add_argument("--precond", default="spectral", choices=list(PRECONDS),
                     help="preconditioner of the main workload's CG (spectral = the benchmark)")
+    ap.add_argument("--steps-per-sync", type=int, default=0,
+                    help="0: each solve is one graph launch with a device-side loop (the benchmark); N > 0: "
+                         "graphs of N rounds polled by the host (kernels visible to ncu, which cannot profile "
+                         "kernels inside conditional graph nodes)")
     ap.add_argument("--method", default="fixed_point", choices=["cg", "fixed_point"],
                     help="fixed_point: the paper's iteration (the benchmark); cg: preconditioned conjugate "
                          "gradients (--precond)")
@@ -447,6 +451,7 @@ def main():
         popts["cheb_degree"] = 3
     if args.method == "fixed_point":
         popts = {"method": vdp.VDP_METHOD_FIXED_POINT}
+    popts["steps_per_sync"] = args.steps_per_sync
     solver = vdp.Solver(nx, ny, nz, prob.L, precision=args.precision, stream=stream, **popts)
     solver.set_density(rho)
 
