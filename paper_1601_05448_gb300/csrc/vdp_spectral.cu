@@ -255,15 +255,14 @@ template <class T, int M1, int M2>
 __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
     k_spec_x_inv(SpecArgs a) {
   constexpr int m = M1 * M2, RY = rows_per_block<M1, M2>();
-  constexpr int SA = pad_stride(m + 1), SB = pad_stride(M2 * (M1 + 1));
-  __shared__ float2 sa[RY * SA], sb[RY * SB];
+  constexpr int SB = pad_stride(M2 * (M1 + 1));
+  __shared__ float2 sb[RY * SB];
   if (!spec_active(a)) return;
   const Tables tb = tables(a);
   const int t = threadIdx.x % M1, r = threadIdx.x / M1;
   const long long rows = (long long)a.ny * a.nz;
   const long long row = (long long)blockIdx.x * RY + r;
   const bool live = row < rows;
-  float2* ra = sa + r * SA;
   float2* rb = sb + r * SB;
   // the output weights of this thread's cells are loaded first, so that their latency overlaps
   // the transforms (cells 2l, 2l + 1 with l = k2 + M2 k1, k2 = t, t + M1, ...)
@@ -278,18 +277,23 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
       wv[rr][k1] = make_float2(1.f, 1.f);
       if (live && om && k2 < M2) wv[rr][k1] = *reinterpret_cast<const float2*>(om + 2 * (k2 + M2 * k1));
     }
+  // Z'[k] = (X[k] + conj X[m-k]) + i conj(W_nx^k) (X[k] - conj X[m-k]); inverse M2-point DFTs.
+  // Both X[k] and X[m-k] are read straight from the spectrum (in L2 after the Y- pass): for a
+  // fixed j2 the lanes of a row read consecutive values, ascending and descending.
   if (live) {
     const float2* src = a.spec + row * a.nxp;
-    for (int k = t; k <= m; k += M1) ra[k] = src[k];
-  }
-  __syncthreads();
-  // Z'[k] = (X[k] + conj X[m-k]) + i conj(W_nx^k) (X[k] - conj X[m-k]); inverse M2-point DFTs
-  if (live) {
+    float2 xa[M2], xb[M2];
+#pragma unroll
+    for (int j2 = 0; j2 < M2; ++j2) {
+      const int k = t + M1 * j2;
+      xa[j2] = src[k];
+      xb[j2] = src[m - k];
+    }
     float2 v[M2], y[M2];
 #pragma unroll
     for (int j2 = 0; j2 < M2; ++j2) {
       const int k = t + M1 * j2;
-      const float2 p = ra[k], q = cconj(ra[m - k]);
+      const float2 p = xa[j2], q = cconj(xb[j2]);
       const float2 e = cadd(p, q);
       const float2 o = cmulc(csub(p, q), tb.wr[k]);
       v[j2] = make_float2(e.x - o.y, e.y + o.x);
