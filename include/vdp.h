@@ -266,6 +266,21 @@ int vdp_batch_remove(vdp_batch *batch, vdp_ctx *ctx);
 /* Number of members (finished ones included until removed). */
 int vdp_batch_size(const vdp_batch *batch);
 
+/*
+ * Bound on each grid-barrier wait of the persistent kernel, in seconds (0 < seconds <= 60;
+ * default 2).  A wait that expires (a lost arrival) ends the run with VDP_ETIMEOUT instead of
+ * hanging; the members stay usable and the next vdp_batch_run continues them.
+ */
+int vdp_batch_set_wait_limit(vdp_batch *batch, double seconds);
+
+/*
+ * Failure injection for testing that path (no counterpart in the paper): the next run of a
+ * persistent batch waits at its first grid barrier for one block more than it launches, so the
+ * wait expires after the limit and the run returns VDP_ETIMEOUT.  Nothing faults or hangs.
+ * VDP_EINVAL for a batch of ordinary launches.
+ */
+int vdp_batch_inject_lost_arrival(vdp_batch *batch);
+
 /* ------------------------------------------------------------------------------------------ */
 /* A solve that allocates no device memory.                                                    */
 /* ------------------------------------------------------------------------------------------ */

@@ -104,6 +104,8 @@ _SIGS = {
     "vdp_batch_done": (ctypes.c_int, [_P, _P]),
     "vdp_batch_remove": (ctypes.c_int, [_P, _P]),
     "vdp_batch_size": (ctypes.c_int, [_P]),
+    "vdp_batch_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_double]),
+    "vdp_batch_inject_lost_arrival": (ctypes.c_int, [_P]),
     "vdp_solve_timed": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.POINTER(vdp_sweep_times)]),
     "vdp_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                          ctypes.c_double, ctypes.c_int, _P, ctypes.POINTER(vdp_stats)]),
@@ -254,6 +256,14 @@ def vdp_batch_remove(batch: int, ctx: int) -> int:
 
 def vdp_batch_size(batch: int) -> int:
     return load().vdp_batch_size(batch)
+
+
+def vdp_batch_set_wait_limit(batch: int, seconds: float) -> int:
+    return load().vdp_batch_set_wait_limit(batch, float(seconds))
+
+
+def vdp_batch_inject_lost_arrival(batch: int) -> int:
+    return load().vdp_batch_inject_lost_arrival(batch)
 
 
 def _stream(stream):
@@ -449,6 +459,20 @@ class Batch:
 
     def __len__(self):
         return vdp_batch_size(self.handle)
+
+    def set_wait_limit(self, seconds: float) -> None:
+        """Bound on each grid-barrier wait of the persistent kernel (an expired wait raises
+        VdpError(VDP_ETIMEOUT) from run(); the members stay usable)."""
+        st = vdp_batch_set_wait_limit(self.handle, seconds)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_batch_set_wait_limit")
+
+    def inject_lost_arrival(self) -> None:
+        """Failure injection for tests: the next persistent run waits for a block that never
+        arrives, so its bounded grid-barrier wait expires."""
+        st = vdp_batch_inject_lost_arrival(self.handle)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_batch_inject_lost_arrival")
 
     def run_to_completion(self, max_pairs: int = 64, max_runs: int = 100000) -> None:
         for _ in range(max_runs):

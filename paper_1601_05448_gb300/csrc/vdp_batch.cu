@@ -57,6 +57,9 @@ struct vdp_batch {
   cudaGraphExec_t gexec = nullptr;
   int g_pairs = 0;
   int grid = 0;
+  double wait_limit_s = 2.0;  // bound on each grid barrier wait of the persistent kernel
+  bool inject = false;        // next persistent run: one arrival more than the grid (tests)
+  bool ctl_stale = false;     // the control words must be reset before the next run
   // graph branches for the members' spectral passes (captured from these streams)
   static constexpr int kBranches = 4;
   cudaStream_t aux[kBranches] = {};
@@ -128,7 +131,9 @@ int rebuild(vdp_batch* b) {
   }
   BatchCtl ctl{};
   ctl.remaining = n;
+  ctl.limit_ns = (unsigned long long)(b->wait_limit_s * 1e9);
   *b->h_ctl = ctl;
+  b->ctl_stale = false;
   VDP_CK(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, b->stream));
   VDP_CK(cudaStreamSynchronize(b->stream));
   drop_graph(b);
@@ -296,6 +301,16 @@ int vdp_batch_run(vdp_batch* b, int max_pairs, int* active_out) {
   if (!b->gexec || b->g_pairs != max_pairs) {
     if ((s = capture(b, max_pairs)) != VDP_OK) return s;
   }
+  if (b->ctl_stale || b->inject) {  // fresh barrier words (after an expired wait, or to inject)
+    BatchCtl ctl{};
+    ctl.remaining = n;
+    ctl.limit_ns = (unsigned long long)(b->wait_limit_s * 1e9);
+    ctl.extra = b->inject ? 1u : 0u;
+    *b->h_ctl = ctl;
+    VDP_CK(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, b->stream));
+    b->ctl_stale = b->inject;  // an injected run leaves words to reset
+    b->inject = false;
+  }
   VDP_CK(cudaGraphLaunch(b->gexec, b->stream));
   VDP_CK(launch_gather(b->d_desc, n, b->d_states, b->stream));
   VDP_CK(cudaMemcpyAsync(b->h_states, b->d_states, sizeof(InstState) * n, cudaMemcpyDeviceToHost,
@@ -323,7 +338,23 @@ int vdp_batch_run(vdp_batch* b, int max_pairs, int* active_out) {
     }
   }
   if (active_out) *active_out = remaining;
-  if (b->h_ctl->fault) return VDP_ETIMEOUT;
+  if (b->h_ctl->fault) {
+    b->ctl_stale = true;  // the members stay usable: their last completed sweeps are consistent
+    return VDP_ETIMEOUT;
+  }
+  return VDP_OK;
+}
+
+int vdp_batch_set_wait_limit(vdp_batch* b, double seconds) {
+  if (!b || !(seconds > 0.0) || !(seconds <= 60.0)) return VDP_EINVAL;
+  b->wait_limit_s = seconds;
+  b->ctl_stale = true;
+  return VDP_OK;
+}
+
+int vdp_batch_inject_lost_arrival(vdp_batch* b) {
+  if (!b || !b->persistent) return VDP_EINVAL;
+  b->inject = true;
   return VDP_OK;
 }
 

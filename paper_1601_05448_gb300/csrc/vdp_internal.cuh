@@ -127,6 +127,9 @@ struct BatchCtl {
   unsigned int gen;    // grid barrier generation
   int remaining;       // unfinished instances
   int fault;           // a grid barrier wait expired
+  unsigned int extra;  // arrivals expected beyond the grid (failure injection for tests; 0)
+  unsigned int pad;
+  unsigned long long limit_ns;  // bound on one grid barrier wait
 };
 
 struct UnitRef {

@@ -1149,8 +1149,8 @@ __global__ void __launch_bounds__(kFlatThreads, 4) k_flat(const InstDesc* __rest
 }
 
 // Grid-wide barrier of the persistent kernel (all CTAs co-resident: cooperative launch).  Bounded:
-// after ~2 s it gives up, sets the fault word and returns false, so a lost arrival ends the
-// launch with an error status instead of a hang.
+// after the batch's wait limit (2 s by default) it gives up, sets the fault word and returns
+// false, so a lost arrival ends the launch with an error status instead of a hang.
 __device__ bool grid_sync(BatchCtl* ctl) {
   __shared__ int ok;
   __syncthreads();
@@ -1159,15 +1159,16 @@ __device__ bool grid_sync(BatchCtl* ctl) {
     const unsigned int gen = *vgen;
     __threadfence();
     const unsigned int arrived = atomicAdd(&ctl->count, 1u) + 1u;
+    const unsigned long long limit = ctl->limit_ns;
     ok = 1;
-    if (arrived == gridDim.x) {
+    if (arrived == gridDim.x + ctl->extra) {
       ctl->count = 0u;
       __threadfence();
       atomicAdd(&ctl->gen, 1u);
     } else {
       const uint64_t t0 = global_ns();
       while (*vgen == gen) {
-        if (global_ns() - t0 > 2000000000ull) {
+        if (global_ns() - t0 > limit) {
           atomicExch(&ctl->fault, 1);
           ok = 0;
           break;

@@ -19,16 +19,17 @@ identical results), so serving changes latency and throughput, never answers.
 from __future__ import annotations
 
 import collections
+import threading
 import time
 from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import PRECISIONS, VDP_METHOD_FIXED_POINT, VDP_PRECOND_JACOBI, VDP_PRECOND_SPECTRAL, Batch, Solver, \
-    VdpError, \
-    spectral_extra_bytes, spectral_supported
+from . import PRECISIONS, VDP_ENOMEM, VDP_METHOD_FIXED_POINT, VDP_PRECOND_JACOBI, VDP_PRECOND_SPECTRAL, Batch, \
+    Solver, VdpError, spectral_extra_bytes, spectral_supported
 
 BYTES_PER_CELL = 96 + 2  # device memory of one context per cell (FP64-sized buffers + BF16 diag)
+CANCELLED = -2           # ServeRequest.status of a request cancelled before it finished
 
 
 @dataclass
@@ -59,6 +60,8 @@ class ServeRequest:
 @dataclass
 class ServeStats:
     completed: int = 0
+    rejected: int = 0         # larger than the whole HBM budget (status VDP_ENOMEM)
+    cancelled: int = 0
     elapsed_s: float = 0.0
     latencies_s: list = field(default_factory=list)
     queue_s: list = field(default_factory=list)
@@ -69,7 +72,8 @@ class ServeStats:
     def summary(self) -> dict:
         lat = np.array(self.latencies_s) if self.latencies_s else np.array([np.nan])
         q = np.array(self.queue_s) if self.queue_s else np.array([np.nan])
-        return {"completed": self.completed, "elapsed_s": self.elapsed_s,
+        return {"completed": self.completed, "rejected": self.rejected, "cancelled": self.cancelled,
+                "elapsed_s": self.elapsed_s,
                 "solves_per_s": self.completed / self.elapsed_s if self.elapsed_s > 0 else None,
                 "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                 "mean_queue_s": float(np.mean(q)), "peak_context_bytes": self.peak_bytes,
@@ -102,6 +106,8 @@ class Server:
         self.device = torch.device(device)
         self.batch = Batch(precision, persistent=persistent)
         self.idle = collections.OrderedDict()   # ctx id -> (Solver, shape) available for reuse
+        self._cancel = set()                     # request ids to cancel (any thread)
+        self._cancel_lock = threading.Lock()
         self.bytes_in_use = 0                    # contexts alive (idle or busy)
         self.stats = ServeStats()
 
@@ -149,6 +155,18 @@ class Server:
     def _release(self, s, shape):
         self.idle[id(s)] = (s, shape)
 
+    def cancel(self, rid: int) -> None:
+        """Cancel request `rid` (safe from another thread or an on_done callback): a waiting
+        request is dropped, a running one leaves the batch at the next step; its status
+        becomes CANCELLED."""
+        with self._cancel_lock:
+            self._cancel.add(rid)
+
+    def _take_cancels(self):
+        with self._cancel_lock:
+            c, self._cancel = self._cancel, set()
+        return c
+
     # ---- the loop ---------------------------------------------------------------------------
 
     def run(self, requests, time_scale: float = 1.0, on_done=None) -> ServeStats:
@@ -160,10 +178,29 @@ class Server:
         active = {}   # ctx id -> (req, solver)
         t0 = time.perf_counter()
         now = lambda: (time.perf_counter() - t0) / time_scale
+        cancelled = set()
         while pending or waiting or active:
             t = now()
             while pending and pending[0].arrival_s <= t:
                 waiting.append(pending.popleft())
+            cancelled |= self._take_cancels()
+            if cancelled:  # drop cancelled requests, waiting or running
+                for req in [r for r in waiting if r.rid in cancelled]:
+                    waiting.remove(req)
+                    req.status, req.t_done = CANCELLED, now()
+                    self.stats.cancelled += 1
+                for k, (req, s) in list(active.items()):
+                    if req.rid in cancelled:
+                        self.batch.remove(s)
+                        del active[k]
+                        req.status, req.t_done, req._f = CANCELLED, now(), None
+                        self._release(s, req.shape)
+                        self.stats.cancelled += 1
+            # a request larger than the whole budget can never be admitted: reject it
+            for req in [r for r in waiting if self._ctx_bytes(r.shape) > self.budget]:
+                waiting.remove(req)
+                req.status, req.t_done = VDP_ENOMEM, now()
+                self.stats.rejected += 1
             # admission: FCFS while a slot and memory allow
             while waiting and len(active) < self.max_active:
                 req = waiting[0]
@@ -196,8 +233,14 @@ class Server:
                         self.stats.queue_s.append(req.queue_s)
                         if on_done:
                             on_done(req)
-            elif pending:
+            elif pending and not waiting:
                 time.sleep(max(0.0, min(0.01, (pending[0].arrival_s - now()) * time_scale)))
+            elif waiting and not active:
+                # nothing runs and the head was not admitted: it cannot get a context even with
+                # every idle one freed (the device or the budget has no room for it): reject it
+                req = waiting.popleft()
+                req.status, req.t_done = VDP_ENOMEM, now()
+                self.stats.rejected += 1
         self.stats.elapsed_s = now()
         return self.stats
 

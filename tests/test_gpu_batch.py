@@ -140,3 +140,39 @@ def test_spectral_members_equal_alone(precision):
     assert np.linalg.norm(outs[3].cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-7
     for _, _, s, *_ in members:
         s.close()
+
+
+def test_grid_barrier_wait_expires_and_batch_recovers():
+    """Failure detection on the GPU without a fault: a run that waits for a block that never
+    arrives gives up after the (shortened) wait limit with VDP_ETIMEOUT; the members stay
+    usable and finish with exactly the results they have alone."""
+    import time
+    items = problems()[:2]
+    members = []
+    for prob, tol in items:
+        s, f = setup(prob, "mixed")
+        p_alone = torch.empty_like(f)
+        s.solve(f, p_alone, tol)
+        members.append((prob, tol, s, f, p_alone))
+    with vdp.Batch("mixed", persistent=True) as b:
+        b.set_wait_limit(0.05)
+        outs = []
+        for prob, tol, s, f, _ in members:
+            p = torch.empty_like(f)
+            b.add(s, f, p, tol)
+            outs.append(p)
+        b.run(2)  # a normal run first
+        b.inject_lost_arrival()
+        t0 = time.perf_counter()
+        with pytest.raises(vdp.VdpError) as e:
+            b.run(2)
+        assert e.value.status == vdp.VDP_ETIMEOUT and time.perf_counter() - t0 < 5.0
+        b.run_to_completion(max_pairs=16)
+        for (prob, tol, s, f, p_alone), p in zip(members, outs):
+            assert b.done(s) and s.stats().ok
+            assert torch.equal(p, p_alone), prob.name
+    with vdp.Batch("mixed", persistent=False) as b2:  # no grid barrier to starve
+        with pytest.raises(vdp.VdpError):
+            b2.inject_lost_arrival()
+    for _, _, s, *_ in members:
+        s.close()

@@ -86,3 +86,28 @@ def test_autotuner_picks_a_valid_layout(tmp_path, monkeypatch):
         st = s.solve(f, p, 1e-9)
     ref, _ = oracle.solve_cg(prob.rho, prob.f, prob.L, tol=1e-13)
     assert st.ok and np.linalg.norm(p.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-8
+
+
+def test_rejection_and_cancellation():
+    """Host-side failure handling: a request larger than the whole HBM budget is rejected with
+    VDP_ENOMEM at once instead of waiting forever; a request cancelled while queued or running
+    leaves with status CANCELLED; everything else completes and matches its solve alone."""
+    reqs = request_stream(count=8, seed=13)
+    big = V.smooth_problem((64, 64, 64), seed=14)
+    reqs.append(serve.ServeRequest(100, 0.0, big.shape, big.L, big.rho, big.f, 1e-8))
+    budget = 2 * serve.BYTES_PER_CELL * 48 ** 3
+    victim = max(r.rid for r in reqs if r.rid != 100)
+    with serve.Server("mixed", hbm_budget=budget, max_active=4, pairs_per_run=2, precond="jacobi") as srv:
+        stats = srv.run(reqs, on_done=lambda r: srv.cancel(victim))
+    by_id = {r.rid: r for r in reqs}
+    assert by_id[100].status == vdp.VDP_ENOMEM and stats.rejected == 1
+    assert stats.cancelled <= 1
+    if stats.cancelled:
+        assert by_id[victim].status == serve.CANCELLED
+    for r in reqs:
+        if r.rid in (100,) or r.status == serve.CANCELLED:
+            continue
+        assert r.status == vdp.VDP_OK
+        p, st = solve_alone(r, "mixed")
+        assert torch.equal(p, r.p) and st.iters == r.iters
+    assert stats.completed + stats.rejected + stats.cancelled == len(reqs)
