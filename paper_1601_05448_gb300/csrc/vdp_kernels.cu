@@ -1110,11 +1110,10 @@ __device__ __forceinline__ void flat_kind_unit(const InstDesc& I, int unit) {
 #ifndef VDP_DIRECT_MIN_BLOCKS
 #define VDP_DIRECT_MIN_BLOCKS 2
 #endif
-// Units per SM the register budget is sized for (measured at 256^3): three (80 registers) for
-// FP32 and for the FP64 CG sweeps; two for the FP64 fixed-point sweep, whose unconstrained
-// allocation (126 registers) keeps more loads in flight and ran 7 % faster.
+// Units per SM the register budget is sized for: three (80 registers, no spills) for every kind;
+// measured at 256^3 against two units with the unconstrained allocation: FP64 CG sweep 315 ->
+// 307 us, FP64 fused fixed-point sweep 299 -> 284 us.
 template <class T, int KIND> struct DirectOcc { static constexpr int kMinBlocks = VDP_DIRECT_MIN_BLOCKS + 1; };
-template <> struct DirectOcc<double, 2> { static constexpr int kMinBlocks = VDP_DIRECT_MIN_BLOCKS; };
 
 template <class T, class BT, int KIND>
 __global__ void __launch_bounds__(kDirectThreads, DirectOcc<T, KIND>::kMinBlocks) k_stencil_direct(
