@@ -135,7 +135,7 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
       break;
     case PH_RES64: {
       const double rr64 = S[0], rrt = S[1];
-      st->sum_p = S[2];
+      if (st->first_res) st->sum_p = S[2];  // later: summed by the correction sweep
       if (st->first_res) {
         st->fn2 = S[3];
         st->first_res = 0;
@@ -266,6 +266,7 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
       break;
     }
     case PH_CORRECT:
+      st->sum_p = S[0];  // sum of the corrected p (for the gauge at the end)
       st->phase = PH_RES64;
       break;
     case PH_FINAL:
@@ -284,6 +285,7 @@ __device__ __forceinline__ int phase_slots(int phase) {
     case PH_RES64: return 4;
     case PH_STENCIL:
     case PH_UPDATE:
+    case PH_CORRECT:
     case PH_CHEB:
     case PH_SPEC: return 1;
     default: return 0;

@@ -244,17 +244,20 @@ __device__ void sweep_meanf(const InstDesc& I, const InstState* st, long long c0
   acc[1] = s2[0] + s2[1];
 }
 
-// p -= D^-1/2 x (x in the inner type)
+// p -= D^-1/2 x (x in the inner type); sums the new p (the final gauge needs its mean)
 template <class T>
-__device__ void sweep_correct(const InstDesc& I, long long c0, long long c1) {
+__device__ void sweep_correct(const InstDesc& I, long long c0, long long c1, double& psum) {
   const T* x = static_cast<const T*>(I.x);
+  double s = 0.0;
   for (long long c = c0 + 2 * threadIdx.x; c < c1; c += 2 * blockDim.x) {
     const double2 sv = __ldg(reinterpret_cast<const double2*>(I.sinv + c));
     double2 p = *reinterpret_cast<double2*>(I.p + c);
     p.x = fma(-sv.x, (double)x[c], p.x);
     p.y = fma(-sv.y, (double)x[c + 1], p.y);
     *reinterpret_cast<double2*>(I.p + c) = p;
+    s += p.x + p.y;
   }
+  psum = s;
 }
 
 // p -= <p>   (or p = 0 when the right-hand side was constant)
@@ -839,12 +842,16 @@ __device__ __forceinline__ void res64_march(const InstDesc& I, const InstState* 
     }
   };
   double pm[VR], pc[VR], pp[VR];
+  double dzm[VR];  // p_c - p_below of the current plane: the upper difference of the plane below
   if (z0 < z1) {
     ldv(p, at(z0 - 1, y) + x0, pm);
     ldv(p, at(z0, y) + x0, pc);
+#pragma unroll
+    for (int k = 0; k < VR; ++k) dzm[k] = pc[k] - pm[k];
   }
-  double a0 = 0, a2 = 0, a3 = 0;
-  T a1 = 0;
+  double a2 = 0, a3 = 0;
+  float a0 = 0.f, a1 = 0.f;  // norms steer the refinement only: summed in FP32 (cells narrowed
+                             // by integer repacking), the FP64 pipe kept for the residual itself
   for (int z = z0; z < z1; ++z) {
     const long long oc = at(z, y), op = at(z + 1, y), oyp = at(z, yp), oym = at(z, ym);
     ldv(p, op + x0, pp);
@@ -880,18 +887,32 @@ __device__ __forceinline__ void res64_march(const InstDesc& I, const InstState* 
       res1 = fma(-byd.y, pd.y - c1, res1);
       res0 = fma(by.x, c0 - pu.x, res0);
       res1 = fma(by.y, c1 - pu.y, res1);
-      res0 = fma(-bzp.x, pp[h] - c0, res0);
-      res1 = fma(-bzp.y, pp[h + 1] - c1, res1);
-      res0 = fma(bz.x, c0 - pm[h], res0);
-      res1 = fma(bz.y, c1 - pm[h + 1], res1);
-      const T t0 = from_double_rn<T>(si.x * res0), t1 = from_double_rn<T>(si.y * res1);
+      const double dzp0 = pp[h] - c0, dzp1 = pp[h + 1] - c1;
+      res0 = fma(-bzp.x, dzp0, res0);
+      res1 = fma(-bzp.y, dzp1, res1);
+      res0 = fma(bz.x, dzm[h], res0);
+      res1 = fma(bz.y, dzm[h + 1], res1);
+      dzm[h] = dzp0;
+      dzm[h + 1] = dzp1;
+      const double u0 = si.x * res0, u1 = si.y * res1;
+      T t0, t1;
+      if constexpr (IsF64<T>::value) {
+        t0 = u0;
+        t1 = u1;
+      } else {  // the inner residual in FP32, rounded toward zero by repacking
+        t0 = narrow(u0);
+        t1 = narrow(u1);
+      }
       if (active) {
         rt[o] = t0;
         rt[o + 1] = t1;
-        a0 = fma(res0, res0, fma(res1, res1, a0));
-        a1 = fma(t0, t0, fma(t1, t1, a1));
-        a2 += c0 + c1;
-        if (FIRST) a3 = fma(f0, f0, fma(f1, f1, a3));
+        const float r0f = narrow(res0), r1f = narrow(res1), t0f = narrow(u0), t1f = narrow(u1);
+        a0 = fmaf(r0f, r0f, fmaf(r1f, r1f, a0));
+        a1 = fmaf(t0f, t0f, fmaf(t1f, t1f, a1));
+        if (FIRST) {
+          a2 += c0 + c1;
+          a3 = fma(f0, f0, fma(f1, f1, a3));
+        }
       }
     }
 #pragma unroll
@@ -900,7 +921,7 @@ __device__ __forceinline__ void res64_march(const InstDesc& I, const InstState* 
       pc[k] = pp[k];
     }
   }
-  acc[0] = a0;
+  acc[0] = (double)a0;
   acc[1] = (double)a1;
   acc[2] = a2;
   acc[3] = a3;
@@ -1099,7 +1120,12 @@ __device__ __forceinline__ void flat_kind_unit(const InstDesc& I, int unit) {
       store_partials<1, T>(part, I.part, I.nunits_f, unit);
       break;
     }
-    case PH_CORRECT: sweep_correct<T>(I, c0, c1); break;
+    case PH_CORRECT: {
+      double ps[1] = {0.0};
+      sweep_correct<T>(I, c0, c1, ps[0]);
+      store_partials<1, double>(ps, I.part, I.nunits_f, unit);
+      break;
+    }
     default: sweep_final(I, &sn, c0, c1); break;
   }
   finish_sweep(I, st, phase, I.nunits_f);
