@@ -14,6 +14,11 @@ What it computes (Pouransari, Mortazavi & Mani, arXiv:1601.05448):
   * ``solve_fixed_point``: the paper's own iteration of Eq. (Pois) (Sec. 3.4), with the
     constant-coefficient inverse applied through a plain DFT; an independent second solver.
 
+  * ``projection_rhs`` / ``projection_correct`` / ``project``: the steps either side of the solve
+    in App. A -- the Poisson right side (div((rho u)~ / rho_new) - RHS^div) / (C_pre dt) and the
+    momentum correction (rho u)_new = (rho u)~ - C_pre dt grad p of Eq. (mom) -- on face momenta
+    stored on the low face of each cell; ``divergence`` and ``face_velocity`` are their parts.
+
 Arrays are numpy float64 of shape (nz, ny, nx) (C order, x fastest).
 """
 from __future__ import annotations
@@ -72,6 +77,14 @@ def _load():
             lib.vdpo_inverse_laplacian.restype = None
             lib.vdpo_solve_fixed_point.argtypes = [i, i, i, d, pd, pd, pd, d, i, d, pd]
             lib.vdpo_solve_fixed_point.restype = i
+            lib.vdpo_divergence.argtypes = [i, i, i, d, pd, pd, pd, pd]
+            lib.vdpo_divergence.restype = None
+            lib.vdpo_face_velocity.argtypes = [i, i, i, pd, pd, pd, pd, pd, pd, pd]
+            lib.vdpo_face_velocity.restype = i
+            lib.vdpo_projection_rhs.argtypes = [i, i, i, d, pd, pd, pd, pd, pd, d, pd]
+            lib.vdpo_projection_rhs.restype = i
+            lib.vdpo_projection_correct.argtypes = [i, i, i, d, pd, d, pd, pd, pd, pd, pd, pd]
+            lib.vdpo_projection_correct.restype = i
             lib.vdpo_num_threads.argtypes = []
             lib.vdpo_num_threads.restype = i
             _lib = lib
@@ -162,3 +175,54 @@ def solve_fixed_point(rho, f, L: float, tol: float = 1e-12, maxit: int = 1000, o
                                         float(omega), _ptr(info))
     return p, {"iters": int(info[0]), "rel_res": float(info[1]), "rhs_mean": float(info[2]),
                "status": STATUS.get(st, st)}
+
+
+def divergence(u, L: float) -> np.ndarray:
+    """Cell-centre divergence of a face field u = (ux, uy, uz) stored on the low faces."""
+    ux, uy, uz = (_f64(x) for x in u)
+    out = np.empty_like(ux)
+    _load().vdpo_divergence(*_dims(ux), float(L), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(out))
+    return out
+
+
+def face_velocity(rho, m):
+    """(ux, uy, uz) = face momenta m divided by the App. B face density."""
+    rho = _f64(rho)
+    mx, my, mz = (_f64(x) for x in m)
+    u = tuple(np.empty_like(rho) for _ in range(3))
+    st = _load().vdpo_face_velocity(*_dims(rho), _ptr(rho), _ptr(mx), _ptr(my), _ptr(mz), *(_ptr(x) for x in u))
+    if st != 0:
+        raise ValueError(f"face_velocity: {STATUS.get(st, st)}")
+    return u
+
+
+def projection_rhs(rho, m, rhs_div, c: float, L: float) -> np.ndarray:
+    """RHS^Pois = (div(m / rho_face) - rhs_div) / c of App. A (mean not removed); rhs_div may be None."""
+    rho = _f64(rho)
+    mx, my, mz = (_f64(x) for x in m)
+    rd = None if rhs_div is None else _f64(rhs_div)
+    f = np.empty_like(rho)
+    st = _load().vdpo_projection_rhs(*_dims(rho), float(L), _ptr(rho), _ptr(mx), _ptr(my), _ptr(mz),
+                                     None if rd is None else _ptr(rd), float(c), _ptr(f))
+    if st != 0:
+        raise ValueError(f"projection_rhs: {STATUS.get(st, st)}")
+    return f
+
+
+def projection_correct(p, m, c: float, L: float):
+    """Eq. (mom): the face momenta m minus c times the face pressure gradient (new arrays)."""
+    p = _f64(p)
+    mx, my, mz = (_f64(x) for x in m)
+    out = tuple(np.empty_like(p) for _ in range(3))
+    st = _load().vdpo_projection_correct(*_dims(p), float(L), _ptr(p), float(c), _ptr(mx), _ptr(my), _ptr(mz),
+                                         *(_ptr(x) for x in out))
+    if st != 0:
+        raise ValueError(f"projection_correct: {STATUS.get(st, st)}")
+    return out
+
+
+def project(rho, m, rhs_div, c: float, L: float, tol: float = 1e-13):
+    """The App. A projection: right side, solve, correction.  Returns (m_new, p, info)."""
+    f = projection_rhs(rho, m, rhs_div, c, L)
+    p, info = solve_cg(rho, f, L, tol=tol)
+    return projection_correct(p, m, c, L), p, info

@@ -34,7 +34,12 @@
  * smooth continuous solution, and agreement of the two independent solvers below (conjugate
  * gradients, and the paper's own fixed-point iteration of Eq. (Pois)).  The face-average choice is
  * a reading, not something the paper fixes: it is pinned only through the 1-D closed form, which
- * is written from that same reading.
+ * is written from that same reading.  The projection steps around the solve (App. A: the Poisson
+ * right side and the momentum correction of Eq. (mom)) are pinned by a pure-gradient field that
+ * the projection removes, a face-density-weighted solenoidal field it leaves alone, the App. A
+ * divergence constraint on the corrected velocity, idempotence, and, on tiny grids, the
+ * density-weighted least-change projection onto the discrete divergence constraint computed by
+ * dense null-space linear algebra.
  *
  * Reductions are deterministic: each z-plane is summed in index order, then the planes are summed
  * in order, so results do not depend on the OpenMP thread count.
@@ -376,6 +381,91 @@ int vdpo_solve_fixed_point(int nx, int ny, int nz, double L, const double *rho, 
 done:
   free(bx); free(by); free(bz); free(f0); free(r); free(dp);
   return status;
+}
+
+/* ---- the steps either side of the solve (App. A) ----------------------------------------------
+ *
+ * Face momenta (rho u_d) are stored like the face coefficients: mx[c] on the low x-face of cell c
+ * (shared with cell c - e_x), likewise my, mz.  The face velocity is the face momentum divided by
+ * the face density of App. B (mean of the two adjacent cell-centre densities), the same face
+ * density the operator A uses, so that the projection below is exact for the discrete operator.
+ */
+
+/* discrete divergence at cell centres of a face field (ux, uy, uz) stored on low faces */
+void vdpo_divergence(int nx, int ny, int nz, double L, const double *ux, const double *uy,
+                     const double *uz, double *out) {
+  double hx = L / nx, hy = L / ny, hz = L / nz;
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < nz; ++k)
+    for (long j = 0; j < ny; ++j)
+      for (long i = 0; i < nx; ++i) {
+        long c = idx(i, j, k, nx, ny, nz);
+        double dx = (ux[idx(i + 1, j, k, nx, ny, nz)] - ux[c]) / hx;
+        double dy = (uy[idx(i, j + 1, k, nx, ny, nz)] - uy[c]) / hy;
+        double dz = (uz[idx(i, j, k + 1, nx, ny, nz)] - uz[c]) / hz;
+        out[c] = dx + dy + dz;
+      }
+}
+
+/* face velocities u_d = m_d / rho_face (App. B face density) */
+int vdpo_face_velocity(int nx, int ny, int nz, const double *rho, const double *mx,
+                       const double *my, const double *mz, double *ux, double *uy, double *uz) {
+  if (nx < 1 || ny < 1 || nz < 1) return VDPO_EINVAL;
+  long n = (long)nx * ny * nz;
+  for (long c = 0; c < n; ++c)
+    if (!(rho[c] > 0.0) || !isfinite(rho[c])) return VDPO_EDENSITY;
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < nz; ++k)
+    for (long j = 0; j < ny; ++j)
+      for (long i = 0; i < nx; ++i) {
+        long c = idx(i, j, k, nx, ny, nz);
+        ux[c] = mx[c] / (0.5 * (rho[idx(i - 1, j, k, nx, ny, nz)] + rho[c]));
+        uy[c] = my[c] / (0.5 * (rho[idx(i, j - 1, k, nx, ny, nz)] + rho[c]));
+        uz[c] = mz[c] / (0.5 * (rho[idx(i, j, k - 1, nx, ny, nz)] + rho[c]));
+      }
+  return VDPO_OK;
+}
+
+/* Right side of the variable-coefficient Poisson equation of App. A, before its mean is removed:
+ *     RHS^Pois = ( div( m~ / rho_new ) - RHS^div ) / c,     c = C_pre[k] * dt,
+ * m~ the face momenta without the pressure gradient, rho_new the cell densities (through the face
+ * density above), RHS^div the cell-centre divergence target (NULL: zero). */
+int vdpo_projection_rhs(int nx, int ny, int nz, double L, const double *rho, const double *mx,
+                        const double *my, const double *mz, const double *rhs_div, double c,
+                        double *f) {
+  if (nx < 1 || ny < 1 || nz < 1 || !(L > 0.0) || !(c > 0.0) || !isfinite(c)) return VDPO_EINVAL;
+  long n = (long)nx * ny * nz;
+  double *ux = (double *)malloc(sizeof(double) * (size_t)n);
+  double *uy = (double *)malloc(sizeof(double) * (size_t)n);
+  double *uz = (double *)malloc(sizeof(double) * (size_t)n);
+  int status = VDPO_ENOMEM;
+  if (!ux || !uy || !uz) goto done;
+  status = vdpo_face_velocity(nx, ny, nz, rho, mx, my, mz, ux, uy, uz);
+  if (status != VDPO_OK) goto done;
+  vdpo_divergence(nx, ny, nz, L, ux, uy, uz, f);
+  for (long q = 0; q < n; ++q) f[q] = (f[q] - (rhs_div ? rhs_div[q] : 0.0)) / c;
+done:
+  free(ux); free(uy); free(uz);
+  return status;
+}
+
+/* Eq. (mom): (rho u_d)_new = (rho u_d)~ - c (dp/dx_d), the pressure difference across each low
+ * face divided by the spacing. */
+int vdpo_projection_correct(int nx, int ny, int nz, double L, const double *p, double c,
+                            const double *mx, const double *my, const double *mz, double *ox,
+                            double *oy, double *oz) {
+  if (nx < 1 || ny < 1 || nz < 1 || !(L > 0.0) || !(c > 0.0) || !isfinite(c)) return VDPO_EINVAL;
+  double hx = L / nx, hy = L / ny, hz = L / nz;
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < nz; ++k)
+    for (long j = 0; j < ny; ++j)
+      for (long i = 0; i < nx; ++i) {
+        long q = idx(i, j, k, nx, ny, nz);
+        ox[q] = mx[q] - c * ((p[q] - p[idx(i - 1, j, k, nx, ny, nz)]) / hx);
+        oy[q] = my[q] - c * ((p[q] - p[idx(i, j - 1, k, nx, ny, nz)]) / hy);
+        oz[q] = mz[q] - c * ((p[q] - p[idx(i, j, k - 1, nx, ny, nz)]) / hz);
+      }
+  return VDPO_OK;
 }
 
 int vdpo_num_threads(void) {

@@ -260,3 +260,141 @@ def test_hotspot_ratio_targeting():
     prob = V.hotspot_problem(32, seed=4, nspots=40, target_ratio=6.0)
     assert abs(prob.rho.max() / prob.rho.min() - 6.0) < 1e-9
     assert prob.rho.min() > 0
+
+
+# ---- 9. the projection steps either side of the solve (App. A, Eq. (mom)) ----------------------
+#
+# Face momenta live on the low face of each cell.  The pins use constructions that do not go
+# through the oracle's own formulas: a discrete gradient built here with np.roll, fields whose
+# every difference vanishes by construction, summation by parts, and the density-weighted
+# least-change characterisation of the projection solved by dense null-space linear algebra.
+
+def _low_face_gradient(phi, L):
+    nz, ny, nx = phi.shape
+    h = (L / nx, L / ny, L / nz)
+    return tuple((phi - np.roll(phi, 1, axis=2 - d)) / h[d] for d in range(3))
+
+
+def _face_density(rho, d):
+    return 0.5 * (np.roll(rho, 1, axis=2 - d) + rho)
+
+
+def test_divergence_is_minus_the_adjoint_of_the_face_gradient():
+    rng = np.random.default_rng(21)
+    shape, L = (5, 7, 6), 1.7
+    phi = rng.standard_normal(shape)
+    u = tuple(rng.standard_normal(shape) for _ in range(3))
+    lhs = float(np.sum(phi * oracle.divergence(u, L)))
+    rhs = -sum(float(np.sum(a * b)) for a, b in zip(u, _low_face_gradient(phi, L)))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1.0)
+
+
+def test_divergence_of_gradient_over_face_density_is_the_operator():
+    # div(grad(phi) / rho_face) composed from the projection parts equals the pinned operator A
+    rng = np.random.default_rng(22)
+    shape, L = (8, 6, 10), 2.5
+    rho = V.density_modes(shape, rng, amplitude=0.7)
+    phi = rng.standard_normal(shape)
+    comp = oracle.divergence(oracle.face_velocity(rho, _low_face_gradient(phi, L)), L)
+    ref = oracle.apply_rho(rho, L, phi)
+    assert np.abs(comp - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_projection_removes_a_pure_gradient():
+    rng = np.random.default_rng(23)
+    shape, L, c = (12, 10, 16), 2.0, 0.3
+    rho = V.density_modes(shape, rng, amplitude=0.8)             # ratio 9
+    phi = rng.standard_normal(shape)
+    m = tuple(c * g for g in _low_face_gradient(phi, L))
+    m_new, p, info = oracle.project(rho, m, None, c, L)
+    assert info["status"] == "ok"
+    scale = max(float(np.abs(x).max()) for x in m)
+    assert max(float(np.abs(x).max()) for x in m_new) <= 1e-9 * scale
+    assert np.abs(p - (phi - phi.mean())).max() <= 1e-9 * np.abs(phi).max()
+
+
+def test_projection_keeps_a_weighted_solenoidal_field():
+    # u_x depends on (y, z) only, u_y on (x, z), u_z on (x, y): each direction's face difference
+    # vanishes, so u is discretely solenoidal and the momenta rho_face u pass unchanged
+    rng = np.random.default_rng(24)
+    shape, L, c = (10, 12, 8), 3.0, 0.05
+    nz, ny, nx = shape
+    rho = V.density_modes(shape, rng, amplitude=0.6)
+    ux = np.broadcast_to(rng.standard_normal((nz, ny, 1)), shape)
+    uy = np.broadcast_to(rng.standard_normal((nz, 1, nx)), shape)
+    uz = np.broadcast_to(rng.standard_normal((1, ny, nx)), shape)
+    m = tuple(np.ascontiguousarray(_face_density(rho, d) * u) for d, u in enumerate((ux, uy, uz)))
+    f = oracle.projection_rhs(rho, m, None, c, L)
+    h = L / max(shape)
+    assert np.abs(f).max() <= 1e-13 * 3.0 * np.abs(ux).max() / (h * c) * 10
+    m_new, p, info = oracle.project(rho, m, None, c, L)
+    for a, b in zip(m_new, m):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("shape", [(8, 6, 10), (16, 16, 16)])
+def test_projection_meets_the_divergence_constraint(shape):
+    # App. A: div u_new = RHS^div - chi with chi = -c <RHS^Pois>; the divergence of the momenta
+    # sums to zero on the periodic box, so chi = <RHS^div> and div u_new = RHS^div - <RHS^div>
+    rng = np.random.default_rng(25)
+    L, c = 2.0 * math.pi, 0.5 * 2e-3
+    rho = V.density_modes(shape, rng, amplitude=0.6)
+    m = V.face_momenta(shape, L, rng)
+    rd = V.divergence_target(shape, rng)
+    f = oracle.projection_rhs(rho, m, rd, c, L)
+    chi = -c * float(f.mean())
+    assert abs(chi - float(rd.mean())) <= 1e-12 * float(np.abs(rd).max()) * 1e3
+    d0 = c * (f - f.mean())                       # divergence the correction has to remove
+    m_new, p, info = oracle.project(rho, m, rd, c, L)
+    assert info["status"] == "ok"
+    div = oracle.divergence(oracle.face_velocity(rho, m_new), L)
+    err = np.abs(div - (rd - rd.mean())).max()
+    assert err <= 1e-11 * float(np.linalg.norm(d0))
+
+
+def test_projection_is_idempotent_and_scales_with_c():
+    rng = np.random.default_rng(26)
+    shape, L = (8, 8, 12), 1.0
+    rho = V.density_modes(shape, rng, amplitude=0.5)
+    m = V.face_momenta(shape, L, rng)
+    m1, p1, _ = oracle.project(rho, m, None, 0.25, L)
+    m2, p2, _ = oracle.project(rho, m1, None, 0.25, L)
+    m3, p3, _ = oracle.project(rho, m, None, 0.5, L)
+    s = max(float(np.abs(x).max()) for x in m)
+    for a, b in zip(m2, m1):
+        assert np.abs(a - b).max() <= 1e-10 * s
+    for a, b in zip(m3, m1):                      # the corrected momenta do not depend on c ...
+        assert np.abs(a - b).max() <= 1e-10 * s
+    assert np.abs(0.5 * p3 - 0.25 * p1).max() <= 1e-10 * np.abs(0.25 * p1).max()  # ... c p does
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (2, 3, 4)])
+def test_projection_is_the_density_weighted_least_change(shape):
+    # Among all face velocities u with div u = RHS^div - <RHS^div>, the corrected one minimises
+    # sum rho_face (u - u~)^2: found here by dense linear algebra on the null space of the
+    # divergence matrix (whose columns are divergences of unit face fields)
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(27)
+    L, c = 1.3, 0.7
+    n = int(np.prod(shape))
+    rho = V.density_modes(shape, rng, amplitude=0.7)
+    m = tuple(rng.standard_normal(shape) for _ in range(3))
+    rd = rng.standard_normal(shape)
+    cols = []
+    for d in range(3):
+        for q in range(n):
+            e = [np.zeros(shape) for _ in range(3)]
+            e[d].flat[q] = 1.0
+            cols.append(oracle.divergence(tuple(e), L).ravel())
+    D = np.stack(cols, axis=1)                                          # n x 3n
+    w = np.concatenate([_face_density(rho, d).ravel() for d in range(3)])
+    u0 = np.concatenate([(m[d] / _face_density(rho, d)).ravel() for d in range(3)])
+    r = (rd - rd.mean()).ravel()
+    up = np.linalg.lstsq(D, r, rcond=None)[0]                           # a particular solution
+    N = scipy_linalg.null_space(D)
+    sw = np.sqrt(w)
+    y = np.linalg.lstsq(sw[:, None] * N, sw * (u0 - up), rcond=None)[0]
+    u_best = up + N @ y
+    m_new, p, info = oracle.project(rho, m, rd, c, L)
+    u_new = np.concatenate([(m_new[d] / _face_density(rho, d)).ravel() for d in range(3)])
+    assert np.abs(u_new - u_best).max() <= 1e-9 * np.abs(u0).max()

@@ -21,6 +21,10 @@ gas around them (Eq. (PEE)).  The recipes below mimic that structure:
   unit variance); f has zero mean by telescoping, like the divergence that feeds the paper's
   pressure equation (App. A).
 
+* ``face_momenta`` / ``divergence_target``: inputs of the projection steps either side of the
+  solve (App. A): random face momenta (rho u)~ on the low faces of each cell, and a smooth
+  cell-centre field standing for RHS^div.
+
 Arrays are float64 with shape (nz, ny, nx) -- C order, x fastest -- and the box is [0, L)^3 with
 cell (i, j, k) centred at ((i+1/2) hx, (j+1/2) hy, (k+1/2) hz), h_d = L / n_d.
 """
@@ -201,6 +205,35 @@ def rhs_divergence(shape, L: float, rng: np.random.Generator, kmax: float = 4.0)
         axis = 2 - d  # numpy axis of direction d
         f += (np.roll(u, -1, axis=axis) - u) / h[d]
     return np.ascontiguousarray(f)
+
+
+def face_momenta(shape, L: float, rng: np.random.Generator, kmax: float = 4.0):
+    """(mx, my, mz): seeded random face momenta, each component sampled on its own low faces
+    (a sum over all integer wave vectors 1 <= |k| <= kmax of a cos(k.x) + b sin(k.x), a, b ~ N(0,1),
+    scaled to unit standard deviation, plus a uniform mean flow in [-1, 1])."""
+    kv = integer_wavevectors(1.0, kmax)
+    out = []
+    for d in range(3):
+        a = rng.standard_normal(len(kv))
+        b = rng.standard_normal(len(kv))
+        off = [0.5, 0.5, 0.5]
+        off[d] = 0.0
+        m = modes_field(shape, kv, a - 1j * b, offset=tuple(off))
+        sd = float(m.std())
+        if sd > 0:
+            m /= sd
+        m += rng.uniform(-1.0, 1.0)
+        out.append(np.ascontiguousarray(m))
+    return tuple(out)
+
+
+def divergence_target(shape, rng: np.random.Generator, mean: float = 0.1, amplitude: float = 0.05,
+                      kmax: float = 4.0) -> np.ndarray:
+    """A seeded cell-centre field standing for RHS^div of App. A (thermal expansion from the
+    heated particles): mean + amplitude * g, g a few random modes spanning [-1, 1]."""
+    kv, coefs = random_modes(rng, 8, kmax)
+    g = _minmax_unit(modes_field(shape, kv, coefs))
+    return np.ascontiguousarray(mean + amplitude * g)
 
 
 @dataclass
