@@ -358,6 +358,58 @@ def run_batch(torch, vdp, dev, probs, persistent=False, precond="fixed_point"):
     return out
 
 
+# one projection substep (App. A) around the solve: FP64 operations and bytes per cell of its two
+# kernels (right side: 4 mul + 5 fma + 1 add, reads m x3, b x3, RHS^div, writes f; correction:
+# 3 sub + 3 fma, reads p, m x3, writes m x3)
+PROJ_COST = {"rhs": {"bytes": 64.0, "fp64_ops": 10.0}, "correct": {"bytes": 56.0, "fp64_ops": 6.0}}
+FP64_OPS_PER_S = FP64_PEAK_TFLOPS * 1e12 / 2.0  # 2 FP64 pipe operations / clk / SM
+
+
+def run_projection(torch, vdp, dev, solver, prob, stream, peaks, steps=5):
+    """The steps either side of the solve (App. A): Poisson right side from seeded face momenta and
+    a divergence target on the benchmark density, the benchmark solve, and the momentum correction
+    of Eq. (mom).  The momenta are restored before every step (outside the events)."""
+    import vdp_inputs as V
+    rng = np.random.default_rng(7)
+    m0 = [torch.from_numpy(x).to(dev) for x in V.face_momenta(prob.shape, prob.L, rng)]
+    rd = torch.from_numpy(V.divergence_target(prob.shape, rng)).to(dev)
+    m = [x.clone() for x in m0]
+    pp = torch.zeros_like(rd)
+    c = 0.5 * 1e-3  # C_pre[0] dt with dt = 1e-3
+    ncell = rd.numel()
+
+    def reset():
+        for a, b in zip(m, m0):
+            a.copy_(b)
+
+    reset()
+    solver.project(m, rd, c, prob.tol, pp)
+    ms_steps, st = [], None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        reset()
+        e0.record(stream)
+        st = solver.project(m, rd, c, prob.tol, pp)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_steps.append(e0.elapsed_time(e1))
+    reset()
+    st_t, kt = solver.project_timed(m, rd, c, prob.tol, pp)
+    out = {"ms_per_step": statistics.median(ms_steps), "steps_per_s": 1e3 / statistics.median(ms_steps),
+           "solve_ms": st.ms, "iters": st.iters, "rel_res": st.rel_res, "status": vdp.vdp_strerror(st.status),
+           "chi": -c * st.rhs_mean, "c": c,
+           "timing": "CUDA events around vdp_project per step (median of %d); kernels from vdp_project_timed"
+                     % steps}
+    for name, key in (("rhs", "rhs_ms"), ("correct", "correct_ms")):
+        t = kt[key] / 1e3
+        cost = PROJ_COST[name]
+        out[name] = {"us": kt[key] * 1e3, "alg_bytes": cost["bytes"] * ncell,
+                     "gbs": cost["bytes"] * ncell / t / 1e9,
+                     "hbm_frac": cost["bytes"] * ncell / t / 1e9 / peaks["hbm_gbs"],
+                     "fp64_pipe_frac": cost["fp64_ops"] * ncell / t / FP64_OPS_PER_S}
+    return out
+
+
 def run_serving(torch, vdp, dev, pool, count=200):
     """Config 4 (first `count` requests of the Poisson stream, lambda = 200/s)."""
     import vdp_inputs as V
@@ -594,6 +646,7 @@ def main():
                 tj = [sj.solve(f, pj, prob.tol) for _ in range(2)]
             bj = min(tj, key=lambda x: x.ms)
             line["fp64_jacobi_1e-10"] = {"solves_per_s": 1e3 / bj.ms, "ms": bj.ms, "iters": bj.iters}
+            line["projection_step"] = run_projection(torch, vdp, dev, solver, prob, stream, peaks)
             try:
                 line["cpu_baseline"] = cpu_baseline(prob)
             except Exception as e:  # the stored iteration count is missing

@@ -192,6 +192,57 @@ int vdp_apply(vdp_ctx *ctx, const double *p, double *out);
 int vdp_inverse_laplacian(vdp_ctx *ctx, const double *g, double *out);
 
 /* ------------------------------------------------------------------------------------------ */
+/* The steps either side of the solve in one projection substep (App. A, Eq. (mom)).           */
+/* ------------------------------------------------------------------------------------------ */
+
+/*
+ * Face momenta: mx, my, mz are nx*ny*nz doubles each; mx[i] is the x-momentum (rho u_x) on the
+ * LOW x-face of cell i (the face shared by cells i - e_x and i, periodic), likewise my, mz.  The
+ * density is the context's (vdp_set_density with rho_new); the face density is the App. B mean of
+ * the two adjacent cell densities, the one the Poisson operator uses.  c = C_pre[k] * dt > 0 is
+ * the substep's pressure coefficient.  All arrays are DEVICE pointers (8-byte aligned; p also
+ * 16-byte aligned for vdp_project) on the context's device; the calls run on the context's stream
+ * and return after it has finished.  VDP_EINVAL: no density set, c not finite and positive, a
+ * host or misaligned pointer, or an output that aliases an input.
+ */
+
+/*
+ * f = RHS^Pois = ( div((rho u)~ / rho_face) - rhs_div ) / c: the right side of the
+ * variable-coefficient Poisson equation of App. A before its mean is removed (the solve removes
+ * it: chi' = -<f>, reported as vdp_stats.rhs_mean).  rhs_div (RHS^div of App. A, cell centres)
+ * may be NULL for zero.  f must not alias an input.
+ */
+int vdp_projection_rhs(vdp_ctx *ctx, const double *mx, const double *my, const double *mz,
+                       const double *rhs_div, double c, double *f);
+
+/*
+ * Eq. (mom): (rho u_d)_new = (rho u_d)~ - c (p[i] - p[i - e_d]) / h_d on every low face, in place
+ * on mx, my, mz.  p is cell-centred.  No density is needed.
+ */
+int vdp_projection_correct(vdp_ctx *ctx, const double *p, double c, double *mx, double *my,
+                           double *mz);
+
+/*
+ * One whole projection: vdp_projection_rhs into a context-owned buffer (allocated on first use,
+ * nx*ny*nz doubles), vdp_solve of div((1/rho) grad p) = RHS^Pois + chi' to relative residual tol
+ * with the context's options (p is the initial guess when opts.use_guess), then
+ * vdp_projection_correct in place.  Afterwards div(u_new) = rhs_div - <rhs_div> on every cell to
+ * the solve's tolerance (App. A).  Returns the solve's status; when it is not VDP_OK the momenta
+ * are left unchanged.  vdp_get_stats describes the solve.
+ */
+int vdp_project(vdp_ctx *ctx, double *mx, double *my, double *mz, const double *rhs_div,
+                double c, double tol, double *p);
+
+/*
+ * vdp_project with its kernels timed: ms[0] = the right-side kernel, ms[1] = the solve
+ * (vdp_stats.ms), ms[2] = the correction kernel, in milliseconds (CUDA events that bracket each
+ * kernel alone; the kernels are captured into small graphs for that, which costs host time).
+ * ms is host memory for 3 floats (VDP_EINVAL if NULL); results are those of vdp_project.
+ */
+int vdp_project_timed(vdp_ctx *ctx, double *mx, double *my, double *mz, const double *rhs_div,
+                      double c, double tol, double *p, float *ms);
+
+/* ------------------------------------------------------------------------------------------ */
 /* Per-kernel timing (instrumentation; the paper has no counterpart).                          */
 /* ------------------------------------------------------------------------------------------ */
 

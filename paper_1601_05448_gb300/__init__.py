@@ -97,6 +97,11 @@ _SIGS = {
     "vdp_version": (ctypes.c_int, []),
     "vdp_apply": (ctypes.c_int, [_P, _P, _P]),
     "vdp_inverse_laplacian": (ctypes.c_int, [_P, _P, _P]),
+    "vdp_projection_rhs": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_double, _P]),
+    "vdp_projection_correct": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
+    "vdp_project": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_double, _P]),
+    "vdp_project_timed": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_double, _P,
+                                         ctypes.POINTER(ctypes.c_float)]),
     "vdp_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_void_p)]),
     "vdp_batch_destroy": (None, [_P]),
     "vdp_batch_add": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double]),
@@ -199,6 +204,34 @@ def vdp_apply(ctx: int, p, out) -> int:
 
 def vdp_inverse_laplacian(ctx: int, g, out) -> int:
     return load().vdp_inverse_laplacian(ctx, _ptr(g), _ptr(out, writable=True))
+
+
+def _opt_ptr(a):
+    return None if a is None else _ptr(a)
+
+
+def vdp_projection_rhs(ctx: int, mx, my, mz, rhs_div, c: float, f) -> int:
+    return load().vdp_projection_rhs(ctx, _ptr(mx), _ptr(my), _ptr(mz), _opt_ptr(rhs_div), float(c),
+                                     _ptr(f, writable=True))
+
+
+def vdp_projection_correct(ctx: int, p, c: float, mx, my, mz) -> int:
+    return load().vdp_projection_correct(ctx, _ptr(p), float(c), _ptr(mx, writable=True),
+                                         _ptr(my, writable=True), _ptr(mz, writable=True))
+
+
+def vdp_project(ctx: int, mx, my, mz, rhs_div, c: float, tol: float, p) -> int:
+    return load().vdp_project(ctx, _ptr(mx, writable=True), _ptr(my, writable=True), _ptr(mz, writable=True),
+                              _opt_ptr(rhs_div), float(c), float(tol), _ptr(p, writable=True))
+
+
+def vdp_project_timed(ctx: int, mx, my, mz, rhs_div, c: float, tol: float, p):
+    """vdp_project with its kernels timed; returns (status, (rhs_ms, solve_ms, correct_ms))."""
+    ms = (ctypes.c_float * 3)()
+    st = load().vdp_project_timed(ctx, _ptr(mx, writable=True), _ptr(my, writable=True),
+                                  _ptr(mz, writable=True), _opt_ptr(rhs_div), float(c), float(tol),
+                                  _ptr(p, writable=True), ms)
+    return st, (ms[0], ms[1], ms[2])
 
 
 def vdp_solve_timed(ctx: int, rhs, p, tol: float):
@@ -396,6 +429,51 @@ class Solver:
         st = vdp_inverse_laplacian(self.ctx, g, out)
         if st != VDP_OK:
             raise VdpError(st, "vdp_inverse_laplacian")
+
+    def projection_rhs(self, m, rhs_div, c: float, f) -> None:
+        """f = (div(m / rho_face) - rhs_div) / c (App. A); m = (mx, my, mz) face momenta on the
+        low faces, rhs_div may be None (device tensors)."""
+        for a, name in zip((*m, f), ("mx", "my", "mz", "f")):
+            self._check(a, name)
+        if rhs_div is not None:
+            self._check(rhs_div, "rhs_div")
+        st = vdp_projection_rhs(self.ctx, *m, rhs_div, c, f)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_projection_rhs")
+
+    def projection_correct(self, p, c: float, m) -> None:
+        """Eq. (mom): m -= c grad p on the low faces, in place (device tensors)."""
+        for a, name in zip((p, *m), ("p", "mx", "my", "mz")):
+            self._check(a, name)
+        st = vdp_projection_correct(self.ctx, p, c, *m)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_projection_correct")
+
+    def project(self, m, rhs_div, c: float, tol: float, p, check: bool = True) -> Stats:
+        """One projection (App. A): right side, solve into p, momentum correction of m in place."""
+        for a, name in zip((p, *m), ("p", "mx", "my", "mz")):
+            self._check(a, name)
+        if rhs_div is not None:
+            self._check(rhs_div, "rhs_div")
+        st = vdp_project(self.ctx, *m, rhs_div, c, tol, p)
+        s = vdp_get_stats(self.ctx)
+        out = Stats(s.status, s.iters, s.outer_iters, s.rel_res, s.rhs_mean, s.ms, s.sweeps, s.launches)
+        if st != VDP_OK and (check or st not in (VDP_ENOTCONV, VDP_EBREAKDOWN)):
+            raise VdpError(st, "vdp_project")
+        return out
+
+    def project_timed(self, m, rhs_div, c: float, tol: float, p, check: bool = True):
+        """project() with its kernels timed: (Stats, {"rhs_ms", "solve_ms", "correct_ms"})."""
+        for a, name in zip((p, *m), ("p", "mx", "my", "mz")):
+            self._check(a, name)
+        if rhs_div is not None:
+            self._check(rhs_div, "rhs_div")
+        st, ms = vdp_project_timed(self.ctx, *m, rhs_div, c, tol, p)
+        s = vdp_get_stats(self.ctx)
+        out = Stats(s.status, s.iters, s.outer_iters, s.rel_res, s.rhs_mean, s.ms, s.sweeps, s.launches)
+        if st != VDP_OK and (check or st not in (VDP_ENOTCONV, VDP_EBREAKDOWN)):
+            raise VdpError(st, "vdp_project_timed")
+        return out, {"rhs_ms": ms[0], "solve_ms": ms[1], "correct_ms": ms[2]}
 
     def apply(self, p, out) -> None:
         self._check(p, "p")

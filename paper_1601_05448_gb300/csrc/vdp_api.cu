@@ -109,7 +109,7 @@ void free_ctx(vdp_ctx* c) {
   void* bufs[] = {c->bx, c->by, c->bz, c->sinv, c->sx, c->sy, c->sz, c->sd, c->x, c->r, c->d0, c->d1,
                   c->za, c->zb, c->dch, c->spec, c->omega, c->sptab, c->rho_w, c->d_rounds,
                   c->q, c->part, c->ticket, c->st, c->desc, c->units, c->flag, c->stage_a,
-                  c->stage_b};
+                  c->stage_b, c->proj_f};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->hstate) cudaFreeHost(c->hstate);

@@ -54,6 +54,7 @@ struct vdp_ctx {
   vdp::UnitRef* units = nullptr;
   int* flag = nullptr;
   double *stage_a = nullptr, *stage_b = nullptr;  // staging for host pointers
+  double* proj_f = nullptr;        // vdp_project: the assembled Poisson right side
   vdp::InstState* hstate = nullptr;     // pinned, 2 entries
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs[2] = {nullptr, nullptr};
   // layout
