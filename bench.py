@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Poisson solves/s and % HBM roofline to 1e-8 rel. residual, mixed vs FP64"
 WORKLOAD = ("256^3 periodic box L=2pi, rho=T0/T (20k hot spots, density ratio 4), rhs=div of random "
             "|k|<=4 velocity; FP64, relative residual 1e-10")
-PRECONDS = {"spectral": 2, "cheb": 1, "jacobi": 0}
+PRECONDS = {"spectral": 2, "cheb": 1, "jacobi": 0, "mg": 3}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # FP64 vector peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -58,7 +58,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 SIZES = {"fp64": (8, 8, False), "mixed": (4, 4, False), "mixed_bf16": (4, 2, True)}
 KERNEL_NAMES = {"res64": "k_res64_direct", "stencil": "k_stencil_direct", "cheb": "k_stencil_direct",
                 "update": "k_flat", "other": "k_flat", "spec_x": "k_spec_x_fwd / k_spec_x_inv",
-                "spec_y": "k_spec_y", "spec_z": "k_spec_z"}
+                "spec_y": "k_spec_y", "spec_z": "k_spec_z",
+                "mg": "k_mg_down / k_mg_restrict / k_mg_coarse / k_mg_prolong / k_mg_up"}
 
 
 def spectrum_bytes(nx: int) -> float:
@@ -487,7 +488,8 @@ def main():
         f"{args.grid}^3 periodic box L=2pi, rho=T0/T (hot spots scaled by volume, density ratio 4), rhs=div of "
         f"random |k|<=4 velocity; {args.precision}, relative residual {prob.tol:g} (profiling case)")
     method = {"spectral": "CG preconditioned by the constant-coefficient FFT inverse (Sec. 3.4)",
-              "cheb": "CG preconditioned by a degree-3 Chebyshev polynomial", "jacobi": "Jacobi-preconditioned CG"}[
+              "cheb": "CG preconditioned by a degree-3 Chebyshev polynomial", "jacobi": "Jacobi-preconditioned CG",
+              "mg": "CG preconditioned by a geometric multigrid V-cycle"}[
         args.precond]
     if args.method == "fixed_point":
         method = ("the paper's fixed-point iteration (Sec. 3.4, Eq. (Pois)): update = constant-coefficient FFT "

@@ -65,7 +65,7 @@ typedef enum {
                              iteration for the unit-diagonal operator on [0.1, 2] (degree - 1
                              stencil sweeps per Krylov iteration; symmetric positive definite,
                              so plain preconditioned CG applies); direct stencil sweep only */
-  VDP_PRECOND_SPECTRAL = 2 /* the constant-coefficient inverse of the paper's Poisson iteration
+  VDP_PRECOND_SPECTRAL = 2, /* the constant-coefficient inverse of the paper's Poisson iteration
                              (Sec. 3.4): z = (-L_h)^-1 r in unscaled variables, L_h the 7-point
                              Laplacian with 1/h^2 faces, applied by FP32 FFTs (five passes per
                              Krylov iteration).  The preconditioned condition number is at most
@@ -73,6 +73,19 @@ typedef enum {
                              of 32, 48, 64, 96, 128, 192, 256, 512; direct stencil sweep only;
                              batch members only in batches of ordinary launches (persistent =
                              0).  Extra memory: about 16 bytes per cell */
+  VDP_PRECOND_MG = 3      /* a geometric multigrid V-cycle (no counterpart in the paper; the
+                             standard mesh-independent alternative to its FFT solve): cell-
+                             centred, periodic, FP32; levels halve every size while all are even
+                             and the level has more than 64 cells; coarse face coefficient = 1/2
+                             x the sum of the four fine faces under it; linear interpolation and
+                             its transpose; one weighted Jacobi sweep (0.8) before and after the
+                             coarse correction; the coarsest level (at most 512 cells, else the
+                             grid is not supported) by a dense pseudo-inverse.  z = W M W rt in
+                             the solve's scaled variables (W = D^1/2).  Iteration counts hardly
+                             grow with the grid or the density ratio.  Needs at least one
+                             coarsening (more than 64 cells, even sizes down to the coarsest);
+                             direct stencil sweep only; not in batches.  Extra memory: about 24
+                             bytes per cell */
 } vdp_precond;
 
 typedef enum {
@@ -191,6 +204,20 @@ int vdp_apply(vdp_ctx *ctx, const double *p, double *out);
  */
 int vdp_inverse_laplacian(vdp_ctx *ctx, const double *g, double *out);
 
+/*
+ * Levels of the multigrid V-cycle for an nx x ny x nz grid (level 0 = the grid), or 0 when the
+ * grid is not supported by VDP_PRECOND_MG.
+ */
+int vdp_mg_levels(int nx, int ny, int nz);
+
+/*
+ * out = M g: one V-cycle of VDP_PRECOND_MG (an approximation of (-A)^-1 in unscaled variables,
+ * with the context's density; FP32 inside).  g and out are nx*ny*nz doubles, device pointers,
+ * 16-byte aligned, out must not alias g.  VDP_EINVAL without a density or for a grid the V-cycle
+ * does not support.  Allocates the levels on first use.
+ */
+int vdp_mg_apply(vdp_ctx *ctx, const double *g, double *out);
+
 /* ------------------------------------------------------------------------------------------ */
 /* The steps either side of the solve in one projection substep (App. A, Eq. (mom)).           */
 /* ------------------------------------------------------------------------------------------ */
@@ -256,7 +283,8 @@ enum {
   VDP_SWEEP_SPEC_X = 5,  /* spectral preconditioner: forward and inverse real FFTs along x     */
   VDP_SWEEP_SPEC_Y = 6,  /* ... forward and inverse FFTs along y                               */
   VDP_SWEEP_SPEC_Z = 7,  /* ... FFT along z, division by the eigenvalues, inverse FFT along z   */
-  VDP_SWEEP_KINDS = 8
+  VDP_SWEEP_MG = 8,      /* one whole multigrid V-cycle (all its launches, timed together)     */
+  VDP_SWEEP_KINDS = 9
 };
 
 typedef struct {

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libvdp.so")
 
 VDP_OK, VDP_EINVAL, VDP_ENOMEM, VDP_EDENSITY, VDP_ENOTCONV, VDP_EBREAKDOWN, VDP_ETIMEOUT, VDP_ECUDA = range(8)
 VDP_FP64, VDP_MIXED, VDP_MIXED_BF16 = 0, 1, 2
-VDP_PRECOND_JACOBI, VDP_PRECOND_CHEB, VDP_PRECOND_SPECTRAL = 0, 1, 2
+VDP_PRECOND_JACOBI, VDP_PRECOND_CHEB, VDP_PRECOND_SPECTRAL, VDP_PRECOND_MG = 0, 1, 2, 3
 VDP_METHOD_CG, VDP_METHOD_FIXED_POINT = 0, 1
 PRECISIONS = {"fp64": VDP_FP64, "mixed": VDP_MIXED, "mixed_bf16": VDP_MIXED_BF16}
 # grid sizes (per direction) the spectral preconditioner's FFT passes support
@@ -68,8 +68,8 @@ class vdp_stats(ctypes.Structure):
 
 
 (VDP_SWEEP_RES64, VDP_SWEEP_STENCIL, VDP_SWEEP_CHEB, VDP_SWEEP_UPDATE, VDP_SWEEP_OTHER, VDP_SWEEP_SPEC_X,
- VDP_SWEEP_SPEC_Y, VDP_SWEEP_SPEC_Z, VDP_SWEEP_KINDS) = range(9)
-SWEEP_NAMES = ("res64", "stencil", "cheb", "update", "other", "spec_x", "spec_y", "spec_z")
+ VDP_SWEEP_SPEC_Y, VDP_SWEEP_SPEC_Z, VDP_SWEEP_MG, VDP_SWEEP_KINDS) = range(10)
+SWEEP_NAMES = ("res64", "stencil", "cheb", "update", "other", "spec_x", "spec_y", "spec_z", "mg")
 
 
 class vdp_sweep_times(ctypes.Structure):
@@ -97,6 +97,8 @@ _SIGS = {
     "vdp_version": (ctypes.c_int, []),
     "vdp_apply": (ctypes.c_int, [_P, _P, _P]),
     "vdp_inverse_laplacian": (ctypes.c_int, [_P, _P, _P]),
+    "vdp_mg_levels": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "vdp_mg_apply": (ctypes.c_int, [_P, _P, _P]),
     "vdp_projection_rhs": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_double, _P]),
     "vdp_projection_correct": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     "vdp_project": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_double, _P]),
@@ -204,6 +206,14 @@ def vdp_apply(ctx: int, p, out) -> int:
 
 def vdp_inverse_laplacian(ctx: int, g, out) -> int:
     return load().vdp_inverse_laplacian(ctx, _ptr(g), _ptr(out, writable=True))
+
+
+def vdp_mg_levels(nx: int, ny: int, nz: int) -> int:
+    return load().vdp_mg_levels(nx, ny, nz)
+
+
+def vdp_mg_apply(ctx: int, g, out) -> int:
+    return load().vdp_mg_apply(ctx, _ptr(g), _ptr(out, writable=True))
 
 
 def _opt_ptr(a):
@@ -429,6 +439,14 @@ class Solver:
         st = vdp_inverse_laplacian(self.ctx, g, out)
         if st != VDP_OK:
             raise VdpError(st, "vdp_inverse_laplacian")
+
+    def mg_apply(self, g, out) -> None:
+        """out = one multigrid V-cycle applied to g (approximately (-A)^-1 g; device tensors)."""
+        self._check(g, "g")
+        self._check(out, "out")
+        st = vdp_mg_apply(self.ctx, g, out)
+        if st != VDP_OK:
+            raise VdpError(st, "vdp_mg_apply")
 
     def projection_rhs(self, m, rhs_div, c: float, f) -> None:
         """f = (div(m / rho_face) - rhs_div) / c (App. A); m = (mx, my, mz) face momenta on the

@@ -93,7 +93,7 @@ const char* vdp_last_cuda_error(void) {
   return g_last_cuda_error.c_str();
 }
 
-int vdp_version(void) { return 1; }
+int vdp_version(void) { return 2; }
 
 }  // extern "C"
 
@@ -106,6 +106,10 @@ void free_ctx(vdp_ctx* c) {
   cudaSetDevice(c->device);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->wexec) cudaGraphExecDestroy(c->wexec);
+  if (c->mg) {
+    mg_free(c->mg);
+    delete c->mg;
+  }
   void* bufs[] = {c->bx, c->by, c->bz, c->sinv, c->sx, c->sy, c->sz, c->sd, c->x, c->r, c->d0, c->d1,
                   c->za, c->zb, c->dch, c->spec, c->omega, c->sptab, c->rho_w, c->d_rounds,
                   c->q, c->part, c->ticket, c->st, c->desc, c->units, c->flag, c->stage_a,
@@ -172,6 +176,7 @@ int configure_layout(vdp_ctx* c, int prec) {
   d.cheb_k = c->opts.precond == VDP_PRECOND_CHEB ? c->opts.cheb_degree : 1;
   d.pc = c->opts.method == VDP_METHOD_FIXED_POINT ? PC_FIXED
          : c->opts.precond == VDP_PRECOND_SPECTRAL ? PC_SPECTRAL
+         : c->opts.precond == VDP_PRECOND_MG       ? PC_MG
                                                    : (d.cheb_k > 1 ? PC_CHEB : PC_JACOBI);
   {
     const double b = 2.0, a = b / kChebRange;
@@ -211,7 +216,10 @@ cudaError_t launch_round(vdp_ctx* c, int prec, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (c->lay.mode == 0)  // the residual sweep has its own kernel in the direct mode
     e = launch_res64(prec, c->desc, c->units, c->lay.nunits, c->lay.threads, s);
-  if (e == cudaSuccess && c->hdesc.pc >= PC_SPECTRAL) {  // z = M^-1 rt before the stencil sweep
+  if (e == cudaSuccess && c->hdesc.pc == PC_MG) {  // z = W M W rt by one V-cycle
+    const MgArgs a{c->r, c->za, c->omega, c->st, c->desc};
+    e = launch_mg_vcycle(*c->mg, prec, a, s);
+  } else if (e == cudaSuccess && c->hdesc.pc >= PC_SPECTRAL) {  // z = M^-1 rt first
     SpecArgs a;
     solve_spec_args(c, prec, &a);
     for (int pass = 0; pass < SPEC_PASSES && e == cudaSuccess; ++pass)
@@ -378,8 +386,47 @@ void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a) {
   (void)prec;
 }
 
+int ensure_mg(vdp_ctx* c) {
+  if (!mg_supported(c->nx, c->ny, c->nz)) return VDP_EINVAL;
+  cudaError_t e = cudaSuccess;
+  if (!c->za) e = cudaMalloc(&c->za, sizeof(double) * (size_t)c->n);
+  if (e == cudaSuccess && !c->omega) {
+    e = cudaMalloc((void**)&c->omega, sizeof(float) * (size_t)c->n);
+    c->omega_valid = false;
+  }
+  if (e == cudaSuccess && !c->mg) {
+    MgHier* h = new MgHier();
+    e = mg_alloc(h, c->nx, c->ny, c->nz);
+    if (e == cudaSuccess) {
+      c->mg = h;
+      c->mg_valid = false;
+    } else {
+      delete h;
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "multigrid buffers");
+  return VDP_OK;
+}
+
+int precond_launches(const vdp_ctx* c) {
+  if (c->hdesc.pc == PC_MG) return c->mg ? mg_launches(*c->mg, c->opts.precision) : 0;
+  return c->hdesc.pc >= PC_SPECTRAL ? SPEC_PASSES : 0;
+}
+
 int prepare_spectral_solve(vdp_ctx* c) {
   if (c->hdesc.pc < PC_SPECTRAL) return VDP_OK;
+  if (c->hdesc.pc == PC_MG) {
+    if (!c->mg) return VDP_EINVAL;
+    if (!c->omega_valid) {
+      VDP_CK(launch_omega(c->sinv, c->n, c->omega, c->stream));
+      c->omega_valid = true;
+    }
+    if (!c->mg_valid) {
+      VDP_CK(mg_setup(c->mg, c->bx, c->by, c->bz, c->sinv, c->stream));
+      c->mg_valid = true;
+    }
+    return VDP_OK;
+  }
   if (c->hdesc.pc == PC_FIXED && !c->rho_w_valid) return VDP_EINVAL;
   if (!c->omega_valid) {
     VDP_CK(launch_omega(c->sinv, c->n, c->omega, c->stream));
@@ -454,7 +501,10 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
   if (o->precision < VDP_FP64 || o->precision > VDP_MIXED_BF16) return VDP_EINVAL;
   if (o->max_iter < 1 || !(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return VDP_EINVAL;
   if (o->precond != VDP_PRECOND_JACOBI && o->precond != VDP_PRECOND_CHEB &&
-      o->precond != VDP_PRECOND_SPECTRAL)
+      o->precond != VDP_PRECOND_SPECTRAL && o->precond != VDP_PRECOND_MG)
+    return VDP_EINVAL;
+  if (o->precond == VDP_PRECOND_MG && o->method == VDP_METHOD_CG &&
+      (o->stencil != 0 || !mg_supported(c->nx, c->ny, c->nz)))
     return VDP_EINVAL;
   if (o->precond == VDP_PRECOND_SPECTRAL &&
       (o->stencil != 0 || !spectral_supported(c->nx, c->ny, c->nz)))
@@ -499,6 +549,13 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
       return sres;
     }
   }
+  if (o->precond == VDP_PRECOND_MG && o->method == VDP_METHOD_CG) {
+    const int mres = ensure_mg(c);
+    if (mres != VDP_OK) {
+      c->opts = old;
+      return mres;
+    }
+  }
   if (o->method == VDP_METHOD_FIXED_POINT && !c->rho_w) {
     cudaError_t e = cudaMalloc((void**)&c->rho_w, sizeof(float) * (size_t)c->n);
     if (e != cudaSuccess) {
@@ -539,6 +596,7 @@ int vdp_set_density(vdp_ctx* c, const double* rho) {
   c->scaled_prec = -1;
   c->omega_valid = false;
   c->rho_w_valid = false;
+  c->mg_valid = false;
   if (c->rho_w) {  // the fixed-point iteration's weight needs rho itself
     VDP_CK(launch_rho_weight(src, c->sinv, c->n, c->rho_w, c->stream));
     c->rho_w_valid = true;
@@ -580,7 +638,7 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
   VDP_CK(cudaEventRecord(c->ev0, c->stream));
   VDP_CK(launch_init(c->desc, drhs, dp, tol, c->opts.inner_tol, c->opts.max_iter,
                      c->opts.max_iter, c->opts.use_guess ? 1 : 0, prec, c->stream));
-  const int per_round = (c->lay.mode == 0 ? 3 : 2) + (c->hdesc.pc >= PC_SPECTRAL ? SPEC_PASSES : 0);
+  const int per_round = (c->lay.mode == 0 ? 3 : 2) + precond_launches(c);
   if (dev_loop) {  // the whole solve is one graph launch; the device decides when to stop
     VDP_CK(cudaMemsetAsync(c->d_rounds, 0, sizeof(unsigned), c->stream));
     VDP_CK(cudaGraphLaunch(c->wexec, c->stream));
@@ -669,6 +727,37 @@ int vdp_inverse_laplacian(vdp_ctx* c, const double* g, double* out) {
   a.I = nullptr;
   for (int pass = 0; pass < SPEC_PASSES; ++pass)
     VDP_CK(launch_spectral_pass(PREC_FP64, pass, a, c->stream));
+  VDP_CK(cudaStreamSynchronize(c->stream));
+  return VDP_OK;
+}
+
+int vdp_mg_levels(int nx, int ny, int nz) {
+  if (nx < 1 || ny < 1 || nz < 1) return 0;
+  int d[kMgMaxLevels][3];
+  return mg_level_dims(nx, ny, nz, d);
+}
+
+int vdp_mg_apply(vdp_ctx* c, const double* g, double* out) {
+  if (!c || !g || !out || g == out || !c->has_density) return VDP_EINVAL;
+  if (!is_device_ptr(g) || !is_device_ptr(out) || ((uintptr_t)g & 15) || ((uintptr_t)out & 15))
+    return VDP_EINVAL;
+  int s;
+  if ((s = ensure_mg(c)) != VDP_OK) return s;
+  if (!c->omega_valid) {
+    VDP_CK(launch_omega(c->sinv, c->n, c->omega, c->stream));
+    c->omega_valid = true;
+  }
+  if (!c->mg_valid) {
+    VDP_CK(mg_setup(c->mg, c->bx, c->by, c->bz, c->sinv, c->stream));
+    c->mg_valid = true;
+  }
+  // the cycle works in the solve's scaled variables: M g = D^-1/2 (W M W) (D^-1/2 g)
+  double* rt = static_cast<double*>(c->d0);  // FP64-sized work vectors of the context
+  double* z = static_cast<double*>(c->d1);
+  VDP_CK(launch_mg_scale(g, c->sinv, c->n, rt, c->stream));
+  const MgArgs a{rt, z, c->omega, nullptr, nullptr};
+  VDP_CK(launch_mg_vcycle(*c->mg, PREC_FP64, a, c->stream));
+  VDP_CK(launch_mg_scale(z, c->sinv, c->n, out, c->stream));
   VDP_CK(cudaStreamSynchronize(c->stream));
   return VDP_OK;
 }

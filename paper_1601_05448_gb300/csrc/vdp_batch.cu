@@ -272,6 +272,8 @@ int vdp_batch_add(vdp_batch* b, vdp_ctx* c, const double* rhs, double* p, double
   if ((c->opts.precond == VDP_PRECOND_SPECTRAL || c->opts.method == VDP_METHOD_FIXED_POINT) &&
       b->persistent)
     return VDP_EINVAL;
+  // the multigrid V-cycle runs in single solves only
+  if (c->opts.precond == VDP_PRECOND_MG && c->opts.method == VDP_METHOD_CG) return VDP_EINVAL;
   if (!is_device_ptr(rhs) || !is_device_ptr(p) || ((uintptr_t)rhs & 15) || ((uintptr_t)p & 15))
     return VDP_EINVAL;
   if (find(b, c, nullptr)) return VDP_EINVAL;  // already a member

@@ -7,6 +7,7 @@
 
 #include "vdp.h"
 #include "vdp_internal.cuh"
+#include "vdp_multigrid.h"
 
 namespace vdp {
 
@@ -44,6 +45,8 @@ struct vdp_ctx {
   bool omega_valid = false;        // omega matches the current density
   float* rho_w = nullptr;          // fixed-point iteration: rho D^1/2 per cell (FP32)
   bool rho_w_valid = false;        // rho_w was computed from the current density
+  vdp::MgHier* mg = nullptr;       // multigrid levels (VDP_PRECOND_MG, vdp_mg_apply)
+  bool mg_valid = false;           // the levels were built from the current density
   int scaled_prec = -1;            // precision the scaled coefficients were built for
   bool has_density = false;
   // bookkeeping
@@ -86,8 +89,14 @@ int ensure_spectral(vdp_ctx* c);
 // the arguments of the five spectral passes of a solve on this context (gated on its state)
 struct SpecArgs;
 void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a);
-// before a solve that uses the spectral passes: the weights for the current density
-// (VDP_EINVAL when the fixed-point method's density weight is missing)
+// allocate the multigrid levels and the z and omega buffers (no-op when present); VDP_EINVAL
+// for grids the V-cycle does not support
+int ensure_mg(vdp_ctx* c);
+// kernel launches of one application of the solve's preconditioner (spectral passes, V-cycle)
+int precond_launches(const vdp_ctx* c);
+// before a solve that uses the spectral passes or the V-cycle: the weights (and the multigrid
+// levels) for the current density (VDP_EINVAL when the fixed-point method's density weight is
+// missing)
 int prepare_spectral_solve(vdp_ctx* c);
 
 }  // namespace vdp

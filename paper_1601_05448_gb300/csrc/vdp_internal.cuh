@@ -27,14 +27,14 @@ enum Phase : int {
   PH_CORRECT = 4,  // p -= D^-1/2 x   (refinement step of the outer FP64 loop)
   PH_FINAL = 5,    // p -= <p>  (gauge)
   PH_CHEB = 6,     // one Chebyshev sweep of the polynomial preconditioner z = P(At) rt
-  PH_SPEC = 7,     // spectral preconditioner z = W (-L_h)^-1 W rt (five FFT passes)
+  PH_SPEC = 7,     // preconditioner z = M^-1 rt: five FFT passes (spectral) or a V-cycle (multigrid)
   PH_DONE = 8
 };
 
 // Preconditioner applied to the Jacobi-scaled inner system (InstDesc::pc).
 // PC_FIXED: not a preconditioner but the paper's fixed-point iteration, which applies the
 // spectral passes (with a density-weighted input) between FP64 residuals instead of running CG.
-enum PrecondKind : int { PC_JACOBI = 0, PC_CHEB = 1, PC_SPECTRAL = 2, PC_FIXED = 3 };
+enum PrecondKind : int { PC_JACOBI = 0, PC_CHEB = 1, PC_SPECTRAL = 2, PC_FIXED = 3, PC_MG = 4 };
 
 enum Prec : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_MIXED_BF16 = 2 };
 

@@ -227,18 +227,35 @@ __device__ __forceinline__ long long flat_begin(const InstDesc& I, int u) {
   return ((long long)u * (I.ncell / 8) / I.nunits_f) * 8;
 }
 
+// Vectors per thread kept in flight by the FP64 flat sweeps below: all loads of a round are issued
+// before the first use (one vector per thread per round left these sweeps latency bound).
+constexpr int kFlatU = 4;
+
+__device__ __forceinline__ double widen_t(float v) { return widen(v); }
+__device__ __forceinline__ double widen_t(double v) { return v; }
+
 // <f>, ||f||^2; p := 0 unless p is the caller's initial guess.
 __device__ void sweep_meanf(const InstDesc& I, const InstState* st, long long c0, long long c1,
                             double (&acc)[kSlots]) {
   const bool zero_p = !st->use_guess;
   double s[2] = {0.0, 0.0}, s2[2] = {0.0, 0.0};
-  for (long long c = c0 + 2 * threadIdx.x; c < c1; c += 2 * blockDim.x) {
-    const double2 fv = __ldg(reinterpret_cast<const double2*>(I.rhs + c));
-    s[0] += fv.x;
-    s[1] += fv.y;
-    s2[0] = fma(fv.x, fv.x, s2[0]);
-    s2[1] = fma(fv.y, fv.y, s2[1]);
-    if (zero_p) *reinterpret_cast<double2*>(I.p + c) = make_double2(0.0, 0.0);
+  const long long step = 2LL * blockDim.x;
+  for (long long cb = c0 + 2 * threadIdx.x; cb < c1; cb += kFlatU * step) {
+    double2 fv[kFlatU];
+#pragma unroll
+    for (int u = 0; u < kFlatU; ++u) {
+      const long long c = cb + u * step;
+      fv[u] = c < c1 ? __ldg(reinterpret_cast<const double2*>(I.rhs + c)) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < kFlatU; ++u) {
+      s[0] += fv[u].x;
+      s[1] += fv[u].y;
+      s2[0] = fma(fv[u].x, fv[u].x, s2[0]);
+      s2[1] = fma(fv[u].y, fv[u].y, s2[1]);
+      const long long c = cb + u * step;
+      if (zero_p && c < c1) *reinterpret_cast<double2*>(I.p + c) = make_double2(0.0, 0.0);
+    }
   }
   acc[0] = s[0] + s[1];
   acc[1] = s2[0] + s2[1];
@@ -249,13 +266,32 @@ template <class T>
 __device__ void sweep_correct(const InstDesc& I, long long c0, long long c1, double& psum) {
   const T* x = static_cast<const T*>(I.x);
   double s = 0.0;
-  for (long long c = c0 + 2 * threadIdx.x; c < c1; c += 2 * blockDim.x) {
-    const double2 sv = __ldg(reinterpret_cast<const double2*>(I.sinv + c));
-    double2 p = *reinterpret_cast<double2*>(I.p + c);
-    p.x = fma(-sv.x, (double)x[c], p.x);
-    p.y = fma(-sv.y, (double)x[c + 1], p.y);
-    *reinterpret_cast<double2*>(I.p + c) = p;
-    s += p.x + p.y;
+  const long long step = 2LL * blockDim.x;
+  constexpr int U = kFlatU / 2;  // four operands per vector: half the vectors in flight
+  for (long long cb = c0 + 2 * threadIdx.x; cb < c1; cb += U * step) {
+    double2 sv[U], pv[U];
+    T xa[U], xb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long c = cb + u * step;
+      if (c < c1) {
+        sv[u] = __ldg(reinterpret_cast<const double2*>(I.sinv + c));
+        pv[u] = *reinterpret_cast<const double2*>(I.p + c);
+        xa[u] = x[c];
+        xb[u] = x[c + 1];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long c = cb + u * step;
+      if (c < c1) {
+        double2 p = pv[u];
+        p.x = fma(-sv[u].x, widen_t(xa[u]), p.x);
+        p.y = fma(-sv[u].y, widen_t(xb[u]), p.y);
+        *reinterpret_cast<double2*>(I.p + c) = p;
+        s += p.x + p.y;
+      }
+    }
   }
   psum = s;
 }
@@ -264,10 +300,21 @@ __device__ void sweep_correct(const InstDesc& I, long long c0, long long c1, dou
 __device__ void sweep_final(const InstDesc& I, const InstState* st, long long c0, long long c1) {
   const double mp = st->sum_p / (double)I.ncell;
   const bool zero = st->zero_sol != 0;
-  for (long long c = c0 + 2 * threadIdx.x; c < c1; c += 2 * blockDim.x) {
-    double2 p = *reinterpret_cast<double2*>(I.p + c);
-    p = zero ? make_double2(0.0, 0.0) : make_double2(p.x - mp, p.y - mp);
-    *reinterpret_cast<double2*>(I.p + c) = p;
+  const long long step = 2LL * blockDim.x;
+  for (long long cb = c0 + 2 * threadIdx.x; cb < c1; cb += kFlatU * step) {
+    double2 pv[kFlatU];
+#pragma unroll
+    for (int u = 0; u < kFlatU; ++u) {
+      const long long c = cb + u * step;
+      if (c < c1) pv[u] = *reinterpret_cast<const double2*>(I.p + c);
+    }
+#pragma unroll
+    for (int u = 0; u < kFlatU; ++u) {
+      const long long c = cb + u * step;
+      if (c < c1)
+        *reinterpret_cast<double2*>(I.p + c) =
+            zero ? make_double2(0.0, 0.0) : make_double2(pv[u].x - mp, pv[u].y - mp);
+    }
   }
 }
 

@@ -23,55 +23,14 @@
 
 #include "vdp.h"
 #include "vdp_ctx.h"
+#include "vdp_march.cuh"
 
 using namespace vdp;
 
 namespace {
 
-constexpr int kTx = 32, kTy = 8;
+constexpr int kTx = kMarchTx, kTy = kMarchTy;
 constexpr int kMinBlocks = 6;  // 6 x 256 threads per SM: at most 40 registers
-
-// Work items are (32 x 8 column tile, z chunk) triples, taken round robin by a grid of exactly
-// the blocks that fit on the GPU at once (one wave: no tail of a partly filled second wave).  The
-// chunk length is chosen so that every block gets nearly the same number of items; a chunk reloads
-// the z-neighbour once at its start, so longer chunks are preferred among near-equal choices.
-struct MarchPlan {
-  int gx, gy, zlen, nzc, blocks, items;
-};
-
-MarchPlan march_plan(int nx, int ny, int nz, int resident) {
-  MarchPlan m;
-  m.gx = (nx + kTx - 1) / kTx;
-  m.gy = (ny + kTy - 1) / kTy;
-  const long long tiles = (long long)m.gx * m.gy;
-  const int R = resident > 0 ? resident : 1;
-  double best = -1.0;
-  m.zlen = 1;
-  for (int zl : {32, 24, 16, 12, 8, 6, 4, 3, 2, 1}) {
-    if (zl > nz && zl > 1) continue;
-    const long long items = tiles * ((nz + zl - 1) / zl);
-    const long long rounds = (items + R - 1) / R;
-    const double eff = (double)items / ((double)rounds * R);  // busy fraction of the block slots
-    if (eff > best + 0.02) {
-      best = eff;
-      m.zlen = zl;
-    }
-  }
-  m.nzc = (nz + m.zlen - 1) / m.zlen;
-  m.items = (int)(tiles * m.nzc);
-  m.blocks = (int)(m.items < R ? m.items : R);
-  return m;
-}
-
-template <class K>
-int resident_blocks(K kernel) {
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kTx * kTy, 0) != cudaSuccess)
-    return 152;
-  return sms * (per_sm > 0 ? per_sm : 1);
-}
 
 // f = ( hx ((bx mx)|_{x+} - bx mx) + hy (...) + hz (...) - rhs_div ) / c
 template <bool DIV>
@@ -83,12 +42,8 @@ __global__ void __launch_bounds__(kTx* kTy, kMinBlocks)
                      double hx, double hy, double hz, double inv_c, double* __restrict__ f) {
   const long long plane = (long long)nx * ny;
   for (int it = blockIdx.x; it < m.items; it += gridDim.x) {
-    const int r = it / m.gx;
-    const int x = (it - r * m.gx) * kTx + threadIdx.x;
-    const int y = (r % m.gy) * kTy + threadIdx.y;
-    const int z0 = (r / m.gy) * m.zlen;
-    if (x >= nx || y >= ny) continue;
-    const int z1 = min(nz, z0 + m.zlen);
+    int x, y, z0, z1;
+    if (!march_item(m, it, threadIdx.x, threadIdx.y, nx, ny, nz, x, y, z0, z1)) continue;
     const long long dxp = x == nx - 1 ? -(long long)(nx - 1) : 1;
     const long long dyp = y == ny - 1 ? -(long long)(ny - 1) * nx : (long long)nx;
     long long c = x + (long long)nx * y + plane * z0;
@@ -114,12 +69,8 @@ __global__ void __launch_bounds__(kTx* kTy, kMinBlocks)
                          double* __restrict__ my, double* __restrict__ mz) {
   const long long plane = (long long)nx * ny;
   for (int it = blockIdx.x; it < m.items; it += gridDim.x) {
-    const int r = it / m.gx;
-    const int x = (it - r * m.gx) * kTx + threadIdx.x;
-    const int y = (r % m.gy) * kTy + threadIdx.y;
-    const int z0 = (r / m.gy) * m.zlen;
-    if (x >= nx || y >= ny) continue;
-    const int z1 = min(nz, z0 + m.zlen);
+    int x, y, z0, z1;
+    if (!march_item(m, it, threadIdx.x, threadIdx.y, nx, ny, nz, x, y, z0, z1)) continue;
     const long long dxm = x == 0 ? (long long)(nx - 1) : -1;
     const long long dym = y == 0 ? (long long)(ny - 1) * nx : -(long long)nx;
     long long c = x + (long long)nx * y + plane * z0;

@@ -61,8 +61,11 @@ int launch_shape(int phase) {
   }
 }
 
-// graphs 3 .. 7: the five spectral passes (SPEC_X_FWD .. SPEC_X_INV)
-constexpr int kTimedGraphs = 3 + SPEC_PASSES;
+// graphs 3 .. 7: the five spectral passes (SPEC_X_FWD .. SPEC_X_INV); graph 8: one whole
+// multigrid V-cycle
+constexpr int kTimedGraphs = 3 + SPEC_PASSES + 1;
+constexpr int kMgGraph = 3 + SPEC_PASSES;
+constexpr int kMgPass = 1000;  // capture_timed: the V-cycle instead of a spectral pass
 constexpr int kSpecKind[SPEC_PASSES] = {VDP_SWEEP_SPEC_X, VDP_SWEEP_SPEC_Y, VDP_SWEEP_SPEC_Z,
                                         VDP_SWEEP_SPEC_Y, VDP_SWEEP_SPEC_X};
 
@@ -85,7 +88,10 @@ cudaError_t capture_timed(vdp_ctx* c, int prec, int phase, int spec_pass, TimedG
   if (e != cudaSuccess) return e;
   cudaError_t e2 = cudaEventRecordWithFlags(t.e0, c->cap, cudaEventRecordExternal);
   if (e2 == cudaSuccess) {
-    if (spec_pass >= 0) {
+    if (spec_pass == kMgPass) {
+      const MgArgs a{c->r, c->za, c->omega, c->st, c->desc};
+      e2 = launch_mg_vcycle(*c->mg, prec, a, c->cap);
+    } else if (spec_pass >= 0) {
       SpecArgs a;
       solve_spec_args(c, prec, &a);
       e2 = launch_spectral_pass(prec, spec_pass, a, c->cap);
@@ -123,12 +129,15 @@ extern "C" int vdp_solve_timed(vdp_ctx* c, const double* rhs, double* p, double 
   VDP_CK(cudaEventCreate(&t.e1));
   const int shape_phase[3] = {PH_RES64, PH_STENCIL, PH_UPDATE};
   for (int i = 0; i < 3; ++i) VDP_CK(capture_timed(c, prec, shape_phase[i], -1, t, &t.g[i]));
-  const bool spectral = c->hdesc.pc >= PC_SPECTRAL;
-  if (spectral) {
+  const bool mg = c->hdesc.pc == PC_MG;
+  const bool spectral = c->hdesc.pc >= PC_SPECTRAL && !mg;
+  if (spectral || mg) {
     if ((s = prepare_spectral_solve(c)) != VDP_OK) return s;
+  }
+  if (spectral)
     for (int i = 0; i < SPEC_PASSES; ++i)
       VDP_CK(capture_timed(c, prec, PH_SPEC, i, t, &t.g[3 + i]));
-  }
+  if (mg) VDP_CK(capture_timed(c, prec, PH_SPEC, kMgPass, t, &t.g[kMgGraph]));
   auto fail = [&](cudaError_t e, const char* where) { return cuda_fail(e, where); };
   cudaError_t e;
   if ((e = cudaEventRecord(c->ev0, c->stream)) != cudaSuccess) return fail(e, "cudaEventRecord");
@@ -150,11 +159,11 @@ extern "C" int vdp_solve_timed(vdp_ctx* c, const double* rhs, double* p, double 
       break;
     }
     const bool spec = spectral && hs.phase == PH_SPEC;
+    const bool vcyc = mg && hs.phase == PH_SPEC;
     for (int pass = 0; pass < (spec ? SPEC_PASSES : 1); ++pass) {
-      const int kind = spec ? kSpecKind[pass] : sweep_kind(hs.phase);
-      if ((e = cudaGraphLaunch(t.g[spec ? 3 + pass : launch_shape(hs.phase)], c->stream)) !=
-          cudaSuccess)
-        return fail(e, "sweep launch");
+      const int kind = spec ? kSpecKind[pass] : (vcyc ? VDP_SWEEP_MG : sweep_kind(hs.phase));
+      const int gi = spec ? 3 + pass : (vcyc ? kMgGraph : launch_shape(hs.phase));
+      if ((e = cudaGraphLaunch(t.g[gi], c->stream)) != cudaSuccess) return fail(e, "sweep launch");
       if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
         return fail(e, "cudaStreamSynchronize");
       float ms = 0.f;

@@ -83,3 +83,12 @@ def test_batch_tuning_keeps_to_batchable_layouts():
         assert bc and all(c["stencil"] == 0 and "steps_per_sync" not in c for c in bc)
         assert any(c["stencil"] == 1 for c in allc)
         assert tune._key(n, n, n, prec) != tune._key(n, n, n, prec, batchable=True)
+
+
+def test_multigrid_level_rule_matches_the_oracle():
+    from oracle import multigrid as MG
+    for nx, ny, nz in ((256, 256, 256), (48, 48, 48), (40, 24, 16), (64, 48, 64), (8, 8, 1), (16, 8, 8),
+                       (48, 36, 40), (24, 9, 16), (512, 512, 512), (80, 80, 80)):
+        shapes = MG.level_shapes(nx, ny, nz)
+        want = len(shapes) if shapes and len(shapes) > 1 else 0   # the library needs a coarser level
+        assert vdp.vdp_mg_levels(nx, ny, nz) == want, (nx, ny, nz)
