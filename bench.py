@@ -93,6 +93,10 @@ def sweep_cost(prec: str, kind: str, cheb_k: int = 1, nx: int = 256, fixed: bool
         return (3 * T + 8 + 2 * S) / 2, 0.0
     if kind in ("spec_y", "spec_z"):
         return 2 * S, 0.0
+    if kind == "mg":  # one V-cycle: level 0 down 24 B, restriction 4.5, prolongation 12, up 24
+        # (FP32 rt, bt, W, t, z), the coarser levels 68.5 B per cell x 1/7 of the fine cells; an
+        # FP64 solve adds the rounding of rt (12 B) and its FP64 z (4 B)
+        return 64.5 + 68.5 / 7.0 + (16.0 if prec == "fp64" else 0.0), 0.0
     if kind == "stencil":
         if prec == "fp64":
             return 5 * T + 3 * B, 18.0
@@ -411,6 +415,27 @@ def run_projection(torch, vdp, dev, solver, prob, stream, peaks, steps=5):
     return out
 
 
+def run_mg_non_fft(torch, vdp, dev, stream, n=160):
+    """A grid the FFT passes cannot take (160 = 2^5 x 5): the hot-spot recipe (hot spots scaled by
+    volume, density ratio 4), mixed to 1e-8, by CG with the multigrid V-cycle and with Jacobi."""
+    import vdp_inputs as V
+    prob = V.hotspot_problem(n, seed=2, nspots=int(round(20000 * n ** 3 / 256 ** 3)), tol=1e-8,
+                             target_ratio=4.0)
+    rho = torch.from_numpy(prob.rho).to(dev)
+    f = torch.from_numpy(prob.f).to(dev)
+    out = {"grid": [n, n, n], "tol": 1e-8, "precision": "mixed",
+           "fft_supported": vdp.spectral_supported(n, n, n)}
+    for name, pc in (("mg", vdp.VDP_PRECOND_MG), ("jacobi", vdp.VDP_PRECOND_JACOBI)):
+        with vdp.Solver(n, n, n, prob.L, precision="mixed", stream=stream, precond=pc) as s:
+            s.set_density(rho)
+            p = torch.empty_like(f)
+            s.solve(f, p, 1e-8)
+            ts = [s.solve(f, p, 1e-8) for _ in range(3)]
+        b = min(ts, key=lambda x: x.ms)
+        out[name] = {"solves_per_s": 1e3 / b.ms, "ms": b.ms, "iters": b.iters, "status": vdp.vdp_strerror(b.status)}
+    return out
+
+
 def run_serving(torch, vdp, dev, pool, count=200):
     """Config 4 (first `count` requests of the Poisson stream, lambda = 200/s)."""
     import vdp_inputs as V
@@ -596,7 +621,8 @@ def main():
                     "mixed_bf16_fixed_point": ("mixed_bf16", "fixed_point", 1),
                     "mixed_bf16_spectral": ("mixed_bf16", "spectral", 1), "fp64_jacobi": ("fp64", "jacobi", 1),
                     "mixed_jacobi": ("mixed", "jacobi", 1), "mixed_cheb3": ("mixed", "cheb", 3),
-                    "mixed_bf16_jacobi": ("mixed_bf16", "jacobi", 1)}
+                    "mixed_bf16_jacobi": ("mixed_bf16", "jacobi", 1), "fp64_mg": ("fp64", "mg", 1),
+                    "mixed_mg": ("mixed", "mg", 1)}
         for label, (prec, pc, k) in variants.items():
             opts = ({"method": vdp.VDP_METHOD_FIXED_POINT, "inner_tol": 1e-5} if pc == "fixed_point"
                     else {"precond": PRECONDS[pc]})
@@ -648,6 +674,15 @@ def main():
                 tj = [sj.solve(f, pj, prob.tol) for _ in range(2)]
             bj = min(tj, key=lambda x: x.ms)
             line["fp64_jacobi_1e-10"] = {"solves_per_s": 1e3 / bj.ms, "ms": bj.ms, "iters": bj.iters}
+            # ... and with the multigrid V-cycle preconditioner
+            with vdp.Solver(nx, ny, nz, prob.L, precision="fp64", stream=stream, precond=vdp.VDP_PRECOND_MG) as sm:
+                sm.set_density(rho)
+                pm = torch.empty_like(f)
+                sm.solve(f, pm, prob.tol)
+                tm = [sm.solve(f, pm, prob.tol) for _ in range(3)]
+            bm = min(tm, key=lambda x: x.ms)
+            line["fp64_cg_mg_1e-10"] = {"solves_per_s": 1e3 / bm.ms, "ms": bm.ms, "iters": bm.iters}
+            line["mg_non_fft_grid"] = run_mg_non_fft(torch, vdp, dev, stream)
             line["projection_step"] = run_projection(torch, vdp, dev, solver, prob, stream, peaks)
             try:
                 line["cpu_baseline"] = cpu_baseline(prob)
