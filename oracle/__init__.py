@@ -13,6 +13,10 @@ What it computes (Pouransari, Mortazavi & Mani, arXiv:1601.05448):
     residual.
   * ``solve_fixed_point``: the paper's own iteration of Eq. (Pois) (Sec. 3.4), with the
     constant-coefficient inverse applied through a plain DFT; an independent second solver.
+  * ``geom=(Lx, Ly, Lz, bc_x)`` on the functions above: per-direction box lengths and, with
+    bc_x = 1, the inflow-outflow duct of Sec. 3.2 (periodic y, z; no pressure flux through the x
+    ends -- a reading, the paper does not state the pressure condition), whose constant-
+    coefficient inverse uses a plain cosine transform along x.
 
   * ``projection_rhs`` / ``projection_correct`` / ``project``: the steps either side of the solve
     in App. A -- the Poisson right side (div((rho u)~ / rho_new) - RHS^div) / (C_pre dt) and the
@@ -77,6 +81,16 @@ def _load():
             lib.vdpo_inverse_laplacian.restype = None
             lib.vdpo_solve_fixed_point.argtypes = [i, i, i, d, pd, pd, pd, d, i, d, pd]
             lib.vdpo_solve_fixed_point.restype = i
+            lib.vdpo_face_coefficients_g.argtypes = [i, i, i, d, d, d, i, pd, pd, pd, pd]
+            lib.vdpo_face_coefficients_g.restype = i
+            lib.vdpo_relative_residual_g.argtypes = [i, i, i, d, d, d, i, pd, pd, pd]
+            lib.vdpo_relative_residual_g.restype = d
+            lib.vdpo_solve_cg_g.argtypes = [i, i, i, d, d, d, i, pd, pd, pd, d, i, pd]
+            lib.vdpo_solve_cg_g.restype = i
+            lib.vdpo_inverse_laplacian_g.argtypes = [i, i, i, d, d, d, i, pd, pd]
+            lib.vdpo_inverse_laplacian_g.restype = None
+            lib.vdpo_solve_fixed_point_g.argtypes = [i, i, i, d, d, d, i, pd, pd, pd, d, i, d, pd]
+            lib.vdpo_solve_fixed_point_g.restype = i
             lib.vdpo_divergence.argtypes = [i, i, i, d, pd, pd, pd, pd]
             lib.vdpo_divergence.restype = None
             lib.vdpo_face_velocity.argtypes = [i, i, i, pd, pd, pd, pd, pd, pd, pd]
@@ -119,11 +133,21 @@ def dot(x, y) -> float:
     return _load().vdpo_dot(*_dims(x), _ptr(x), _ptr(y))
 
 
-def face_coefficients(rho, L: float):
-    """(bx, by, bz): coefficient of the low face of every cell, 1/rho_face/h^2."""
+def _geom(L, geom):
+    """(Lx, Ly, Lz, bc_x): the cube of side L (periodic) unless geom is given."""
+    if geom is None:
+        return float(L), float(L), float(L), 0
+    Lx, Ly, Lz, bc_x = geom
+    return float(Lx), float(Ly), float(Lz), int(bc_x)
+
+
+def face_coefficients(rho, L: float, geom=None):
+    """(bx, by, bz): coefficient of the low face of every cell, 1/rho_face/h^2.  geom = (Lx, Ly,
+    Lz, bc_x) selects per-direction lengths and, with bc_x = 1, the inflow-outflow duct (no flux
+    through the x ends: bx = 0 on the faces of cells i = 0)."""
     rho = _f64(rho)
     bx, by, bz = (np.empty_like(rho) for _ in range(3))
-    st = _load().vdpo_face_coefficients(*_dims(rho), float(L), _ptr(rho), _ptr(bx), _ptr(by), _ptr(bz))
+    st = _load().vdpo_face_coefficients_g(*_dims(rho), *_geom(L, geom), _ptr(rho), _ptr(bx), _ptr(by), _ptr(bz))
     if st != 0:
         raise ValueError(f"face_coefficients: {STATUS.get(st, st)}")
     return bx, by, bz
@@ -138,41 +162,43 @@ def apply(b, p) -> np.ndarray:
     return out
 
 
-def apply_rho(rho, L: float, p) -> np.ndarray:
-    return apply(face_coefficients(rho, L), p)
+def apply_rho(rho, L: float, p, geom=None) -> np.ndarray:
+    return apply(face_coefficients(rho, L, geom), p)
 
 
-def relative_residual(rho, L: float, f, p) -> float:
+def relative_residual(rho, L: float, f, p, geom=None) -> float:
     """||(f - <f>) - A p||_2 / ||f - <f>||_2 evaluated with the oracle's operator."""
     rho, f, p = _f64(rho), _f64(f), _f64(p)
-    return _load().vdpo_relative_residual(*_dims(rho), float(L), _ptr(rho), _ptr(f), _ptr(p))
+    return _load().vdpo_relative_residual_g(*_dims(rho), *_geom(L, geom), _ptr(rho), _ptr(f), _ptr(p))
 
 
-def solve_cg(rho, f, L: float, tol: float = 1e-13, maxit: int = 100000):
+def solve_cg(rho, f, L: float, tol: float = 1e-13, maxit: int = 100000, geom=None):
     """Zero-mean p with A p = f - <f>; returns (p, info) with info keys iters, rel_res, rhs_mean, status."""
     rho, f = _f64(rho), _f64(f)
     p = np.empty_like(f)
     info = np.zeros(3)
-    st = _load().vdpo_solve_cg(*_dims(f), float(L), _ptr(rho), _ptr(f), _ptr(p), float(tol), int(maxit), _ptr(info))
+    st = _load().vdpo_solve_cg_g(*_dims(f), *_geom(L, geom), _ptr(rho), _ptr(f), _ptr(p), float(tol), int(maxit),
+                                 _ptr(info))
     return p, {"iters": int(info[0]), "rel_res": float(info[1]), "rhs_mean": float(info[2]),
                "status": STATUS.get(st, st)}
 
 
-def inverse_laplacian(g, L: float) -> np.ndarray:
-    """Constant-coefficient periodic 7-point Laplacian inverse (zero mode removed), by plain DFT."""
+def inverse_laplacian(g, L: float, geom=None) -> np.ndarray:
+    """Constant-coefficient 7-point Laplacian inverse (zero mode removed), by plain DFTs (a plain
+    cosine transform along x in the duct)."""
     g = _f64(g)
     out = np.empty_like(g)
-    _load().vdpo_inverse_laplacian(*_dims(g), float(L), _ptr(g), _ptr(out))
+    _load().vdpo_inverse_laplacian_g(*_dims(g), *_geom(L, geom), _ptr(g), _ptr(out))
     return out
 
 
-def solve_fixed_point(rho, f, L: float, tol: float = 1e-12, maxit: int = 1000, omega: float = 1.0):
+def solve_fixed_point(rho, f, L: float, tol: float = 1e-12, maxit: int = 1000, omega: float = 1.0, geom=None):
     """The paper's iteration of Eq. (Pois); returns (p, info) like solve_cg."""
     rho, f = _f64(rho), _f64(f)
     p = np.empty_like(f)
     info = np.zeros(3)
-    st = _load().vdpo_solve_fixed_point(*_dims(f), float(L), _ptr(rho), _ptr(f), _ptr(p), float(tol), int(maxit),
-                                        float(omega), _ptr(info))
+    st = _load().vdpo_solve_fixed_point_g(*_dims(f), *_geom(L, geom), _ptr(rho), _ptr(f), _ptr(p), float(tol),
+                                          int(maxit), float(omega), _ptr(info))
     return p, {"iters": int(info[0]), "rel_res": float(info[1]), "rhs_mean": float(info[2]),
                "status": STATUS.get(st, st)}
 

@@ -13,7 +13,9 @@
  * header, table or constant with it, and neither side calls the other.
  *
  * Layout: every field is n = nx*ny*nz doubles, cell (i,j,k) at index c = i + nx*(j + ny*k)
- * (x fastest); spacing h_d = L / n_d; neighbours wrap periodically.  Face arrays bx, by, bz hold
+ * (x fastest); spacing h_d = L / n_d; neighbours wrap periodically.  The `_g` entry points take
+ * the box lengths per direction and the boundary condition in x: periodic, or the inflow-outflow
+ * duct of Sec. 3.2 (case 2), where the pressure has no flux through the two x ends (see geom).  Face arrays bx, by, bz hold
  * one coefficient per cell: bx[c] belongs to the LOW x-face of cell c, i.e. the face shared by
  * cells (i-1,j,k) and (i,j,k); likewise by, bz.
  *
@@ -107,13 +109,36 @@ double vdpo_mean(int nx, int ny, int nz, const double *x) {
 
 /* ---- face coefficients (Sec. 3.1 staggered layout, App. B averaging) ------------------------ */
 
-int vdpo_face_coefficients(int nx, int ny, int nz, double L, const double *rho, double *bx,
-                           double *by, double *bz) {
-  if (nx < 1 || ny < 1 || nz < 1 || !(L > 0.0)) return VDPO_EINVAL;
+/*
+ * Geometry: box lengths per direction and the boundary condition in x.  bc_x = 0: periodic (the
+ * triply periodic box, Sec. 3.2 case 1).  bc_x = 1: the inflow-outflow duct (Sec. 3.2 case 2):
+ * periodic in y and z, and the pressure has no flux through the inflow and outflow faces
+ * (homogeneous Neumann; the paper does not state the pressure condition, this is the reading
+ * taken).  The face at x = 0 and the face at x = Lx share the storage slot bx[i = 0], whose
+ * coefficient is then 0: no term couples cell 0 with cell nx - 1.
+ */
+typedef struct {
+  double Lx, Ly, Lz;
+  int bc_x;
+} geom;
+
+static geom cube(double L) {
+  geom g = {L, L, L, 0};
+  return g;
+}
+
+static int geom_ok(geom g) {
+  return g.Lx > 0.0 && g.Ly > 0.0 && g.Lz > 0.0 && isfinite(g.Lx) && isfinite(g.Ly) &&
+         isfinite(g.Lz) && (g.bc_x == 0 || g.bc_x == 1);
+}
+
+static int face_coefficients_g(int nx, int ny, int nz, geom G, const double *rho, double *bx,
+                               double *by, double *bz) {
+  if (nx < 1 || ny < 1 || nz < 1 || !geom_ok(G)) return VDPO_EINVAL;
   long n = (long)nx * ny * nz;
   for (long c = 0; c < n; ++c)
     if (!(rho[c] > 0.0) || !isfinite(rho[c])) return VDPO_EDENSITY;
-  double hx = L / nx, hy = L / ny, hz = L / nz;
+  double hx = G.Lx / nx, hy = G.Ly / ny, hz = G.Lz / nz;
 #pragma omp parallel for schedule(static)
   for (long k = 0; k < nz; ++k)
     for (long j = 0; j < ny; ++j)
@@ -123,11 +148,22 @@ int vdpo_face_coefficients(int nx, int ny, int nz, double L, const double *rho, 
         double rx = 0.5 * (rho[idx(i - 1, j, k, nx, ny, nz)] + rho[c]);
         double ry = 0.5 * (rho[idx(i, j - 1, k, nx, ny, nz)] + rho[c]);
         double rz = 0.5 * (rho[idx(i, j, k - 1, nx, ny, nz)] + rho[c]);
-        bx[c] = (1.0 / rx) / (hx * hx);
+        bx[c] = (G.bc_x == 1 && i == 0) ? 0.0 : (1.0 / rx) / (hx * hx);  /* duct: no x wrap */
         by[c] = (1.0 / ry) / (hy * hy);
         bz[c] = (1.0 / rz) / (hz * hz);
       }
   return VDPO_OK;
+}
+
+int vdpo_face_coefficients(int nx, int ny, int nz, double L, const double *rho, double *bx,
+                           double *by, double *bz) {
+  return face_coefficients_g(nx, ny, nz, cube(L), rho, bx, by, bz);
+}
+
+int vdpo_face_coefficients_g(int nx, int ny, int nz, double Lx, double Ly, double Lz, int bc_x,
+                             const double *rho, double *bx, double *by, double *bz) {
+  geom G = {Lx, Ly, Lz, bc_x};
+  return face_coefficients_g(nx, ny, nz, G, rho, bx, by, bz);
 }
 
 /* ---- the discrete operator A ~ div((1/rho) grad .)  (Sec. 3.4) ------------------------------ */
@@ -174,15 +210,15 @@ static double true_residual(int nx, int ny, int nz, const double *bx, const doub
   return sqrt(vdpo_dot(nx, ny, nz, r, r)) / f0norm;
 }
 
-double vdpo_relative_residual(int nx, int ny, int nz, double L, const double *rho,
-                              const double *f, const double *p) {
+static double relative_residual_g(int nx, int ny, int nz, geom G, const double *rho,
+                                  const double *f, const double *p) {
   long n = (long)nx * ny * nz;
   double *bx = malloc(sizeof(double) * n), *by = malloc(sizeof(double) * n);
   double *bz = malloc(sizeof(double) * n), *f0 = malloc(sizeof(double) * n);
   double *r = malloc(sizeof(double) * n);
   double res = -1.0;
   if (bx && by && bz && f0 && r &&
-      vdpo_face_coefficients(nx, ny, nz, L, rho, bx, by, bz) == VDPO_OK) {
+      face_coefficients_g(nx, ny, nz, G, rho, bx, by, bz) == VDPO_OK) {
     double mf = vdpo_mean(nx, ny, nz, f);
     for (long c = 0; c < n; ++c) f0[c] = f[c] - mf;
     double fn = sqrt(vdpo_dot(nx, ny, nz, f0, f0));
@@ -193,6 +229,17 @@ double vdpo_relative_residual(int nx, int ny, int nz, double L, const double *rh
   return res;
 }
 
+double vdpo_relative_residual(int nx, int ny, int nz, double L, const double *rho,
+                              const double *f, const double *p) {
+  return relative_residual_g(nx, ny, nz, cube(L), rho, f, p);
+}
+
+double vdpo_relative_residual_g(int nx, int ny, int nz, double Lx, double Ly, double Lz, int bc_x,
+                                const double *rho, const double *f, const double *p) {
+  geom G = {Lx, Ly, Lz, bc_x};
+  return relative_residual_g(nx, ny, nz, G, rho, f, p);
+}
+
 /*
  * Solver 1: Jacobi-preconditioned conjugate gradients on the symmetric positive semi-definite
  * system (-A) p = -(f - <f>), started from p = 0 so every iterate stays mean-free in exact
@@ -200,8 +247,8 @@ double vdpo_relative_residual(int nx, int ny, int nz, double L, const double *rh
  * stop (on a miss the true residual replaces the recursive one and the search restarts).
  * info[0] = iterations, info[1] = final relative residual, info[2] = <f> removed (chi' of App. A).
  */
-int vdpo_solve_cg(int nx, int ny, int nz, double L, const double *rho, const double *f, double *p,
-                  double tol, int maxit, double *info) {
+static int solve_cg_g(int nx, int ny, int nz, geom G, const double *rho, const double *f,
+                      double *p, double tol, int maxit, double *info) {
   long n = (long)nx * ny * nz;
   int status = VDPO_OK;
   double *bx = malloc(sizeof(double) * n), *by = malloc(sizeof(double) * n);
@@ -211,7 +258,7 @@ int vdpo_solve_cg(int nx, int ny, int nz, double L, const double *rho, const dou
   double *q = malloc(sizeof(double) * n);
   info[0] = 0; info[1] = 0; info[2] = 0;
   if (!bx || !by || !bz || !dg || !f0 || !r || !z || !d || !q) { status = VDPO_ENOMEM; goto done; }
-  status = vdpo_face_coefficients(nx, ny, nz, L, rho, bx, by, bz);
+  status = face_coefficients_g(nx, ny, nz, G, rho, bx, by, bz);
   if (status != VDPO_OK) goto done;
   neg_diagonal(nx, ny, nz, bx, by, bz, dg);
 
@@ -268,6 +315,18 @@ done:
   return status;
 }
 
+int vdpo_solve_cg(int nx, int ny, int nz, double L, const double *rho, const double *f, double *p,
+                  double tol, int maxit, double *info) {
+  return solve_cg_g(nx, ny, nz, cube(L), rho, f, p, tol, maxit, info);
+}
+
+int vdpo_solve_cg_g(int nx, int ny, int nz, double Lx, double Ly, double Lz, int bc_x,
+                    const double *rho, const double *f, double *p, double tol, int maxit,
+                    double *info) {
+  geom G = {Lx, Ly, Lz, bc_x};
+  return solve_cg_g(nx, ny, nz, G, rho, f, p, tol, maxit, info);
+}
+
 /* ---- Solver 2: the paper's iteration, Eq. (Pois) of Sec. 3.4 -------------------------------- */
 
 /*
@@ -312,28 +371,84 @@ static void dft_axis(int nx, int ny, int nz, double *re, double *im, int axis, i
 }
 
 /*
- * out = L_h^{-1} g for the constant-coefficient 7-point Laplacian L_h (coefficient 1/h_d^2 on
- * every face) on the periodic grid, with the k = 0 mode set to zero.  Eigenvalues of L_h:
- *   lambda(k) = -sum_d 4 sin^2(pi k_d / n_d) / h_d^2.
+ * Plain cosine transforms along x of a real 3-D array (the eigenvectors of the x second
+ * difference with zero flux through both ends, cell-centred: cos(pi k (2i + 1) / (2 nx))).
+ * Forward: C_k = sum_i v_i cos(pi k (2i + 1) / (2 nx)).  Inverse:
+ * v_i = (C_0 + 2 sum_{k >= 1} C_k cos(pi k (2i + 1) / (2 nx))) / nx.  O(nx^2) per line.
  */
-void vdpo_inverse_laplacian(int nx, int ny, int nz, double L, const double *g, double *out) {
+static void dct_x(int nx, int ny, int nz, double *v, int inverse) {
+  long nlines = (long)ny * nz;
+  double *cs = malloc(sizeof(double) * (size_t)nx * nx);
+  for (int k = 0; k < nx; ++k)
+    for (int i = 0; i < nx; ++i) cs[(long)k * nx + i] = cos(M_PI * k * (2.0 * i + 1.0) / (2.0 * nx));
+#pragma omp parallel
+  {
+    double *line = malloc(sizeof(double) * nx);
+#pragma omp for schedule(static)
+    for (long l = 0; l < nlines; ++l) {
+      double *row = v + l * nx;
+      for (int a = 0; a < nx; ++a) line[a] = row[a];
+      for (int o = 0; o < nx; ++o) {
+        double s = 0.0;
+        if (!inverse) {
+          for (int i = 0; i < nx; ++i) s += line[i] * cs[(long)o * nx + i];
+        } else {
+          s = line[0];
+          for (int k = 1; k < nx; ++k) s += 2.0 * line[k] * cs[(long)k * nx + o];
+          s /= nx;
+        }
+        row[o] = s;
+      }
+    }
+    free(line);
+  }
+  free(cs);
+}
+
+/*
+ * out = L_h^{-1} g for the constant-coefficient 7-point Laplacian L_h (coefficient 1/h_d^2 on
+ * every face; in the duct no face at the x ends) with the zero mode set to zero.  Eigenvalues:
+ *   periodic x:  lambda(k) = -sum_d 4 sin^2(pi k_d / n_d) / h_d^2 (Fourier modes in x, y, z);
+ *   duct:        lambda(k) = -4 sin^2(pi k_x / (2 n_x)) / h_x^2 - (the y, z terms) (cosine modes
+ *                in x, Fourier modes in y, z).
+ */
+static void inverse_laplacian_g(int nx, int ny, int nz, geom G, const double *g, double *out) {
   long n = (long)nx * ny * nz;
-  double hx = L / nx, hy = L / ny, hz = L / nz;
+  double hx = G.Lx / nx, hy = G.Ly / ny, hz = G.Lz / nz;
   double *re = malloc(sizeof(double) * n), *im = calloc((size_t)n, sizeof(double));
   memcpy(re, g, sizeof(double) * n);
-  for (int a = 0; a < 3; ++a) dft_axis(nx, ny, nz, re, im, a, -1);
+  if (G.bc_x == 1) dct_x(nx, ny, nz, re, 0);
+  else dft_axis(nx, ny, nz, re, im, 0, -1);
+  for (int a = 1; a < 3; ++a) dft_axis(nx, ny, nz, re, im, a, -1);
   for (long k = 0; k < nz; ++k)
     for (long j = 0; j < ny; ++j)
       for (long i = 0; i < nx; ++i) {
         long c = i + nx * (j + ny * k);
-        double sx = sin(M_PI * i / nx), sy = sin(M_PI * j / ny), sz = sin(M_PI * k / nz);
+        double sx = G.bc_x == 1 ? sin(M_PI * i / (2.0 * nx)) : sin(M_PI * i / nx);
+        double sy = sin(M_PI * j / ny), sz = sin(M_PI * k / nz);
         double lam = -4.0 * (sx * sx / (hx * hx) + sy * sy / (hy * hy) + sz * sz / (hz * hz));
         if (c == 0) { re[c] = 0.0; im[c] = 0.0; }
         else { re[c] /= lam; im[c] /= lam; }
       }
-  for (int a = 0; a < 3; ++a) dft_axis(nx, ny, nz, re, im, a, +1);
-  for (long c = 0; c < n; ++c) out[c] = re[c] / (double)n;
+  for (int a = 2; a >= 1; --a) dft_axis(nx, ny, nz, re, im, a, +1);
+  if (G.bc_x == 1) {
+    dct_x(nx, ny, nz, re, 1);
+    for (long c = 0; c < n; ++c) out[c] = re[c] / ((double)ny * nz);
+  } else {
+    dft_axis(nx, ny, nz, re, im, 0, +1);
+    for (long c = 0; c < n; ++c) out[c] = re[c] / (double)n;
+  }
   free(re); free(im);
+}
+
+void vdpo_inverse_laplacian(int nx, int ny, int nz, double L, const double *g, double *out) {
+  inverse_laplacian_g(nx, ny, nz, cube(L), g, out);
+}
+
+void vdpo_inverse_laplacian_g(int nx, int ny, int nz, double Lx, double Ly, double Lz, int bc_x,
+                              const double *g, double *out) {
+  geom G = {Lx, Ly, Lz, bc_x};
+  inverse_laplacian_g(nx, ny, nz, G, g, out);
 }
 
 /*
@@ -346,8 +461,9 @@ void vdpo_inverse_laplacian(int nx, int ny, int nz, double L, const double *g, d
  * omega (1 = the paper's update) scales dp.  Its fixed point is the solution of A p = f0.
  * info[0] = iterations, info[1] = final relative residual, info[2] = <f>.
  */
-int vdpo_solve_fixed_point(int nx, int ny, int nz, double L, const double *rho, const double *f,
-                           double *p, double tol, int maxit, double omega, double *info) {
+static int solve_fixed_point_g(int nx, int ny, int nz, geom G, const double *rho,
+                               const double *f, double *p, double tol, int maxit, double omega,
+                               double *info) {
   long n = (long)nx * ny * nz;
   int status = VDPO_OK;
   double *bx = malloc(sizeof(double) * n), *by = malloc(sizeof(double) * n);
@@ -355,7 +471,7 @@ int vdpo_solve_fixed_point(int nx, int ny, int nz, double L, const double *rho, 
   double *r = malloc(sizeof(double) * n), *dp = malloc(sizeof(double) * n);
   info[0] = 0; info[1] = 0; info[2] = 0;
   if (!bx || !by || !bz || !f0 || !r || !dp) { status = VDPO_ENOMEM; goto done; }
-  status = vdpo_face_coefficients(nx, ny, nz, L, rho, bx, by, bz);
+  status = face_coefficients_g(nx, ny, nz, G, rho, bx, by, bz);
   if (status != VDPO_OK) goto done;
   double mf = vdpo_mean(nx, ny, nz, f);
   info[2] = mf;
@@ -367,7 +483,7 @@ int vdpo_solve_fixed_point(int nx, int ny, int nz, double L, const double *rho, 
   while (res > tol) {
     if (it >= maxit || !isfinite(res)) { status = VDPO_ENOTCONV; break; }
     for (long c = 0; c < n; ++c) r[c] *= rho[c]; /* rho (f0 - A p_g) */
-    vdpo_inverse_laplacian(nx, ny, nz, L, r, dp);
+    inverse_laplacian_g(nx, ny, nz, G, r, dp);
     for (long c = 0; c < n; ++c) p[c] += omega * dp[c];
     ++it;
     res = true_residual(nx, ny, nz, bx, by, bz, f0, p, r, fn);
@@ -381,6 +497,18 @@ int vdpo_solve_fixed_point(int nx, int ny, int nz, double L, const double *rho, 
 done:
   free(bx); free(by); free(bz); free(f0); free(r); free(dp);
   return status;
+}
+
+int vdpo_solve_fixed_point(int nx, int ny, int nz, double L, const double *rho, const double *f,
+                           double *p, double tol, int maxit, double omega, double *info) {
+  return solve_fixed_point_g(nx, ny, nz, cube(L), rho, f, p, tol, maxit, omega, info);
+}
+
+int vdpo_solve_fixed_point_g(int nx, int ny, int nz, double Lx, double Ly, double Lz, int bc_x,
+                             const double *rho, const double *f, double *p, double tol, int maxit,
+                             double omega, double *info) {
+  geom G = {Lx, Ly, Lz, bc_x};
+  return solve_fixed_point_g(nx, ny, nz, G, rho, f, p, tol, maxit, omega, info);
 }
 
 /* ---- the steps either side of the solve (App. A) ----------------------------------------------
