@@ -59,6 +59,18 @@ typedef enum {
   VDP_MIXED_BF16 = 2   /* as VDP_MIXED with BF16-stored face coefficients (ablation) */
 } vdp_precision;
 
+/* Boundary condition in x (vdp_create_bc).  y and z are always periodic. */
+typedef enum {
+  VDP_BC_PERIODIC = 0,  /* the triply periodic box (Sec. 3.2, configuration 1) */
+  VDP_BC_DUCT = 1       /* the inflow-outflow duct (Sec. 3.2, configuration 2): no pressure flux
+                           through the two x ends (homogeneous Neumann; the paper does not state
+                           the pressure condition, this is the reading taken).  The faces at
+                           x = 0 and x = Lx carry no coefficient, and the spectral passes transform
+                           the even extension of each x row (2 nx points), so 2 nx must be a
+                           supported length (nx in 16, 24, 32, 48, 64, 96, 128, 256) for the
+                           spectral preconditioner and the fixed-point method */
+} vdp_bc;
+
 typedef enum {
   VDP_PRECOND_JACOBI = 0, /* diagonal (Jacobi) scaling, folded into the operator */
   VDP_PRECOND_CHEB = 1,   /* Jacobi + fixed polynomial: cheb_degree terms of the Chebyshev
@@ -84,7 +96,7 @@ typedef enum {
                              the solve's scaled variables (W = D^1/2).  Iteration counts hardly
                              grow with the grid or the density ratio.  Needs at least one
                              coarsening (more than 64 cells, even sizes down to the coarsest);
-                             direct stencil sweep only; not in batches.  Extra memory: about 24
+                             direct stencil sweep only; not in batches; periodic box only.  Extra memory: about 24
                              bytes per cell */
 } vdp_precond;
 
@@ -149,6 +161,15 @@ void vdp_default_options(vdp_opts *o);
  * ny, nz >= 1.  Allocates all device memory the solve needs.  *out = NULL on failure.
  */
 int vdp_create(int nx, int ny, int nz, double L, vdp_ctx **out);
+
+/*
+ * As vdp_create with box lengths Lx, Ly, Lz (h_d = L_d / n_d) and the boundary condition in x
+ * (vdp_bc).  VDP_EINVAL for lengths that are not finite and positive or an unknown bc_x.  In the
+ * duct every solve method works (the multigrid preconditioner and the projection steps are for
+ * the periodic box only: VDP_EINVAL there).
+ */
+int vdp_create_bc(int nx, int ny, int nz, double Lx, double Ly, double Lz, int bc_x,
+                  vdp_ctx **out);
 
 /* Replace the options (takes effect at the next set_density / solve). */
 int vdp_set_options(vdp_ctx *ctx, const vdp_opts *opts);
@@ -230,7 +251,8 @@ int vdp_mg_apply(vdp_ctx *ctx, const double *g, double *out);
  * the substep's pressure coefficient.  All arrays are DEVICE pointers (8-byte aligned; p also
  * 16-byte aligned for vdp_project) on the context's device; the calls run on the context's stream
  * and return after it has finished.  VDP_EINVAL: no density set, c not finite and positive, a
- * host or misaligned pointer, or an output that aliases an input.
+ * host or misaligned pointer, an output that aliases an input, or a duct context (the face
+ * momenta of the two x ends would need their own storage: periodic box only).
  */
 
 /*

@@ -23,6 +23,7 @@ VDP_OK, VDP_EINVAL, VDP_ENOMEM, VDP_EDENSITY, VDP_ENOTCONV, VDP_EBREAKDOWN, VDP_
 VDP_FP64, VDP_MIXED, VDP_MIXED_BF16 = 0, 1, 2
 VDP_PRECOND_JACOBI, VDP_PRECOND_CHEB, VDP_PRECOND_SPECTRAL, VDP_PRECOND_MG = 0, 1, 2, 3
 VDP_METHOD_CG, VDP_METHOD_FIXED_POINT = 0, 1
+VDP_BC_PERIODIC, VDP_BC_DUCT = 0, 1
 PRECISIONS = {"fp64": VDP_FP64, "mixed": VDP_MIXED, "mixed_bf16": VDP_MIXED_BF16}
 # grid sizes (per direction) the spectral preconditioner's FFT passes support
 SPECTRAL_SIZES = (32, 48, 64, 96, 128, 192, 256, 512)
@@ -88,6 +89,8 @@ _SIGS = {
                                   ctypes.POINTER(ctypes.c_void_p)]),
     "vdp_set_options": (ctypes.c_int, [_P, ctypes.POINTER(vdp_opts)]),
     "vdp_get_options": (ctypes.c_int, [_P, ctypes.POINTER(vdp_opts)]),
+    "vdp_create_bc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "vdp_set_density": (ctypes.c_int, [_P, _P]),
     "vdp_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
     "vdp_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(vdp_stats)]),
@@ -154,6 +157,15 @@ def vdp_create(nx: int, ny: int, nz: int, L: float) -> int:
     st = load().vdp_create(int(nx), int(ny), int(nz), float(L), ctypes.byref(h))
     if st != VDP_OK:
         raise VdpError(st, "vdp_create")
+    return h.value
+
+
+def vdp_create_bc(nx: int, ny: int, nz: int, Lx: float, Ly: float, Lz: float, bc_x: int) -> int:
+    h = ctypes.c_void_p()
+    st = load().vdp_create_bc(int(nx), int(ny), int(nz), float(Lx), float(Ly), float(Lz), int(bc_x),
+                              ctypes.byref(h))
+    if st != VDP_OK:
+        raise VdpError(st, "vdp_create_bc")
     return h.value
 
 
@@ -358,10 +370,16 @@ class Solver:
     solve, other than ENOTCONV/EBREAKDOWN when ``check=False``)."""
 
     def __init__(self, nx: int, ny: int, nz: int, L: float, precision: str = "fp64", stream=None,
-                 **opts):
+                 lengths=None, bc_x: int = VDP_BC_PERIODIC, **opts):
+        """L: side of the cube; lengths = (Lx, Ly, Lz) instead, and bc_x = VDP_BC_DUCT for the
+        inflow-outflow duct (no pressure flux through the x ends)."""
         self.shape = (nz, ny, nx)
         self.L = float(L)
-        self.ctx = vdp_create(nx, ny, nz, L)
+        if lengths is None and bc_x == VDP_BC_PERIODIC:
+            self.ctx = vdp_create(nx, ny, nz, L)
+        else:
+            Lx, Ly, Lz = lengths if lengths is not None else (L, L, L)
+            self.ctx = vdp_create_bc(nx, ny, nz, Lx, Ly, Lz, bc_x)
         o = vdp_default_options()
         o.precision = PRECISIONS[precision]
         if stream is not None:

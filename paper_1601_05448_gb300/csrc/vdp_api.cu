@@ -329,7 +329,7 @@ int ensure_scaled(vdp_ctx* c, int prec) {
 }
 
 int ensure_spectral(vdp_ctx* c) {
-  if (!spectral_supported(c->nx, c->ny, c->nz)) return VDP_EINVAL;
+  if (!spectral_supported(spectral_nx(c), c->ny, c->nz)) return VDP_EINVAL;
   if (c->spec && c->sptab && c->za) return VDP_OK;
   static std::mutex mu;
   static std::vector<int> uploaded;  // devices whose register-DFT roots are in place
@@ -341,8 +341,9 @@ int ensure_spectral(vdp_ctx* c) {
     }
   }
   std::vector<float> tab;
-  spectral_tables(c->nx, c->ny, c->nz, c->L, tab);
-  const size_t spec_bytes = sizeof(float2) * (size_t)spectral_pitch(c->nx) * c->ny * c->nz;
+  spectral_tables(spectral_nx(c), c->ny, c->nz, c->Lx / c->nx, c->Ly / c->ny, c->Lz / c->nz, tab);
+  const size_t spec_bytes =
+      sizeof(float2) * (size_t)spectral_pitch(spectral_nx(c)) * c->ny * c->nz;
   cudaError_t e = cudaSuccess;
   if (!c->za) e = cudaMalloc(&c->za, sizeof(double) * (size_t)c->n);
   if (e == cudaSuccess && !c->spec) e = cudaMalloc((void**)&c->spec, spec_bytes);
@@ -362,7 +363,8 @@ int ensure_spectral(vdp_ctx* c) {
 }
 
 void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a) {
-  const int m = c->nx / 2;
+  const int nxt = spectral_nx(c);  // x transform length (twice the cells in the duct)
+  const int m = nxt / 2;
   const bool fixed = c->opts.method == VDP_METHOD_FIXED_POINT;
   a->in = c->r;
   // CG: z = W (-L_h)^-1 W rt, W = D^1/2.  Fixed point: with rt = D^-1/2 r the input weight
@@ -375,14 +377,17 @@ void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a) {
   a->spec = c->spec;
   a->tw = reinterpret_cast<const float2*>(c->sptab);
   a->lam = c->sptab + 2 * (2 * m + 1 + c->ny + c->nz);
-  a->nx = c->nx;
+  a->nx = nxt;
   a->ny = c->ny;
   a->nz = c->nz;
-  a->nxp = spectral_pitch(c->nx);
-  a->scale = (float)((fixed ? c->opts.damping : 1.0) / (double)c->n);
+  a->nxp = spectral_pitch(nxt);
+  a->nxd = c->nx;
+  a->mirror = c->bc_x == VDP_BC_DUCT;
+  a->ewt = a->mirror ? 0.5f : 1.f;
+  a->scale = (float)((fixed ? c->opts.damping : 1.0) / ((double)nxt * c->ny * c->nz));
   a->st = c->st;
   a->I = c->desc;
-  a->zunits = spectral_units(c->nx, c->ny, c->nz);
+  a->zunits = spectral_units(nxt, c->ny, c->nz);
   (void)prec;
 }
 
@@ -440,9 +445,16 @@ int prepare_spectral_solve(vdp_ctx* c) {
 extern "C" {
 
 int vdp_create(int nx, int ny, int nz, double L, vdp_ctx** out) {
+  return vdp_create_bc(nx, ny, nz, L, L, L, VDP_BC_PERIODIC, out);
+}
+
+int vdp_create_bc(int nx, int ny, int nz, double Lx, double Ly, double Lz, int bc_x,
+                  vdp_ctx** out) {
   if (!out) return VDP_EINVAL;
   *out = nullptr;
-  if (nx < 8 || nx % 8 != 0 || ny < 1 || nz < 1 || !(L > 0.0) || !std::isfinite(L))
+  auto ok = [](double v) { return v > 0.0 && std::isfinite(v); };
+  if (nx < 8 || nx % 8 != 0 || ny < 1 || nz < 1 || !ok(Lx) || !ok(Ly) || !ok(Lz) ||
+      (bc_x != VDP_BC_PERIODIC && bc_x != VDP_BC_DUCT))
     return VDP_EINVAL;
   if ((long long)nx * ny * nz > (1LL << 34)) return VDP_EINVAL;
   vdp_ctx* c = new (std::nothrow) vdp_ctx();
@@ -450,7 +462,10 @@ int vdp_create(int nx, int ny, int nz, double L, vdp_ctx** out) {
   c->nx = nx;
   c->ny = ny;
   c->nz = nz;
-  c->L = L;
+  c->Lx = Lx;
+  c->Ly = Ly;
+  c->Lz = Lz;
+  c->bc_x = bc_x;
   c->n = (long long)nx * ny * nz;
   vdp_default_options(&c->opts);
   cudaGetDevice(&c->device);
@@ -504,14 +519,14 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
       o->precond != VDP_PRECOND_SPECTRAL && o->precond != VDP_PRECOND_MG)
     return VDP_EINVAL;
   if (o->precond == VDP_PRECOND_MG && o->method == VDP_METHOD_CG &&
-      (o->stencil != 0 || !mg_supported(c->nx, c->ny, c->nz)))
+      (o->stencil != 0 || !mg_supported(c->nx, c->ny, c->nz) || c->bc_x != VDP_BC_PERIODIC))
     return VDP_EINVAL;
   if (o->precond == VDP_PRECOND_SPECTRAL &&
-      (o->stencil != 0 || !spectral_supported(c->nx, c->ny, c->nz)))
+      (o->stencil != 0 || !spectral_supported(spectral_nx(c), c->ny, c->nz)))
     return VDP_EINVAL;
   if (o->method != VDP_METHOD_CG && o->method != VDP_METHOD_FIXED_POINT) return VDP_EINVAL;
   if (o->method == VDP_METHOD_FIXED_POINT &&
-      (o->stencil != 0 || !spectral_supported(c->nx, c->ny, c->nz) || !(o->damping > 0.0) ||
+      (o->stencil != 0 || !spectral_supported(spectral_nx(c), c->ny, c->nz) || !(o->damping > 0.0) ||
        o->damping > 2.0))
     return VDP_EINVAL;
   if (o->precond == VDP_PRECOND_CHEB && (o->cheb_degree < 1 || o->cheb_degree > 16 || o->stencil != 0))
@@ -591,8 +606,9 @@ int vdp_set_density(vdp_ctx* c, const double* rho) {
   VDP_CK(cudaMemcpyAsync(&bad, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   VDP_CK(cudaStreamSynchronize(c->stream));
   if (bad) return VDP_EDENSITY;
-  VDP_CK(launch_build_coefficients(src, c->nx, c->ny, c->nz, c->L, c->bx, c->by, c->bz, c->sinv,
-                                   c->stream));
+  VDP_CK(launch_build_coefficients(src, c->nx, c->ny, c->nz, c->Lx / c->nx, c->Ly / c->ny,
+                                   c->Lz / c->nz, c->bc_x == VDP_BC_DUCT, c->bx, c->by, c->bz,
+                                   c->sinv, c->stream));
   c->scaled_prec = -1;
   c->omega_valid = false;
   c->rho_w_valid = false;
@@ -722,7 +738,7 @@ int vdp_inverse_laplacian(vdp_ctx* c, const double* g, double* out) {
   a.out_f32 = 0;
   a.omega_in = nullptr;
   a.omega_out = nullptr;
-  a.scale = (float)(-1.0 / (double)c->n);  // L_h^-1 (negative definite), not (-L_h)^-1
+  a.scale = (float)(-1.0 / ((double)a.nx * c->ny * c->nz));  // L_h^-1, not (-L_h)^-1
   a.st = nullptr;
   a.I = nullptr;
   for (int pass = 0; pass < SPEC_PASSES; ++pass)
@@ -738,7 +754,8 @@ int vdp_mg_levels(int nx, int ny, int nz) {
 }
 
 int vdp_mg_apply(vdp_ctx* c, const double* g, double* out) {
-  if (!c || !g || !out || g == out || !c->has_density) return VDP_EINVAL;
+  if (!c || !g || !out || g == out || !c->has_density || c->bc_x != VDP_BC_PERIODIC)
+    return VDP_EINVAL;
   if (!is_device_ptr(g) || !is_device_ptr(out) || ((uintptr_t)g & 15) || ((uintptr_t)out & 15))
     return VDP_EINVAL;
   int s;

@@ -26,7 +26,8 @@ bool is_device_ptr(const void* p);
 
 struct vdp_ctx {
   int nx = 0, ny = 0, nz = 0;
-  double L = 0;
+  double Lx = 0, Ly = 0, Lz = 0;   // box lengths
+  int bc_x = VDP_BC_PERIODIC;      // VDP_BC_DUCT: no pressure flux through the x ends
   long long n = 0;
   int device = 0;
   vdp_opts opts{};
@@ -84,6 +85,8 @@ namespace vdp {
 // layout (and its device description) configured.
 int configure_layout(vdp_ctx* c, int prec);
 int ensure_scaled(vdp_ctx* c, int prec);
+// length of the x transform of the spectral passes: nx, or 2 nx in the duct (even extension)
+inline int spectral_nx(const vdp_ctx* c) { return c->bc_x == VDP_BC_DUCT ? 2 * c->nx : c->nx; }
 // allocate the spectral buffers and tables (no-op when present); VDP_EINVAL for unsupported grids
 int ensure_spectral(vdp_ctx* c);
 // the arguments of the five spectral passes of a solve on this context (gated on its state)

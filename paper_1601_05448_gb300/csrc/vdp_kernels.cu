@@ -1315,8 +1315,9 @@ __global__ void k_check_density(const double* __restrict__ rho, long long n, int
 }
 
 // b_d[c] = 2 / (rho[c - e_d] + rho[c]) / h_d^2 on the low d-face of every cell
+// duct: the face at the x ends (slot x = 0, shared by x = 0 and x = Lx) carries no flux
 __global__ void k_faces(const double* __restrict__ rho, int nx, int ny, int nz, double ihx2,
-                        double ihy2, double ihz2, double* bx, double* by, double* bz) {
+                        double ihy2, double ihz2, int duct, double* bx, double* by, double* bz) {
   const long long n = (long long)nx * ny * nz;
   const long long plane = (long long)nx * ny;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
@@ -1328,7 +1329,7 @@ __global__ void k_faces(const double* __restrict__ rho, int nx, int ny, int nz, 
     const long long cym = c + (long long)((y == 0 ? ny - 1 : y - 1) - y) * nx;
     const long long czm = c + (long long)((z == 0 ? nz - 1 : z - 1) - z) * plane;
     const double rc = rho[c];
-    bx[c] = 2.0 / (rho[cxm] + rc) * ihx2;
+    bx[c] = (duct && x == 0) ? 0.0 : 2.0 / (rho[cxm] + rc) * ihx2;
     by[c] = 2.0 / (rho[cym] + rc) * ihy2;
     bz[c] = 2.0 / (rho[czm] + rc) * ihz2;
   }
@@ -1455,13 +1456,12 @@ cudaError_t launch_check_density(const double* rho, long long n, int* bad, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_coefficients(const double* rho, int nx, int ny, int nz, double L,
-                                      double* bx, double* by, double* bz, double* sinv,
-                                      cudaStream_t s) {
+cudaError_t launch_build_coefficients(const double* rho, int nx, int ny, int nz, double hx,
+                                      double hy, double hz, int duct, double* bx, double* by,
+                                      double* bz, double* sinv, cudaStream_t s) {
   const long long n = (long long)nx * ny * nz;
-  const double hx = L / nx, hy = L / ny, hz = L / nz;
   k_faces<<<grid_for(n), 256, 0, s>>>(rho, nx, ny, nz, 1.0 / (hx * hx), 1.0 / (hy * hy),
-                                      1.0 / (hz * hz), bx, by, bz);
+                                      1.0 / (hz * hz), duct, bx, by, bz);
   k_diag<<<grid_for(n), 256, 0, s>>>(bx, by, bz, nx, ny, nz, sinv);
   return cudaGetLastError();
 }

@@ -123,7 +123,7 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
   NA_CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   NA_CK(cudaStreamSynchronize(s));
   if (bad) return VDP_EDENSITY;
-  NA_CK(launch_build_coefficients(rho, nx, ny, nz, L, bx, by, bz, sinv, s));
+  NA_CK(launch_build_coefficients(rho, nx, ny, nz, L / nx, L / ny, L / nz, 0, bx, by, bz, sinv, s));
   NA_CK(launch_scaled(precision, bx, by, bz, sinv, nx, ny, nz, sx, sy, sz, sd, s));
 
   // the default unit layout of vdp_solve

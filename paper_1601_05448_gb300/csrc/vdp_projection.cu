@@ -107,7 +107,7 @@ bool bad_c(double c) { return !(c > 0.0) || !std::isfinite(c); }
 
 cudaError_t launch_rhs(const vdp_ctx* ctx, const double* mx, const double* my, const double* mz,
                        const double* rd, double c, double* f, cudaStream_t s) {
-  const double hx = ctx->L / ctx->nx, hy = ctx->L / ctx->ny, hz = ctx->L / ctx->nz;
+  const double hx = ctx->Lx / ctx->nx, hy = ctx->Ly / ctx->ny, hz = ctx->Lz / ctx->nz;
   if (rd) {
     static const int R = resident_blocks(k_projection_rhs<true>);
     const MarchPlan m = march_plan(ctx->nx, ctx->ny, ctx->nz, R);
@@ -128,7 +128,7 @@ cudaError_t launch_correct(const vdp_ctx* ctx, const double* p, double c, double
                            double* mz, cudaStream_t s) {
   static const int R = resident_blocks(k_projection_correct);
   const MarchPlan m = march_plan(ctx->nx, ctx->ny, ctx->nz, R);
-  const double hx = ctx->L / ctx->nx, hy = ctx->L / ctx->ny, hz = ctx->L / ctx->nz;
+  const double hx = ctx->Lx / ctx->nx, hy = ctx->Ly / ctx->ny, hz = ctx->Lz / ctx->nz;
   k_projection_correct<<<m.blocks, dim3(kTx, kTy), 0, s>>>(p, ctx->nx, ctx->ny, ctx->nz, m, c / hx,
                                                            c / hy, c / hz, mx, my, mz);
   return cudaGetLastError();
@@ -176,7 +176,7 @@ cudaError_t time_on_graph(vdp_ctx* ctx, Body body, float* ms) {
 
 extern "C" int vdp_projection_rhs(vdp_ctx* ctx, const double* mx, const double* my,
                                   const double* mz, const double* rhs_div, double c, double* f) {
-  if (!ctx || !ctx->has_density || bad_c(c)) return VDP_EINVAL;
+  if (!ctx || !ctx->has_density || bad_c(c) || ctx->bc_x != VDP_BC_PERIODIC) return VDP_EINVAL;
   if (!dev_aligned(mx) || !dev_aligned(my) || !dev_aligned(mz) || !dev_aligned(f) ||
       (rhs_div && !dev_aligned(rhs_div)))
     return VDP_EINVAL;
@@ -188,7 +188,7 @@ extern "C" int vdp_projection_rhs(vdp_ctx* ctx, const double* mx, const double* 
 
 extern "C" int vdp_projection_correct(vdp_ctx* ctx, const double* p, double c, double* mx,
                                       double* my, double* mz) {
-  if (!ctx || bad_c(c)) return VDP_EINVAL;
+  if (!ctx || bad_c(c) || ctx->bc_x != VDP_BC_PERIODIC) return VDP_EINVAL;
   if (!dev_aligned(p) || !dev_aligned(mx) || !dev_aligned(my) || !dev_aligned(mz))
     return VDP_EINVAL;
   const void* all[] = {p, mx, my, mz};
@@ -200,7 +200,8 @@ extern "C" int vdp_projection_correct(vdp_ctx* ctx, const double* p, double c, d
 
 static int project(vdp_ctx* ctx, double* mx, double* my, double* mz, const double* rhs_div,
                    double c, double tol, double* p, float* ms) {
-  if (!ctx || !ctx->has_density || bad_c(c) || !(tol > 0.0) || !std::isfinite(tol))
+  if (!ctx || !ctx->has_density || bad_c(c) || !(tol > 0.0) || !std::isfinite(tol) ||
+      ctx->bc_x != VDP_BC_PERIODIC)
     return VDP_EINVAL;
   if (!dev_aligned(mx) || !dev_aligned(my) || !dev_aligned(mz) || !dev_aligned(p) ||
       ((uintptr_t)p & 15) || (rhs_div && !dev_aligned(rhs_div)))

@@ -201,18 +201,22 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
   float2* rb = sb + r * SB;
   // step A: M2-point DFTs over j2 of z[t + M1 j2] = (x[2j], x[2j+1]) * W
   if (live) {
-    const T* in = static_cast<const T*>(a.in) + row * a.nx;
-    const float* om = a.omega_in ? a.omega_in + row * a.nx : nullptr;
+    const T* in = static_cast<const T*>(a.in) + row * a.nxd;
+    const float* om = a.omega_in ? a.omega_in + row * a.nxd : nullptr;
     float2 v[M2], y[M2];
 #pragma unroll
     for (int j2 = 0; j2 < M2; ++j2) {
       const int j = t + M1 * j2;
-      float2 z = Pair<T>::ld(in + 2 * j);
+      // pair j of the transformed row; mirrored rows read their second half backwards:
+      // cells (2j, 2j + 1) of the extension are cells (q + 1, q) of the row, q = 2 nxd - 2 - 2j
+      const bool back = a.mirror && 2 * j >= a.nxd;
+      const int q = back ? 2 * a.nxd - 2 - 2 * j : 2 * j;
+      float2 z = Pair<T>::ld(in + q);
       if (om) {
-        const float2 w = *reinterpret_cast<const float2*>(om + 2 * j);
+        const float2 w = *reinterpret_cast<const float2*>(om + q);
         z = make_float2(z.x * w.x, z.y * w.y);
       }
-      v[j2] = z;
+      v[j2] = back ? make_float2(z.y, z.x) : z;
     }
     dft<M2, 0, 1, false>(v, y);
 #pragma unroll
@@ -268,14 +272,15 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
   // the transforms (cells 2l, 2l + 1 with l = k2 + M2 k1, k2 = t, t + M1, ...)
   constexpr int R = (M2 + M1 - 1) / M1;
   float2 wv[R][M1];
-  const float* om = a.omega_out ? a.omega_out + row * a.nx : nullptr;
+  const float* om = a.omega_out ? a.omega_out + row * a.nxd : nullptr;
 #pragma unroll
   for (int rr = 0; rr < R; ++rr)
 #pragma unroll
     for (int k1 = 0; k1 < M1; ++k1) {
       const int k2 = t + M1 * rr;
+      const int l = k2 + M2 * k1;
       wv[rr][k1] = make_float2(1.f, 1.f);
-      if (live && om && k2 < M2) wv[rr][k1] = *reinterpret_cast<const float2*>(om + 2 * (k2 + M2 * k1));
+      if (live && om && k2 < M2 && 2 * l < a.nxd) wv[rr][k1] = *reinterpret_cast<const float2*>(om + 2 * l);
     }
   // Z'[k] = (X[k] + conj X[m-k]) + i conj(W_nx^k) (X[k] - conj X[m-k]); inverse M2-point DFTs.
   // Both X[k] and X[m-k] are read straight from the spectrum (in L2 after the Y- pass): for a
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
   }
   __syncthreads();
   if (live) {
-    T* out = static_cast<T*>(a.out) + row * a.nx;
+    T* out = static_cast<T*>(a.out) + row * a.nxd;
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
       const int k2 = t + M1 * rr;
@@ -317,6 +322,7 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
 #pragma unroll
       for (int k1 = 0; k1 < M1; ++k1) {
         const int l = k2 + M2 * k1;  // cells 2l, 2l + 1 of the row
+        if (2 * l >= a.nxd) continue;  // mirrored rows: the second half is the reflection
         const float2 z = make_float2(o[k1].x * wv[rr][k1].x, o[k1].y * wv[rr][k1].y);
         Pair<T>::st(out + 2 * l, z);
       }
@@ -446,7 +452,7 @@ __global__ void __launch_bounds__(M1 * kTX) k_spec_z(SpecArgs a) {
     for (int l1 = 0; l1 < M2; ++l1) g[(t + M1 * l1) * es] = o[l1];
   }
   if (a.st) {
-    const float part[1] = {energy};
+    const float part[1] = {energy * a.ewt};
     store_partials<1, float>(part, a.I->part, gridDim.x, blockIdx.x);
   }
 }
@@ -543,7 +549,8 @@ size_t spectral_table_floats(int nx, int ny, int nz) {
   return 2 * (size_t)(2 * m + 1 + ny + nz) + (size_t)(m + 1 + ny + nz);
 }
 
-void spectral_tables(int nx, int ny, int nz, double L, std::vector<float>& out) {
+void spectral_tables(int nx, int ny, int nz, double hx, double hy, double hz,
+                     std::vector<float>& out) {
   const int m = nx / 2;
   out.assign(spectral_table_floats(nx, ny, nz), 0.f);
   size_t i = 0;
@@ -558,16 +565,15 @@ void spectral_tables(int nx, int ny, int nz, double L, std::vector<float>& out) 
   roots(nx, m + 1);
   roots(ny, ny);
   roots(nz, nz);
-  auto eig = [&](int n, int count) {
-    const double h = L / n;
+  auto eig = [&](int n, int count, double h) {
     for (int k = 0; k < count; ++k) {
       const double s = std::sin(M_PI * (double)k / (double)n);
       out[i++] = (float)(4.0 * s * s / (h * h));
     }
   };
-  eig(nx, m + 1);
-  eig(ny, ny);
-  eig(nz, nz);
+  eig(nx, m + 1, hx);
+  eig(ny, ny, hy);
+  eig(nz, nz, hz);
 }
 
 cudaError_t spectral_upload_roots() {

@@ -15,7 +15,7 @@ enum SpecPass : int { SPEC_X_FWD = 0, SPEC_Y_FWD = 1, SPEC_Z = 2, SPEC_Y_INV = 3
 
 // Arguments of every spectral pass (by value).
 struct SpecArgs {
-  const void* in;        // X+: nx*ny*nz values of the inner type (FP64 or FP32)
+  const void* in;        // X+: nxd*ny*nz values of the inner type (FP64 or FP32)
   void* out;             // X-: output, same layout; the inner type, or FP32 with out_f32
   int out_f32;           // X-: store FP32 (the fixed-point iteration's z)
   const float* omega_in;   // per-cell weight applied before X+ (or null: 1)
@@ -23,7 +23,12 @@ struct SpecArgs {
   float2* spec;          // half spectrum [nz][ny][nxp]
   const float2* tw;      // tables built by spectral_tables (twiddles first, then eigenvalues)
   const float* lam;
-  int nx, ny, nz, nxp;
+  int nx, ny, nz, nxp;   // transform lengths (nx: the x transform) and the spectrum's row pitch
+  int nxd;               // cells per row of in / out: nx, or nx / 2 with mirror
+  int mirror;            // duct: the x transform acts on the even extension of each row
+                         // (cells 0 .. nxd - 1, then nxd - 1 .. 0), whose periodic Laplacian
+                         // is the zero-flux one on the first half; X- keeps the first half
+  float ewt;             // weight of the <rt, z> energy (1, or 1/2 for the doubled rows)
   float scale;           // sign / (nx ny nz): +1 applies (-L_h)^-1, -1 applies L_h^-1
   InstState* st;         // the solve's state: passes run only in PH_SPEC (null: always run)
   const InstDesc* I;     // the solve's description, with st: Z stores the partial sums of
@@ -36,7 +41,8 @@ int spectral_pitch(int nx);                       // nxp
 size_t spectral_table_floats(int nx, int ny, int nz);
 // twiddles (float2 pairs) W_m (m = nx/2), W_nx (m + 1), W_ny, W_nz, then the eigenvalue factors
 // 4 sin^2(pi k / n_d) / h_d^2 for kx = 0..m, ky, kz; computed in double, stored as float
-void spectral_tables(int nx, int ny, int nz, double L, std::vector<float>& out);
+void spectral_tables(int nx, int ny, int nz, double hx, double hy, double hz,
+                     std::vector<float>& out);
 cudaError_t spectral_upload_roots();               // the register-DFT roots, once per device
 cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStream_t s);
 int spectral_units(int nx, int ny, int nz);        // CTAs of the Z pass (partial slots)

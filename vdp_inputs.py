@@ -236,6 +236,19 @@ def divergence_target(shape, rng: np.random.Generator, mean: float = 0.1, amplit
     return np.ascontiguousarray(mean + amplitude * g)
 
 
+def duct_problem(shape, lengths, seed: int, amplitude: float = 0.6, tol: float = 1e-10):
+    """A seeded problem on the inflow-outflow duct of lengths (Lx, Ly, Lz): rho = 1 + amplitude g
+    (8 random modes, density ratio (1 + a) / (1 - a)) and f = the discrete divergence recipe above
+    with the spacing of y (any mean-free right side will do for the pressure solve)."""
+    rng = np.random.default_rng(seed)
+    rho = density_modes(shape, rng, amplitude=amplitude)
+    f = rhs_divergence(shape, float(lengths[1]), rng)
+    f -= f.mean()
+    prob = Problem("duct", tuple(shape), float(lengths[1]), rho, f, tol, "fp64",
+                   {"ratio": float(rho.max() / rho.min()), "seed": seed, "lengths": tuple(lengths)})
+    return prob
+
+
 @dataclass
 class Problem:
     """One seeded solve: shape (nz, ny, nx), box length L, rho, f, tolerance and precision mode."""
