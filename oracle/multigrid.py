@@ -105,12 +105,29 @@ def coarsen(b):
     return out
 
 
-def prolong(xc):
-    """Cell-centred linear interpolation to the grid twice as fine in every direction."""
+def _neighbours(x, ax, wall):
+    """The coarse neighbours below and above along axis ax, periodic; with wall (the duct's x
+    ends) a cell at an end is its own neighbour there (the interpolant is constant up to the
+    wall, as zero flux through it implies)."""
+    below, above = np.roll(x, 1, axis=ax), np.roll(x, -1, axis=ax)
+    if wall:
+        first = [slice(None)] * 3
+        last = [slice(None)] * 3
+        first[ax] = 0
+        last[ax] = -1
+        below[tuple(first)] = x[tuple(first)]
+        above[tuple(last)] = x[tuple(last)]
+    return below, above
+
+
+def prolong(xc, bc_x: int = 0):
+    """Cell-centred linear interpolation to the grid twice as fine in every direction (bc_x = 1:
+    no interpolation across the duct's x ends)."""
     x = xc
     for ax in range(3):
-        lo = 0.75 * x + 0.25 * np.roll(x, 1, axis=ax)    # fine child on the low side
-        hi = 0.75 * x + 0.25 * np.roll(x, -1, axis=ax)   # fine child on the high side
+        below, above = _neighbours(x, ax, bc_x == 1 and ax == 2)
+        lo = 0.75 * x + 0.25 * below    # fine child on the low side
+        hi = 0.75 * x + 0.25 * above    # fine child on the high side
         shape = list(x.shape)
         shape[ax] *= 2
         y = np.empty(shape)
@@ -124,7 +141,7 @@ def prolong(xc):
     return x
 
 
-def restrict(r):
+def restrict(r, bc_x: int = 0):
     """The transpose of prolong (axis by axis, in the reverse order)."""
     x = r
     for ax in (2, 1, 0):
@@ -135,7 +152,16 @@ def restrict(r):
         lo, hi = x[tuple(s_lo)], x[tuple(s_hi)]
         # coarse C collects 3/4 of both children, 1/4 of the low child of C+1 and of the high
         # child of C-1 (the fine cells whose interpolation used C as the neighbour)
-        x = 0.75 * lo + 0.75 * hi + 0.25 * np.roll(lo, -1, axis=ax) + 0.25 * np.roll(hi, 1, axis=ax)
+        from_above = np.roll(lo, -1, axis=ax)
+        from_below = np.roll(hi, 1, axis=ax)
+        if bc_x == 1 and ax == 2:  # at the duct's ends the own child took that 1/4 instead
+            first = [slice(None)] * 3
+            last = [slice(None)] * 3
+            first[ax] = 0
+            last[ax] = -1
+            from_below[tuple(first)] = lo[tuple(first)]
+            from_above[tuple(last)] = hi[tuple(last)]
+        x = 0.75 * lo + 0.75 * hi + 0.25 * from_above + 0.25 * from_below
     return x
 
 
@@ -154,9 +180,11 @@ def dense_negative_operator(b):
 class Hierarchy:
     """The levels of a V-cycle for face coefficients b (level 0)."""
 
-    def __init__(self, b, max_levels: int = 0):
+    def __init__(self, b, max_levels: int = 0, bc_x: int = 0):
         """max_levels > 0 keeps only that many levels (the last one still solved exactly; for the
-        two-grid pins)."""
+        two-grid pins).  bc_x = 1: the duct (b has no x faces at the ends; the transfers do not
+        reach across them)."""
+        self.bc_x = int(bc_x)
         nz, ny, nx = b[0].shape
         if max_levels > 0:
             shapes = [(nz, ny, nx)]
@@ -174,8 +202,9 @@ class Hierarchy:
         self.coarse_pinv = np.linalg.pinv(dense_negative_operator(self.b[-1]))
 
     @classmethod
-    def from_density(cls, rho, L: float, max_levels: int = 0):
-        return cls(face_coefficients(rho, L), max_levels)
+    def from_density(cls, rho, L: float, max_levels: int = 0, geom=None):
+        bc_x = 0 if geom is None else int(geom[3])
+        return cls(face_coefficients(rho, L, geom), max_levels, bc_x)
 
     @property
     def nlevels(self):
@@ -188,16 +217,16 @@ class Hierarchy:
             return (self.coarse_pinv @ r.ravel()).reshape(r.shape)
         x = OMEGA * r / D                               # pre-smoothing sweep from x = 0
         res = r + apply(b, x)                           # r - (-A) x
-        xc = self.vcycle(restrict(res), level + 1)      # coarse-grid correction
-        x = x + prolong(xc)
+        xc = self.vcycle(restrict(res, self.bc_x), level + 1)      # coarse-grid correction
+        x = x + prolong(xc, self.bc_x)
         x = x + OMEGA * (r + apply(b, x)) / D           # post-smoothing sweep
         return x
 
 
-def solve_pcg(rho, f, L: float, tol: float = 1e-12, maxit: int = 1000):
+def solve_pcg(rho, f, L: float, tol: float = 1e-12, maxit: int = 1000, geom=None):
     """CG on -A p = -(f - <f>) preconditioned by the V-cycle; returns (p, info) with the zero-mean
     p and info keys iters, rel_res (true residual), rhs_mean, status."""
-    H = Hierarchy.from_density(rho, L)
+    H = Hierarchy.from_density(rho, L, geom=geom)
     b = H.b[0]
     f = np.asarray(f, dtype=np.float64)
     mu = float(f.mean())

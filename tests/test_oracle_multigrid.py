@@ -160,3 +160,51 @@ def test_coarse_faces_are_half_the_piecewise_constant_galerkin_faces():
                     C = i + cx * (j + cy * k)
                     Cm = (i - ex) % cx + cx * ((j - ey) % cy + cy * ((k - ez) % cz))
                     assert abs(-G[C, Cm] - 2.0 * bc[d][k, j, i]) <= 1e-12 * abs(G[C, Cm])
+
+
+# ---- the inflow-outflow duct: no faces at the x ends, transfers that do not reach across them ---
+
+DUCT = (4.0, 1.0, 1.0, 1)
+
+
+def test_duct_transfers_are_adjoint_and_keep_constants():
+    rng = np.random.default_rng(35)
+    xc = rng.standard_normal((3, 4, 5))
+    rf = rng.standard_normal((6, 8, 10))
+    lhs = float(np.sum(MG.prolong(xc, 1) * rf))
+    rhs = float(np.sum(xc * MG.restrict(rf, 1)))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    assert np.allclose(MG.prolong(np.ones((3, 4, 5)), 1), 1.0, rtol=0, atol=1e-15)
+    # nothing crosses the ends: a coarse value at the last x cell does not reach the first fine one
+    e = np.zeros((3, 4, 5))
+    e[:, :, -1] = 1.0
+    assert np.all(MG.prolong(e, 1)[:, :, 0] == 0.0)
+    assert np.all(MG.prolong(e, 0)[:, :, 0] > 0.0)   # (it does in the periodic box)
+
+
+def test_duct_vcycle_is_symmetric_positive_definite():
+    rng = np.random.default_rng(36)
+    shape = (8, 8, 16)
+    rho = V.density_modes(shape, rng, amplitude=(30 - 1) / (30 + 1), kmax=3.0)
+    H = MG.Hierarchy.from_density(rho, 0.0, geom=(2.0, 1.0, 1.0, 1))
+    n = rho.size
+    Pm = np.eye(n) - 1.0 / n
+    M = np.zeros((n, n))
+    for q in range(n):
+        M[:, q] = H.vcycle(Pm[:, q].reshape(shape)).ravel()
+    M = Pm @ M @ Pm
+    assert np.abs(M - M.T).max() <= 1e-12 * np.abs(M).max()
+    lam = np.sort(np.linalg.eigvals(M @ MG.dense_negative_operator(H.b[0])).real)[1:]
+    assert lam.min() > 0.05 and lam.max() <= 1.0 + 1e-9
+
+
+def test_duct_pcg_reaches_the_oracle_solution_with_mesh_independent_iterations():
+    its = []
+    for n in (16, 32):
+        prob = V.duct_problem((n, n, 4 * n), DUCT[:3], seed=n)
+        p, info = MG.solve_pcg(prob.rho, prob.f, 0.0, tol=1e-11, geom=DUCT)
+        ref, _ = oracle.solve_cg(prob.rho, prob.f, 0.0, tol=1e-13, geom=DUCT)
+        assert info["status"] == "ok"
+        assert np.linalg.norm(p - ref) <= 1e-9 * np.linalg.norm(ref)
+        its.append(info["iters"])
+    assert max(its) - min(its) <= 2 and max(its) <= 25, its
