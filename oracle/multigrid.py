@@ -199,7 +199,9 @@ class Hierarchy:
         for _ in shapes[1:]:
             self.b.append(tuple(coarsen(self.b[-1])))
         self.D = [diagonal(x) for x in self.b]
-        self.coarse_pinv = np.linalg.pinv(dense_negative_operator(self.b[-1]))
+        # the exact null space of -A is the constants (eigenvalue 0); rounding leaves it at about
+        # 1e-16 of the largest eigenvalue, which a pseudo-inverse must not invert
+        self.coarse_pinv = np.linalg.pinv(dense_negative_operator(self.b[-1]), rcond=1e-10, hermitian=True)
 
     @classmethod
     def from_density(cls, rho, L: float, max_levels: int = 0, geom=None):
