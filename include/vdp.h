@@ -96,7 +96,8 @@ typedef enum {
                              the solve's scaled variables (W = D^1/2).  Iteration counts hardly
                              grow with the grid or the density ratio.  Needs at least one
                              coarsening (more than 64 cells, even sizes down to the coarsest);
-                             direct stencil sweep only; not in batches; periodic box only.  Extra memory: about 24
+                             direct stencil sweep only; not in batches.  In the duct the
+                             transfers do not reach across the x ends  Extra memory: about 24
                              bytes per cell */
 } vdp_precond;
 
@@ -165,8 +166,8 @@ int vdp_create(int nx, int ny, int nz, double L, vdp_ctx **out);
 /*
  * As vdp_create with box lengths Lx, Ly, Lz (h_d = L_d / n_d) and the boundary condition in x
  * (vdp_bc).  VDP_EINVAL for lengths that are not finite and positive or an unknown bc_x.  In the
- * duct every solve method works (the multigrid preconditioner and the projection steps are for
- * the periodic box only: VDP_EINVAL there).
+ * duct every solve method and preconditioner works; the projection steps are for the periodic
+ * box only (VDP_EINVAL there).
  */
 int vdp_create_bc(int nx, int ny, int nz, double Lx, double Ly, double Lz, int bc_x,
                   vdp_ctx **out);

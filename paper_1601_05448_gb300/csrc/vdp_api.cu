@@ -401,7 +401,7 @@ int ensure_mg(vdp_ctx* c) {
   }
   if (e == cudaSuccess && !c->mg) {
     MgHier* h = new MgHier();
-    e = mg_alloc(h, c->nx, c->ny, c->nz);
+    e = mg_alloc(h, c->nx, c->ny, c->nz, c->bc_x == VDP_BC_DUCT);
     if (e == cudaSuccess) {
       c->mg = h;
       c->mg_valid = false;
@@ -519,7 +519,7 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
       o->precond != VDP_PRECOND_SPECTRAL && o->precond != VDP_PRECOND_MG)
     return VDP_EINVAL;
   if (o->precond == VDP_PRECOND_MG && o->method == VDP_METHOD_CG &&
-      (o->stencil != 0 || !mg_supported(c->nx, c->ny, c->nz) || c->bc_x != VDP_BC_PERIODIC))
+      (o->stencil != 0 || !mg_supported(c->nx, c->ny, c->nz)))
     return VDP_EINVAL;
   if (o->precond == VDP_PRECOND_SPECTRAL &&
       (o->stencil != 0 || !spectral_supported(spectral_nx(c), c->ny, c->nz)))
@@ -754,8 +754,7 @@ int vdp_mg_levels(int nx, int ny, int nz) {
 }
 
 int vdp_mg_apply(vdp_ctx* c, const double* g, double* out) {
-  if (!c || !g || !out || g == out || !c->has_density || c->bc_x != VDP_BC_PERIODIC)
-    return VDP_EINVAL;
+  if (!c || !g || !out || g == out || !c->has_density) return VDP_EINVAL;
   if (!is_device_ptr(g) || !is_device_ptr(out) || ((uintptr_t)g & 15) || ((uintptr_t)out & 15))
     return VDP_EINVAL;
   int s;

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kMgThreads, 4)
 template <class T>
 __global__ void __launch_bounds__(kMgThreads, 4)
     k_mg_prolong(MgLevel lv, MgLevel cv, MarchPlan m, const T* __restrict__ rt,
-                 const float* __restrict__ om, const InstState* st) {
+                 const float* __restrict__ om, int wall_x, const InstState* st) {
   if (!mg_active(st)) return;
   const int cx = cv.nx, cy = cv.ny, cz = cv.nz;
   const long long cplane = (long long)cx * cy;
@@ -173,7 +173,9 @@ __global__ void __launch_bounds__(kMgThreads, 4)
   MG_MARCH_BEGIN(lv)
   (void)d;
   const int I0 = x >> 1, J0 = y >> 1;
-  const int I1 = (x & 1) ? (I0 + 1 == cx ? 0 : I0 + 1) : (I0 == 0 ? cx - 1 : I0 - 1);
+  // neighbour of the parent on the fine cell's side; at the duct's x ends the parent itself
+  const int I1 = (x & 1) ? (I0 + 1 == cx ? (wall_x ? I0 : 0) : I0 + 1)
+                         : (I0 == 0 ? (wall_x ? I0 : cx - 1) : I0 - 1);
   const int J1 = (y & 1) ? (J0 + 1 == cy ? 0 : J0 + 1) : (J0 == 0 ? cy - 1 : J0 - 1);
   const long long q00 = I0 + (long long)cx * J0, q10 = I1 + (long long)cx * J0;
   const long long q01 = I0 + (long long)cx * J1, q11 = I1 + (long long)cx * J1;
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(kMgThreads, 4)
 // (solved unscaled by the pseudo-inverse; oinv null).
 __global__ void __launch_bounds__(kMgThreads, 4)
     k_mg_restrict(MgLevel fv, MgLevel cv, MarchPlan m, const float* __restrict__ oinv,
-                  const InstState* st) {
+                  int wall_x, const InstState* st) {
   if (!mg_active(st)) return;
   const int nx = fv.nx, ny = fv.ny, nz = fv.nz;
   const int cx = cv.nx, cy = cv.ny, cz = cv.nz;
@@ -241,6 +243,9 @@ __global__ void __launch_bounds__(kMgThreads, 4)
         float right = __shfl_down_sync(0xffffffffu, v.x, 1);
         if (on && lload) left = __ldg(row + xl);
         if (on && rload) right = __ldg(row + xr);
+        // the duct's x ends: the end child took the quarter the far side would have given
+        if (wall_x && Ic == 0) left = v.x;
+        if (wall_x && Ic == cx - 1) right = v.y;
         const float rs = fmaf(0.25f, left + right, 0.75f * (v.x + v.y));
         const float wb = (b == 0 || b == 3) ? 0.25f : 0.75f;
         sum = fmaf(wb, rs, sum);
@@ -453,7 +458,7 @@ size_t mg_bytes(int nx, int ny, int nz) {
   return sizeof(float) * (cells + nc * nc) + 64 * (size_t)(8 * L + 1);
 }
 
-cudaError_t mg_alloc(MgHier* h, int nx, int ny, int nz) {
+cudaError_t mg_alloc(MgHier* h, int nx, int ny, int nz, int wall_x) {
   int d[kMgMaxLevels][3];
   const int L = mg_level_dims(nx, ny, nz, d);
   if (!L) return cudaErrorInvalidValue;
@@ -469,6 +474,7 @@ cudaError_t mg_alloc(MgHier* h, int nx, int ny, int nz) {
   };
   MgHier hh;
   hh.nlev = L;
+  hh.wall_x = wall_x;
   for (int l = 0; l < L; ++l) {
     MgLevel& v = hh.lev[l];
     v.nx = d[l][0];
@@ -577,13 +583,15 @@ static cudaError_t vcycle(const MgHier& h, const MgArgs& a, cudaStream_t s) {
     const MarchPlan m = march_plan(v.nx, v.ny, v.nz, cached_resident(k_mg_down0<float>, &r_down));
     k_mg_down0<float><<<m.blocks, kMgThreads, 0, s>>>(v, m, rhs(l), wgt(l), a.st);
     const MarchPlan mr = march_plan(cv.nx, cv.ny, cv.nz, cached_resident(k_mg_restrict, &r_res));
-    k_mg_restrict<<<mr.blocks, kMgThreads, 0, s>>>(v, cv, mr, l + 1 < L - 1 ? cv.oinv : nullptr, a.st);
+    k_mg_restrict<<<mr.blocks, kMgThreads, 0, s>>>(v, cv, mr, l + 1 < L - 1 ? cv.oinv : nullptr,
+                                                   h.wall_x, a.st);
   }
   k_mg_coarse<<<1, kCoarseThreads, 0, s>>>(h.lev[L - 1], h.pinv, h.ncoarse, a.st);
   for (int l = L - 2; l >= 0; --l) {
     const MgLevel& v = h.lev[l];
     const MarchPlan mp = march_plan(v.nx, v.ny, v.nz, cached_resident(k_mg_prolong<float>, &r_pro));
-    k_mg_prolong<float><<<mp.blocks, kMgThreads, 0, s>>>(v, h.lev[l + 1], mp, rhs(l), wgt(l), a.st);
+    k_mg_prolong<float><<<mp.blocks, kMgThreads, 0, s>>>(v, h.lev[l + 1], mp, rhs(l), wgt(l),
+                                                         h.wall_x, a.st);
     if (l == 0) {
       const MarchPlan m = march_plan(v.nx, v.ny, v.nz, cached_resident(k_mg_up<float, T, false>, &r_up0));
       k_mg_up<float, T, false><<<m.blocks, kMgThreads, 0, s>>>(v, m, in, out, a.st, a.I);

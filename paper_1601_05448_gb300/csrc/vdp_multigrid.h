@@ -31,6 +31,7 @@ struct MgLevel {
 
 struct MgHier {
   int nlev = 0;
+  int wall_x = 0;         // the duct: transfers do not reach across the x ends
   MgLevel lev[kMgMaxLevels] = {};
   float* pinv = nullptr;  // ncoarse x ncoarse pseudo-inverse of -A on the coarsest level
   int ncoarse = 0;
@@ -46,7 +47,7 @@ inline bool mg_supported(int nx, int ny, int nz) {
   return mg_level_dims(nx, ny, nz, d) > 0;
 }
 size_t mg_bytes(int nx, int ny, int nz);
-cudaError_t mg_alloc(MgHier* h, int nx, int ny, int nz);
+cudaError_t mg_alloc(MgHier* h, int nx, int ny, int nz, int wall_x);
 void mg_free(MgHier* h);
 // Build every level's coefficients from the FP64 face coefficients of the grid (level 0 scaled
 // by sinv = D^-1/2 on both sides) and the coarsest level's pseudo-inverse (host, double

@@ -11,6 +11,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
+from oracle import multigrid as MG  # noqa: E402
 import paper_1601_05448_gb300 as vdp  # noqa: E402
 import vdp_inputs as V  # noqa: E402
 
@@ -115,8 +116,6 @@ def test_spectral_cg_and_fixed_point_match_the_oracle(shape, lengths, precision,
 def test_duct_limits():
     with pytest.raises(vdp.VdpError):       # 2 x 40 = 80 is not an FFT length
         vdp.Solver(40, 32, 32, 1.0, lengths=(4.0, 1.0, 1.0), bc_x=vdp.VDP_BC_DUCT, precond=vdp.VDP_PRECOND_SPECTRAL)
-    with pytest.raises(vdp.VdpError):       # the V-cycle is for the periodic box
-        vdp.Solver(64, 32, 32, 1.0, lengths=(4.0, 1.0, 1.0), bc_x=vdp.VDP_BC_DUCT, precond=vdp.VDP_PRECOND_MG)
     with pytest.raises(vdp.VdpError):
         vdp.Solver(64, 32, 32, 1.0, lengths=(4.0, -1.0, 1.0), bc_x=vdp.VDP_BC_DUCT)
     with pytest.raises(vdp.VdpError):
@@ -139,3 +138,27 @@ def test_periodic_box_with_unequal_lengths():
         st = s.solve(_dev(prob.f), p, 1e-10)
     ref, _ = oracle.solve_cg(prob.rho, prob.f, 0.0, tol=1e-13, geom=(2.0, 1.0, 0.5, 0))
     assert st.ok and rel(p.cpu().numpy(), ref) <= 1e-9
+
+
+@pytest.mark.parametrize("shape,lengths", [((16, 16, 64), (4.0, 1.0, 1.0)), ((12, 20, 48), (3.0, 1.25, 0.75))])
+def test_vcycle_in_the_duct_matches_the_oracle_cycle(shape, lengths):
+    prob = V.duct_problem(shape, lengths, seed=sum(shape) + 4)
+    nz, ny, nx = shape
+    g = np.random.default_rng(6).standard_normal(shape)
+    out = torch.empty(shape, dtype=torch.float64, device=DEV)
+    with vdp.Solver(nx, ny, nz, 1.0, lengths=lengths, bc_x=vdp.VDP_BC_DUCT) as s:
+        s.set_density(_dev(prob.rho))
+        s.mg_apply(_dev(g), out)
+    ref = MG.Hierarchy.from_density(prob.rho, 0.0, geom=(*lengths, 1)).vcycle(g)
+    assert rel(out.cpu().numpy(), ref) <= 2e-5, rel(out.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-10, 1e-9), ("mixed", 1e-9, 1e-8)])
+def test_cg_mg_in_the_duct_matches_the_oracle(precision, tol, bound):
+    prob = V.duct_problem((32, 32, 128), (4.0, 1.0, 1.0), seed=12)
+    ref = _ref(prob, "mg")
+    p, st = _solve(prob, precision, tol, precond=vdp.VDP_PRECOND_MG)
+    assert st.ok and rel(p, ref) <= bound, (st, rel(p, ref))
+    if precision == "fp64":
+        _, info = MG.solve_pcg(prob.rho, prob.f, 0.0, tol=tol, geom=_geom(prob))
+        assert abs(st.iters - info["iters"]) <= 2, (st.iters, info["iters"])
