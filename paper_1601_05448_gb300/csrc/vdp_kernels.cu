@@ -1197,8 +1197,12 @@ __global__ void __launch_bounds__(kDirectThreads, DirectOcc<T, KIND>::kMinBlocks
 
 // Direct register march, RES64 phase only (a few launches per solve do work; the kernel has its
 // own register allocation so that the FP64 residual does not limit the stencil's occupancy).
+// Units per SM: three for the FP64 inner type (80 registers, no spills), two for FP32 (whose
+// variant would spill at three).
+template <class T> struct Res64Occ { static constexpr int kMinBlocks = IsF64<T>::value ? 3 : 2; };
+
 template <class T>
-__global__ void __launch_bounds__(kDirectThreads, 2) k_res64_direct(
+__global__ void __launch_bounds__(kDirectThreads, Res64Occ<T>::kMinBlocks) k_res64_direct(
     const InstDesc* __restrict__ insts, const UnitRef* __restrict__ units) {
   const UnitRef ur = units[blockIdx.x];
   stencil_kind_unit<T, T, 0, 2>(insts[ur.inst], ur.unit, nullptr);

@@ -185,7 +185,7 @@ __device__ __forceinline__ int ex(int k2, int j1) { return k2 * (M1 + 1) + j1; }
 
 // ---- X+ : real rows -> half spectrum -----------------------------------------------------------
 
-template <class T, int M1, int M2>
+template <class T, int M1, int M2, bool MIRROR>
 __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
     k_spec_x_fwd(SpecArgs a) {
   constexpr int m = M1 * M2, RY = rows_per_block<M1, M2>();
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
       const int j = t + M1 * j2;
       // pair j of the transformed row; mirrored rows read their second half backwards:
       // cells (2j, 2j + 1) of the extension are cells (q + 1, q) of the row, q = 2 nxd - 2 - 2j
-      const bool back = a.mirror && 2 * j >= a.nxd;
+      const bool back = MIRROR && 2 * j >= a.nxd;
       const int q = back ? 2 * a.nxd - 2 - 2 * j : 2 * j;
       float2 z = Pair<T>::ld(in + q);
       if (om) {
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
 
 // ---- X- : half spectrum -> real rows, z = W x ----------------------------------------------------
 
-template <class T, int M1, int M2>
+template <class T, int M1, int M2, bool MIRROR>
 __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
     k_spec_x_inv(SpecArgs a) {
   constexpr int m = M1 * M2, RY = rows_per_block<M1, M2>();
@@ -280,7 +280,8 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
       const int k2 = t + M1 * rr;
       const int l = k2 + M2 * k1;
       wv[rr][k1] = make_float2(1.f, 1.f);
-      if (live && om && k2 < M2 && 2 * l < a.nxd) wv[rr][k1] = *reinterpret_cast<const float2*>(om + 2 * l);
+      if (live && om && k2 < M2 && (!MIRROR || 2 * l < a.nxd))
+        wv[rr][k1] = *reinterpret_cast<const float2*>(om + 2 * l);
     }
   // Z'[k] = (X[k] + conj X[m-k]) + i conj(W_nx^k) (X[k] - conj X[m-k]); inverse M2-point DFTs.
   // Both X[k] and X[m-k] are read straight from the spectrum (in L2 after the Y- pass): for a
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
 #pragma unroll
       for (int k1 = 0; k1 < M1; ++k1) {
         const int l = k2 + M2 * k1;  // cells 2l, 2l + 1 of the row
-        if (2 * l >= a.nxd) continue;  // mirrored rows: the second half is the reflection
+        if (MIRROR && 2 * l >= a.nxd) continue;  // the second half is the reflection
         const float2 z = make_float2(o[k1].x * wv[rr][k1].x, o[k1].y * wv[rr][k1].y);
         Pair<T>::st(out + 2 * l, z);
       }
@@ -481,13 +482,14 @@ void factor(int n, int* m1, int* m2) {
 using SpecKernel = void (*)(SpecArgs);
 
 template <class T>
-SpecKernel x_kernel(int m, bool inverse, int* threads) {
+SpecKernel x_kernel(int m, bool inverse, bool mirror, int* threads) {
   int m1, m2;
   factor(m, &m1, &m2);
-#define VDP_X(M1, M2)                                                       \
-  if (m1 == M1 && m2 == M2) {                                               \
-    *threads = M1 * rows_per_block<M1, M2>();                               \
-    return inverse ? k_spec_x_inv<T, M1, M2> : k_spec_x_fwd<T, M1, M2>;     \
+#define VDP_X(M1, M2)                                                                       \
+  if (m1 == M1 && m2 == M2) {                                                               \
+    *threads = M1 * rows_per_block<M1, M2>();                                               \
+    if (mirror) return inverse ? k_spec_x_inv<T, M1, M2, true> : k_spec_x_fwd<T, M1, M2, true>; \
+    return inverse ? k_spec_x_inv<T, M1, M2, false> : k_spec_x_fwd<T, M1, M2, false>;       \
   }
   VDP_X(4, 4) VDP_X(4, 6) VDP_X(4, 8) VDP_X(6, 8) VDP_X(8, 8) VDP_X(8, 12) VDP_X(8, 16)
   VDP_X(16, 16)
@@ -528,7 +530,7 @@ SpecKernel yz_kernel(int n, int which, int* threads) {  // which: 0 = Y+, 1 = Y-
 bool x_supported(int nx) {
   if (nx % 2) return false;
   int threads = 0;
-  return x_kernel<float>(nx / 2, false, &threads) != nullptr;
+  return x_kernel<float>(nx / 2, false, false, &threads) != nullptr;
 }
 
 bool yz_supported(int n) {
@@ -596,7 +598,8 @@ cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStre
     case SPEC_X_INV: {
       const bool inv = pass == SPEC_X_INV;
       const bool f64 = prec == PREC_FP64 && !(inv && a.out_f32);
-      k = f64 ? x_kernel<double>(m, inv, &threads) : x_kernel<float>(m, inv, &threads);
+      k = f64 ? x_kernel<double>(m, inv, a.mirror != 0, &threads)
+              : x_kernel<float>(m, inv, a.mirror != 0, &threads);
       const int ry = x_rows_per_block(m);
       grid = ry ? (unsigned)((rows + ry - 1) / ry) : 0;
       break;
