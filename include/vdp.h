@@ -4,13 +4,17 @@
  *
  *        div( (1/rho) grad p ) = f ,                                   (Sec. 3.4 of [1])
  *
- * on a uniform, triply periodic, staggered grid (Sec. 3.1 and Sec. 3.2 case 1 of [1]).
+ * on a uniform, triply periodic, staggered grid (Sec. 3.1 and Sec. 3.2 case 1 of [1]), or on the
+ * inflow-outflow duct of Sec. 3.2 case 2 (periodic y, z; see vdp_create_bc).  Also: the steps
+ * either side of the solve in a projection substep (App. A), a multigrid V-cycle, and a
+ * constant-coefficient inverse.
  *
  * [1] H. Pouransari, M. Mortazavi, A. Mani, "Parallel variable-density particle-laden turbulence
  *     simulation", CTR Annual Research Briefs (arXiv:1601.05448).
  *
  * Discretisation (the paper gives only the continuous equation and "staggered, second order"):
- *   cell (i,j,k), index c = i + nx*(j + ny*k) (x fastest), spacing h_d = L/n_d, periodic wrap;
+ *   cell (i,j,k), index c = i + nx*(j + ny*k) (x fastest), spacing h_d = L_d/n_d, periodic wrap
+ *   (in the duct the faces at the two x ends carry no coefficient);
  *   1/rho on a face = 1 / (arithmetic mean of the two adjacent cell-centre densities) -- the
  *   averaging App. B of [1] uses to move rho off the cell centres;
  *   (A p)_c = sum_d b_d[c+e_d](p[c+e_d]-p[c]) - b_d[c](p[c]-p[c-e_d]),
