@@ -100,8 +100,9 @@ typedef enum {
                              the solve's scaled variables (W = D^1/2).  Iteration counts hardly
                              grow with the grid or the density ratio.  Needs at least one
                              coarsening (more than 64 cells, even sizes down to the coarsest);
-                             direct stencil sweep only; not in batches.  In the duct the
-                             transfers do not reach across the x ends  Extra memory: about 24
+                             direct stencil sweep only; batch members only in batches of
+                             ordinary launches (persistent = 0).  In the duct the transfers do
+                             not reach across the x ends  Extra memory: about 24
                              bytes per cell */
 } vdp_precond;
 

@@ -161,7 +161,7 @@ int capture(vdp_batch* b, int pairs) {
     const int kind = nfixed == (int)b->active.size() ? 2 : (ncheb || nfixed) ? 1 : 0;
     for (int i = 0; i < pairs && e == cudaSuccess; ++i) {
       e = launch_res64(b->prec, b->d_desc, b->d_units, b->ns, kDirectThreads, b->cap);
-      // members with the spectral passes: their five FFT kernels (each gated on its own
+      // members with the spectral passes or the V-cycle: their kernels (each gated on its own
       // member's phase), between the residual and the stencil sweeps as in a solve alone.  The
       // members' chains are independent, so they go to up to four graph branches that the GPU
       // runs concurrently (small grids alone would leave most SMs idle).
@@ -174,9 +174,14 @@ int capture(vdp_batch* b, int pairs) {
       for (size_t k = 0; k < b->active.size() && e == cudaSuccess; ++k) {
         const vdp_ctx* c = b->members[b->active[k]].ctx;
         if (c->hdesc.pc < PC_SPECTRAL) continue;
+        cudaStream_t br = b->aux[slot++ % nb];
+        if (c->hdesc.pc == PC_MG) {
+          const MgArgs a{c->r, c->za, c->omega, c->st, c->desc};
+          e = launch_mg_vcycle(*c->mg, b->prec, a, br);
+          continue;
+        }
         SpecArgs a;
         solve_spec_args(c, b->prec, &a);
-        cudaStream_t br = b->aux[slot++ % nb];
         for (int pass = 0; pass < SPEC_PASSES && e == cudaSuccess; ++pass)
           e = launch_spectral_pass(b->prec, pass, a, br);
       }
@@ -267,13 +272,12 @@ void vdp_batch_destroy(vdp_batch* b) {
 int vdp_batch_add(vdp_batch* b, vdp_ctx* c, const double* rhs, double* p, double tol) {
   if (!b || !c || !rhs || !p || !(tol > 0.0)) return VDP_EINVAL;
   if (!c->has_density || c->opts.precision != b->prec || c->opts.stencil != 0) return VDP_EINVAL;
-  // the spectral passes are separate kernels: members with that preconditioner need the batch
+  // the spectral passes and the V-cycle are separate kernels: members with them need the batch
   // of ordinary launches, not the persistent kernel
-  if ((c->opts.precond == VDP_PRECOND_SPECTRAL || c->opts.method == VDP_METHOD_FIXED_POINT) &&
+  if ((c->opts.precond == VDP_PRECOND_SPECTRAL || c->opts.precond == VDP_PRECOND_MG ||
+       c->opts.method == VDP_METHOD_FIXED_POINT) &&
       b->persistent)
     return VDP_EINVAL;
-  // the multigrid V-cycle runs in single solves only
-  if (c->opts.precond == VDP_PRECOND_MG && c->opts.method == VDP_METHOD_CG) return VDP_EINVAL;
   if (!is_device_ptr(rhs) || !is_device_ptr(p) || ((uintptr_t)rhs & 15) || ((uintptr_t)p & 15))
     return VDP_EINVAL;
   if (find(b, c, nullptr)) return VDP_EINVAL;  // already a member

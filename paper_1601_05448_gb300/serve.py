@@ -25,10 +25,12 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import PRECISIONS, VDP_ENOMEM, VDP_METHOD_FIXED_POINT, VDP_PRECOND_JACOBI, VDP_PRECOND_SPECTRAL, Batch, \
-    Solver, VdpError, spectral_extra_bytes, spectral_supported
+from . import PRECISIONS, VDP_ENOMEM, VDP_METHOD_FIXED_POINT, VDP_PRECOND_JACOBI, VDP_PRECOND_MG, \
+    VDP_PRECOND_SPECTRAL, Batch, Solver, VdpError, spectral_extra_bytes, spectral_supported, vdp_mg_levels
 
 BYTES_PER_CELL = 96 + 2  # device memory of one context per cell (FP64-sized buffers + BF16 diag)
+# the multigrid levels (about 25 B per fine cell), z (8 B) and the weights (4 B)
+MG_EXTRA_BYTES_PER_CELL = 25 + 8 + 4
 CANCELLED = -2           # ServeRequest.status of a request cancelled before it finished
 
 
@@ -84,8 +86,9 @@ class Server:
     """``Server(precision="mixed", hbm_budget=64 GB, max_active=64).run(requests)``.
 
     precond="fixed_point" solves every request whose grid the FFT passes support by the paper's
-    fixed-point iteration, "spectral" by CG with the spectral preconditioner (the others by
-    Jacobi-preconditioned CG); both need the batch of ordinary launches (persistent=False).
+    fixed-point iteration, "spectral" by CG with the spectral preconditioner (the others by CG
+    with the multigrid V-cycle where the grid coarsens, else Jacobi-preconditioned CG); both need
+    the batch of ordinary launches (persistent=False).
     precond="jacobi" uses Jacobi-preconditioned CG everywhere.  inner_tol: the mixed path's
     reduction per inner solve."""
 
@@ -117,9 +120,15 @@ class Server:
         nz, ny, nx = shape
         return self.precond != "jacobi" and spectral_supported(nx, ny, nz)
 
+    def _multigrid(self, shape) -> bool:
+        nz, ny, nx = shape
+        return self.precond != "jacobi" and not self._spectral(shape) and vdp_mg_levels(nx, ny, nz) > 0
+
     def _ctx_bytes(self, shape) -> int:
         nz, ny, nx = shape
         extra = spectral_extra_bytes(nx, ny, nz) if self._spectral(shape) else 0
+        if self._multigrid(shape):
+            extra = MG_EXTRA_BYTES_PER_CELL * nx * ny * nz
         return BYTES_PER_CELL * nx * ny * nz + extra
 
     def _acquire(self, shape, L):
@@ -139,7 +148,8 @@ class Server:
         if self.tuned:
             from .tune import cached_options
             opts = cached_options(nx, ny, nz, self.precision, batchable=True) or {}
-        opts["precond"] = VDP_PRECOND_SPECTRAL if self._spectral(shape) else VDP_PRECOND_JACOBI
+        opts["precond"] = (VDP_PRECOND_SPECTRAL if self._spectral(shape) else
+                           VDP_PRECOND_MG if self._multigrid(shape) else VDP_PRECOND_JACOBI)
         if self._spectral(shape) and self.precond == "fixed_point":
             opts["method"] = VDP_METHOD_FIXED_POINT
         opts["inner_tol"] = self.inner_tol

@@ -132,7 +132,44 @@ def test_mg_limits():
         assert vdp.vdp_mg_apply(s.ctx, g, out) == vdp.VDP_EINVAL   # no density yet
         s.set_density(_dev(prob.rho))
         p = torch.empty_like(g)
-        with vdp.Batch("mixed", persistent=False) as b:
+        with vdp.Batch("mixed", persistent=True) as b:     # the persistent kernel has no V-cycle
             s.set_options(precision="mixed")
             with pytest.raises(vdp.VdpError):
                 b.add(s, g, p, 1e-8)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_mg_members_in_a_batch_equal_alone(precision):
+    """Batch of ordinary launches with V-cycle members of different sizes (FFT-unfriendly 40^3
+    among them), a spectral member and a Jacobi member: every result equals its solve alone,
+    bit for bit."""
+    mg = {"precond": vdp.VDP_PRECOND_MG}
+    probs = [(V.smooth_problem((40, 40, 40), seed=71), 1e-9, mg),
+             (V.hotspot_problem(64, seed=72, nspots=300, target_ratio=6.0), 1e-8, mg),
+             (V.smooth_problem((16, 24, 32), seed=73), 1e-10, mg),
+             (V.smooth_problem((32, 32, 32), seed=74), 1e-9, {"precond": vdp.VDP_PRECOND_SPECTRAL}),
+             (V.smooth_problem((12, 20, 24), seed=75), 1e-9, {})]
+    members = []
+    for prob, tol, opts in probs:
+        nz, ny, nx = prob.shape
+        s = vdp.Solver(nx, ny, nz, prob.L, precision=precision, **opts)
+        s.set_density(_dev(prob.rho))
+        f = _dev(prob.f)
+        p_alone = torch.empty_like(f)
+        st_alone = s.solve(f, p_alone, tol)
+        members.append((prob, tol, s, f, p_alone, st_alone))
+    with vdp.Batch(precision, persistent=False) as b:
+        outs = []
+        for prob, tol, s, f, *_ in members:
+            p = torch.full_like(f, -1.0)
+            b.add(s, f, p, tol)
+            outs.append(p)
+        b.run_to_completion(max_pairs=8)
+        for (prob, tol, s, f, p_alone, st_alone), p in zip(members, outs):
+            st = s.stats()
+            assert st.ok and st.iters == st_alone.iters and st.rel_res <= tol
+            assert torch.equal(p, p_alone), prob.name
+    ref, _ = oracle.solve_cg(probs[0][0].rho, probs[0][0].f, probs[0][0].L, tol=1e-13)
+    assert rel(outs[0].cpu().numpy(), ref) <= 1e-7
+    for _, _, s, *_ in members:
+        s.close()
