@@ -166,10 +166,26 @@ template <> struct Pair<double> {
 // line groups) a warp touches then fall on alternating halves of the 32 banks.
 __host__ __device__ constexpr int pad_stride(int len) { return ((len + 7) / 16) * 16 + 8; }
 
+// Shared memory of one row in the X passes: the four-step exchange, reused for the whole
+// transformed row (X+ unpack).
+template <int M1, int M2>
+constexpr int x_row_stride() {
+  return pad_stride(M2 * (M1 + 1)) > pad_stride(M1 * M2 + 1) ? pad_stride(M2 * (M1 + 1))
+                                                              : pad_stride(M1 * M2 + 1);
+}
+
 // Rows per block of the X passes: at most 256 threads and about 40 KB of shared memory, and a
 // multiple of 32 threads (the block reduction works on whole warps).
 template <int M1, int M2>
 constexpr int rows_per_block() {
+  for (int ry = 256 / M1; ry > 1; --ry)
+    if ((M1 * ry) % 32 == 0 && 8 * ry * x_row_stride<M1, M2>() <= 40960) return ry;
+  return 32;  // not reached for the supported sizes
+}
+
+// Rows per block of X- (register bound: half the rows of X+, so that more blocks share an SM).
+template <int M1, int M2>
+constexpr int inv_rows_per_block() {
   for (int ry = 256 / M1; ry > 1; --ry)
     if ((M1 * ry) % 32 == 0 &&
         8 * ry * (pad_stride(M2 * (M1 + 1)) + pad_stride(M1 * M2 + 1)) <= 40960)
@@ -186,19 +202,19 @@ __device__ __forceinline__ int ex(int k2, int j1) { return k2 * (M1 + 1) + j1; }
 // ---- X+ : real rows -> half spectrum -----------------------------------------------------------
 
 template <class T, int M1, int M2, bool MIRROR>
-__global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
+__global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>(), 1024 / (M1 * rows_per_block<M1, M2>()))
     k_spec_x_fwd(SpecArgs a) {
   constexpr int m = M1 * M2, RY = rows_per_block<M1, M2>();
-  constexpr int SA = pad_stride(M2 * (M1 + 1)), SB = pad_stride(m + 1);
-  __shared__ float2 sa[RY * SA], sb[RY * SB];
+  constexpr int SX = x_row_stride<M1, M2>();
+  __shared__ float2 sx[RY * SX];  // per row: the exchange, then the transformed row
   if (!spec_active(a)) return;
   const Tables tb = tables(a);
   const int t = threadIdx.x % M1, r = threadIdx.x / M1;
   const long long rows = (long long)a.ny * a.nz;
   const long long row = (long long)blockIdx.x * RY + r;
   const bool live = row < rows;
-  float2* ra = sa + r * SA;
-  float2* rb = sb + r * SB;
+  float2* ra = sx + r * SX;
+  float2* rb = ra;
   // step A: M2-point DFTs over j2 of z[t + M1 j2] = (x[2j], x[2j+1]) * W
   if (live) {
     const T* in = static_cast<const T*>(a.in) + row * a.nxd;
@@ -224,15 +240,31 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
       ra[ex<M1>(k2, t)] = k2 == 0 || t == 0 ? y[k2] : cmul(y[k2], tb.wm[t * k2]);
   }
   __syncthreads();
-  // step B: M1-point DFTs over j1 -> Z[k2 + M2 k1]
+  // step B: M1-point DFTs over j1 -> Z[k2 + M2 k1]; the exchange is read completely before the
+  // transformed row overwrites it
+  constexpr int R = (M2 + M1 - 1) / M1;
+  float2 u[R][M1];
   if (live) {
-    for (int k2 = t; k2 < M2; k2 += M1) {
-      float2 u[M1], o[M1];
 #pragma unroll
-      for (int j1 = 0; j1 < M1; ++j1) u[j1] = ra[ex<M1>(k2, j1)];
-      dft<M1, 0, 1, false>(u, o);
+    for (int rr = 0; rr < R; ++rr) {
+      const int k2 = t + M1 * rr;
+      if (k2 < M2) {
 #pragma unroll
-      for (int k1 = 0; k1 < M1; ++k1) rb[k2 + M2 * k1] = o[k1];
+        for (int j1 = 0; j1 < M1; ++j1) u[rr][j1] = ra[ex<M1>(k2, j1)];
+      }
+    }
+  }
+  __syncthreads();
+  if (live) {
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int k2 = t + M1 * rr;
+      if (k2 < M2) {
+        float2 o[M1];
+        dft<M1, 0, 1, false>(u[rr], o);
+#pragma unroll
+        for (int k1 = 0; k1 < M1; ++k1) rb[k2 + M2 * k1] = o[k1];
+      }
     }
   }
   __syncthreads();
@@ -256,9 +288,9 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
 // ---- X- : half spectrum -> real rows, z = W x ----------------------------------------------------
 
 template <class T, int M1, int M2, bool MIRROR>
-__global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>())
+__global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
     k_spec_x_inv(SpecArgs a) {
-  constexpr int m = M1 * M2, RY = rows_per_block<M1, M2>();
+  constexpr int m = M1 * M2, RY = inv_rows_per_block<M1, M2>();
   constexpr int SB = pad_stride(M2 * (M1 + 1));
   __shared__ float2 sb[RY * SB];
   if (!spec_active(a)) return;
@@ -487,7 +519,7 @@ SpecKernel x_kernel(int m, bool inverse, bool mirror, int* threads) {
   factor(m, &m1, &m2);
 #define VDP_X(M1, M2)                                                                       \
   if (m1 == M1 && m2 == M2) {                                                               \
-    *threads = M1 * rows_per_block<M1, M2>();                                               \
+    *threads = M1 * (inverse ? inv_rows_per_block<M1, M2>() : rows_per_block<M1, M2>());     \
     if (mirror) return inverse ? k_spec_x_inv<T, M1, M2, true> : k_spec_x_fwd<T, M1, M2, true>; \
     return inverse ? k_spec_x_inv<T, M1, M2, false> : k_spec_x_fwd<T, M1, M2, false>;       \
   }
@@ -497,11 +529,11 @@ SpecKernel x_kernel(int m, bool inverse, bool mirror, int* threads) {
   return nullptr;
 }
 
-int x_rows_per_block(int m) {
+int x_rows_per_block(int m, bool inverse) {
   int m1, m2;
   factor(m, &m1, &m2);
 #define VDP_R(M1, M2) \
-  if (m1 == M1 && m2 == M2) return rows_per_block<M1, M2>();
+  if (m1 == M1 && m2 == M2) return inverse ? inv_rows_per_block<M1, M2>() : rows_per_block<M1, M2>();
   VDP_R(4, 4) VDP_R(4, 6) VDP_R(4, 8) VDP_R(6, 8) VDP_R(8, 8) VDP_R(8, 12) VDP_R(8, 16)
   VDP_R(16, 16)
 #undef VDP_R
@@ -600,7 +632,7 @@ cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStre
       const bool f64 = prec == PREC_FP64 && !(inv && a.out_f32);
       k = f64 ? x_kernel<double>(m, inv, a.mirror != 0, &threads)
               : x_kernel<float>(m, inv, a.mirror != 0, &threads);
-      const int ry = x_rows_per_block(m);
+      const int ry = x_rows_per_block(m, inv);
       grid = ry ? (unsigned)((rows + ry - 1) / ry) : 0;
       break;
     }
