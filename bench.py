@@ -69,12 +69,11 @@ def spectrum_bytes(nx: int) -> float:
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
 # kernel at this precision and grid (profiles/k_stencil_direct_fp64_192.md and
 # profiles/k_spec_passes_192.md: 192^3, fixed-point method, FP64), keyed (precision, sweep, grid,
-# fixed-point); 256^3 entries scale by the cell count 256^3 / 192^3.  spec_x is the mean of X+ and
-# X-.  A changed kernel drops its entries until it is re-captured; the residual is left out (the
-# capture holds the residual from p = 0 only, the table averages both kinds).
+# fixed-point); 256^3 entries scale by the cell count 256^3 / 192^3.  A changed kernel drops its
+# entries until it is re-captured (the X+ pass since), and the residual is left out (the capture
+# holds the residual from p = 0 only, the table averages both kinds).
 _SCALE_256 = (256 / 192) ** 3
 _TRAFFIC_192 = {("fp64", "stencil", True): 259.5e6 + 84.7e6,
-                ("fp64", "spec_x", True): (85.0e6 + 4.0e6 + 59.0e6 + 2.5e6) / 2,
                 ("fp64", "spec_y", True): 30.7e6, ("fp64", "spec_z", True): 30.7e6}
 TRAFFIC = {(p, k, 192, f): v for (p, k, f), v in _TRAFFIC_192.items()}
 TRAFFIC.update({(p, k, 256, f): v * _SCALE_256 for (p, k, f), v in _TRAFFIC_192.items()})
