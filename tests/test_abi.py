@@ -85,7 +85,7 @@ def test_batch_tuning_keeps_to_batchable_layouts():
         assert tune._key(n, n, n, prec) != tune._key(n, n, n, prec, batchable=True)
 
 
-def test_multigrid_level_rule_matches_the_oracle():
+def test_multigrid_level_rule_matches_the_oracle(lib):
     from oracle import multigrid as MG
     for nx, ny, nz in ((256, 256, 256), (48, 48, 48), (40, 24, 16), (64, 48, 64), (8, 8, 1), (16, 8, 8),
                        (48, 36, 40), (24, 9, 16), (512, 512, 512), (80, 80, 80)):
