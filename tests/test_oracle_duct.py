@@ -142,3 +142,42 @@ def test_second_order_convergence_in_a_duct():
         p, info = oracle.solve_cg(rho, f, 0.0, tol=1e-13, geom=(Lx, Ly, Lz, 1))
         errs.append(np.abs(p - (p_ex - p_ex.mean())).max())
     assert errs[1] < errs[0] / 3.0 and errs[2] < errs[1] / 3.0, errs
+
+
+def _fft_tridiagonal_inverse(g, geom):
+    """The paper's constant-coefficient solve in the duct (Sec. 3.4): Fourier transforms in the
+    periodic directions y, z, then one tridiagonal solve along x per (ky, kz) with zero flux
+    through both ends; the zero mode is removed.  numpy FFTs and a dense tridiagonal solve."""
+    nz, ny, nx = g.shape
+    Lx, Ly, Lz, _ = geom
+    hx, hy, hz = Lx / nx, Ly / ny, Lz / nz
+    G = np.fft.fft(np.fft.fft(g, axis=1), axis=0)          # (kz, ky, x)
+    T = np.zeros((nx, nx))
+    for i in range(nx):                                     # second difference along x, no end flux
+        if i > 0:
+            T[i, i - 1] = 1.0
+            T[i, i] -= 1.0
+        if i < nx - 1:
+            T[i, i + 1] = 1.0
+            T[i, i] -= 1.0
+    T /= hx * hx
+    P = np.empty_like(G)
+    for kz in range(nz):
+        for ky in range(ny):
+            lam = (4 / hy ** 2 * math.sin(math.pi * ky / ny) ** 2 + 4 / hz ** 2 * math.sin(math.pi * kz / nz) ** 2)
+            M = T - lam * np.eye(nx)
+            if kz == 0 and ky == 0:                         # singular: the constant is free
+                sol = np.linalg.lstsq(M, G[kz, ky], rcond=None)[0]
+                P[kz, ky] = sol - sol.mean()
+            else:
+                P[kz, ky] = np.linalg.solve(M, G[kz, ky])
+    return np.real(np.fft.ifft(np.fft.ifft(P, axis=0), axis=1))
+
+
+@pytest.mark.parametrize("shape,geom", [((6, 8, 20), (3.0, 1.0, 0.75, 1)), ((4, 5, 12), (2.0, 0.5, 1.5, 1))])
+def test_cosine_inverse_equals_the_papers_fft_tridiagonal_solve(shape, geom):
+    rng = np.random.default_rng(45)
+    g = rng.standard_normal(shape)
+    ref = _fft_tridiagonal_inverse(g, geom)
+    got = oracle.inverse_laplacian(g, 0.0, geom=geom)
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
