@@ -398,3 +398,16 @@ def test_projection_is_the_density_weighted_least_change(shape):
     m_new, p, info = oracle.project(rho, m, rd, c, L)
     u_new = np.concatenate([(m_new[d] / _face_density(rho, d)).ravel() for d in range(3)])
     assert np.abs(u_new - u_best).max() <= 1e-9 * np.abs(u0).max()
+
+
+@pytest.mark.parametrize("geom", [None, (3.0, 1.0, 0.75, 1)])
+def test_paper_iteration_is_exact_in_one_step_for_constant_density(geom):
+    # Eq. (Pois): with rho constant the dropped term rho grad(1/rho) . grad(dp) is zero, so one
+    # step p = L^-1 (rho f) solves div((1/rho) grad p) = f exactly (periodic box and duct)
+    rng = np.random.default_rng(46)
+    shape = (6, 8, 24)
+    rho = np.full(shape, 2.5)
+    f = rng.standard_normal(shape)
+    p, info = oracle.solve_fixed_point(rho, f, 1.3, tol=1e-12, geom=geom)
+    assert info["status"] == "ok" and info["iters"] == 1 and info["rel_res"] <= 1e-13
+    assert oracle.relative_residual(rho, 1.3, f, p, geom=geom) <= 1e-13
