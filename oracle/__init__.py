@@ -252,3 +252,6 @@ def project(rho, m, rhs_div, c: float, L: float, tol: float = 1e-13):
     f = projection_rhs(rho, m, rhs_div, c, L)
     p, info = solve_cg(rho, f, L, tol=tol)
     return projection_correct(p, m, c, L), p, info
+
+
+from .spectral_cg import fft_inverse_laplacian, solve_pcg_spectral  # noqa: E402,F401

@@ -411,3 +411,71 @@ def test_paper_iteration_is_exact_in_one_step_for_constant_density(geom):
     p, info = oracle.solve_fixed_point(rho, f, 1.3, tol=1e-12, geom=geom)
     assert info["status"] == "ok" and info["iters"] == 1 and info["rel_res"] <= 1e-13
     assert oracle.relative_residual(rho, 1.3, f, p, geom=geom) <= 1e-13
+
+
+# ---- 10. the large-grid reference solver (oracle.solve_pcg_spectral) ----------------------------
+#
+# CG on the pinned operator, preconditioned by the constant-coefficient inverse through a library
+# FFT.  Its answer is pinned to the dense solve and to the oracle's Jacobi CG; its FFT inverse to
+# the oracle's plain DFT and to a Fourier mode's closed form.  A wrong preconditioner could only
+# slow it down (the true residual of the pinned operator decides the stop), which the last pin
+# shows with a deliberately wrong eigenvalue.
+
+@pytest.mark.parametrize("shape,L", [((8, 12, 16), 2.0), ((16, 16, 16), TWO_PI), ((6, 10, 24), (3.0, 1.5, 0.75))])
+def test_fft_inverse_equals_the_plain_dft_inverse(shape, L):
+    g = np.random.default_rng(sum(shape)).standard_normal(shape)
+    if np.isscalar(L):
+        ref = oracle.inverse_laplacian(g, L)
+    else:
+        ref = oracle.inverse_laplacian(g, None, geom=(L[0], L[1], L[2], 0))
+    assert rel(oracle.fft_inverse_laplacian(g, L), ref) < 1e-12
+
+
+def test_fft_inverse_on_a_mode():
+    shape, L, k = (12, 10, 16), 2.0, (3, -2, 1)
+    u, lam = _mode(shape, L, k)
+    u = u - u.mean()
+    assert rel(oracle.fft_inverse_laplacian(u, L), u / lam) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (8, 8, 8), (4, 6, 8)])
+def test_spectral_pcg_equals_dense_solve(shape):
+    nz, ny, nx = shape
+    L = 2.0
+    rng = np.random.default_rng(nx * ny * nz)      # the dense pin's density and right side
+    rho = rng.uniform(0.25, 2.5, shape)
+    f = rng.standard_normal(shape)
+    p_cg, _ = oracle.solve_cg(rho, f, L, tol=1e-13)
+    p, info = oracle.solve_pcg_spectral(rho, f, L, tol=1e-13)
+    assert info["status"] == "ok" and info["rel_res"] <= 1e-13
+    assert rel(p, p_cg) < 1e-11
+
+
+@pytest.mark.parametrize("make", [lambda: V.config0(),
+                                  lambda: V.hotspot_problem(48, seed=66, nspots=130, target_ratio=8.0)])
+def test_spectral_pcg_equals_jacobi_cg(make):
+    prob = make()
+    p_cg, i_cg = oracle.solve_cg(prob.rho, prob.f, prob.L, tol=1e-13)
+    p, info = oracle.solve_pcg_spectral(prob.rho, prob.f, prob.L, tol=1e-13)
+    assert info["status"] == "ok" and abs(info["rhs_mean"] - i_cg["rhs_mean"]) < 1e-15
+    assert rel(p, p_cg) < 1e-11
+    assert abs(float(p.mean())) < 1e-14 * float(np.abs(p).max())
+    assert oracle.relative_residual(prob.rho, prob.L, prob.f, p) <= 1e-13
+    assert 5 * info["iters"] < i_cg["iters"]        # the preconditioner does its job
+
+
+def test_spectral_pcg_answer_does_not_depend_on_the_preconditioner(monkeypatch):
+    """A planted mistake in the eigenvalues (sin instead of sin^2) leaves the answer alone and only
+    costs iterations: the stop is decided by the pinned operator's true residual."""
+    from oracle import spectral_cg as S
+    prob = V.hotspot_problem(32, seed=67, nspots=40, target_ratio=5.0)
+    p_ok, i_ok = oracle.solve_pcg_spectral(prob.rho, prob.f, prob.L, tol=1e-13)
+    good = S.laplacian_eigenvalues
+
+    def wrong(shape, L):
+        lam = good(shape, L)
+        return -np.sqrt(-lam) * 3.0
+    monkeypatch.setattr(S, "laplacian_eigenvalues", wrong)
+    p_bad, i_bad = oracle.solve_pcg_spectral(prob.rho, prob.f, prob.L, tol=1e-13)
+    assert i_bad["status"] == "ok" and rel(p_bad, p_ok) < 1e-11
+    assert i_bad["iters"] > i_ok["iters"]
