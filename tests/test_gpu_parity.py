@@ -87,6 +87,7 @@ def test_config0_mixed(precision):
     err = rel(p, ref)
     print(f"config0 {precision} tol 1e-8: iters={st.iters} outer={st.outer_iters} rel_res={st.rel_res:.3e} err={err:.3e}")
     assert st.ok and st.rel_res <= 1e-8
+    assert err <= 1e-8, err
 
 
 def test_hotspot_96_all_precisions():
@@ -225,56 +226,13 @@ def test_timed_solve_is_the_solve(precision, cheb):
         assert (k["ms"] > 0) == (k["launches"] > 0) and k["ms_min"] <= k["ms_mean"] + 1e-12
 
 
-_C1 = {}
-
-
-def config1_problem():
-    if "p" not in _C1:
-        _C1["p"] = V.config1()
-    return _C1["p"]
-
-
-@pytest.mark.parametrize("precision,tol,precond", [("fp64", 1e-10, 0), ("mixed", 1e-8, 0), ("mixed_bf16", 1e-8, 0),
-                                                   ("fp64", 1e-10, 2), ("mixed", 1e-8, 2)])
-def test_full_size_256_residual_in_oracle_operator(precision, tol, precond):
-    """The 256^3 hot-spot workload in the benchmark's launch configuration: the oracle's own
-    operator must confirm the relative residual of the returned pressure, on every cell; a
-    sample of cells is also checked against the flux form evaluated one cell at a time."""
-    prob = config1_problem()
-    nz, ny, nx = prob.shape
-    stream = torch.cuda.current_stream()
-    rho = torch.from_numpy(prob.rho).to(DEV)
-    f = torch.from_numpy(prob.f).to(DEV)
-    p = torch.empty_like(f)
-    with vdp.Solver(nx, ny, nz, prob.L, precision=precision, stream=stream, precond=precond) as s:
-        s.set_density(rho)
-        st = s.solve(f, p, tol)
-    ph = p.cpu().numpy()
-    rr = oracle.relative_residual(prob.rho, prob.L, prob.f, ph)
-    print(f"256^3 {precision} precond {precond}: iters={st.iters} outer={st.outer_iters} rel_res={st.rel_res:.3e} oracle={rr:.3e}")
-    assert st.ok and st.rel_res <= tol and rr <= 1.01 * tol
-    assert abs(float(ph.mean())) <= 1e-13 * float(np.abs(ph).max())
-    # sampled cells, flux form written out per cell (Eq. Pois with face 1/rho from the
-    # averaged face density): no cell's residual can exceed the L2 norm of the whole residual
-    rng = np.random.default_rng(64)
-    h = prob.L / nx
-    fm = prob.f - prob.f.mean()
-    bound = 1.01 * tol * np.linalg.norm(fm)
-    for _ in range(200):
-        k, j, i = (int(rng.integers(0, n)) for n in prob.shape)
-        acc = 0.0
-        for dk, dj, di in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
-            kp, jp, ip = (k + dk) % nz, (j + dj) % ny, (i + di) % nx
-            km, jm, im = (k - dk) % nz, (j - dj) % ny, (i - di) % nx
-            bp = 2.0 / (prob.rho[k, j, i] + prob.rho[kp, jp, ip])
-            bm = 2.0 / (prob.rho[k, j, i] + prob.rho[km, jm, im])
-            acc += (bp * (ph[kp, jp, ip] - ph[k, j, i]) - bm * (ph[k, j, i] - ph[km, jm, im])) / (h * h)
-        assert abs(acc - fm[k, j, i]) <= bound
-
-
 # ---- the spectral preconditioner (the paper's constant-coefficient inverse, Sec. 3.4) -----------
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (48, 64, 32), (64, 48, 96), (32, 32, 512), (96, 32, 48)])
+# (nz, ny, nx): every supported line length along some axis, including 192 and 256 along x (the
+# X passes' half-length complex FFTs of 96 and 128), y and z (the 256^3 and 192^3 workloads)
+@pytest.mark.parametrize("shape", [(32, 32, 32), (48, 64, 32), (64, 48, 96), (32, 32, 512), (96, 32, 48),
+                                   (256, 32, 32), (32, 256, 64), (192, 48, 32), (32, 192, 32), (32, 32, 256),
+                                   (32, 48, 192)])
 def test_inverse_laplacian_matches_oracle(shape):
     nz, ny, nx = shape
     L = 2.0 * np.pi
@@ -413,30 +371,3 @@ def test_device_loop_equals_polling_schedule(opts):
     print(f"device loop {st_dev.launches} launches, polling {st_host.launches}")
     assert np.array_equal(p_dev, p_host)
     assert (st_dev.iters, st_dev.outer_iters, st_dev.sweeps) == (st_host.iters, st_host.outer_iters, st_host.sweeps)
-
-
-def test_full_size_512_mixed():
-    """The 512^3 workload (200k hot spots, density ratio up to 10), mixed precision refined to
-    1e-8, by the paper's fixed-point iteration and by spectrally preconditioned CG: the oracle's
-    operator confirms the relative residual of each result on every cell (its own 512^3 solve
-    would take hours), and the two answers agree to the accuracy the tolerance implies."""
-    prob = V.config2()
-    nz, ny, nx = prob.shape
-    rho = torch.from_numpy(prob.rho).to(DEV)
-    f = torch.from_numpy(prob.f).to(DEV)
-    results = {}
-    for label, opts in (("fixed point", {"method": vdp.VDP_METHOD_FIXED_POINT}),
-                        ("CG spectral", {"precond": vdp.VDP_PRECOND_SPECTRAL})):
-        p = torch.empty_like(f)
-        with vdp.Solver(nx, ny, nz, prob.L, precision="mixed", **opts) as s:
-            s.set_density(rho)
-            st = s.solve(f, p, 1e-8)
-        ph = p.cpu().numpy()
-        rr = oracle.relative_residual(prob.rho, prob.L, prob.f, ph)
-        print(f"512^3 mixed {label}: ratio {prob.info['ratio']:.2f} iters={st.iters} outer={st.outer_iters} "
-              f"ms={st.ms:.1f} rel_res={st.rel_res:.2e} oracle={rr:.2e}")
-        assert st.ok and st.rel_res <= 1e-8 and rr <= 1.01e-8
-        results[label] = ph
-        del p
-    a, b = results["fixed point"], results["CG spectral"]
-    assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 1e-6

@@ -69,8 +69,12 @@ def test_hbm_budget_admission():
     with serve.Server("mixed", hbm_budget=budget, max_active=8, pairs_per_run=4, precond="jacobi") as srv:
         stats = srv.run(reqs)
     assert stats.completed == len(reqs) and stats.peak_bytes <= budget
-    ref, _ = oracle.solve_cg(reqs[0].rho, reqs[0].f, reqs[0].L, tol=1e-13)
-    assert np.linalg.norm(reqs[0].p.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-7
+    # every served pressure against the oracle, at the accuracy its tolerance states (mixed
+    # precision: 1e-8 for requests asking 1e-8 or less, the request's tolerance above that)
+    for r in reqs:
+        ref, _ = oracle.solve_cg(r.rho, r.f, r.L, tol=1e-13)
+        err = np.linalg.norm(r.p.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err <= max(r.tol, 1e-8), (r.rid, r.tol, err)
 
 
 def test_autotuner_picks_a_valid_layout(tmp_path, monkeypatch):
