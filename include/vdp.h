@@ -389,15 +389,29 @@ int vdp_batch_set_wait_limit(vdp_batch *batch, double seconds);
 int vdp_batch_inject_lost_arrival(vdp_batch *batch);
 
 /* ------------------------------------------------------------------------------------------ */
+/* Measurement helper.                                                                         */
+/* ------------------------------------------------------------------------------------------ */
+
+/*
+ * The FP64 FMA throughput of the current GPU, in TFLOP/s (one FMA = 2 flop), measured on
+ * `stream` (cudaStream_t, NULL = legacy default) by a kernel of independent FMA chains over
+ * 4 blocks of 256 threads per SM; the best of three timed launches after a warm-up.  No
+ * counterpart in the paper: the FP64 stencil and residual sweeps are bound by the FP64 pipe,
+ * and their roofline divides by this figure.  VDP_EINVAL for a NULL output, VDP_ECUDA on a CUDA
+ * error.  Synchronises the stream.
+ */
+int vdp_probe_fp64(void *stream, double *tflops);
+
+/* ------------------------------------------------------------------------------------------ */
 /* A solve that allocates no device memory.                                                    */
 /* ------------------------------------------------------------------------------------------ */
 
 /*
  * The paper has no counterpart to this entry point; it exists for callers that cannot call
- * cudaMalloc: code that runs while a CUDA graph is being captured on its stream (an allocation
- * there can break the capture or synchronise the device), hosts whose device memory belongs to
- * a pool or budget manager that forbids side allocations, and latency-critical loops that
- * cannot take the implicit device synchronisation of cudaMalloc/cudaFree.
+ * cudaMalloc: hosts whose device memory belongs to a pool or budget manager that reserves the
+ * GPU up front and forbids side allocations (a cudaMalloc there fails, or takes memory promised
+ * to another user), and latency-critical loops that cannot take the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree.
  *
  * vdp_solve_noalloc does what vdp_create + vdp_set_density + vdp_solve + vdp_destroy do with
  * default options (and gives the same pressure), for grids of at most VDP_NOALLOC_MAX_CELLS
@@ -409,20 +423,24 @@ int vdp_batch_inject_lost_arrival(vdp_batch *batch);
  *
  *   nx, ny, nz, L   grid and box as in vdp_create (nx a multiple of 8); nx*ny*nz above
  *                   VDP_NOALLOC_MAX_CELLS is rejected with VDP_EINVAL
- *   rho, rhs        device pointers, nx*ny*nz doubles (rhs 16-byte aligned); not modified
- *   p               device pointer, nx*ny*nz doubles, 16-byte aligned; output (zero mean)
+ *   rho, rhs        device pointers of the current device, nx*ny*nz doubles (rhs 16-byte
+ *                   aligned); not modified
+ *   p               device pointer of the current device, nx*ny*nz doubles, 16-byte aligned;
+ *                   output (zero mean)
  *   tol             relative residual target as in vdp_solve
  *   precision       vdp_precision
- *   stream          cudaStream_t for all work (NULL = legacy default stream); the call returns
- *                   after the work has finished
+ *   stream          cudaStream_t for all work (NULL = legacy default stream); the call
+ *                   synchronises this stream and returns after the work has finished
  *   stats           optional (may be NULL); ms is not measured (0)
- * Returns a vdp_status as vdp_solve / vdp_set_density do; host pointers give VDP_EINVAL.
+ * Returns a vdp_status as vdp_solve / vdp_set_density do.  VDP_EINVAL for host pointers,
+ * pointers of another device, and buffers whose allocation ends before nx*ny*nz doubles.
  *
- * The first call on a device looks up the device address of the array for that device (the
- * current device at the call); make that first call before any stream capture begins.  All calls
- * in the process share the one array and it keeps the contents of the last call: calls whose GPU
- * work overlaps -- from two host threads, or on two streams -- race and corrupt each other, so
- * serialise them.
+ * Set-up: the first call on a device (and the first after that device's context was destroyed
+ * and created again, e.g. by cudaDeviceReset) looks up the device address of the array in the
+ * current context with cudaGetSymbolAddress; make that first call before any stream capture
+ * begins.  All calls in the process share the one array and it keeps the contents of the last
+ * call (the solve clears what must start at zero): calls whose GPU work overlaps -- from two host
+ * threads, or on two streams -- race and corrupt each other, so serialise them.
  */
 #define VDP_NOALLOC_MAX_CELLS 65536
 #define VDP_NOALLOC_SCRATCH_BYTES 6752000

@@ -117,6 +117,7 @@ _SIGS = {
     "vdp_batch_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_double]),
     "vdp_batch_inject_lost_arrival": (ctypes.c_int, [_P]),
     "vdp_solve_timed": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.POINTER(vdp_sweep_times)]),
+    "vdp_probe_fp64": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "vdp_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                          ctypes.c_double, ctypes.c_int, _P, ctypes.POINTER(vdp_stats)]),
 }
@@ -265,17 +266,33 @@ def vdp_solve_timed(ctx: int, rhs, p, tol: float):
 
 def vdp_solve_noalloc(nx: int, ny: int, nz: int, L: float, rho, rhs, p, tol: float, precision: int = VDP_FP64,
                       stream=None):
-    """Solve without any device allocation (device tensors only, nx*ny*nz <= VDP_NOALLOC_MAX_CELLS).
+    """Solve without any device allocation (device tensors of the current device only,
+    nx*ny*nz <= VDP_NOALLOC_MAX_CELLS).
 
-    For callers that must not allocate device memory (inside a stream capture, under an external
-    memory pool, or in latency-critical loops); intermediates live in a fixed device array owned
-    by the library.  Calls share that array: do not run two at once.  Returns (status, stats)."""
+    For callers that cannot allocate device memory: hosts whose GPU memory is reserved by a pool
+    or budget manager that forbids side allocations, and latency-critical loops that cannot take
+    the device-wide synchronisation of cudaMalloc/cudaFree.  Intermediates live in a fixed device
+    array owned by the library; calls share it, so do not run two at once.  Returns (status,
+    stats); arrays of the wrong size raise ValueError before the C call."""
+    n = int(nx) * int(ny) * int(nz)
+    for a, name in ((rho, "rho"), (rhs, "rhs"), (p, "p")):
+        if _numel(a) != n:
+            raise ValueError(f"{name}: expected {n} elements, got {_numel(a)}")
     s = vdp_stats()
     st = load().vdp_solve_noalloc(int(nx), int(ny), int(nz), float(L), _ptr(rho), _ptr(rhs),
                                   _ptr(p, writable=True), float(tol), int(precision),
                                   stream if (stream is None or isinstance(stream, int)) else stream.cuda_stream,
                                   ctypes.byref(s))
     return st, s
+
+
+def vdp_probe_fp64(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current GPU in TFLOP/s (see include/vdp.h)."""
+    t = ctypes.c_double(0.0)
+    st = load().vdp_probe_fp64(_stream(stream), ctypes.byref(t))
+    if st != VDP_OK:
+        raise VdpError(st, "vdp_probe_fp64")
+    return t.value
 
 
 def vdp_batch_create(precision: int = VDP_MIXED, persistent: int = 1, stream=None) -> int:

@@ -1,17 +1,17 @@
 // vdp_noalloc.cu -- vdp_solve_noalloc: a complete small solve that allocates no device memory.
 //
-// Who needs this.  Some callers cannot call cudaMalloc: code that runs while another component
-// captures the stream into a CUDA graph (an allocation there can invalidate the capture or
-// synchronise the device), hosts whose device memory is owned by a pool or budget manager that
-// forbids side allocations, and latency-sensitive loops that cannot afford the implicit device
-// synchronisation of cudaMalloc/cudaFree.  vdp_solve_noalloc serves them: the caller passes
-// rho, rhs and p; every intermediate the solve needs (face coefficients, Jacobi scaling, Krylov
-// vectors, partial sums, solver state) lives in one file-scope __device__ array of fixed size
-// that the CUDA runtime creates when the library is loaded, on every GPU that loads it, and
-// keeps until the process exits.
+// Who needs this.  Some callers cannot call cudaMalloc: hosts whose device memory is owned by a
+// pool or budget manager that reserves the GPU up front and forbids side allocations (there a
+// cudaMalloc fails, or takes memory the manager has promised to someone else), and latency-
+// sensitive loops that cannot take the implicit device-wide synchronisation of cudaMalloc and
+// cudaFree.  vdp_solve_noalloc serves them: the caller passes rho, rhs and p; every intermediate
+// the solve needs (face coefficients, Jacobi scaling, Krylov vectors, partial sums, solver state)
+// lives in one file-scope __device__ array of fixed size that the CUDA runtime creates when the
+// library is loaded, on every GPU that loads it, and keeps until the process exits.
 //
 // The solve runs the same kernels, unit layout and state machine as vdp_solve with default
 // options, so the two return the same pressure.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,36 +46,105 @@ constexpr size_t kOffTicket = kOffState + align_up(sizeof(InstState));
 constexpr size_t kOffFlag = kOffTicket + kAlign;
 constexpr size_t kScratchBytes = kOffFlag + kAlign;
 
-// The scratch array.  Its name is only a host-side stand-in in host code; the device address
-// comes from cudaGetSymbolAddress (see scratch_base).
+// The scratch array.  In host code its name is only a host-side stand-in, not a device address
+// (a kernel given it would fault, or silently use the wrong memory); the device address comes
+// from cudaGetSymbolAddress (see scratch_base).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
-unsigned char* g_base[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Driver calls reached through the runtime's entry-point lookup (the library does not link
+// libcuda directly, so it still loads on machines without a driver).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+using MemGetAddressRangeFn = CUresult (*)(CUdeviceptr*, size_t*, CUdeviceptr);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+MemGetAddressRangeFn g_addr_range = nullptr;
+bool g_driver_looked_up = false;
+
+template <class F>
+bool driver_fn(const char* name, F* out) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  if (cudaGetDriverEntryPointByVersion(name, &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  *out = reinterpret_cast<F>(fn);
+  return true;
+}
+
+bool driver_ready() {  // called with g_mu held
+  if (!g_driver_looked_up) {
+    g_driver_looked_up = true;
+    if (!driver_fn("cuCtxGetCurrent", &g_ctx_current) || !driver_fn("cuCtxGetId", &g_ctx_id) ||
+        !driver_fn("cuMemGetAddressRange", &g_addr_range)) {
+      g_ctx_current = nullptr;
+      g_ctx_id = nullptr;
+      g_addr_range = nullptr;
+    }
+  }
+  return g_ctx_current && g_ctx_id && g_addr_range;
+}
+
+// The symbol address is looked up once per device and context: a context that was torn down
+// and created again (cudaDeviceReset) gets a new id, and with it a fresh lookup, since the
+// module -- and so the array -- may then sit at another address.
+struct Slot {
+  unsigned long long ctx_id = 0;
+  unsigned char* base = nullptr;
+};
+Slot g_slot[kMaxDevices];
+
+// Device address of the scratch array in the current device's current context.
 int scratch_base(unsigned char** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VDP_ECUDA;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_base[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return VDP_ECUDA;
-    g_base[dev] = static_cast<unsigned char*>(p);
+  if (!driver_ready()) return VDP_ECUDA;
+  CUcontext ctx = nullptr;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS) return VDP_ECUDA;
+  void* p = nullptr;
+  if (!ctx) {  // no context current yet: the runtime creates the primary one on this lookup
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return VDP_ECUDA;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return VDP_ECUDA;
   }
-  *out = g_base[dev];
+  unsigned long long id = 0;
+  if (g_ctx_id(ctx, &id) != CUDA_SUCCESS) return VDP_ECUDA;
+  Slot& sl = g_slot[dev];
+  if (!sl.base || sl.ctx_id != id) {
+    if (!p && (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)) return VDP_ECUDA;
+    sl.base = static_cast<unsigned char*>(p);
+    sl.ctx_id = id;
+  }
+  *out = sl.base;
   return VDP_OK;
 }
 
-bool on_device(const void* p) {
+// True when p is device (or managed) memory of the current device and the allocation it lies
+// in holds at least `bytes` bytes from p on.
+bool on_this_device(const void* p, size_t bytes) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (!(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) return false;
+  if (a.type == cudaMemoryTypeDevice && a.device != dev) return false;
+  CUdeviceptr base = 0;
+  size_t size = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!driver_ready()) return false;
+    if (g_addr_range(&base, &size, (CUdeviceptr)(uintptr_t)p) != CUDA_SUCCESS) return false;
+  }
+  const uintptr_t lo = (uintptr_t)p, end = (uintptr_t)base + size;
+  return lo >= (uintptr_t)base && lo <= end && end - lo >= bytes;
 }
 
 #define NA_CK(call)                             \
@@ -96,7 +165,10 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
   if (precision < VDP_FP64 || precision > VDP_MIXED_BF16) return VDP_EINVAL;
   const long long n = (long long)nx * ny * nz;
   if (n > kMaxCells) return VDP_EINVAL;  // larger than the fixed scratch array
-  if (!rho || !rhs || !p || !on_device(rho) || !on_device(rhs) || !on_device(p)) return VDP_EINVAL;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  if (!rho || !rhs || !p || !on_this_device(rho, bytes) || !on_this_device(rhs, bytes) ||
+      !on_this_device(p, bytes))
+    return VDP_EINVAL;
   if (((uintptr_t)rhs & 15) || ((uintptr_t)p & 15)) return VDP_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned char* base = nullptr;

@@ -1,5 +1,6 @@
-"""vdp_solve_noalloc: the solve for callers that cannot allocate device memory (inside a stream
-capture, under an external memory pool, in latency-critical loops).  Its intermediates live in a
+"""vdp_solve_noalloc: the solve for callers that cannot allocate device memory (hosts whose GPU
+memory is reserved by a pool or budget manager that forbids side allocations, latency-critical
+loops that cannot take cudaMalloc's device-wide synchronisation).  Its intermediates live in a
 fixed device array owned by the library, so it is checked against the ordinary vdp_solve entry
 point, through the C ABI, on two calls in a row (the second call must not be disturbed by what
 the first one left in the shared array).  This file is collected last on purpose."""
@@ -28,7 +29,7 @@ def reference(prob, tol, precision):
     return p.cpu().numpy(), st
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_bf16"])
 def test_noalloc_matches_vdp_solve_twice(precision):
     probs = [V.smooth_problem((32, 32, 32), seed=31), V.hotspot_problem(40, seed=32, nspots=80, target_ratio=6.0)]
     for prob in probs:  # two calls in a row, different sizes and densities
@@ -52,3 +53,19 @@ def test_noalloc_rejects_oversize_and_host_pointers():
     h = np.ones((8, 8, 8))
     st, _ = vdp.vdp_solve_noalloc(8, 8, 8, 1.0, h, h, np.empty_like(h), 1e-8)
     assert st == vdp.VDP_EINVAL
+    # arrays of the wrong size: the binding refuses them before the call
+    b = torch.ones((8, 8, 8), dtype=torch.float64, device=DEV)
+    with pytest.raises(ValueError):
+        vdp.vdp_solve_noalloc(8, 8, 8, 1.0, b, b[:-1], torch.empty_like(b), 1e-8)
+    # through the C ABI directly, an output whose allocation ends before nx*ny*nz doubles is
+    # rejected: after emptying torch's cache, a 12 MB tensor is one fresh cudaMalloc of exactly
+    # that size, so its last 64 doubles end the allocation
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    big = torch.zeros(12 << 17, dtype=torch.float64, device=DEV)
+    tail = big[-64:]
+    s = vdp.vdp_stats()
+    st = vdp.load().vdp_solve_noalloc(8, 8, 8, 1.0, b.data_ptr(), b.data_ptr(), tail.data_ptr(), 1e-8, 0, None,
+                                      vdp.ctypes.byref(s))
+    assert st == vdp.VDP_EINVAL
+    assert bool((big == 0).all())
