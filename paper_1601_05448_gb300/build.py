@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvdp.so")
 SOURCES = ["vdp_kernels.cu", "vdp_api.cu", "vdp_batch.cu", "vdp_noalloc.cu", "vdp_timed.cu",
-           "vdp_spectral.cu", "vdp_projection.cu", "vdp_multigrid.cu"]
+           "vdp_spectral.cu", "vdp_projection.cu", "vdp_multigrid.cu", "vdp_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
