@@ -822,7 +822,8 @@ def main():
 
 
 def _serve_jobs():
-    return [(n, 200000 + 10 * n + k) for n in __import__("vdp_inputs").SERVE_SIZES for k in range(2)]
+    import vdp_inputs as V
+    return [(n, 200000 + 10 * n + k) for n in V.SERVE_SIZES for k in range(2)]
 
 
 def run_c1(torch, vdp, dev, prob, stream, peaks, args, barrier):

@@ -135,6 +135,20 @@ def _ratio(T: np.ndarray) -> float:
     return float(T.max() / T.min())
 
 
+def _extreme_candidates(base: np.ndarray, H: np.ndarray, S: float):
+    """The cells that can hold the maximum or the minimum of base + s H for some s in [0, S]
+    (H >= 0), as flat arrays (base, H).  Both extremes are nondecreasing in s: a cell can be the
+    maximum only if base + S H reaches max(base), and the minimum only if base stays at or below
+    min(base + S H).  The extremes over these cells equal those over the whole grid, value for
+    value, so a bisection over them takes the same steps, just faster."""
+    b, h = base.ravel(), H.ravel()
+    if float(h.min()) < 0.0:
+        return b, h
+    top = b + S * h
+    keep = (top >= float(b.max())) | (b <= float(top.min()))
+    return b[keep], h[keep]
+
+
 def density_hotspots(shape, L: float, rng: np.random.Generator, nspots: int, kmax_F: float = 8.0,
                      nmodes_F: int = 16, F_amp: float = 0.3, target_ratio: float | None = None,
                      max_ratio: float | None = None):
@@ -172,9 +186,10 @@ def density_hotspots(shape, L: float, rng: np.random.Generator, nspots: int, kma
             lo, hi = 0.0, 1.0
             while _ratio(base + hi * H) < goal and hi < 1e6:
                 hi *= 2.0
+            bc, Hc = _extreme_candidates(base, H, hi)
             for _ in range(60):
                 mid = 0.5 * (lo + hi)
-                if _ratio(base + mid * H) < goal:
+                if _ratio(bc + mid * Hc) < goal:
                     lo = mid
                 else:
                     hi = mid
