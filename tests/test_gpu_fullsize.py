@@ -12,8 +12,9 @@ FP64 oracle's pressure on the same seeded input, element by element (relative L2
 
 The oracle's pressure comes from ``oracle.solve_pcg_spectral`` (CG on the oracle's pinned
 operator, preconditioned by the constant-coefficient inverse through a library FFT) converged to
-relative residual 1e-13 and confirmed by the true residual; it is computed once per session
-(about half a minute at 256^3 and a few minutes at 512^3 on the host cores).
+relative residual 1e-13 at 256^3 and 5e-12 at 512^3 (near the FP64 floor of the true residual
+there) and confirmed by the true residual; it is computed once per session (about half a minute
+at 256^3 and a few minutes at 512^3 on the host cores).
 """
 import numpy as np
 import pytest
@@ -42,10 +43,13 @@ def workload(name):
     """(problem, oracle pressure) of a workload, computed once per session."""
     if name not in _CACHE:
         prob = V.config1() if name == "c1" else V.config2()
-        p_ref, info = oracle.solve_pcg_spectral(prob.rho, prob.f, prob.L, tol=1e-13)
-        assert info["status"] == "ok" and info["rel_res"] <= 1e-13, info
-        # the oracle's answer also satisfies the oracle's Jacobi-CG stopping test
-        assert oracle.relative_residual(prob.rho, prob.L, prob.f, p_ref) <= 1e-13
+        # FP64 cannot take the true residual of this operator much below eps ||A|| ||p|| / ||f||:
+        # about 1e-13 at 256^3 and 2e-12 at 512^3, both far below the GPU tolerances tested
+        tol = 1e-13 if name == "c1" else 5e-12
+        p_ref, info = oracle.solve_pcg_spectral(prob.rho, prob.f, prob.L, tol=tol)
+        assert info["status"] == "ok" and info["rel_res"] <= tol, info
+        # the true residual, evaluated separately with the oracle's operator
+        assert oracle.relative_residual(prob.rho, prob.L, prob.f, p_ref) <= tol
         print(f"oracle {name}: {info['iters']} spectral-PCG iterations, rel_res {info['rel_res']:.2e}")
         _CACHE[name] = (prob, p_ref)
     return _CACHE[name]
