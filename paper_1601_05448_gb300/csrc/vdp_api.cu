@@ -662,9 +662,9 @@ int vdp_solve(vdp_ctx* c, const double* rhs, double* p, double tol) {
                            c->stream));
     VDP_CK(cudaEventRecord(c->ev1, c->stream));
     if (host_p) VDP_CK(cudaMemcpyAsync(p, dp, bytes, cudaMemcpyDeviceToHost, c->stream));
+    unsigned loops = 0;  // on the solver's stream: solves on other streams are not waited for
+    VDP_CK(cudaMemcpyAsync(&loops, c->d_rounds, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     VDP_CK(cudaStreamSynchronize(c->stream));
-    unsigned loops = 0;
-    VDP_CK(cudaMemcpy(&loops, c->d_rounds, sizeof(unsigned), cudaMemcpyDeviceToHost));
     const InstState& hs = c->hstate[0];
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);

@@ -44,13 +44,15 @@ def solve_alone(req, precision, precond="jacobi"):
     return p, st
 
 
-@pytest.mark.parametrize("persistent,precond", [(True, "jacobi"), (False, "jacobi"), (False, "spectral"),
-                                               (False, "fixed_point")])
-def test_served_results_equal_alone(persistent, precond):
+@pytest.mark.parametrize("mode,persistent,precond", [("batch", True, "jacobi"), ("batch", False, "jacobi"),
+                                                    ("batch", False, "spectral"), ("batch", False, "fixed_point"),
+                                                    ("streams", False, "fixed_point"), ("streams", False, "jacobi")])
+def test_served_results_equal_alone(mode, persistent, precond):
     reqs = request_stream()
     seen_overlap = []
 
-    with serve.Server("mixed", max_active=8, pairs_per_run=4, persistent=persistent, precond=precond) as srv:
+    with serve.Server("mixed", max_active=4 if mode == "streams" else 8, pairs_per_run=4, persistent=persistent,
+                      precond=precond, mode=mode) as srv:
         stats = srv.run(reqs, on_done=lambda r: seen_overlap.append(r.t_admit))
     s = stats.summary()
     assert s["completed"] == len(reqs) and s["p99_latency_s"] >= s["p50_latency_s"] > 0

@@ -149,6 +149,29 @@ def _extreme_candidates(base: np.ndarray, H: np.ndarray, S: float):
     return b[keep], h[keep]
 
 
+def hotspot_scale(base: np.ndarray, H: np.ndarray, goal: float, cand=None) -> float:
+    """s >= 0 with max(base + s H) / min(base + s H) = goal (H >= 0): the first power of two whose
+    ratio reaches the goal brackets s, then 60 bisection steps.  cand: (base, H) restricted to
+    the cells that can hold the extremes for every s up to the bracket (``_extreme_candidates``
+    with a bound at least as large), or None to find them here."""
+    lo, hi = 0.0, 1.0
+    if cand is None:
+        while _ratio(base + hi * H) < goal and hi < 1e6:
+            hi *= 2.0
+        bc, Hc = _extreme_candidates(base, H, hi)
+    else:
+        bc, Hc = cand
+        while _ratio(bc + hi * Hc) < goal and hi < 1e6:
+            hi *= 2.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if _ratio(bc + mid * Hc) < goal:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
 def density_hotspots(shape, L: float, rng: np.random.Generator, nspots: int, kmax_F: float = 8.0,
                      nmodes_F: int = 16, F_amp: float = 0.3, target_ratio: float | None = None,
                      max_ratio: float | None = None):
@@ -183,17 +206,7 @@ def density_hotspots(shape, L: float, rng: np.random.Generator, nspots: int, kma
             fa = 0.5 * (lo + hi)
             base = 1.0 + fa * F
         else:
-            lo, hi = 0.0, 1.0
-            while _ratio(base + hi * H) < goal and hi < 1e6:
-                hi *= 2.0
-            bc, Hc = _extreme_candidates(base, H, hi)
-            for _ in range(60):
-                mid = 0.5 * (lo + hi)
-                if _ratio(bc + mid * Hc) < goal:
-                    lo = mid
-                else:
-                    hi = mid
-            s = 0.5 * (lo + hi)
+            s = hotspot_scale(base, H, goal)
     T = base + s * H
     rho = 1.0 / T
     info = {"hotspot_scale": s, "F_amp": fa, "nspots": nspots, "ratio": float(rho.max() / rho.min())}
@@ -362,6 +375,44 @@ def config4_requests(count: int = 5000, rate: float = 200.0, seed: int = 99999):
         tol = float(10.0 ** rng.uniform(-10.0, -6.0))
         out.append(Request(j, float(t[j]), n, R, tol, 100000 + j))
     return out
+
+
+SERVE_BANK = 4          # seeded field sets per served grid size
+
+
+def serve_bank(n: int, k: int):
+    """Field set k of the served grid size n (seed 300000 + 10 n + k): the hot-spot recipe's
+    pieces before the density ratio is chosen -- base = 1 + 0.3 F (F: 16 random modes |k| <= 8,
+    max-abs normalised) and H (hot spots scaled by volume, 20000 n^3 / 256^3) -- and f (the
+    divergence recipe).  Returns (base, H, f)."""
+    rng = np.random.default_rng(300000 + 10 * n + k)
+    shape = (n, n, n)
+    kv, c = random_modes(rng, 16, 8.0)
+    F = modes_field(shape, kv, c)
+    F = F / float(np.abs(F).max())
+    H = hotspot_field(shape, TWO_PI, rng, int(round(20000 * n ** 3 / 256 ** 3)))
+    f = rhs_divergence(shape, TWO_PI, rng)
+    return 1.0 + 0.3 * F, H, f
+
+
+def request_draw(req: Request, bank_size: int = SERVE_BANK):
+    """Request j's seeded choices (seed 100000 + j): its field set, and the periodic shifts (in
+    cells, per axis z, y, x) applied to its density and to its right side."""
+    rng = np.random.default_rng(req.seed)
+    k = int(rng.integers(0, bank_size))
+    shift_rho = tuple(int(x) for x in rng.integers(0, req.n, size=3))
+    shift_f = tuple(int(x) for x in rng.integers(0, req.n, size=3))
+    return k, shift_rho, shift_f
+
+
+def request_fields(req: Request, bank, draw):
+    """rho and f of a served request (numpy): rho = 1 / (base + s H) of its field set, s =
+    hotspot_scale(base, H, req.ratio), and f, each shifted periodically by its draw."""
+    base, H, f = bank
+    _, shift_rho, shift_f = draw
+    s = hotspot_scale(base, H, req.ratio)
+    rho = np.roll(1.0 / (base + s * H), shift_rho, axis=(0, 1, 2))
+    return np.ascontiguousarray(rho), np.ascontiguousarray(np.roll(f, shift_f, axis=(0, 1, 2)))
 
 
 def request_problem(req: Request) -> Problem:
