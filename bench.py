@@ -97,20 +97,38 @@ TRAFFIC = {(p, k, 192, f): v for (p, k, f), v in _TRAFFIC_192.items()}
 TRAFFIC.update({(p, k, 256, f): v * _SCALE_256 for (p, k, f), v in _TRAFFIC_192.items()})
 
 
+def spec_bytes(prec: str, kind: str, nx: int, ncell: int, slabbed: bool, fixed: bool):
+    """(operand bytes, HBM bytes) per cell of the spectral passes of kind spec_x (X+ and X-),
+    spec_y (Y+ and Y-) or spec_z over one application.  X+ reads rt (T) and its weight (4) and
+    writes the half spectrum (S per cell); Y+ / Y- read and write it; Z reads and writes it; X-
+    reads it and its weight (4) and writes z (4 for the fixed-point iteration, else T).  When the
+    whole spectrum fits in L2 (256^3: 71 MB) no S byte reaches HBM; when the passes run slab by
+    slab (512^3) X+ hands its slab to Y+ and Y- to X- through L2, so only Y+'s write and Y-'s
+    read of S reach HBM."""
+    T = SIZES[prec][0]
+    zT = 4 if fixed else T
+    S = spectrum_bytes(nx)
+    whole_l2 = S * ncell <= 0.6 * L2_BYTES
+    if kind == "spec_x":
+        alg = T + 4 + S + S + 4 + zT
+        hbm = T + 4 + 4 + zT + (0 if (whole_l2 or slabbed) else 2 * S)
+    elif kind == "spec_y":
+        alg = 4 * S
+        hbm = 0 if whole_l2 else (2 * S if slabbed else 4 * S)
+    else:
+        alg = 2 * S
+        hbm = 0 if whole_l2 else 2 * S
+    return alg, hbm
+
+
 def sweep_cost(prec: str, kind: str, cheb_k: int = 1, nx: int = 256, fixed: bool = False, ncell: int = 0):
-    """(bytes, flops, hbm_bytes) per cell of one launch of sweep `kind`, or None.  hbm_bytes
-    differs from bytes only for the spectral passes whose half spectrum stays in L2."""
+    """(bytes, flops, hbm_bytes) per cell of one launch of sweep `kind`, or None (the spectral
+    passes: see spec_bytes, per application)."""
     T, B, diag = SIZES[prec]
     Bd = B if diag else 0
-    S = spectrum_bytes(nx)
-    in_l2 = ncell > 0 and S * ncell <= 0.6 * L2_BYTES
     if fixed and kind == "stencil":
         b = 4 + 4 * T + 3 * B + Bd
         return b, 14.0 + (2.0 if diag else 0.0), b
-    if kind == "spec_x":
-        return (3 * T + 8 + 2 * S) / 2, 0.0, (3 * T + 8 + (0 if in_l2 else 2 * S)) / 2
-    if kind in ("spec_y", "spec_z"):
-        return 2 * S, 0.0, 0.0 if in_l2 else 2 * S
     if kind == "mg":  # one V-cycle: level 0 down 24 B, restriction 4.5, prolongation 12, up 24
         # (FP32 rt, bt, W, t, z), the coarser levels 68.5 B per cell x 1/7 of the fine cells; an
         # FP64 solve adds the rounding of rt (12 B) and its FP64 z (4 B)
@@ -133,42 +151,53 @@ def sweep_cost(prec: str, kind: str, cheb_k: int = 1, nx: int = 256, fixed: bool
 
 
 def algorithmic(prec: str, ncell: int, iters: int, outer: int, spectral: bool = False, nx: int = 256,
-                fixed: bool = False):
+                fixed: bool = False, slabbed: bool = False):
     """Algorithmic HBM bytes of a whole solve (the roofline of the step as a whole)."""
     T = SIZES[prec][0]
-    if fixed:  # per update: five spectral passes and the fused sweep
-        per_iter = sum(c * sweep_cost(prec, k, nx=nx, fixed=True, ncell=ncell)[2]
-                       for k, c in (("spec_x", 2), ("spec_y", 2), ("spec_z", 1), ("stencil", 1)))
+    spec = sum(spec_bytes(prec, k, nx, ncell, slabbed, fixed)[1] for k in ("spec_x", "spec_y", "spec_z"))
+    if fixed:  # per update: one application and the fused sweep
+        per_iter = spec + sweep_cost(prec, "stencil", fixed=True)[2]
     else:
-        per_iter = sweep_cost(prec, "stencil")[2] + sweep_cost(prec, "update")[2]
-        if spectral:
-            per_iter += sum(c * sweep_cost(prec, k, nx=nx, ncell=ncell)[2]
-                            for k, c in (("spec_x", 2), ("spec_y", 2), ("spec_z", 1)))
+        per_iter = sweep_cost(prec, "stencil")[2] + sweep_cost(prec, "update")[2] + (spec if spectral else 0)
     return (iters * per_iter + outer * (48 + T) + max(outer - 1, 0) * (24 + T) + 32) * ncell
 
 
 def kernel_table(prec: str, ncell: int, kinds: dict, peaks: dict, grid: int, cheb_k: int = 1, nx: int = 256,
-                 fixed: bool = False):
+                 fixed: bool = False, slabbed: bool = False):
     """Per sweep kind: launches, mean/min duration (CUDA events around each launch), share of the
     summed kernel time, algorithmic GB/s (all operand bytes), the HBM fraction of the bytes that
-    reach HBM, and for FP64 sweeps the FP64 TFLOP/s and its fraction of the measured FP64 peak."""
+    reach HBM, and for FP64 sweeps the FP64 TFLOP/s and its fraction of the measured FP64 peak.
+    Spectral kinds are counted per application (their launches may be slabs)."""
     total = sum(k["ms"] for k in kinds.values()) or 1.0
+    apps = max(kinds.get("spec_z", {}).get("launches", 0), 1)
     out = {}
     for name, k in kinds.items():
         if not k["launches"]:
             continue
         row = {"kernel": KERNEL_NAMES[name], "launches": k["launches"], "mean_us": 1e3 * k["ms_mean"],
                "min_us": 1e3 * k["ms_min"], "share": k["ms"] / total}
+        t_all = k["ms"] / 1e3
+        if name.startswith("spec_"):
+            alg, hbm = spec_bytes(prec, name, nx, ncell, slabbed, fixed)
+            row["us_per_application"] = 1e6 * t_all / apps
+            row["alg_bytes_per_launch"] = alg * ncell * apps / k["launches"]
+            row["gbs"] = alg * ncell * apps / t_all / 1e9
+            if hbm > 0:
+                row["hbm_alg_bytes_per_launch"] = hbm * ncell * apps / k["launches"]
+                row["hbm_frac"] = hbm * ncell * apps / t_all / 1e9 / peaks["hbm_gbs"]
+            else:
+                row["bytes_in"] = "L2 (half spectrum resident): gbs is L2 traffic, no HBM fraction"
+            row["tflops"] = 0.0
+            row["traffic"] = None
+            out[name] = row
+            continue
         cost = sweep_cost(prec, name, cheb_k, nx, fixed, ncell)
         if cost is not None:
             t = k["ms_mean"] / 1e3
             row["alg_bytes_per_launch"] = cost[0] * ncell
             row["gbs"] = cost[0] * ncell / t / 1e9
-            if cost[2] > 0:
-                row["hbm_alg_bytes_per_launch"] = cost[2] * ncell
-                row["hbm_frac"] = cost[2] * ncell / t / 1e9 / peaks["hbm_gbs"]
-            else:
-                row["bytes_in"] = "L2 (half spectrum resident): gbs is L2 traffic, no HBM fraction"
+            row["hbm_alg_bytes_per_launch"] = cost[2] * ncell
+            row["hbm_frac"] = cost[2] * ncell / t / 1e9 / peaks["hbm_gbs"]
             row["tflops"] = cost[1] * ncell / t / 1e12
             if prec == "fp64" and cost[1] > 0:
                 row["fp64_flop_frac"] = row["tflops"] / peaks["fp64_tflops"]
@@ -756,9 +785,10 @@ def main():
     st_t, kinds = solver.solve_timed(f, pt, prob.tol)
     assert st_t.iters == iters and torch.equal(pt, p), "instrumented solve differs from the timed solves"
     del pt
-    table = kernel_table(prec, ncell, kinds, peaks, nx, nx=nx, fixed=fixed)
+    slabbed = solver.spectral_slabs() > 1
+    table = kernel_table(prec, ncell, kinds, peaks, nx, nx=nx, fixed=fixed, slabbed=slabbed)
     roof = roofline(prec, table, peaks)
-    b_solve = algorithmic(prec, ncell, iters, outer, args.precond == "spectral", nx, fixed)
+    b_solve = algorithmic(prec, ncell, iters, outer, args.precond == "spectral", nx, fixed, slabbed)
     dtype = {"fp64": "f64", "mixed": "f32 inner, f64 outer",
              "mixed_bf16": "f32 inner (bf16 coefficients), f64 outer"}[prec]
     line = {
@@ -778,6 +808,7 @@ def main():
         "gdof_iter_per_s": ncell * iters * args.steps * world / elapsed / 1e9,
         "solve_hbm_frac": b_solve * args.steps * world / elapsed / 1e9 / peaks["hbm_gbs"],
         "fp64_peak": {k: peaks[k] for k in ("fp64_tflops", "fp64_tflops_derived", "fp64_source") if k in peaks},
+        "spectral_slabs": solver.spectral_slabs(),
         "kernels": table,
     }
 
@@ -810,7 +841,8 @@ def main():
                 p64 = torch.empty_like(f)
                 el64, st64 = timed(torch, s64, f, p64, prob.tol, args.steps, args.warmup, stream, barrier)
                 _, k64 = s64.solve_timed(f, p64, prob.tol)
-            tab = kernel_table("fp64", ncell, k64, peaks, nx, nx=nx, fixed=True)
+                sl64 = s64.spectral_slabs() > 1
+            tab = kernel_table("fp64", ncell, k64, peaks, nx, nx=nx, fixed=True, slabbed=sl64)
             return {"solves_per_s": args.steps / el64, "ms_per_step": 1e3 * el64 / args.steps,
                     "iters": st64[-1].iters, "outer": st64[-1].outer_iters, "rel_res": st64[-1].rel_res,
                     "roofline": roofline("fp64", tab, peaks),

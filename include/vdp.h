@@ -143,6 +143,9 @@ typedef struct {
   int method;          /* vdp_method (default VDP_METHOD_CG) */
   double damping;      /* VDP_METHOD_FIXED_POINT: scale of each update, 0 < damping <= 2
                           (default 1, the paper's update) */
+  int spec_slab;       /* spectral passes: z planes per slab when the half spectrum is too large
+                          for L2 (the X and Y passes then alternate slab by slab); 0 = automatic
+                          (one slab of about 32 MB of spectrum above 72 MB, else the whole grid) */
 } vdp_opts;
 
 typedef struct {
@@ -387,6 +390,13 @@ int vdp_batch_set_wait_limit(vdp_batch *batch, double seconds);
  * VDP_EINVAL for a batch of ordinary launches.
  */
 int vdp_batch_inject_lost_arrival(vdp_batch *batch);
+
+/*
+ * Number of slabs the spectral passes of ctx's solve run in (vdp_opts.spec_slab): 1 when the
+ * whole grid is transformed at once, more when X+/Y+ and Y-/X- alternate slab by slab; 0 when
+ * the solve does not use the spectral passes, or ctx is NULL.
+ */
+int vdp_spectral_slabs(const vdp_ctx *ctx);
 
 /* ------------------------------------------------------------------------------------------ */
 /* Measurement helper.                                                                         */

@@ -59,7 +59,7 @@ class vdp_opts(ctypes.Structure):
                 ("precond", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("use_guess", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("stencil", ctypes.c_int), ("tile_y", ctypes.c_int), ("units", ctypes.c_int),
                 ("stages", ctypes.c_int), ("threads", ctypes.c_int), ("steps_per_sync", ctypes.c_int),
-                ("method", ctypes.c_int), ("damping", ctypes.c_double)]
+                ("method", ctypes.c_int), ("damping", ctypes.c_double), ("spec_slab", ctypes.c_int)]
 
 
 class vdp_stats(ctypes.Structure):
@@ -117,6 +117,7 @@ _SIGS = {
     "vdp_batch_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_double]),
     "vdp_batch_inject_lost_arrival": (ctypes.c_int, [_P]),
     "vdp_solve_timed": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.POINTER(vdp_sweep_times)]),
+    "vdp_spectral_slabs": (ctypes.c_int, [_P]),
     "vdp_probe_fp64": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "vdp_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
                                          ctypes.c_double, ctypes.c_int, _P, ctypes.POINTER(vdp_stats)]),
@@ -284,6 +285,10 @@ def vdp_solve_noalloc(nx: int, ny: int, nz: int, L: float, rho, rhs, p, tol: flo
                                   stream if (stream is None or isinstance(stream, int)) else stream.cuda_stream,
                                   ctypes.byref(s))
     return st, s
+
+
+def vdp_spectral_slabs(ctx: int) -> int:
+    return load().vdp_spectral_slabs(ctx)
 
 
 def vdp_probe_fp64(stream=None) -> float:
@@ -466,6 +471,10 @@ class Solver:
             kinds[name] = {"launches": n, "ms": t.ms[i], "ms_min": t.ms_min[i],
                            "ms_mean": t.ms[i] / n if n else 0.0}
         return out, kinds
+
+    def spectral_slabs(self) -> int:
+        """Slabs the spectral passes run in (1: the whole grid at once; 0: no spectral passes)."""
+        return vdp_spectral_slabs(self.ctx)
 
     def inverse_laplacian(self, g, out) -> None:
         """out = L_h^-1 g, the constant-coefficient periodic solve (device tensors)."""

@@ -72,6 +72,7 @@ void vdp_default_options(vdp_opts* o) {
   o->steps_per_sync = 0;
   o->method = VDP_METHOD_CG;
   o->damping = 1.0;
+  o->spec_slab = 0;
 }
 
 const char* vdp_strerror(int s) {
@@ -222,8 +223,7 @@ cudaError_t launch_round(vdp_ctx* c, int prec, cudaStream_t s) {
   } else if (e == cudaSuccess && c->hdesc.pc >= PC_SPECTRAL) {  // z = M^-1 rt first
     SpecArgs a;
     solve_spec_args(c, prec, &a);
-    for (int pass = 0; pass < SPEC_PASSES && e == cudaSuccess; ++pass)
-      e = launch_spectral_pass(prec, pass, a, s);
+    e = launch_spectral_apply(prec, a, spec_slab(c), s);
   }
   if (e == cudaSuccess)
     e = launch_stencil(prec, c->lay.mode, stencil_kind(c->hdesc.pc), c->desc, c->units,
@@ -388,7 +388,14 @@ void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a) {
   a->st = c->st;
   a->I = c->desc;
   a->zunits = spectral_units(nxt, c->ny, c->nz);
+  a->z0 = 0;
+  a->z1 = c->nz;
+  a->xunits = spectral_xinv_units(nxt, c->ny, c->nz, c->nz);
   (void)prec;
+}
+
+int spec_slab(const vdp_ctx* c) {
+  return spectral_slab_planes(spectral_nx(c), c->ny, c->nz, c->opts.spec_slab);
 }
 
 int ensure_mg(vdp_ctx* c) {
@@ -532,7 +539,7 @@ int vdp_set_options(vdp_ctx* c, const vdp_opts* o) {
   if (o->precond == VDP_PRECOND_CHEB && (o->cheb_degree < 1 || o->cheb_degree > 16 || o->stencil != 0))
     return VDP_EINVAL;
   if (o->tile_y < 0 || o->units < 0 || o->stages < 0 || o->threads < 0 || o->steps_per_sync < 0 ||
-      o->stencil < 0 || o->stencil > 1)
+      o->stencil < 0 || o->stencil > 1 || o->spec_slab < 0)
     return VDP_EINVAL;
   if (o->units > 152 * 16 || o->stages > kMaxStages || (o->stages > 0 && o->stages < 4))
     return VDP_EINVAL;
@@ -725,6 +732,13 @@ int vdp_get_stats(const vdp_ctx* c, vdp_stats* s) {
   return VDP_OK;
 }
 
+int vdp_spectral_slabs(const vdp_ctx* c) {
+  if (!c || !(c->opts.precond == VDP_PRECOND_SPECTRAL || c->opts.method == VDP_METHOD_FIXED_POINT))
+    return 0;
+  const int slab = spec_slab(c);
+  return slab > 0 ? (c->nz + slab - 1) / slab : 0;
+}
+
 int vdp_inverse_laplacian(vdp_ctx* c, const double* g, double* out) {
   if (!c || !g || !out || g == out) return VDP_EINVAL;
   if (!is_device_ptr(g) || !is_device_ptr(out) || ((uintptr_t)g & 15) || ((uintptr_t)out & 15))
@@ -741,8 +755,7 @@ int vdp_inverse_laplacian(vdp_ctx* c, const double* g, double* out) {
   a.scale = (float)(-1.0 / ((double)a.nx * c->ny * c->nz));  // L_h^-1, not (-L_h)^-1
   a.st = nullptr;
   a.I = nullptr;
-  for (int pass = 0; pass < SPEC_PASSES; ++pass)
-    VDP_CK(launch_spectral_pass(PREC_FP64, pass, a, c->stream));
+  VDP_CK(launch_spectral_apply(PREC_FP64, a, spec_slab(c), c->stream));
   VDP_CK(cudaStreamSynchronize(c->stream));
   return VDP_OK;
 }

@@ -182,8 +182,7 @@ int capture(vdp_batch* b, int pairs) {
         }
         SpecArgs a;
         solve_spec_args(c, b->prec, &a);
-        for (int pass = 0; pass < SPEC_PASSES && e == cudaSuccess; ++pass)
-          e = launch_spectral_pass(b->prec, pass, a, br);
+        e = launch_spectral_apply(b->prec, a, spec_slab(c), br);
       }
       for (int j = 0; j < nb && e == cudaSuccess; ++j) {
         e = cudaEventRecord(b->join[j], b->aux[j]);

@@ -92,6 +92,7 @@ int ensure_spectral(vdp_ctx* c);
 // the arguments of the five spectral passes of a solve on this context (gated on its state)
 struct SpecArgs;
 void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a);
+int spec_slab(const vdp_ctx* c);  // planes per slab of the spectral passes
 // allocate the multigrid levels and the z and omega buffers (no-op when present); VDP_EINVAL
 // for grids the V-cycle does not support
 int ensure_mg(vdp_ctx* c);

@@ -210,9 +210,8 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>(), 1024 / (M1 * ro
   if (!spec_active(a)) return;
   const Tables tb = tables(a);
   const int t = threadIdx.x % M1, r = threadIdx.x / M1;
-  const long long rows = (long long)a.ny * a.nz;
-  const long long row = (long long)blockIdx.x * RY + r;
-  const bool live = row < rows;
+  const long long row = (long long)a.z0 * a.ny + (long long)blockIdx.x * RY + r;
+  const bool live = row < (long long)a.z1 * a.ny;
   float2* ra = sx + r * SX;
   float2* rb = ra;
   // step A: M2-point DFTs over j2 of z[t + M1 j2] = (x[2j], x[2j+1]) * W
@@ -296,9 +295,8 @@ __global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
   if (!spec_active(a)) return;
   const Tables tb = tables(a);
   const int t = threadIdx.x % M1, r = threadIdx.x / M1;
-  const long long rows = (long long)a.ny * a.nz;
-  const long long row = (long long)blockIdx.x * RY + r;
-  const bool live = row < rows;
+  const long long row = (long long)a.z0 * a.ny + (long long)blockIdx.x * RY + r;
+  const bool live = row < (long long)a.z1 * a.ny;
   float2* rb = sb + r * SB;
   // the output weights of this thread's cells are loaded first, so that their latency overlaps
   // the transforms (cells 2l, 2l + 1 with l = k2 + M2 k1, k2 = t, t + M1, ...)
@@ -361,10 +359,10 @@ __global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
       }
     }
   }
-  if (a.st) {  // the solve: the last block of this pass completes the preconditioner sweep, with
-               // <rt, z> from the partial sums the Z pass stored
+  if (a.st) {  // the solve: the last block of the application's X- launches completes the
+               // preconditioner sweep, with <rt, z> from the partial sums the Z pass stored
     const InstDesc& I = *a.I;
-    finish_sweep(I, I.st, PH_SPEC, gridDim.x, a.zunits);
+    finish_sweep(I, I.st, PH_SPEC, a.xunits, a.zunits);
   }
 }
 
@@ -387,7 +385,7 @@ __global__ void __launch_bounds__(M1 * kTX) k_spec_y(SpecArgs a) {
   const Tables tb = tables(a);
   const int c = threadIdx.x % kTX, t = threadIdx.x / kTX;
   const int tiles = a.nxp / kTX;
-  const int kz = blockIdx.x / tiles, kx = (blockIdx.x % tiles) * kTX + c;
+  const int kz = a.z0 + blockIdx.x / tiles, kx = (blockIdx.x % tiles) * kTX + c;
   float2* g = a.spec + (long long)kz * a.ny * a.nxp + kx;
   const long long es = a.nxp;  // element stride along y
   {
@@ -624,7 +622,7 @@ cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStre
   SpecKernel k = nullptr;
   unsigned grid = 0;
   const int m = a.nx / 2;
-  const long long rows = (long long)a.ny * a.nz;
+  if (a.z0 < 0 || a.z1 > a.nz || a.z0 >= a.z1) return cudaErrorInvalidValue;
   switch (pass) {
     case SPEC_X_FWD:
     case SPEC_X_INV: {
@@ -633,13 +631,14 @@ cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStre
       k = f64 ? x_kernel<double>(m, inv, a.mirror != 0, &threads)
               : x_kernel<float>(m, inv, a.mirror != 0, &threads);
       const int ry = x_rows_per_block(m, inv);
-      grid = ry ? (unsigned)((rows + ry - 1) / ry) : 0;
+      const long long srows = (long long)a.ny * (a.z1 - a.z0);
+      grid = ry ? (unsigned)((srows + ry - 1) / ry) : 0;
       break;
     }
     case SPEC_Y_FWD:
     case SPEC_Y_INV:
       k = yz_kernel(a.ny, pass == SPEC_Y_FWD ? 0 : 1, &threads);
-      grid = (unsigned)((a.nxp / kTX) * a.nz);
+      grid = (unsigned)((a.nxp / kTX) * (a.z1 - a.z0));
       break;
     case SPEC_Z:
       k = yz_kernel(a.nz, 2, &threads);
@@ -651,6 +650,65 @@ cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStre
   if (!k || !grid) return cudaErrorInvalidValue;
   k<<<grid, threads, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+// Slab budget: a slab's half spectrum (X+ output, Y+ input) must stay in the 129 MB L2 while
+// the pass streams its input through it; spectra up to kSlabAll are transformed whole.
+constexpr size_t kSlabBytes = 32u << 20;
+constexpr size_t kSlabAll = 72u << 20;
+
+int spectral_slab_planes(int nx, int ny, int nz, int req) {
+  if (req > 0) return req < nz ? req : nz;
+  const size_t plane = sizeof(float2) * (size_t)spectral_pitch(nx) * ny;
+  if (plane * nz <= kSlabAll) return nz;
+  const size_t p = kSlabBytes / plane;
+  return p < 1 ? 1 : (p > (size_t)nz ? nz : (int)p);
+}
+
+void spectral_schedule(int nz, int slab, std::vector<SpecLaunch>& out) {
+  out.clear();
+  if (slab < 1) slab = nz;
+  for (int z0 = 0; z0 < nz; z0 += slab) {
+    const int z1 = z0 + slab < nz ? z0 + slab : nz;
+    out.push_back(SpecLaunch{SPEC_X_FWD, z0, z1});
+    out.push_back(SpecLaunch{SPEC_Y_FWD, z0, z1});
+  }
+  out.push_back(SpecLaunch{SPEC_Z, 0, nz});
+  for (int z0 = 0; z0 < nz; z0 += slab) {
+    const int z1 = z0 + slab < nz ? z0 + slab : nz;
+    out.push_back(SpecLaunch{SPEC_Y_INV, z0, z1});
+    out.push_back(SpecLaunch{SPEC_X_INV, z0, z1});
+  }
+}
+
+int spectral_xinv_units(int nx, int ny, int nz, int slab) {
+  const int ry = x_rows_per_block(nx / 2, true);
+  if (ry <= 0) return 0;
+  if (slab < 1) slab = nz;
+  long long u = 0;
+  for (int z0 = 0; z0 < nz; z0 += slab) {
+    const int z1 = z0 + slab < nz ? z0 + slab : nz;
+    u += ((long long)ny * (z1 - z0) + ry - 1) / ry;
+  }
+  return (int)u;
+}
+
+SpecArgs spectral_launch_args(const SpecArgs& a, const SpecLaunch& l, int slab) {
+  SpecArgs b = a;
+  b.z0 = l.z0;
+  b.z1 = l.z1;
+  b.xunits = spectral_xinv_units(a.nx, a.ny, a.nz, slab);
+  return b;
+}
+
+cudaError_t launch_spectral_apply(int prec, const SpecArgs& a, int slab, cudaStream_t s) {
+  std::vector<SpecLaunch> sched;
+  spectral_schedule(a.nz, slab, sched);
+  for (const SpecLaunch& l : sched) {
+    const cudaError_t e = launch_spectral_pass(prec, l.pass, spectral_launch_args(a, l, slab), s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int spectral_units(int nx, int ny, int nz) {  // CTAs of the Z pass (they store <rt, z> parts)

@@ -34,6 +34,14 @@ struct SpecArgs {
   const InstDesc* I;     // the solve's description, with st: Z stores the partial sums of
                          // <rt, z>, X- completes the sweep
   int zunits;            // CTAs of the Z pass (partial slots), with st
+  int z0, z1;            // X and Y passes: the planes [z0, z1) of this launch (a slab)
+  int xunits;            // CTAs of all X- launches of one application (the sweep's arrivals)
+};
+
+// One launch of an application: the pass and its plane range.
+struct SpecLaunch {
+  int pass;
+  int z0, z1;
 };
 
 bool spectral_supported(int nx, int ny, int nz);
@@ -46,6 +54,18 @@ void spectral_tables(int nx, int ny, int nz, double hx, double hy, double hz,
 cudaError_t spectral_upload_roots();               // the register-DFT roots, once per device
 cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStream_t s);
 int spectral_units(int nx, int ny, int nz);        // CTAs of the Z pass (partial slots)
+// Planes per slab of one application (nz: a single slab).  When the half spectrum is larger
+// than a slab budget the X+ / Y+ passes (and Y- / X-) run slab by slab, interleaved, so that a
+// slab's spectrum is still in L2 when the next pass reads it.  req > 0 forces the slab size.
+int spectral_slab_planes(int nx, int ny, int nz, int req);
+// The launch sequence of one application: X+, Y+ per slab; Z; Y-, X- per slab.
+void spectral_schedule(int nz, int slab, std::vector<SpecLaunch>& out);
+// CTAs of all X- launches of one application
+int spectral_xinv_units(int nx, int ny, int nz, int slab);
+// Args of launch l (the plane range and the X- unit count filled in).
+SpecArgs spectral_launch_args(const SpecArgs& a, const SpecLaunch& l, int slab);
+// All launches of one application, in order.
+cudaError_t launch_spectral_apply(int prec, const SpecArgs& a, int slab, cudaStream_t s);
 cudaError_t launch_omega(const double* sinv, long long n, float* omega, cudaStream_t s);
 // out = rho / sinv (the fixed-point iteration's input weight)
 cudaError_t launch_rho_weight(const double* rho, const double* sinv, long long n, float* out,

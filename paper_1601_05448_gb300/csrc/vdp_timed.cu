@@ -10,6 +10,8 @@
 // submitted the kernel, and the submission latency would be counted as kernel time.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -61,10 +63,10 @@ int launch_shape(int phase) {
   }
 }
 
-// graphs 3 .. 7: the five spectral passes (SPEC_X_FWD .. SPEC_X_INV); graph 8: one whole
-// multigrid V-cycle
-constexpr int kTimedGraphs = 3 + SPEC_PASSES + 1;
-constexpr int kMgGraph = 3 + SPEC_PASSES;
+// graph 3: one whole multigrid V-cycle; the spectral launches of one application (X+ and Y+
+// slab by slab, Z, Y- and X- slab by slab) have a graph each in TimedGraphs::spec
+constexpr int kTimedGraphs = 4;
+constexpr int kMgGraph = 3;
 constexpr int kMgPass = 1000;  // capture_timed: the V-cycle instead of a spectral pass
 constexpr int kSpecKind[SPEC_PASSES] = {VDP_SWEEP_SPEC_X, VDP_SWEEP_SPEC_Y, VDP_SWEEP_SPEC_Z,
                                         VDP_SWEEP_SPEC_Y, VDP_SWEEP_SPEC_X};
@@ -72,29 +74,34 @@ constexpr int kSpecKind[SPEC_PASSES] = {VDP_SWEEP_SPEC_X, VDP_SWEEP_SPEC_Y, VDP_
 struct TimedGraphs {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaGraphExec_t g[kTimedGraphs] = {};
+  std::vector<cudaGraphExec_t> spec;
+  std::vector<SpecLaunch> sched;
   ~TimedGraphs() {
     for (auto& x : g)
+      if (x) cudaGraphExecDestroy(x);
+    for (auto& x : spec)
       if (x) cudaGraphExecDestroy(x);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
   }
 };
 
-// spec_pass >= 0: that spectral pass instead of the phase's kernel
-cudaError_t capture_timed(vdp_ctx* c, int prec, int phase, int spec_pass, TimedGraphs& t,
+// spec_launch >= 0: that launch of the spectral schedule instead of the phase's kernel
+cudaError_t capture_timed(vdp_ctx* c, int prec, int phase, int spec_launch, TimedGraphs& t,
                           cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   cudaError_t e2 = cudaEventRecordWithFlags(t.e0, c->cap, cudaEventRecordExternal);
   if (e2 == cudaSuccess) {
-    if (spec_pass == kMgPass) {
+    if (spec_launch == kMgPass) {
       const MgArgs a{c->r, c->za, c->omega, c->st, c->desc};
       e2 = launch_mg_vcycle(*c->mg, prec, a, c->cap);
-    } else if (spec_pass >= 0) {
+    } else if (spec_launch >= 0) {
       SpecArgs a;
       solve_spec_args(c, prec, &a);
-      e2 = launch_spectral_pass(prec, spec_pass, a, c->cap);
+      const SpecLaunch& l = t.sched[spec_launch];
+      e2 = launch_spectral_pass(prec, l.pass, spectral_launch_args(a, l, spec_slab(c)), c->cap);
     } else {
       e2 = launch_for_phase(c, prec, phase, c->cap);
     }
@@ -134,9 +141,12 @@ extern "C" int vdp_solve_timed(vdp_ctx* c, const double* rhs, double* p, double 
   if (spectral || mg) {
     if ((s = prepare_spectral_solve(c)) != VDP_OK) return s;
   }
-  if (spectral)
-    for (int i = 0; i < SPEC_PASSES; ++i)
-      VDP_CK(capture_timed(c, prec, PH_SPEC, i, t, &t.g[3 + i]));
+  if (spectral) {
+    spectral_schedule(c->nz, spec_slab(c), t.sched);
+    t.spec.assign(t.sched.size(), nullptr);
+    for (size_t i = 0; i < t.sched.size(); ++i)
+      VDP_CK(capture_timed(c, prec, PH_SPEC, (int)i, t, &t.spec[i]));
+  }
   if (mg) VDP_CK(capture_timed(c, prec, PH_SPEC, kMgPass, t, &t.g[kMgGraph]));
   auto fail = [&](cudaError_t e, const char* where) { return cuda_fail(e, where); };
   cudaError_t e;
@@ -160,10 +170,11 @@ extern "C" int vdp_solve_timed(vdp_ctx* c, const double* rhs, double* p, double 
     }
     const bool spec = spectral && hs.phase == PH_SPEC;
     const bool vcyc = mg && hs.phase == PH_SPEC;
-    for (int pass = 0; pass < (spec ? SPEC_PASSES : 1); ++pass) {
-      const int kind = spec ? kSpecKind[pass] : (vcyc ? VDP_SWEEP_MG : sweep_kind(hs.phase));
-      const int gi = spec ? 3 + pass : (vcyc ? kMgGraph : launch_shape(hs.phase));
-      if ((e = cudaGraphLaunch(t.g[gi], c->stream)) != cudaSuccess) return fail(e, "sweep launch");
+    const int nl = spec ? (int)t.sched.size() : 1;
+    for (int l = 0; l < nl; ++l) {
+      const int kind = spec ? kSpecKind[t.sched[l].pass] : (vcyc ? VDP_SWEEP_MG : sweep_kind(hs.phase));
+      cudaGraphExec_t ge = spec ? t.spec[l] : t.g[vcyc ? kMgGraph : launch_shape(hs.phase)];
+      if ((e = cudaGraphLaunch(ge, c->stream)) != cudaSuccess) return fail(e, "sweep launch");
       if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
         return fail(e, "cudaStreamSynchronize");
       float ms = 0.f;

@@ -371,3 +371,32 @@ def test_device_loop_equals_polling_schedule(opts):
     print(f"device loop {st_dev.launches} launches, polling {st_host.launches}")
     assert np.array_equal(p_dev, p_host)
     assert (st_dev.iters, st_dev.outer_iters, st_dev.sweeps) == (st_host.iters, st_host.outer_iters, st_host.sweeps)
+
+
+@pytest.mark.parametrize("slab", [1, 7, 16])
+def test_spectral_slabs_change_nothing(slab):
+    """The spectral passes run slab by slab (X+ / Y+ and Y- / X- alternating over groups of z
+    planes) give bitwise the answer of one whole-grid application: the inverse alone, the paper's
+    iteration and spectral CG, including an uneven last slab."""
+    prob = V.hotspot_problem(48, seed=68, nspots=130, target_ratio=5.0)
+    nz, ny, nx = prob.shape
+    g = torch.from_numpy(np.random.default_rng(5).standard_normal(prob.shape)).to(DEV)
+    outs = []
+    for sl in (0, slab):
+        with vdp.Solver(nx, ny, nz, prob.L, spec_slab=sl) as s:
+            o = torch.empty_like(g)
+            s.inverse_laplacian(g, o)
+            outs.append(o)
+    assert torch.equal(outs[0], outs[1])
+    for opts in ({"method": vdp.VDP_METHOD_FIXED_POINT}, {"precond": vdp.VDP_PRECOND_SPECTRAL}):
+        p0, st0 = gpu_solve(prob, "mixed", tol=1e-9, **opts)
+        p1, st1 = gpu_solve(prob, "mixed", tol=1e-9, spec_slab=slab, **opts)
+        assert np.array_equal(p0, p1) and st0.iters == st1.iters
+    with vdp.Solver(nx, ny, nz, prob.L, spec_slab=slab, method=vdp.VDP_METHOD_FIXED_POINT) as s:
+        assert s.spectral_slabs() == (nz + slab - 1) // slab
+        s.set_density(torch.from_numpy(prob.rho).to(DEV))
+        f = torch.from_numpy(prob.f).to(DEV)
+        p2 = torch.empty_like(f)
+        st2, kinds = s.solve_timed(f, p2, 1e-9)
+        assert kinds["spec_z"]["launches"] == st2.iters
+        assert kinds["spec_x"]["launches"] == 2 * s.spectral_slabs() * st2.iters
