@@ -622,12 +622,13 @@ def run_serving(torch, vdp, dev, banks, count=5000):
             req.f = torch.roll(f, d[2], dims=(0, 1, 2))
         client.synchronize()
 
+    def done(req):  # the client takes the result and lets go of the inputs and the result
+        req.rho = req.f = req.p = None
+
     torch.cuda.synchronize(dev)
     with serve.Server("mixed", hbm_budget=96 << 30, max_active=8, precond="fixed_point", mode="streams") as srv:
-        stats = srv.run(reqs, source=source)
+        stats = srv.run(reqs, source=source, on_done=done)
     ok = all(r.status == vdp.VDP_OK for r in reqs)
-    for r in reqs:  # results and inputs are not kept
-        r.p = r.rho = r.f = None
     s = stats.summary()
     s.update({"requests": count, "offered_rate_per_s": 200.0, "engine": "streams (8 worker slots)",
               "method": "the paper's fixed-point iteration, mixed precision, per-request tolerance",

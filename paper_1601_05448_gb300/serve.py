@@ -118,6 +118,7 @@ class _Slot:
                 solver.set_density(rho)
                 st = solver.solve(f, p, req.tol, check=False)
                 req.p = p
+                del rho, f, p
                 server._done.put((self, req, solver, st.status, st.iters, None))
             except Exception as e:  # reported to the dispatcher, which records the failure
                 server._done.put((self, req, solver, -1, 0, e))
