@@ -627,10 +627,12 @@ def run_serving(torch, vdp, dev, banks, count=5000):
 
     torch.cuda.synchronize(dev)
     with serve.Server("mixed", hbm_budget=96 << 30, max_active=8, precond="fixed_point", mode="streams") as srv:
+        warmed = srv.warm([(n, n, n) for n in V.SERVE_SIZES], V.TWO_PI)
         stats = srv.run(reqs, source=source, on_done=done)
     ok = all(r.status == vdp.VDP_OK for r in reqs)
     s = stats.summary()
     s.update({"requests": count, "offered_rate_per_s": 200.0, "engine": "streams (8 worker slots)",
+              "contexts_warmed": warmed,
               "method": "the paper's fixed-point iteration, mixed precision, per-request tolerance",
               "statuses_ok": ok,
               "inputs": f"per request: its seeded field set ({V.SERVE_BANK} per grid size), density ratio U[2,10] "

@@ -143,9 +143,9 @@ typedef struct {
   int method;          /* vdp_method (default VDP_METHOD_CG) */
   double damping;      /* VDP_METHOD_FIXED_POINT: scale of each update, 0 < damping <= 2
                           (default 1, the paper's update) */
-  int spec_slab;       /* spectral passes: z planes per slab when the half spectrum is too large
-                          for L2 (the X and Y passes then alternate slab by slab); 0 = automatic
-                          (one slab of about 32 MB of spectrum above 72 MB, else the whole grid) */
+  int spec_slab;       /* spectral passes: z planes per slab, X+/Y+ and Y-/X- then alternate
+                          slab by slab so a slab's spectrum is handed over in L2; 0 (default) =
+                          the whole grid at once (faster on the grids measured) */
 } vdp_opts;
 
 typedef struct {

@@ -54,9 +54,9 @@ void spectral_tables(int nx, int ny, int nz, double hx, double hy, double hz,
 cudaError_t spectral_upload_roots();               // the register-DFT roots, once per device
 cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStream_t s);
 int spectral_units(int nx, int ny, int nz);        // CTAs of the Z pass (partial slots)
-// Planes per slab of one application (nz: a single slab).  When the half spectrum is larger
-// than a slab budget the X+ / Y+ passes (and Y- / X-) run slab by slab, interleaved, so that a
-// slab's spectrum is still in L2 when the next pass reads it.  req > 0 forces the slab size.
+// Planes per slab of one application: req (vdp_opts.spec_slab) when positive and below nz, else
+// nz (a single slab).  With slabs the X+ / Y+ passes (and Y- / X-) run slab by slab,
+// interleaved, so that a slab's spectrum can still be in L2 when the next pass reads it.
 int spectral_slab_planes(int nx, int ny, int nz, int req);
 // The launch sequence of one application: X+, Y+ per slab; Z; Y-, X- per slab.
 void spectral_schedule(int nz, int slab, std::vector<SpecLaunch>& out);

@@ -225,6 +225,31 @@ class Server:
     def _release(self, s, shape, slot=None):
         self.idle[id(s)] = (s, shape, None if slot is None else slot.index)
 
+    def warm(self, shapes, L: float) -> int:
+        """Create the contexts the stream will need before it starts: for every slot (streams
+        mode; one set in batch mode) and every grid shape, a context within the budget, with its
+        solve graph captured by one solve of a zero right side (which returns at once).  Context
+        creation allocates device memory and captures graphs -- work that would otherwise stall
+        admissions in the middle of the stream.  Returns the contexts created."""
+        torch = self.torch
+        made = 0
+        slots = self._slots if self.mode == "streams" else [None]
+        for slot in slots:
+            for shape in shapes:
+                if self._ctx_bytes(shape) + self.bytes_in_use > self.budget:
+                    continue
+                s = self._acquire(tuple(shape), L, slot)
+                if s is None:
+                    continue
+                made += 1
+                rho = torch.ones(shape, dtype=torch.float64, device=self.device)
+                z = torch.zeros(shape, dtype=torch.float64, device=self.device)
+                s.set_density(rho)
+                s.solve(z, torch.empty_like(z), 1e-8)
+                self._release(s, tuple(shape), slot)
+        torch.cuda.synchronize(self.device)
+        return made
+
     def cancel(self, rid: int) -> None:
         """Cancel request `rid` (safe from another thread or an on_done callback): a waiting
         request is dropped; a running one leaves at its next step (batch mode) or has its result

@@ -53,6 +53,8 @@ def test_served_results_equal_alone(mode, persistent, precond):
 
     with serve.Server("mixed", max_active=4 if mode == "streams" else 8, pairs_per_run=4, persistent=persistent,
                       precond=precond, mode=mode) as srv:
+        if mode == "streams":  # contexts made before the stream, as the benchmark does
+            assert srv.warm(sorted({r.shape for r in reqs}), reqs[0].L) > 0
         stats = srv.run(reqs, on_done=lambda r: seen_overlap.append(r.t_admit))
     s = stats.summary()
     assert s["completed"] == len(reqs) and s["p99_latency_s"] >= s["p50_latency_s"] > 0
