@@ -405,7 +405,7 @@ int vdp_spectral_slabs(const vdp_ctx *ctx);
 /*
  * The FP64 FMA throughput of the current GPU, in TFLOP/s (one FMA = 2 flop), measured on
  * `stream` (cudaStream_t, NULL = legacy default) by a kernel of independent FMA chains over
- * 4 blocks of 256 threads per SM; the best of three timed launches after a warm-up.  No
+ * 8 blocks of 256 threads per SM; the best of three timed launches after a warm-up.  No
  * counterpart in the paper: the FP64 stencil and residual sweeps are bound by the FP64 pipe,
  * and their roofline divides by this figure.  VDP_EINVAL for a NULL output, VDP_ECUDA on a CUDA
  * error.  Synchronises the stream.
@@ -453,7 +453,7 @@ int vdp_probe_fp64(void *stream, double *tflops);
  * threads, or on two streams -- race and corrupt each other, so serialise them.
  */
 #define VDP_NOALLOC_MAX_CELLS 65536
-#define VDP_NOALLOC_SCRATCH_BYTES 6752000
+#define VDP_NOALLOC_SCRATCH_BYTES 7276288
 int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double *rho, const double *rhs,
                       double *p, double tol, int precision, void *stream, vdp_stats *stats);
 

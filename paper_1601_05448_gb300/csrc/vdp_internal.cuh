@@ -99,6 +99,7 @@ struct InstDesc {
   const double* by;
   const double* bz;
   const double* sinv;  // D^-1/2, D = sum of the six face coefficients of a cell
+  const double* dg;    // D itself (the FP64 residual's diagonal term)
   const void* sx;      // scaled coefficients bt = b sinv_l sinv_r in the inner storage type
   const void* sy;
   const void* sz;

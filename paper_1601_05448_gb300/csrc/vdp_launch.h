@@ -11,7 +11,7 @@ cudaError_t launch_check_density(const double* rho, long long n, int* bad, cudaS
 // face coefficients on the low faces (spacings h_d; duct: no flux through the x ends) and D^-1/2
 cudaError_t launch_build_coefficients(const double* rho, int nx, int ny, int nz, double hx,
                                       double hy, double hz, int duct, double* bx, double* by,
-                                      double* bz, double* sinv, cudaStream_t s);
+                                      double* bz, double* sinv, double* dg, cudaStream_t s);
 cudaError_t launch_scaled(int prec, const double* bx, const double* by, const double* bz,
                           const double* sinv, int nx, int ny, int nz, void* sx, void* sy, void* sz,
                           void* sd, cudaStream_t s);

@@ -35,8 +35,8 @@ constexpr size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign;
 // Layout of the scratch array for kMaxCells cells (offsets in bytes).
 constexpr size_t kF64 = align_up(sizeof(double) * kMaxCells);     // one FP64 field
 constexpr size_t kBf16 = align_up(sizeof(uint16_t) * kMaxCells);  // the BF16 diagonal correction
-constexpr size_t kOffFields = 0;                                   // bx by bz sinv sx sy sz x r d0 d1 q
-constexpr size_t kNumF64 = 12;
+constexpr size_t kOffFields = 0;  // bx by bz sinv sx sy sz x r d0 d1 q dg
+constexpr size_t kNumF64 = 13;
 constexpr size_t kOffSd = kOffFields + kNumF64 * kF64;
 constexpr size_t kOffPart = kOffSd + kBf16;
 constexpr size_t kOffUnits = kOffPart + align_up(sizeof(double) * kSlots * kMaxUnits);
@@ -195,7 +195,8 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
   NA_CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   NA_CK(cudaStreamSynchronize(s));
   if (bad) return VDP_EDENSITY;
-  NA_CK(launch_build_coefficients(rho, nx, ny, nz, L / nx, L / ny, L / nz, 0, bx, by, bz, sinv, s));
+  double* dg = f64[12];
+  NA_CK(launch_build_coefficients(rho, nx, ny, nz, L / nx, L / ny, L / nz, 0, bx, by, bz, sinv, dg, s));
   NA_CK(launch_scaled(precision, bx, by, bz, sinv, nx, ny, nz, sx, sy, sz, sd, s));
 
   // the default unit layout of vdp_solve
@@ -222,6 +223,7 @@ extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double*
   d.by = by;
   d.bz = bz;
   d.sinv = sinv;
+  d.dg = dg;
   d.sx = sx;
   d.sy = sy;
   d.sz = sz;

@@ -3,7 +3,7 @@
 // The FP64 stencil sweeps of the solver are bound by the FP64 pipe, not by HBM, so their roofline
 // needs the pipe's peak.  This probe measures it with the instruction those sweeps spend their
 // time on: every thread advances kChains independent FMA chains a = a * b + c (independent so the
-// pipe, not the FMA latency, sets the rate) for `iters` steps, over a grid of 4 blocks of 256
+// pipe, not the FMA latency, sets the rate) for `iters` steps, over a grid of 8 blocks of 256
 // threads per SM; CUDA events on the caller's stream time the launch.  FLOPs = 2 per FMA.
 #include <cuda_runtime.h>
 
@@ -11,7 +11,7 @@
 
 namespace {
 
-constexpr int kChains = 8;
+constexpr int kChains = 16;
 constexpr int kThreads = 256;
 
 __device__ double g_probe_sink;  // keeps the chains alive; written only on an impossible value
@@ -40,7 +40,7 @@ extern "C" int vdp_probe_fp64(void* stream, double* tflops) {
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
     return VDP_ECUDA;
-  const int blocks = 4 * sms, iters = 4096;
+  const int blocks = 8 * sms, iters = 2048;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return VDP_ECUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
