@@ -631,6 +631,21 @@ def run_serving(torch, vdp, dev, banks, count=5000):
         stats = srv.run(reqs, source=source, on_done=done)
     ok = all(r.status == vdp.VDP_OK for r in reqs)
     s = stats.summary()
+    by = {}
+    for n in V.SERVE_SIZES:  # latency (arrival to result) and service time (admission to result)
+        rs = [r for r in reqs if r.shape[0] == n and r.status == vdp.VDP_OK]
+        if rs:
+            lat = np.array([r.latency_s for r in rs])
+            svc = np.array([r.t_done - r.t_admit for r in rs])
+            by[n] = {"requests": len(rs), "p50_latency_s": float(np.percentile(lat, 50)),
+                     "p99_latency_s": float(np.percentile(lat, 99)), "p50_service_s": float(np.percentile(svc, 50)),
+                     "p99_service_s": float(np.percentile(svc, 99)), "mean_iters": float(np.mean([r.iters for r in rs]))}
+    s["by_grid"] = by
+    arr = np.array([r.arrival_s for r in reqs])
+    late = [r for r in reqs if r.latency_s > 0.1]
+    s["late_over_100ms"] = {"count": len(late), "first_arrival_s": float(min((r.arrival_s for r in late), default=0)),
+                           "last_arrival_s": float(max((r.arrival_s for r in late), default=0)),
+                           "stream_s": float(arr.max())}
     s.update({"requests": count, "offered_rate_per_s": 200.0, "engine": "streams (8 worker slots)",
               "contexts_warmed": warmed,
               "method": "the paper's fixed-point iteration, mixed precision, per-request tolerance",
