@@ -555,6 +555,12 @@ def run_duct(torch, vdp, dev, stream, shape=(128, 128, 256), lengths=(4.0 * math
     return out
 
 
+# Serving: worker slots (each a CUDA stream and a host thread); the process asks the driver for
+# as many hardware work queues as there are slots (CUDA_DEVICE_MAX_CONNECTIONS, read when CUDA
+# starts) so that the slots' streams do not share queues.
+SERVE_SLOTS = 16
+
+
 def _serve_bank_jobs():
     import vdp_inputs as V
     return [(n, k) for n in V.SERVE_SIZES for k in range(V.SERVE_BANK)]
@@ -626,7 +632,8 @@ def run_serving(torch, vdp, dev, banks, count=5000):
         req.rho = req.f = req.p = None
 
     torch.cuda.synchronize(dev)
-    with serve.Server("mixed", hbm_budget=96 << 30, max_active=8, precond="fixed_point", mode="streams") as srv:
+    with serve.Server("mixed", hbm_budget=96 << 30, max_active=SERVE_SLOTS, precond="fixed_point",
+                      mode="streams") as srv:
         warmed = srv.warm([(n, n, n) for n in V.SERVE_SIZES], V.TWO_PI)
         stats = srv.run(reqs, source=source, on_done=done)
     ok = all(r.status == vdp.VDP_OK for r in reqs)
@@ -646,7 +653,7 @@ def run_serving(torch, vdp, dev, banks, count=5000):
     s["late_over_100ms"] = {"count": len(late), "first_arrival_s": float(min((r.arrival_s for r in late), default=0)),
                            "last_arrival_s": float(max((r.arrival_s for r in late), default=0)),
                            "stream_s": float(arr.max())}
-    s.update({"requests": count, "offered_rate_per_s": 200.0, "engine": "streams (8 worker slots)",
+    s.update({"requests": count, "offered_rate_per_s": 200.0, "engine": f"streams ({SERVE_SLOTS} worker slots)",
               "contexts_warmed": warmed,
               "method": "the paper's fixed-point iteration, mixed precision, per-request tolerance",
               "statuses_ok": ok,
@@ -720,6 +727,7 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", str(2 * SERVE_SLOTS))
 
     import multiprocessing as mp
     import vdp_inputs as V

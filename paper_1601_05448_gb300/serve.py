@@ -227,26 +227,40 @@ class Server:
 
     def warm(self, shapes, L: float) -> int:
         """Create the contexts the stream will need before it starts: for every slot (streams
-        mode; one set in batch mode) and every grid shape, a context within the budget, with its
-        solve graph captured by one solve of a zero right side (which returns at once).  Context
-        creation allocates device memory and captures graphs -- work that would otherwise stall
-        admissions in the middle of the stream.  Returns the contexts created."""
+        mode; one set in batch mode) and every grid shape, a context within the budget, and run
+        one short solve on it (a density ratio of 2 to relative residual 1e-2) through the slot's
+        own thread, so context creation, graph capture and each thread's first allocations on
+        its stream -- work that would otherwise stall admissions early in the stream -- are
+        done.  Returns the contexts created."""
         torch = self.torch
         made = 0
         slots = self._slots if self.mode == "streams" else [None]
-        for slot in slots:
-            for shape in shapes:
+        for shape in shapes:
+            shape = tuple(shape)
+            nz, ny, nx = shape
+            x = torch.arange(nx, dtype=torch.float64, device=self.device) * (6.283185307179586 / nx)
+            rho = (1.5 + 0.5 * torch.cos(x)).expand(nz, ny, nx).contiguous()
+            f = torch.sin(x).expand(nz, ny, nx).contiguous()
+            for slot in slots:
                 if self._ctx_bytes(shape) + self.bytes_in_use > self.budget:
                     continue
-                s = self._acquire(tuple(shape), L, slot)
+                s = self._acquire(shape, L, slot)
                 if s is None:
                     continue
                 made += 1
-                rho = torch.ones(shape, dtype=torch.float64, device=self.device)
-                z = torch.zeros(shape, dtype=torch.float64, device=self.device)
-                s.set_density(rho)
-                s.solve(z, torch.empty_like(z), 1e-8)
-                self._release(s, tuple(shape), slot)
+                if slot is None:
+                    s.set_density(rho)
+                    s.solve(f, torch.empty_like(f), 1e-2)
+                    self._release(s, shape, slot)
+                    continue
+                req = ServeRequest(-1, 0.0, shape, L, rho, f, 1e-2)
+                slot.busy = True
+                slot.inbox.put((req, s))
+                done_slot, _, s_back, status, _, exc = self._done.get()
+                done_slot.busy = False
+                self._release(s_back, shape, done_slot)
+                if exc is not None:
+                    raise exc
         torch.cuda.synchronize(self.device)
         return made
 
