@@ -139,7 +139,7 @@ class Server:
 
     def __init__(self, precision: str = "mixed", hbm_budget: int = 64 << 30, max_active: int = 8,
                  pairs_per_run: int = 8, persistent: bool = False, tuned: bool = False, device: str = "cuda:0",
-                 precond: str = "fixed_point", inner_tol: float = 1e-5, mode: str = "streams"):
+                 precond: str = "fixed_point", inner_tol: float = 1e-4, mode: str = "streams"):
         import torch
         self.torch = torch
         self.precision = precision

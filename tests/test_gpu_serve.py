@@ -34,7 +34,7 @@ def solve_alone(req, precision, precond="jacobi"):
     nz, ny, nx = req.shape
     fft = precond != "jacobi" and vdp.spectral_supported(nx, ny, nz)
     mg = precond != "jacobi" and not fft and vdp.vdp_mg_levels(nx, ny, nz) > 0
-    opts = {"precond": vdp.VDP_PRECOND_SPECTRAL if fft else (vdp.VDP_PRECOND_MG if mg else 0), "inner_tol": 1e-5}
+    opts = {"precond": vdp.VDP_PRECOND_SPECTRAL if fft else (vdp.VDP_PRECOND_MG if mg else 0), "inner_tol": 1e-4}
     if fft and precond == "fixed_point":
         opts["method"] = vdp.VDP_METHOD_FIXED_POINT
     with vdp.Solver(nx, ny, nz, req.L, precision=precision, **opts) as s:
