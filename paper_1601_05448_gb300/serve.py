@@ -75,6 +75,8 @@ class ServeStats:
     peak_bytes: int = 0
     contexts_created: int = 0
     runs: int = 0
+    max_loop_gap_s: float = 0.0     # longest pause of the dispatcher loop (streams engine)
+    max_loop_gap_at_s: float = 0.0  # when it ended (stream time)
 
     def summary(self) -> dict:
         lat = np.array(self.latencies_s) if self.latencies_s else np.array([np.nan])
@@ -84,7 +86,8 @@ class ServeStats:
                 "solves_per_s": self.completed / self.elapsed_s if self.elapsed_s > 0 else None,
                 "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                 "mean_queue_s": float(np.mean(q)), "peak_context_bytes": self.peak_bytes,
-                "contexts_created": self.contexts_created, "batch_runs": self.runs}
+                "contexts_created": self.contexts_created, "batch_runs": self.runs,
+                "max_loop_gap_s": self.max_loop_gap_s, "max_loop_gap_at_s": self.max_loop_gap_at_s}
 
 
 class _Slot:
@@ -328,7 +331,13 @@ class Server:
         running = {}      # rid -> (req, slot)
         cancelled = set()
         error = None
+        last = time.perf_counter()
         while pending or waiting or running:
+            now_w = time.perf_counter()
+            if now_w - last > self.stats.max_loop_gap_s:
+                self.stats.max_loop_gap_s = now_w - last
+                self.stats.max_loop_gap_at_s = self._now()
+            last = now_w
             self._arrivals(pending, waiting, source)
             cancelled |= self._take_cancels()
             self._drop_cancelled_waiting(waiting, cancelled)
