@@ -622,16 +622,18 @@ def run_serving(torch, vdp, dev, banks, count=5000):
     client = torch.cuda.Stream(device=dev)
     reqs = [serve.ServeRequest(r.j, r.arrival_s, (r.n, r.n, r.n), V.TWO_PI, None, None, r.tol) for r in meta]
 
-    def source(req):  # the client makes the request's inputs on the GPU when it arrives
+    def source(req):  # the client makes the request's inputs on the GPU when it arrives (its
+        # own stream; the event tells the serving slot when they are written)
         r, d = meta[req.rid], draws[req.rid]
         base, H, f = gb[(r.n, d[0])]
         with torch.cuda.stream(client):
             req.rho = torch.roll(1.0 / (base + scales[req.rid] * H), d[1], dims=(0, 1, 2))
             req.f = torch.roll(f, d[2], dims=(0, 1, 2))
-        client.synchronize()
+            req.ready = torch.cuda.Event()
+            req.ready.record(client)
 
     def done(req):  # the client takes the result and lets go of the inputs and the result
-        req.rho = req.f = req.p = None
+        req.rho = req.f = req.p = req.ready = None
 
     # the client makes two requests' fields of every size once before the stream (its kernels
     # loaded and its allocations cached on its stream, as in a client that is already running)

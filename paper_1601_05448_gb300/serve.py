@@ -48,6 +48,9 @@ class ServeRequest:
     rho: object               # host numpy array or torch tensor (float64)
     f: object
     tol: float
+    # optional torch.cuda.Event recorded after the device tensors rho and f were written: the
+    # slot's stream waits for it (a client need not synchronise before submitting)
+    ready: object = None
     # filled in by the server
     t_admit: float = float("nan")
     t_done: float = float("nan")
@@ -113,11 +116,14 @@ class _Slot:
             req, solver = item
             try:
                 with torch.cuda.stream(self.stream):
+                    if req.ready is not None:  # the client's writes of rho and f come first
+                        self.stream.wait_event(req.ready)
                     rho = torch.as_tensor(req.rho, dtype=torch.float64).to(server.device, non_blocking=False)
                     f = torch.as_tensor(req.f, dtype=torch.float64).to(server.device, non_blocking=False)
                     rho, f = rho.contiguous(), f.contiguous()
                     p = torch.empty_like(f)
-                self.stream.synchronize()  # inputs in place before the library's calls on this stream
+                # (the library works on this stream, after the copies above; its own calls wait
+                # for the results)
                 solver.set_density(rho)
                 st = solver.solve(f, p, req.tol, check=False)
                 req.p = p
@@ -349,8 +355,8 @@ class Server:
                     break
                 req = waiting[0]
                 # prefer a free slot that already holds an idle context of this size
-                slot = next((sl for sl in free for (_, shp, si) in self.idle.values()
-                             if shp == req.shape and si == sl.index), free[0])
+                holders = {si for (_, shp, si) in self.idle.values() if shp == req.shape}
+                slot = next((sl for sl in free if sl.index in holders), free[0])
                 s = self._acquire(req.shape, req.L, slot)
                 if s is None:
                     if not running:  # nothing runs and no room even with every idle context freed
