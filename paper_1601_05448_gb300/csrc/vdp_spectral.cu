@@ -201,18 +201,14 @@ __device__ __forceinline__ int ex(int k2, int j1) { return k2 * (M1 + 1) + j1; }
 
 // ---- X+ : real rows -> half spectrum -----------------------------------------------------------
 
-template <class T, int M1, int M2, bool MIRROR>
-__global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>(), 1024 / (M1 * rows_per_block<M1, M2>()))
-    k_spec_x_fwd(SpecArgs a) {
-  constexpr int m = M1 * M2, RY = rows_per_block<M1, M2>();
-  constexpr int SX = x_row_stride<M1, M2>();
-  __shared__ float2 sx[RY * SX];  // per row: the exchange, then the transformed row
-  if (!spec_active(a)) return;
-  const Tables tb = tables(a);
-  const int t = threadIdx.x % M1, r = threadIdx.x / M1;
-  const long long row = (long long)a.z0 * a.ny + (long long)blockIdx.x * RY + r;
-  const bool live = row < (long long)a.z1 * a.ny;
-  float2* ra = sx + r * SX;
+// The X+ transform of RY rows (one per group of M1 threads: t = lane in the row, r = row in the
+// group), row `row` of the grid in thread group r; `ra` is the row's shared buffer of SX values
+// (the exchange, then the transformed row).  store(k, X) receives bin k of the row's half
+// spectrum for k < nxp (zero beyond nx/2).  Every thread of the block calls it (barriers).
+template <class T, int M1, int M2, bool MIRROR, class Store>
+__device__ __forceinline__ void x_fwd_rows(const SpecArgs& a, const Tables& tb, float2* ra,
+                                           long long row, bool live, int t, Store&& store) {
+  constexpr int m = M1 * M2;
   float2* rb = ra;
   // step A: M2-point DFTs over j2 of z[t + M1 j2] = (x[2j], x[2j+1]) * W
   if (live) {
@@ -269,7 +265,6 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>(), 1024 / (M1 * ro
   __syncthreads();
   // unpack: X[k] = E[k] + W_nx^k O[k], E = (Z[k] + conj Z[m-k]) / 2, O = (Z[k] - conj Z[m-k]) / 2i
   if (live) {
-    float2* out = a.spec + row * a.nxp;
     for (int k = t; k < a.nxp; k += M1) {
       float2 X = make_float2(0.f, 0.f);
       if (k <= m) {
@@ -279,25 +274,36 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>(), 1024 / (M1 * ro
         const float2 o = make_float2(0.5f * d.y, -0.5f * d.x);
         X = cadd(e, cmul(tb.wr[k], o));
       }
-      out[k] = X;
+      store(k, X);
     }
   }
 }
 
-// ---- X- : half spectrum -> real rows, z = W x ----------------------------------------------------
-
 template <class T, int M1, int M2, bool MIRROR>
-__global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
-    k_spec_x_inv(SpecArgs a) {
-  constexpr int m = M1 * M2, RY = inv_rows_per_block<M1, M2>();
-  constexpr int SB = pad_stride(M2 * (M1 + 1));
-  __shared__ float2 sb[RY * SB];
+__global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>(), 1024 / (M1 * rows_per_block<M1, M2>()))
+    k_spec_x_fwd(SpecArgs a) {
+  constexpr int RY = rows_per_block<M1, M2>();
+  constexpr int SX = x_row_stride<M1, M2>();
+  __shared__ float2 sx[RY * SX];  // per row: the exchange, then the transformed row
   if (!spec_active(a)) return;
   const Tables tb = tables(a);
   const int t = threadIdx.x % M1, r = threadIdx.x / M1;
   const long long row = (long long)a.z0 * a.ny + (long long)blockIdx.x * RY + r;
   const bool live = row < (long long)a.z1 * a.ny;
-  float2* rb = sb + r * SB;
+  float2* out = a.spec + row * a.nxp;
+  x_fwd_rows<T, M1, M2, MIRROR>(a, tb, sx + r * SX, row, live, t,
+                                 [&](int k, float2 X) { out[k] = X; });
+}
+
+// ---- X- : half spectrum -> real rows, z = W x ----------------------------------------------------
+
+// The X- transform of one row per group of M1 threads: `src` is the row of the half spectrum
+// (global or shared memory), `rb` the group's shared exchange buffer; z = W x is stored to row
+// `row` of a.out.  Every thread of the block calls it (barrier).
+template <class T, int M1, int M2, bool MIRROR>
+__device__ __forceinline__ void x_inv_rows(const SpecArgs& a, const Tables& tb, float2* rb,
+                                           const float2* src, long long row, bool live, int t) {
+  constexpr int m = M1 * M2;
   // the output weights of this thread's cells are loaded first, so that their latency overlaps
   // the transforms (cells 2l, 2l + 1 with l = k2 + M2 k1, k2 = t, t + M1, ...)
   constexpr int R = (M2 + M1 - 1) / M1;
@@ -314,10 +320,9 @@ __global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
         wv[rr][k1] = *reinterpret_cast<const float2*>(om + 2 * l);
     }
   // Z'[k] = (X[k] + conj X[m-k]) + i conj(W_nx^k) (X[k] - conj X[m-k]); inverse M2-point DFTs.
-  // Both X[k] and X[m-k] are read straight from the spectrum (in L2 after the Y- pass): for a
-  // fixed j2 the lanes of a row read consecutive values, ascending and descending.
+  // Both X[k] and X[m-k] are read straight from the spectrum: for a fixed j2 the lanes of a row
+  // read consecutive values, ascending and descending.
   if (live) {
-    const float2* src = a.spec + row * a.nxp;
     float2 xa[M2], xb[M2];
 #pragma unroll
     for (int j2 = 0; j2 < M2; ++j2) {
@@ -359,6 +364,20 @@ __global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
       }
     }
   }
+}
+
+template <class T, int M1, int M2, bool MIRROR>
+__global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
+    k_spec_x_inv(SpecArgs a) {
+  constexpr int RY = inv_rows_per_block<M1, M2>();
+  constexpr int SB = pad_stride(M2 * (M1 + 1));
+  __shared__ float2 sb[RY * SB];
+  if (!spec_active(a)) return;
+  const Tables tb = tables(a);
+  const int t = threadIdx.x % M1, r = threadIdx.x / M1;
+  const long long row = (long long)a.z0 * a.ny + (long long)blockIdx.x * RY + r;
+  const bool live = row < (long long)a.z1 * a.ny;
+  x_inv_rows<T, M1, M2, MIRROR>(a, tb, sb + r * SB, a.spec + row * a.nxp, row, live, t);
   if (a.st) {  // the solve: the last block of the application's X- launches completes the
                // preconditioner sweep, with <rt, z> from the partial sums the Z pass stored
     const InstDesc& I = *a.I;
@@ -377,6 +396,37 @@ __device__ __forceinline__ int tx(int group, int e, int c) {
   return group * pad_stride(G * kTX) + e * kTX + c;
 }
 
+// The Y transform (forward or inverse) of one tile of kTX columns by M1 x kTX threads (t = slot
+// in the line, c = column): load(e) gives line element e of the thread's column, store(e, v)
+// takes the result; `sm` is the tile's exchange buffer.  Every thread of the block calls it.
+template <int M1, int M2, bool INV, class Load, class Store>
+__device__ __forceinline__ void y_tile(const Tables& tb, float2* sm, int t, int c, bool live,
+                                       Load&& load, Store&& store) {
+  if (live) {
+    float2 v[M2], y[M2];
+#pragma unroll
+    for (int j2 = 0; j2 < M2; ++j2) v[j2] = load(t + M1 * j2);
+    dft<M2, 0, 1, INV>(v, y);
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) {
+      const float2 w = tb.wy[t * k2];
+      sm[tx<M1>(k2, t, c)] = k2 == 0 || t == 0 ? y[k2] : (INV ? cmulc(y[k2], w) : cmul(y[k2], w));
+    }
+  }
+  __syncthreads();
+  if (live) {
+    for (int k2 = t; k2 < M2; k2 += M1) {
+      float2 u[M1], o[M1];
+#pragma unroll
+      for (int j1 = 0; j1 < M1; ++j1) u[j1] = sm[tx<M1>(k2, j1, c)];
+      dft<M1, 0, 1, INV>(u, o);
+#pragma unroll
+      for (int k1 = 0; k1 < M1; ++k1) store(k2 + M2 * k1, o[k1]);
+    }
+  }
+  __syncthreads();  // sm may be reused by the next tile
+}
+
 // Y pass (forward or inverse), in place: block = (column tile, kz).
 template <int M1, int M2, bool INV>
 __global__ void __launch_bounds__(M1 * kTX) k_spec_y(SpecArgs a) {
@@ -388,107 +438,132 @@ __global__ void __launch_bounds__(M1 * kTX) k_spec_y(SpecArgs a) {
   const int kz = a.z0 + blockIdx.x / tiles, kx = (blockIdx.x % tiles) * kTX + c;
   float2* g = a.spec + (long long)kz * a.ny * a.nxp + kx;
   const long long es = a.nxp;  // element stride along y
-  {
-    float2 v[M2], y[M2];
-#pragma unroll
-    for (int j2 = 0; j2 < M2; ++j2) v[j2] = g[(t + M1 * j2) * es];
-    dft<M2, 0, 1, INV>(v, y);
-#pragma unroll
-    for (int k2 = 0; k2 < M2; ++k2) {
-      const float2 w = tb.wy[t * k2];
-      sm[tx<M1>(k2, t, c)] = k2 == 0 || t == 0 ? y[k2] : (INV ? cmulc(y[k2], w) : cmul(y[k2], w));
-    }
-  }
-  __syncthreads();
-  for (int k2 = t; k2 < M2; k2 += M1) {
-    float2 u[M1], o[M1];
-#pragma unroll
-    for (int j1 = 0; j1 < M1; ++j1) u[j1] = sm[tx<M1>(k2, j1, c)];
-    dft<M1, 0, 1, INV>(u, o);
-#pragma unroll
-    for (int k1 = 0; k1 < M1; ++k1) g[(k2 + M2 * k1) * es] = o[k1];
-  }
+  y_tile<M1, M2, INV>(tb, sm, t, c, true, [&](int e) { return g[e * es]; },
+                      [&](int e, float2 v) { g[e * es] = v; });
 }
 
-// Z pass: forward FFT along z, scale by sign / (N lambda), inverse FFT along z; block =
-// (column tile, ky).  Forward: A (M2-point, over j2) and B (M1-point, over j1), leaving owner
-// k2 with X[k2 + M2 k1]; inverse: A' (M1-point over k1 in registers), B' (M2-point over k2).
-// In the solve it also stores this tile's part of <y, (-L_h)^-1 y> = sum_k |Y(k)|^2 s(k)
-// (Parseval; y = W rt, the half spectrum counting kx = 1 .. nx/2 - 1 twice), which is <rt, z>.
-// Lines of 512 (M2 = 32): at least four resident blocks per SM (128 registers, a few spilled to
-// L1): the measured Z pass of the 512^3 solve 586 -> 487 us against the unbounded 168 registers.
-template <int M2> struct ZOcc { static constexpr int kMinBlocks = M2 >= 32 ? 4 : 1; };
+// 16-byte asynchronous copy global -> shared (cached in L2 only), and its group wait: the copies
+// hold no registers while in flight, so a block can fetch its next tile while it finishes this
+// one.  wait_group is a hardware wait for this thread's own copies (no spin loop).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Z pass: forward FFT along z, scale by sign / (N lambda), inverse FFT along z.  Tiles are
+// (column tile, ky); a persistent grid walks them (tile = block, block + grid, ...).  The twiddles
+// W_nz^k and the z eigenvalues are copied to shared memory once per block (every lookup of a
+// thread is then a shared-memory load: the table loads from L1 were the pass's main stall), and
+// the copies of a tile's nz x 8 values go out as soon as the previous tile's values are read, so
+// they overlap its inverse transform and stores.  Element e = t + M1 j2 of column c arrives at
+// slot (j2, t, c); forward: A (M2-point over j2, thread (t, c)) writes slot (k2, t, c), B
+// (M1-point over j1 = t) leaves owner k2 with X[k2 + M2 k1]; the owner scales and runs A' (M1-
+// point over k1) and writes back to the slots it read, (k2, l2), so B -> scaling -> A' needs no
+// barrier and keeps no line in registers across one; B' (M2-point over k2) reads slots (k2, t).
+// In the solve it also stores this block's part of <y, (-L_h)^-1 y> = sum_k |Y(k)|^2 s(k)
+// (Parseval; y = W rt, the half spectrum counting kx = 1 .. nx/2 - 1 twice), which is <rt, z>:
+// FP32 per tile, summed over the block's tiles in FP64, always in the same order.
+template <int M1, int M2>
+constexpr int z_buffer() { return M2 * pad_stride(M1 * kTX); }  // complex values of the tile buffer
+template <int M1, int M2>
+constexpr size_t z_smem() {  // tile buffer, twiddles W_nz^k, eigenvalues lz
+  return sizeof(float2) * (size_t)(z_buffer<M1, M2>() + M1 * M2) + sizeof(float) * (size_t)(M1 * M2);
+}
+// At least 512 resident threads per SM (at most 128 registers a thread); lines of 512: four
+// blocks of 128 threads, 41 KB of shared memory each.
+template <int M1> struct ZOcc { static constexpr int kMinBlocks = (512 + M1 * kTX - 1) / (M1 * kTX); };
 
 template <int M1, int M2>
-__global__ void __launch_bounds__(M1 * kTX, ZOcc<M2>::kMinBlocks) k_spec_z(SpecArgs a) {
+__global__ void __launch_bounds__(M1 * kTX, ZOcc<M1>::kMinBlocks) k_spec_z(SpecArgs a) {
   constexpr int R = (M2 + M1 - 1) / M1;
-  constexpr int SZ = M2 * pad_stride(M1 * kTX) > M1 * pad_stride(M2 * kTX) ? M2 * pad_stride(M1 * kTX)
-                                                                             : M1 * pad_stride(M2 * kTX);
-  __shared__ float2 sm[SZ];
+  constexpr int n = M1 * M2;
+  constexpr int S = pad_stride(M1 * kTX);
+  extern __shared__ __align__(16) float2 zbuf[];
+  float2* sm = zbuf;                         // the tile
+  float2* wz = zbuf + z_buffer<M1, M2>();    // W_nz^k, k < nz
+  float* lz = reinterpret_cast<float*>(wz + n);
   if (!spec_active(a)) return;
   const Tables tb = tables(a);
   const int c = threadIdx.x % kTX, t = threadIdx.x / kTX;
   const int tiles = a.nxp / kTX;
-  const int ky = blockIdx.x / tiles, kx = (blockIdx.x % tiles) * kTX + c;
-  float2* g = a.spec + (long long)ky * a.nxp + kx;
+  const int ntile = tiles * a.ny;
   const long long es = (long long)a.ny * a.nxp;  // element stride along z
-  {
-    float2 v[M2], y[M2];
-#pragma unroll
-    for (int j2 = 0; j2 < M2; ++j2) v[j2] = g[(t + M1 * j2) * es];
-    dft<M2, 0, 1, false>(v, y);
-#pragma unroll
-    for (int k2 = 0; k2 < M2; ++k2)
-      sm[tx<M1>(k2, t, c)] = k2 == 0 || t == 0 ? y[k2] : cmul(y[k2], tb.wz[t * k2]);
-  }
-  __syncthreads();
   const int m = a.nx / 2;
-  const bool pad = kx > m;  // padding columns of the row pitch: set to 0
-  const float lxy = pad ? 0.f : tb.lx[kx] + tb.ly[ky];
-  const float wkx = (kx == 0 || kx == m) ? 1.f : 2.f;  // conjugate partners of the half spectrum
-  float energy = 0.f;
-  float2 X[R][M1];
+  // copies of tile `tile`: 4 pieces of 16 bytes per line element
+  auto fetch = [&](int tile) {
+    const float2* g = a.spec + (long long)(tile / tiles) * a.nxp + (tile % tiles) * kTX;
+    for (int q = threadIdx.x; q < 4 * n; q += M1 * kTX) {
+      const int e = q >> 2, part = q & 3;
+      cp_async16(sm + (e / M1) * S + (e % M1) * kTX + 2 * part, g + e * es + 2 * part);
+    }
+    cp_async_commit();
+  };
+  int tile = blockIdx.x;
+  if (tile < ntile) fetch(tile);
+  for (int k = threadIdx.x; k < n; k += M1 * kTX) {
+    wz[k] = tb.wz[k];
+    lz[k] = tb.lz[k];
+  }
+  double energy_sum = 0.0;
+  for (; tile < ntile; tile += gridDim.x) {
+    cp_async_wait_all();  // this thread's copies of the tile have landed
+    __syncthreads();      // ... and every other thread's (and the tables are in place)
+    const int ky = tile / tiles, kx = (tile % tiles) * kTX + c;
+    {
+      float2 v[M2], y[M2];
 #pragma unroll
-  for (int rr = 0; rr < R; ++rr) {
-    const int k2 = t + M1 * rr;
-    if (k2 < M2) {
-      float2 u[M1], o[M1];
+      for (int j2 = 0; j2 < M2; ++j2) v[j2] = sm[j2 * S + t * kTX + c];
+      dft<M2, 0, 1, false>(v, y);
+      __syncthreads();  // every input slot is read before the exchange overwrites it
 #pragma unroll
-      for (int j1 = 0; j1 < M1; ++j1) u[j1] = sm[tx<M1>(k2, j1, c)];
-      dft<M1, 0, 1, false>(u, o);
+      for (int k2 = 0; k2 < M2; ++k2)
+        sm[tx<M1>(k2, t, c)] = k2 == 0 || t == 0 ? y[k2] : cmul(y[k2], wz[t * k2]);
+    }
+    __syncthreads();
+    const bool pad = kx > m;  // padding columns of the row pitch: set to 0
+    const float lxy = pad ? 0.f : tb.lx[kx] + tb.ly[ky];
+    const float wkx = (kx == 0 || kx == m) ? 1.f : 2.f;  // conjugate partners of the half spectrum
+    float energy = 0.f;
 #pragma unroll
-      for (int k1 = 0; k1 < M1; ++k1) {
-        const float lam = lxy + tb.lz[k2 + M2 * k1];
-        const float s = (lam > 0.f && !pad) ? a.scale / lam : 0.f;  // zero mode removed
-        energy = fmaf(wkx * s, fmaf(o[k1].x, o[k1].x, o[k1].y * o[k1].y), energy);
-        X[rr][k1] = cscale(o[k1], s);
+    for (int rr = 0; rr < R; ++rr) {
+      const int k2 = t + M1 * rr;
+      if (k2 < M2) {
+        float2 u[M1], o[M1];
+#pragma unroll
+        for (int j1 = 0; j1 < M1; ++j1) u[j1] = sm[tx<M1>(k2, j1, c)];
+        dft<M1, 0, 1, false>(u, o);
+#pragma unroll
+        for (int k1 = 0; k1 < M1; ++k1) {
+          const float lam = lxy + lz[k2 + M2 * k1];
+          // zero mode removed; the quotient is the hardware's approximate one (2 ulp)
+          const float s = (lam > 0.f && !pad) ? __fdividef(a.scale, lam) : 0.f;
+          energy = fmaf(wkx * s, fmaf(o[k1].x, o[k1].x, o[k1].y * o[k1].y), energy);
+          o[k1] = cscale(o[k1], s);
+        }
+        dft<M1, 0, 1, true>(o, u);
+#pragma unroll
+        for (int l2 = 0; l2 < M1; ++l2)
+          sm[tx<M1>(k2, l2, c)] = l2 == 0 || k2 == 0 ? u[l2] : cmulc(u[l2], wz[k2 * l2]);
       }
     }
-  }
-  __syncthreads();  // the forward exchange buffer is reused
+    energy_sum += (double)energy;
+    __syncthreads();
+    float2 w[M2];
 #pragma unroll
-  for (int rr = 0; rr < R; ++rr) {
-    const int k2 = t + M1 * rr;
-    if (k2 < M2) {
-      float2 u[M1];
-      dft<M1, 0, 1, true>(X[rr], u);
-#pragma unroll
-      for (int l2 = 0; l2 < M1; ++l2)
-        sm[tx<M2>(l2, k2, c)] = l2 == 0 || k2 == 0 ? u[l2] : cmulc(u[l2], tb.wz[k2 * l2]);
-    }
-  }
-  __syncthreads();
-  {
-    float2 w[M2], o[M2];
-#pragma unroll
-    for (int k2 = 0; k2 < M2; ++k2) w[k2] = sm[tx<M2>(t, k2, c)];
+    for (int k2 = 0; k2 < M2; ++k2) w[k2] = sm[tx<M1>(k2, t, c)];
+    __syncthreads();  // the tile is read: the next tile's copies may go out
+    if (tile + (int)gridDim.x < ntile) fetch(tile + gridDim.x);
+    float2 o[M2];
     dft<M2, 0, 1, true>(w, o);
+    float2* g = a.spec + (long long)ky * a.nxp + kx;
 #pragma unroll
     for (int l1 = 0; l1 < M2; ++l1) g[(t + M1 * l1) * es] = o[l1];
   }
   if (a.st) {
-    const float part[1] = {energy * a.ewt};
-    store_partials<1, float>(part, a.I->part, gridDim.x, blockIdx.x);
+    const double part[1] = {energy_sum * (double)a.ewt};
+    store_partials<1, double>(part, a.I->part, gridDim.x, blockIdx.x);
   }
 }
 
@@ -542,7 +617,8 @@ int x_rows_per_block(int m, bool inverse) {
   return 0;
 }
 
-SpecKernel yz_kernel(int n, int which, int* threads) {  // which: 0 = Y+, 1 = Y-, 2 = Z
+SpecKernel yz_kernel(int n, int which, int* threads, size_t* smem = nullptr) {
+  // which: 0 = Y+, 1 = Y-, 2 = Z; smem: the Z pass's dynamic shared memory
   int m1, m2;
   factor(n, &m1, &m2);
   if (n == 48) {  // blocks of M1 * 8 threads: a whole number of warps for the block reduction
@@ -552,6 +628,7 @@ SpecKernel yz_kernel(int n, int which, int* threads) {  // which: 0 = Y+, 1 = Y-
 #define VDP_YZ(M1, M2)                                                                  \
   if (m1 == M1 && m2 == M2) {                                                           \
     *threads = M1 * kTX;                                                                \
+    if (smem) *smem = which == 2 ? z_smem<M1, M2>() : 0;                               \
     return which == 0 ? k_spec_y<M1, M2, false> : which == 1 ? k_spec_y<M1, M2, true>   \
                                                              : k_spec_z<M1, M2>;        \
   }
@@ -559,6 +636,24 @@ SpecKernel yz_kernel(int n, int which, int* threads) {  // which: 0 = Y+, 1 = Y-
   VDP_YZ(16, 16) VDP_YZ(16, 32)
 #undef VDP_YZ
   return nullptr;
+}
+
+// Resident Z blocks per SM for each supported line length, per device (filled when the
+// spectral passes are first prepared on the device): the persistent Z grid is that times the SMs.
+constexpr int kZLengths[] = {32, 48, 64, 96, 128, 192, 256, 512};
+constexpr int kZCount = sizeof(kZLengths) / sizeof(kZLengths[0]);
+constexpr int kMaxDevices = 64;
+int g_z_per_sm[kMaxDevices][kZCount];
+
+int current_device() {
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevices ? dev : -1;
+}
+
+int z_index(int n) {
+  for (int i = 0; i < kZCount; ++i)
+    if (kZLengths[i] == n) return i;
+  return -1;
 }
 
 bool x_supported(int nx) {
@@ -618,11 +713,27 @@ cudaError_t spectral_upload_roots() {
     const double ang = -2.0 * M_PI * (double)k / 96.0;
     w[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
   }
-  return cudaMemcpyToSymbol(c_w96, w, sizeof(w));
+  cudaError_t e = cudaMemcpyToSymbol(c_w96, w, sizeof(w));
+  const int dev = current_device();
+  if (e == cudaSuccess && dev < 0) e = cudaErrorInvalidDevice;
+  // the Z pass's tile buffer and tables: dynamic shared memory (41 KB for lines of 512), then
+  // the resident blocks per SM that size the persistent grid
+  for (int i = 0; i < kZCount && e == cudaSuccess; ++i) {
+    int threads = 0;
+    size_t smem = 0;
+    const SpecKernel k = yz_kernel(kZLengths[i], 2, &threads, &smem);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) g_z_per_sm[dev][i] = per_sm;
+  }
+  return e;
 }
 
 cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStream_t s) {
   int threads = 0;
+  size_t smem = 0;
   SpecKernel k = nullptr;
   unsigned grid = 0;
   const int m = a.nx / 2;
@@ -645,14 +756,14 @@ cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStre
       grid = (unsigned)((a.nxp / kTX) * (a.z1 - a.z0));
       break;
     case SPEC_Z:
-      k = yz_kernel(a.nz, 2, &threads);
-      grid = (unsigned)((a.nxp / kTX) * a.ny);
+      k = yz_kernel(a.nz, 2, &threads, &smem);
+      grid = (unsigned)spectral_units(a.nx, a.ny, a.nz);
       break;
     default:
       break;
   }
   if (!k || !grid) return cudaErrorInvalidValue;
-  k<<<grid, threads, 0, s>>>(a);
+  k<<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -712,8 +823,12 @@ cudaError_t launch_spectral_apply(int prec, const SpecArgs& a, int slab, cudaStr
 }
 
 int spectral_units(int nx, int ny, int nz) {  // CTAs of the Z pass (they store <rt, z> parts)
-  (void)nz;
-  return (spectral_pitch(nx) / kTX) * ny;
+  const int dev = current_device(), i = z_index(nz);
+  const int per_sm = dev >= 0 && i >= 0 ? g_z_per_sm[dev][i] : 0;
+  const long long tiles = (long long)(spectral_pitch(nx) / kTX) * ny;
+  if (per_sm < 1) return 0;  // not prepared on this device: no launch
+  const long long grid = (long long)per_sm * kSMs;
+  return (int)(tiles < grid ? tiles : grid);
 }
 
 __global__ void k_omega(const double* __restrict__ sinv, long long n, float* __restrict__ omega) {
