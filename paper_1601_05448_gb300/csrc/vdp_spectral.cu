@@ -396,52 +396,6 @@ __device__ __forceinline__ int tx(int group, int e, int c) {
   return group * pad_stride(G * kTX) + e * kTX + c;
 }
 
-// The Y transform (forward or inverse) of one tile of kTX columns by M1 x kTX threads (t = slot
-// in the line, c = column): load(e) gives line element e of the thread's column, store(e, v)
-// takes the result; `sm` is the tile's exchange buffer.  Every thread of the block calls it.
-template <int M1, int M2, bool INV, class Load, class Store>
-__device__ __forceinline__ void y_tile(const Tables& tb, float2* sm, int t, int c, bool live,
-                                       Load&& load, Store&& store) {
-  if (live) {
-    float2 v[M2], y[M2];
-#pragma unroll
-    for (int j2 = 0; j2 < M2; ++j2) v[j2] = load(t + M1 * j2);
-    dft<M2, 0, 1, INV>(v, y);
-#pragma unroll
-    for (int k2 = 0; k2 < M2; ++k2) {
-      const float2 w = tb.wy[t * k2];
-      sm[tx<M1>(k2, t, c)] = k2 == 0 || t == 0 ? y[k2] : (INV ? cmulc(y[k2], w) : cmul(y[k2], w));
-    }
-  }
-  __syncthreads();
-  if (live) {
-    for (int k2 = t; k2 < M2; k2 += M1) {
-      float2 u[M1], o[M1];
-#pragma unroll
-      for (int j1 = 0; j1 < M1; ++j1) u[j1] = sm[tx<M1>(k2, j1, c)];
-      dft<M1, 0, 1, INV>(u, o);
-#pragma unroll
-      for (int k1 = 0; k1 < M1; ++k1) store(k2 + M2 * k1, o[k1]);
-    }
-  }
-  __syncthreads();  // sm may be reused by the next tile
-}
-
-// Y pass (forward or inverse), in place: block = (column tile, kz).
-template <int M1, int M2, bool INV>
-__global__ void __launch_bounds__(M1 * kTX) k_spec_y(SpecArgs a) {
-  __shared__ float2 sm[M2 * pad_stride(M1 * kTX)];
-  if (!spec_active(a)) return;
-  const Tables tb = tables(a);
-  const int c = threadIdx.x % kTX, t = threadIdx.x / kTX;
-  const int tiles = a.nxp / kTX;
-  const int kz = a.z0 + blockIdx.x / tiles, kx = (blockIdx.x % tiles) * kTX + c;
-  float2* g = a.spec + (long long)kz * a.ny * a.nxp + kx;
-  const long long es = a.nxp;  // element stride along y
-  y_tile<M1, M2, INV>(tb, sm, t, c, true, [&](int e) { return g[e * es]; },
-                      [&](int e, float2 v) { g[e * es] = v; });
-}
-
 // 16-byte asynchronous copy global -> shared (cached in L2 only), and its group wait: the copies
 // hold no registers while in flight, so a block can fetch its next tile while it finishes this
 // one.  wait_group is a hardware wait for this thread's own copies (no spin loop).
@@ -451,6 +405,98 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Tiles of the Y and Z passes: nz (or ny) line elements of kTX columns.  Element e = t + M1 j2 of
+// column c is copied to slot (j2, t, c) of the tile buffer, the layout step A reads; step A
+// writes the exchange to slots (k2, t, c) of the same buffer.
+template <int M1, int M2>
+constexpr int line_buffer() { return M2 * pad_stride(M1 * kTX); }  // complex values of one tile
+// At least 512 resident threads per SM (at most 128 registers a thread); lines of 512: four
+// blocks of 128 threads.
+template <int M1> struct LineOcc { static constexpr int kMinBlocks = (512 + M1 * kTX - 1) / (M1 * kTX); };
+
+// Copies of the tile of n = M1 x M2 line elements at g (element stride es) into the buffer sm:
+// 4 pieces of 16 bytes per element, spread over the block's threads; one commit group.
+template <int M1, int M2>
+__device__ __forceinline__ void fetch_tile(float2* sm, const float2* g, long long es) {
+  constexpr int S = pad_stride(M1 * kTX);
+  for (int q = threadIdx.x; q < 4 * M1 * M2; q += M1 * kTX) {
+    const int e = q >> 2, part = q & 3;
+    cp_async16(sm + (e / M1) * S + (e % M1) * kTX + 2 * part, g + e * es + 2 * part);
+  }
+  cp_async_commit();
+}
+
+template <int M1, int M2>
+constexpr size_t y_smem() {  // tile buffer, twiddles W_ny^k
+  return sizeof(float2) * (size_t)(line_buffer<M1, M2>() + M1 * M2);
+}
+
+// Y pass (forward or inverse), in place.  Tiles are (column tile, kz); a persistent grid walks
+// them (tile = block, block + grid, ...).  The twiddles W_ny^k are copied to shared memory once
+// per block; a tile's copies go out as soon as the previous tile's exchange is read, so they
+// overlap its step B and stores.  Step A: M2-point DFTs over j2 (thread (t, c)), twiddles, the
+// exchange; step B: M1-point DFTs over j1 by owner k2, element k2 + M2 k1 stored.
+template <int M1, int M2, bool INV>
+__global__ void __launch_bounds__(M1 * kTX, LineOcc<M1>::kMinBlocks) k_spec_y(SpecArgs a) {
+  constexpr int R = (M2 + M1 - 1) / M1;
+  constexpr int n = M1 * M2;
+  constexpr int S = pad_stride(M1 * kTX);
+  extern __shared__ __align__(16) float2 ybuf[];
+  float2* sm = ybuf;                          // the tile
+  float2* wy = ybuf + line_buffer<M1, M2>();  // W_ny^k, k < ny
+  if (!spec_active(a)) return;
+  const Tables tb = tables(a);
+  const int c = threadIdx.x % kTX, t = threadIdx.x / kTX;
+  const int tiles = a.nxp / kTX;
+  const int ntile = tiles * (a.z1 - a.z0);
+  const long long es = a.nxp;  // element stride along y
+  auto base = [&](int tile) {
+    return a.spec + (long long)(a.z0 + tile / tiles) * a.ny * a.nxp + (tile % tiles) * kTX;
+  };
+  int tile = blockIdx.x;
+  if (tile < ntile) fetch_tile<M1, M2>(sm, base(tile), es);
+  for (int k = threadIdx.x; k < n; k += M1 * kTX) wy[k] = tb.wy[k];
+  for (; tile < ntile; tile += gridDim.x) {
+    cp_async_wait_all();  // this thread's copies of the tile have landed
+    __syncthreads();      // ... and every other thread's (and the twiddles are in place)
+    {
+      float2 v[M2], y[M2];
+#pragma unroll
+      for (int j2 = 0; j2 < M2; ++j2) v[j2] = sm[j2 * S + t * kTX + c];
+      dft<M2, 0, 1, INV>(v, y);
+      __syncthreads();  // every input slot is read before the exchange overwrites it
+#pragma unroll
+      for (int k2 = 0; k2 < M2; ++k2) {
+        const float2 w = wy[t * k2];
+        sm[tx<M1>(k2, t, c)] = k2 == 0 || t == 0 ? y[k2] : (INV ? cmulc(y[k2], w) : cmul(y[k2], w));
+      }
+    }
+    __syncthreads();
+    float2 u[R][M1];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int k2 = t + M1 * rr;
+      if (k2 < M2) {
+#pragma unroll
+        for (int j1 = 0; j1 < M1; ++j1) u[rr][j1] = sm[tx<M1>(k2, j1, c)];
+      }
+    }
+    __syncthreads();  // the tile is read: the next tile's copies may go out
+    if (tile + (int)gridDim.x < ntile) fetch_tile<M1, M2>(sm, base(tile + gridDim.x), es);
+    float2* g = base(tile) + c;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int k2 = t + M1 * rr;
+      if (k2 < M2) {
+        float2 o[M1];
+        dft<M1, 0, 1, INV>(u[rr], o);
+#pragma unroll
+        for (int k1 = 0; k1 < M1; ++k1) g[(k2 + M2 * k1) * es] = o[k1];
+      }
+    }
+  }
+}
 
 // Z pass: forward FFT along z, scale by sign / (N lambda), inverse FFT along z.  Tiles are
 // (column tile, ky); a persistent grid walks them (tile = block, block + grid, ...).  The twiddles
@@ -466,23 +512,18 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // (Parseval; y = W rt, the half spectrum counting kx = 1 .. nx/2 - 1 twice), which is <rt, z>:
 // FP32 per tile, summed over the block's tiles in FP64, always in the same order.
 template <int M1, int M2>
-constexpr int z_buffer() { return M2 * pad_stride(M1 * kTX); }  // complex values of the tile buffer
-template <int M1, int M2>
 constexpr size_t z_smem() {  // tile buffer, twiddles W_nz^k, eigenvalues lz
-  return sizeof(float2) * (size_t)(z_buffer<M1, M2>() + M1 * M2) + sizeof(float) * (size_t)(M1 * M2);
+  return sizeof(float2) * (size_t)(line_buffer<M1, M2>() + M1 * M2) + sizeof(float) * (size_t)(M1 * M2);
 }
-// At least 512 resident threads per SM (at most 128 registers a thread); lines of 512: four
-// blocks of 128 threads, 41 KB of shared memory each.
-template <int M1> struct ZOcc { static constexpr int kMinBlocks = (512 + M1 * kTX - 1) / (M1 * kTX); };
 
 template <int M1, int M2>
-__global__ void __launch_bounds__(M1 * kTX, ZOcc<M1>::kMinBlocks) k_spec_z(SpecArgs a) {
+__global__ void __launch_bounds__(M1 * kTX, LineOcc<M1>::kMinBlocks) k_spec_z(SpecArgs a) {
   constexpr int R = (M2 + M1 - 1) / M1;
   constexpr int n = M1 * M2;
   constexpr int S = pad_stride(M1 * kTX);
   extern __shared__ __align__(16) float2 zbuf[];
   float2* sm = zbuf;                         // the tile
-  float2* wz = zbuf + z_buffer<M1, M2>();    // W_nz^k, k < nz
+  float2* wz = zbuf + line_buffer<M1, M2>();  // W_nz^k, k < nz
   float* lz = reinterpret_cast<float*>(wz + n);
   if (!spec_active(a)) return;
   const Tables tb = tables(a);
@@ -491,14 +532,8 @@ __global__ void __launch_bounds__(M1 * kTX, ZOcc<M1>::kMinBlocks) k_spec_z(SpecA
   const int ntile = tiles * a.ny;
   const long long es = (long long)a.ny * a.nxp;  // element stride along z
   const int m = a.nx / 2;
-  // copies of tile `tile`: 4 pieces of 16 bytes per line element
   auto fetch = [&](int tile) {
-    const float2* g = a.spec + (long long)(tile / tiles) * a.nxp + (tile % tiles) * kTX;
-    for (int q = threadIdx.x; q < 4 * n; q += M1 * kTX) {
-      const int e = q >> 2, part = q & 3;
-      cp_async16(sm + (e / M1) * S + (e % M1) * kTX + 2 * part, g + e * es + 2 * part);
-    }
-    cp_async_commit();
+    fetch_tile<M1, M2>(sm, a.spec + (long long)(tile / tiles) * a.nxp + (tile % tiles) * kTX, es);
   };
   int tile = blockIdx.x;
   if (tile < ntile) fetch(tile);
@@ -618,7 +653,7 @@ int x_rows_per_block(int m, bool inverse) {
 }
 
 SpecKernel yz_kernel(int n, int which, int* threads, size_t* smem = nullptr) {
-  // which: 0 = Y+, 1 = Y-, 2 = Z; smem: the Z pass's dynamic shared memory
+  // which: 0 = Y+, 1 = Y-, 2 = Z; smem: the pass's dynamic shared memory
   int m1, m2;
   factor(n, &m1, &m2);
   if (n == 48) {  // blocks of M1 * 8 threads: a whole number of warps for the block reduction
@@ -628,7 +663,7 @@ SpecKernel yz_kernel(int n, int which, int* threads, size_t* smem = nullptr) {
 #define VDP_YZ(M1, M2)                                                                  \
   if (m1 == M1 && m2 == M2) {                                                           \
     *threads = M1 * kTX;                                                                \
-    if (smem) *smem = which == 2 ? z_smem<M1, M2>() : 0;                               \
+    if (smem) *smem = which == 2 ? z_smem<M1, M2>() : y_smem<M1, M2>();               \
     return which == 0 ? k_spec_y<M1, M2, false> : which == 1 ? k_spec_y<M1, M2, true>   \
                                                              : k_spec_z<M1, M2>;        \
   }
@@ -638,22 +673,32 @@ SpecKernel yz_kernel(int n, int which, int* threads, size_t* smem = nullptr) {
   return nullptr;
 }
 
-// Resident Z blocks per SM for each supported line length, per device (filled when the
-// spectral passes are first prepared on the device): the persistent Z grid is that times the SMs.
-constexpr int kZLengths[] = {32, 48, 64, 96, 128, 192, 256, 512};
-constexpr int kZCount = sizeof(kZLengths) / sizeof(kZLengths[0]);
+// Resident blocks per SM of the Y+ / Y- / Z passes for each supported line length, per device
+// (filled when the spectral passes are first prepared on the device): a persistent grid is that
+// times the SMs.
+constexpr int kLineLengths[] = {32, 48, 64, 96, 128, 192, 256, 512};
+constexpr int kLineCount = sizeof(kLineLengths) / sizeof(kLineLengths[0]);
 constexpr int kMaxDevices = 64;
-int g_z_per_sm[kMaxDevices][kZCount];
+int g_per_sm[kMaxDevices][3][kLineCount];
 
 int current_device() {
   int dev = -1;
   return cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevices ? dev : -1;
 }
 
-int z_index(int n) {
-  for (int i = 0; i < kZCount; ++i)
-    if (kZLengths[i] == n) return i;
+int line_index(int n) {
+  for (int i = 0; i < kLineCount; ++i)
+    if (kLineLengths[i] == n) return i;
   return -1;
+}
+
+// Persistent grid of a Y (which 0, 1) or Z (2) pass over `tiles` tiles: 0 if not prepared.
+long long line_grid(int which, int n, long long tiles) {
+  const int dev = current_device(), i = line_index(n);
+  const int per_sm = dev >= 0 && i >= 0 ? g_per_sm[dev][which][i] : 0;
+  if (per_sm < 1) return 0;
+  const long long grid = (long long)per_sm * kSMs;
+  return tiles < grid ? tiles : grid;
 }
 
 bool x_supported(int nx) {
@@ -716,18 +761,20 @@ cudaError_t spectral_upload_roots() {
   cudaError_t e = cudaMemcpyToSymbol(c_w96, w, sizeof(w));
   const int dev = current_device();
   if (e == cudaSuccess && dev < 0) e = cudaErrorInvalidDevice;
-  // the Z pass's tile buffer and tables: dynamic shared memory (41 KB for lines of 512), then
-  // the resident blocks per SM that size the persistent grid
-  for (int i = 0; i < kZCount && e == cudaSuccess; ++i) {
-    int threads = 0;
-    size_t smem = 0;
-    const SpecKernel k = yz_kernel(kZLengths[i], 2, &threads, &smem);
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
-    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
-    if (e == cudaSuccess) g_z_per_sm[dev][i] = per_sm;
-  }
+  // the Y and Z passes' tile buffer and tables: dynamic shared memory (37 and 41 KB for lines
+  // of 512), then the resident blocks per SM that size their persistent grids
+  for (int which = 0; which < 3 && e == cudaSuccess; ++which)
+    for (int i = 0; i < kLineCount && e == cudaSuccess; ++i) {
+      int threads = 0;
+      size_t smem = 0;
+      const SpecKernel k = yz_kernel(kLineLengths[i], which, &threads, &smem);
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int per_sm = 0;
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+      if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+      if (e == cudaSuccess) g_per_sm[dev][which][i] = per_sm;
+    }
   return e;
 }
 
@@ -751,10 +798,12 @@ cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStre
       break;
     }
     case SPEC_Y_FWD:
-    case SPEC_Y_INV:
-      k = yz_kernel(a.ny, pass == SPEC_Y_FWD ? 0 : 1, &threads);
-      grid = (unsigned)((a.nxp / kTX) * (a.z1 - a.z0));
+    case SPEC_Y_INV: {
+      const int which = pass == SPEC_Y_FWD ? 0 : 1;
+      k = yz_kernel(a.ny, which, &threads, &smem);
+      grid = (unsigned)line_grid(which, a.ny, (long long)(a.nxp / kTX) * (a.z1 - a.z0));
       break;
+    }
     case SPEC_Z:
       k = yz_kernel(a.nz, 2, &threads, &smem);
       grid = (unsigned)spectral_units(a.nx, a.ny, a.nz);
@@ -823,12 +872,7 @@ cudaError_t launch_spectral_apply(int prec, const SpecArgs& a, int slab, cudaStr
 }
 
 int spectral_units(int nx, int ny, int nz) {  // CTAs of the Z pass (they store <rt, z> parts)
-  const int dev = current_device(), i = z_index(nz);
-  const int per_sm = dev >= 0 && i >= 0 ? g_z_per_sm[dev][i] : 0;
-  const long long tiles = (long long)(spectral_pitch(nx) / kTX) * ny;
-  if (per_sm < 1) return 0;  // not prepared on this device: no launch
-  const long long grid = (long long)per_sm * kSMs;
-  return (int)(tiles < grid ? tiles : grid);
+  return (int)line_grid(2, nz, (long long)(spectral_pitch(nx) / kTX) * ny);
 }
 
 __global__ void k_omega(const double* __restrict__ sinv, long long n, float* __restrict__ omega) {
