@@ -391,8 +391,7 @@ void solve_spec_args(const vdp_ctx* c, int prec, SpecArgs* a) {
   a->zunits = spectral_units(nxt, c->ny, c->nz);
   a->z0 = 0;
   a->z1 = c->nz;
-  a->xunits = spectral_xinv_units(nxt, c->ny, c->nz, c->nz);
-  (void)prec;
+  a->xunits = spectral_xinv_units(prec, *a, c->nz);
 }
 
 int spec_slab(const vdp_ctx* c) {

@@ -279,6 +279,22 @@ __device__ __forceinline__ void x_fwd_rows(const SpecArgs& a, const Tables& tb, 
   }
 }
 
+// The X tables W_m^k (k < m) and W_nx^k (k <= m) copied to the block's shared memory (every
+// lookup of a row transform is then a shared-memory load); returns the tables with them.
+template <int M1, int M2>
+__device__ __forceinline__ Tables x_tables_shared(const SpecArgs& a, float2* st) {
+  constexpr int m = M1 * M2;
+  Tables tb = tables(a);
+  for (int k = threadIdx.x; k < 2 * m + 1; k += blockDim.x) st[k] = k < m ? tb.wm[k] : tb.wr[k - m];
+  __syncthreads();
+  tb.wm = st;
+  tb.wr = st + m;
+  return tb;
+}
+
+// X+ of FP32 rows: one group of RY rows per block, tables read through L1.  The 512^3 mixed solve
+// takes 33.6 ms with it against 34.4 ms with the persistent form below for FP32 rows too (whose
+// loop needs 80 registers: one block per SM less for the loads in flight).
 template <class T, int M1, int M2, bool MIRROR>
 __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>(), 1024 / (M1 * rows_per_block<M1, M2>()))
     k_spec_x_fwd(SpecArgs a) {
@@ -293,6 +309,30 @@ __global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>(), 1024 / (M1 * ro
   float2* out = a.spec + row * a.nxp;
   x_fwd_rows<T, M1, M2, MIRROR>(a, tb, sx + r * SX, row, live, t,
                                  [&](int k, float2 X) { out[k] = X; });
+}
+
+// X+ of FP64 rows on a persistent grid: groups of RY rows (group = block, block + grid, ...) of
+// the planes [z0, z1), tables in shared memory; at least 768 resident threads per SM (80
+// registers a thread).  The 512^3 FP64 solve: 47.3 ms against 49.2 ms with the form above.
+template <class T, int M1, int M2, bool MIRROR>
+__global__ void __launch_bounds__(M1 * rows_per_block<M1, M2>(), 768 / (M1 * rows_per_block<M1, M2>()))
+    k_spec_x_fwd_persistent(SpecArgs a) {
+  constexpr int RY = rows_per_block<M1, M2>();
+  constexpr int SX = x_row_stride<M1, M2>();
+  __shared__ float2 sx[RY * SX];  // per row: the exchange, then the transformed row
+  __shared__ float2 stab[2 * M1 * M2 + 1];
+  if (!spec_active(a)) return;
+  const Tables tb = x_tables_shared<M1, M2>(a, stab);
+  const int t = threadIdx.x % M1, r = threadIdx.x / M1;
+  const long long rows = (long long)(a.z1 - a.z0) * a.ny;
+  for (long long g = blockIdx.x; g * RY < rows; g += gridDim.x) {
+    const long long row = (long long)a.z0 * a.ny + g * RY + r;
+    const bool live = g * RY + r < rows;
+    float2* out = a.spec + row * a.nxp;
+    x_fwd_rows<T, M1, M2, MIRROR>(a, tb, sx + r * SX, row, live, t,
+                                   [&](int k, float2 X) { out[k] = X; });
+    __syncthreads();  // the row buffers are reused by the next group
+  }
 }
 
 // ---- X- : half spectrum -> real rows, z = W x ----------------------------------------------------
@@ -366,6 +406,7 @@ __device__ __forceinline__ void x_inv_rows(const SpecArgs& a, const Tables& tb, 
   }
 }
 
+// X-: one group of RY rows per block, tables read through L1.
 template <class T, int M1, int M2, bool MIRROR>
 __global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
     k_spec_x_inv(SpecArgs a) {
@@ -384,6 +425,37 @@ __global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
     finish_sweep(I, I.st, PH_SPEC, a.xunits, a.zunits);
   }
 }
+
+// X- on a persistent grid: groups of RY rows (group = block, block + grid, ...), tables in
+// shared memory.  The 512^3 mixed solve: 33.6 ms against 34.1 ms with the form above; and a
+// launch in another phase of the solve exits after 3 us instead of 29 us.
+template <class T, int M1, int M2, bool MIRROR>
+__global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
+    k_spec_x_inv_persistent(SpecArgs a) {
+  constexpr int RY = inv_rows_per_block<M1, M2>();
+  constexpr int SB = pad_stride(M2 * (M1 + 1));
+  __shared__ float2 sb[RY * SB];
+  __shared__ float2 stab[2 * M1 * M2 + 1];
+  if (!spec_active(a)) return;
+  const Tables tb = x_tables_shared<M1, M2>(a, stab);
+  const int t = threadIdx.x % M1, r = threadIdx.x / M1;
+  const long long rows = (long long)(a.z1 - a.z0) * a.ny;
+  for (long long g = blockIdx.x; g * RY < rows; g += gridDim.x) {
+    const long long row = (long long)a.z0 * a.ny + g * RY + r;
+    const bool live = g * RY + r < rows;
+    x_inv_rows<T, M1, M2, MIRROR>(a, tb, sb + r * SB, a.spec + row * a.nxp, row, live, t);
+    __syncthreads();  // the exchange buffers are reused by the next group
+  }
+  if (a.st) {  // as above
+    const InstDesc& I = *a.I;
+    finish_sweep(I, I.st, PH_SPEC, a.xunits, a.zunits);
+  }
+}
+
+// Which X kernels run on persistent grids (measured at 512^3, see the forms above; X+ of FP64
+// rows always does).
+constexpr bool kXInvPersistent = true;
+constexpr bool kXFwdF32Persistent = false;
 
 // ---- Y and Z: tiles of TX consecutive kx columns, whole lines -----------------------------------
 
@@ -632,8 +704,18 @@ SpecKernel x_kernel(int m, bool inverse, bool mirror, int* threads) {
 #define VDP_X(M1, M2)                                                                       \
   if (m1 == M1 && m2 == M2) {                                                               \
     *threads = M1 * (inverse ? inv_rows_per_block<M1, M2>() : rows_per_block<M1, M2>());     \
-    if (mirror) return inverse ? k_spec_x_inv<T, M1, M2, true> : k_spec_x_fwd<T, M1, M2, true>; \
-    return inverse ? k_spec_x_inv<T, M1, M2, false> : k_spec_x_fwd<T, M1, M2, false>;       \
+    if (inverse) {                                                                          \
+      if constexpr (kXInvPersistent)                                                        \
+        return mirror ? k_spec_x_inv_persistent<T, M1, M2, true>                            \
+                      : k_spec_x_inv_persistent<T, M1, M2, false>;                          \
+      else                                                                                  \
+        return mirror ? k_spec_x_inv<T, M1, M2, true> : k_spec_x_inv<T, M1, M2, false>;    \
+    }                                                                                       \
+    if constexpr (sizeof(T) == 8 || kXFwdF32Persistent)                                     \
+      return mirror ? k_spec_x_fwd_persistent<T, M1, M2, true>                              \
+                    : k_spec_x_fwd_persistent<T, M1, M2, false>;                            \
+    else                                                                                    \
+      return mirror ? k_spec_x_fwd<T, M1, M2, true> : k_spec_x_fwd<T, M1, M2, false>;     \
   }
   VDP_X(4, 4) VDP_X(4, 6) VDP_X(4, 8) VDP_X(6, 8) VDP_X(8, 8) VDP_X(8, 12) VDP_X(8, 16)
   VDP_X(16, 16)
@@ -690,6 +772,35 @@ int line_index(int n) {
   for (int i = 0; i < kLineCount; ++i)
     if (kLineLengths[i] == n) return i;
   return -1;
+}
+
+// Resident blocks per SM of the X kernels, per device (filled with the line tables).
+std::vector<std::pair<SpecKernel, int>> g_x_per_sm[kMaxDevices];
+constexpr int kXHalfLengths[] = {16, 24, 32, 48, 64, 96, 128, 256};  // nx / 2
+
+bool x_f64(int prec, bool inv, const SpecArgs& a) { return prec == PREC_FP64 && !(inv && a.out_f32); }
+
+SpecKernel x_pass_kernel(int prec, bool inv, const SpecArgs& a, int* threads) {
+  const int m = a.nx / 2;
+  return x_f64(prec, inv, a) ? x_kernel<double>(m, inv, a.mirror != 0, threads)
+                             : x_kernel<float>(m, inv, a.mirror != 0, threads);
+}
+
+// Grid of an X pass over `rows` rows: a persistent grid for the persistent forms (0 if not
+// prepared), else one block per group of rows.
+long long x_grid(int prec, bool inv, const SpecArgs& a, long long rows) {
+  int threads = 0;
+  const SpecKernel k = x_pass_kernel(prec, inv, a, &threads);
+  const int dev = current_device(), ry = x_rows_per_block(a.nx / 2, inv);
+  if (!k || dev < 0 || ry <= 0) return 0;
+  const bool persistent = inv ? kXInvPersistent : (x_f64(prec, inv, a) || kXFwdF32Persistent);
+  if (!persistent) return (rows + ry - 1) / ry;
+  int per_sm = 0;
+  for (const auto& e : g_x_per_sm[dev])
+    if (e.first == k) per_sm = e.second;
+  if (per_sm < 1) return 0;
+  const long long groups = (rows + ry - 1) / ry, grid = (long long)per_sm * kSMs;
+  return groups < grid ? groups : grid;
 }
 
 // Persistent grid of a Y (which 0, 1) or Z (2) pass over `tiles` tiles: 0 if not prepared.
@@ -775,6 +886,19 @@ cudaError_t spectral_upload_roots() {
       if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
       if (e == cudaSuccess) g_per_sm[dev][which][i] = per_sm;
     }
+  // the X kernels (static shared memory): resident blocks per SM, for the persistent grids
+  g_x_per_sm[dev < 0 ? 0 : dev].clear();
+  for (const int m : kXHalfLengths)
+    for (int v = 0; v < 8 && e == cudaSuccess; ++v) {
+      const bool f64 = v & 1, inv = v & 2, mirror = v & 4;
+      int threads = 0, per_sm = 0;
+      const SpecKernel k = f64 ? x_kernel<double>(m, inv, mirror, &threads)
+                               : x_kernel<float>(m, inv, mirror, &threads);
+      if (!k) continue;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0);
+      if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+      if (e == cudaSuccess) g_x_per_sm[dev].push_back({k, per_sm});
+    }
   return e;
 }
 
@@ -783,18 +907,13 @@ cudaError_t launch_spectral_pass(int prec, int pass, const SpecArgs& a, cudaStre
   size_t smem = 0;
   SpecKernel k = nullptr;
   unsigned grid = 0;
-  const int m = a.nx / 2;
   if (a.z0 < 0 || a.z1 > a.nz || a.z0 >= a.z1) return cudaErrorInvalidValue;
   switch (pass) {
     case SPEC_X_FWD:
     case SPEC_X_INV: {
       const bool inv = pass == SPEC_X_INV;
-      const bool f64 = prec == PREC_FP64 && !(inv && a.out_f32);
-      k = f64 ? x_kernel<double>(m, inv, a.mirror != 0, &threads)
-              : x_kernel<float>(m, inv, a.mirror != 0, &threads);
-      const int ry = x_rows_per_block(m, inv);
-      const long long srows = (long long)a.ny * (a.z1 - a.z0);
-      grid = ry ? (unsigned)((srows + ry - 1) / ry) : 0;
+      k = x_pass_kernel(prec, inv, a, &threads);
+      grid = (unsigned)x_grid(prec, inv, a, (long long)a.ny * (a.z1 - a.z0));
       break;
     }
     case SPEC_Y_FWD:
@@ -841,23 +960,21 @@ void spectral_schedule(int nz, int slab, std::vector<SpecLaunch>& out) {
   }
 }
 
-int spectral_xinv_units(int nx, int ny, int nz, int slab) {
-  const int ry = x_rows_per_block(nx / 2, true);
-  if (ry <= 0) return 0;
-  if (slab < 1) slab = nz;
+int spectral_xinv_units(int prec, const SpecArgs& a, int slab) {
+  if (slab < 1) slab = a.nz;
   long long u = 0;
-  for (int z0 = 0; z0 < nz; z0 += slab) {
-    const int z1 = z0 + slab < nz ? z0 + slab : nz;
-    u += ((long long)ny * (z1 - z0) + ry - 1) / ry;
+  for (int z0 = 0; z0 < a.nz; z0 += slab) {
+    const int z1 = z0 + slab < a.nz ? z0 + slab : a.nz;
+    u += x_grid(prec, true, a, (long long)a.ny * (z1 - z0));
   }
   return (int)u;
 }
 
-SpecArgs spectral_launch_args(const SpecArgs& a, const SpecLaunch& l, int slab) {
+SpecArgs spectral_launch_args(int prec, const SpecArgs& a, const SpecLaunch& l, int slab) {
   SpecArgs b = a;
   b.z0 = l.z0;
   b.z1 = l.z1;
-  b.xunits = spectral_xinv_units(a.nx, a.ny, a.nz, slab);
+  b.xunits = spectral_xinv_units(prec, a, slab);
   return b;
 }
 
@@ -865,7 +982,7 @@ cudaError_t launch_spectral_apply(int prec, const SpecArgs& a, int slab, cudaStr
   std::vector<SpecLaunch> sched;
   spectral_schedule(a.nz, slab, sched);
   for (const SpecLaunch& l : sched) {
-    const cudaError_t e = launch_spectral_pass(prec, l.pass, spectral_launch_args(a, l, slab), s);
+    const cudaError_t e = launch_spectral_pass(prec, l.pass, spectral_launch_args(prec, a, l, slab), s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

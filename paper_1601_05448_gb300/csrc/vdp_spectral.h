@@ -37,6 +37,9 @@ struct SpecArgs {
   int z0, z1;            // X and Y passes: the planes [z0, z1) of this launch (a slab)
   int xunits;            // CTAs of all X- launches of one application (the sweep's arrivals)
 };
+// Passed by value to every pass: kept at 128 bytes.  One more int (136 bytes) made the X and Z
+// passes of the 512^3 mixed solve 5-20 % slower (the solve 35.9 against 34.1 ms, same kernels).
+static_assert(sizeof(SpecArgs) <= 128, "SpecArgs grew past 128 bytes");
 
 // One launch of an application: the pass and its plane range.
 struct SpecLaunch {
@@ -60,10 +63,10 @@ int spectral_units(int nx, int ny, int nz);        // CTAs of the Z pass (partia
 int spectral_slab_planes(int nx, int ny, int nz, int req);
 // The launch sequence of one application: X+, Y+ per slab; Z; Y-, X- per slab.
 void spectral_schedule(int nz, int slab, std::vector<SpecLaunch>& out);
-// CTAs of all X- launches of one application
-int spectral_xinv_units(int nx, int ny, int nz, int slab);
+// CTAs of all X- launches of one application (prec: PREC_*, as passed to the launches)
+int spectral_xinv_units(int prec, const SpecArgs& a, int slab);
 // Args of launch l (the plane range and the X- unit count filled in).
-SpecArgs spectral_launch_args(const SpecArgs& a, const SpecLaunch& l, int slab);
+SpecArgs spectral_launch_args(int prec, const SpecArgs& a, const SpecLaunch& l, int slab);
 // All launches of one application, in order.
 cudaError_t launch_spectral_apply(int prec, const SpecArgs& a, int slab, cudaStream_t s);
 cudaError_t launch_omega(const double* sinv, long long n, float* omega, cudaStream_t s);

@@ -101,7 +101,7 @@ cudaError_t capture_timed(vdp_ctx* c, int prec, int phase, int spec_launch, Time
       SpecArgs a;
       solve_spec_args(c, prec, &a);
       const SpecLaunch& l = t.sched[spec_launch];
-      e2 = launch_spectral_pass(prec, l.pass, spectral_launch_args(a, l, spec_slab(c)), c->cap);
+      e2 = launch_spectral_pass(prec, l.pass, spectral_launch_args(prec, a, l, spec_slab(c)), c->cap);
     } else {
       e2 = launch_for_phase(c, prec, phase, c->cap);
     }
