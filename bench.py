@@ -59,8 +59,12 @@ L2_BYTES = 129e6
 #            rt -= At z: 6 FMA, x += z: 1 add, rt - q: 1 add; FP64 <rt,rt> is summed in FP32
 #                                                                        -> 14 flop, 8 FP64 pipe ops
 #   update : read x, d, q, rt; write x, rt                                -> 6T;  3 FMA -> 6 flop
-#   res64  : read p, f, sinv, 3 FP64 coefficients; write rt                -> 48 + T
-#            6 x (difference + FMA), f - Ap, scaling, |r|^2                -> 22 flop
+#   res64  : read p, f, sinv, D, 3 FP64 coefficients; write rt             -> 56 + T
+#            r = (f - <f>) + D p - sum of 6 b p_nb: 1 add + 7 FMA (+ the FP64 inner's scaling
+#            multiply)                                                     -> 15 flop (16), 8 FP64 ops (9)
+#            the first residual of a solve from p = 0 is f - <f>: read f, sinv; write rt -> 16 + T,
+#            FP64 inner: subtraction, scaling, |r|^2, |rt|^2 in FP64      -> 6 flop, 4 FP64 ops;
+#            FP32 inner: the subtraction in FP64, scaling and norms in FP32 -> 1 FP64 flop
 #   cheb   : sweep 1 reads rt and 3 coefficients, writes z, dz           -> 3T + 3B (+B)
 #            later sweeps also read z and dz                              -> 5T + 3B (+B); 18 flop
 #   other  : rhs mean removal, refinement correction, gauge: not in the roofline
@@ -73,10 +77,10 @@ L2_BYTES = 129e6
 #   is the L2 bandwidth, reported as plain GB/s without an HBM fraction).
 SIZES = {"fp64": (8, 8, False), "mixed": (4, 4, False), "mixed_bf16": (4, 2, True)}
 KERNEL_NAMES = {"res64": "k_res64_direct", "stencil": "k_stencil_direct", "cheb": "k_stencil_direct",
-                "update": "k_flat", "other": "k_flat", "spec_x": "k_spec_x_fwd / k_spec_x_inv",
+                "update": "k_flat", "other": "k_flat", "spec_x": "k_spec_x_fwd(_persistent) / k_spec_x_inv_persistent",
                 "spec_y": "k_spec_y", "spec_z": "k_spec_z",
                 "mg": "k_mg_down / k_mg_restrict / k_mg_coarse / k_mg_prolong / k_mg_up"}
-FP64_PIPE_OPS = {"stencil_fixed": 8.0, "res64": 13.0}
+FP64_PIPE_OPS = {"stencil_fixed": 8.0, "res64": 9.0, "res64_first": 4.0}  # FP64 inner type
 
 
 def spectrum_bytes(nx: int) -> float:
@@ -145,7 +149,11 @@ def sweep_cost(prec: str, kind: str, cheb_k: int = 1, nx: int = 256, fixed: bool
     if kind == "update":
         return 6 * T, 6.0, 6 * T
     if kind == "res64":
-        return 48 + T, 22.0, 48 + T
+        f64 = prec == "fp64"
+        return 56 + T, 16.0 if f64 else 15.0, 56 + T
+    if kind == "res64_first":
+        f64 = prec == "fp64"
+        return 16 + T, 6.0 if f64 else 1.0, 16 + T
     if kind == "cheb":
         k = max(cheb_k - 1, 1)
         b = ((3 * T + 3 * B + Bd) + (k - 1) * (5 * T + 3 * B + Bd)) / k
@@ -162,7 +170,8 @@ def algorithmic(prec: str, ncell: int, iters: int, outer: int, spectral: bool = 
         per_iter = spec + sweep_cost(prec, "stencil", fixed=True)[2]
     else:
         per_iter = sweep_cost(prec, "stencil")[2] + sweep_cost(prec, "update")[2] + (spec if spectral else 0)
-    return (iters * per_iter + outer * (48 + T) + max(outer - 1, 0) * (24 + T) + 32) * ncell
+    res = sweep_cost(prec, "res64")[2] * max(outer - 1, 0) + sweep_cost(prec, "res64_first")[2]
+    return (iters * per_iter + res + max(outer - 1, 0) * (24 + T) + 32) * ncell
 
 
 def kernel_table(prec: str, ncell: int, kinds: dict, peaks: dict, grid: int, cheb_k: int = 1, nx: int = 256,
@@ -195,6 +204,13 @@ def kernel_table(prec: str, ncell: int, kinds: dict, peaks: dict, grid: int, che
             out[name] = row
             continue
         cost = sweep_cost(prec, name, cheb_k, nx, fixed, ncell)
+        ops = FP64_PIPE_OPS.get("stencil_fixed" if (fixed and name == "stencil") else name)
+        if name == "res64" and k["launches"] > 0:
+            # every benchmarked solve starts from p = 0: one of its residual launches is the
+            # short first one; the row averages over the launches (bytes, flops, FP64 ops)
+            n, first = k["launches"], sweep_cost(prec, "res64_first")
+            cost = tuple(((n - 1) * c + f) / n for c, f in zip(cost, first))
+            ops = ((n - 1) * ops + FP64_PIPE_OPS["res64_first"]) / n
         if cost is not None:
             t = k["ms_mean"] / 1e3
             row["alg_bytes_per_launch"] = cost[0] * ncell
@@ -204,7 +220,6 @@ def kernel_table(prec: str, ncell: int, kinds: dict, peaks: dict, grid: int, che
             row["tflops"] = cost[1] * ncell / t / 1e12
             if prec == "fp64" and cost[1] > 0:
                 row["fp64_flop_frac"] = row["tflops"] / peaks["fp64_tflops"]
-                ops = FP64_PIPE_OPS.get("stencil_fixed" if (fixed and name == "stencil") else name)
                 if ops:
                     row["fp64_issue_frac"] = ops * ncell / t / (peaks["fp64_tflops"] * 1e12 / 2.0)
             row["traffic"] = TRAFFIC.get((prec, name, grid, fixed))

@@ -443,7 +443,10 @@ int vdp_probe_fp64(void *stream, double *tflops);
  *                   synchronises this stream and returns after the work has finished
  *   stats           optional (may be NULL); ms is not measured (0)
  * Returns a vdp_status as vdp_solve / vdp_set_density do.  VDP_EINVAL for host pointers,
- * pointers of another device, and buffers whose allocation ends before nx*ny*nz doubles.
+ * pointers of another device, and buffers whose allocation ends before nx*ny*nz doubles -- the
+ * allocation as the driver sees it: an array carved out of a larger allocation by a caching
+ * allocator (a PyTorch tensor, a memory pool) passes this check whatever its own length, so such
+ * callers must pass arrays of nx*ny*nz doubles (the Python binding checks their sizes).
  *
  * Set-up: the first call on a device (and the first after that device's context was destroyed
  * and created again, e.g. by cudaDeviceReset) looks up the device address of the array in the

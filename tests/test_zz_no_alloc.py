@@ -4,6 +4,8 @@ loops that cannot take cudaMalloc's device-wide synchronisation).  Its intermedi
 fixed device array owned by the library, so it is checked against the ordinary vdp_solve entry
 point, through the C ABI, on two calls in a row (the second call must not be disturbed by what
 the first one left in the shared array).  This file is collected last on purpose."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -58,14 +60,37 @@ def test_noalloc_rejects_oversize_and_host_pointers():
     with pytest.raises(ValueError):
         vdp.vdp_solve_noalloc(8, 8, 8, 1.0, b, b[:-1], torch.empty_like(b), 1e-8)
     # through the C ABI directly, an output whose allocation ends before nx*ny*nz doubles is
-    # rejected: after emptying torch's cache, a 12 MB tensor is one fresh cudaMalloc of exactly
-    # that size, so its last 64 doubles end the allocation
-    torch.cuda.synchronize()
-    torch.cuda.empty_cache()
-    big = torch.zeros(12 << 17, dtype=torch.float64, device=DEV)
-    tail = big[-64:]
-    s = vdp.vdp_stats()
-    st = vdp.load().vdp_solve_noalloc(8, 8, 8, 1.0, b.data_ptr(), b.data_ptr(), tail.data_ptr(), 1e-8, 0, None,
-                                      vdp.ctypes.byref(s))
-    assert st == vdp.VDP_EINVAL
-    assert bool((big == 0).all())
+    # rejected and left untouched: a 12 MB buffer from cudaMalloc itself (a tensor of torch's
+    # caching allocator may sit inside a larger driver allocation), its last 64 doubles passed
+    rt = _cudart()
+    ptr = ctypes.c_void_p()
+    nbytes = 12 << 20
+    assert rt.cudaMalloc(ctypes.byref(ptr), ctypes.c_size_t(nbytes)) == 0
+    try:
+        assert rt.cudaMemset(ptr, ctypes.c_int(0), ctypes.c_size_t(nbytes)) == 0
+        tail = ptr.value + nbytes - 64 * 8
+        s = vdp.vdp_stats()
+        st = vdp.load().vdp_solve_noalloc(8, 8, 8, 1.0, b.data_ptr(), b.data_ptr(), tail, 1e-8, 0, None,
+                                          vdp.ctypes.byref(s))
+        assert st == vdp.VDP_EINVAL
+        host = np.ones(nbytes // 8)
+        assert rt.cudaMemcpy(host.ctypes.data_as(ctypes.c_void_p), ptr, ctypes.c_size_t(nbytes), 2) == 0
+        assert not host.any()
+    finally:
+        rt.cudaFree(ptr)
+
+
+def _cudart():
+    """The CUDA runtime the library is linked with (already loaded with it)."""
+    vdp.load()
+    for name in ("libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            lib = ctypes.CDLL(name)
+        except OSError:
+            continue
+        lib.cudaMalloc.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t]
+        lib.cudaMemset.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t]
+        lib.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+        lib.cudaFree.argtypes = [ctypes.c_void_p]
+        return lib
+    pytest.skip("CUDA runtime library not found")
