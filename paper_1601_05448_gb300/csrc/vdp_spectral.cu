@@ -42,9 +42,28 @@ namespace vdp {
 // exp(-2 pi i k / 96): the roots of unity of every register DFT size used here (all divide 96).
 __constant__ float2 c_w96[96];
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// Complex sums, differences and real scalings as one paired FP32 instruction (add / sub / mul
+// .rn.f32x2: both lanes rounded as the scalar operation would round them); the FFT butterflies
+// are mostly these, and the Z pass is bound by its instruction issue.
+#define VDP_F32X2(op)                                                                        \
+  "{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n " op        \
+  ".rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  float2 r;
+  asm(VDP_F32X2("add") : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  float2 r;
+  asm(VDP_F32X2("sub") : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) {
+  float2 r;
+  asm(VDP_F32X2("mul") : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(s), "f"(s));
+  return r;
+}
+#undef VDP_F32X2
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
