@@ -502,9 +502,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // writes the exchange to slots (k2, t, c) of the same buffer.
 template <int M1, int M2>
 constexpr int line_buffer() { return M2 * pad_stride(M1 * kTX); }  // complex values of one tile
-// At least 512 resident threads per SM (at most 128 registers a thread); lines of 512: four
-// blocks of 128 threads.
+// Y: at least 512 resident threads per SM (at most 128 registers a thread); lines of 512: four
+// blocks of 128 threads.  Z: at least 640 (96 registers, a few bytes spilled): at 512^3 Z
+// 352 -> 327 us with five blocks per SM, while Y at five (or six) blocks ran 191 -> 209 us.
 template <int M1> struct LineOcc { static constexpr int kMinBlocks = (512 + M1 * kTX - 1) / (M1 * kTX); };
+template <int M1> struct ZOcc { static constexpr int kMinBlocks = (640 + M1 * kTX - 1) / (M1 * kTX); };
 
 // Copies of the tile of n = M1 x M2 line elements at g (element stride es) into the buffer sm:
 // 4 pieces of 16 bytes per element, spread over the block's threads; one commit group.
@@ -608,7 +610,7 @@ constexpr size_t z_smem() {  // tile buffer, twiddles W_nz^k, eigenvalues lz
 }
 
 template <int M1, int M2>
-__global__ void __launch_bounds__(M1 * kTX, LineOcc<M1>::kMinBlocks) k_spec_z(SpecArgs a) {
+__global__ void __launch_bounds__(M1 * kTX, ZOcc<M1>::kMinBlocks) k_spec_z(SpecArgs a) {
   constexpr int R = (M2 + M1 - 1) / M1;
   constexpr int n = M1 * M2;
   constexpr int S = pad_stride(M1 * kTX);
