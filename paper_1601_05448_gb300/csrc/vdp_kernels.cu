@@ -990,7 +990,6 @@ __device__ void res64_zero_p(const InstDesc& I, const InstState* st, int unit,
   T* rt = static_cast<T*>(I.r);
   double a0 = 0;
   T a1 = 0;
-  float a0f = 0.f;
   if (row < I.ty && yr < ny) {
     for (int z = z0; z < z1; ++z) {
       const long long o = ((long long)z * ny + yr) * nx + x0;
@@ -1006,18 +1005,17 @@ __device__ void res64_zero_p(const InstDesc& I, const InstState* st, int unit,
           a0 = fma(f0, f0, fma(f1, f1, a0));
           a1 = fma(t0, t0, fma(t1, t1, a1));
         } else {  // as the full residual of the mixed precisions: the FP32 product of the narrowed
-                  // factors and FP32 norms, one FP64 operation (the subtraction) per cell
-          const float r0f = narrow(f0), r1f = narrow(f1);
-          const float t0 = narrow(si.x) * r0f, t1 = narrow(si.y) * r1f;
+                  // factors; ||f - <f>||^2, the denominator of every relative residual of the
+                  // solve, stays an FP64 sum (any magnitude of f)
+          const float t0 = narrow(si.x) * narrow(f0), t1 = narrow(si.y) * narrow(f1);
           rt[o + h] = t0;
           rt[o + h + 1] = t1;
-          a0f = fmaf(r0f, r0f, fmaf(r1f, r1f, a0f));
+          a0 = fma(f0, f0, fma(f1, f1, a0));
           a1 = fmaf(t0, t0, fmaf(t1, t1, a1));
         }
       }
     }
   }
-  if constexpr (!IsF64<T>::value) a0 = (double)a0f;
   acc[0] = a0;          // ||r||^2
   acc[1] = (double)a1;  // ||rt||^2
   acc[2] = 0.0;         // sum of p

@@ -28,6 +28,7 @@ import vdp_inputs as V  # noqa: E402
 
 DEV = "cuda:0"
 FP = {"method": vdp.VDP_METHOD_FIXED_POINT, "inner_tol": 1e-4}   # the benchmark's fixed-point options
+FP_512_MIXED = {"method": vdp.VDP_METHOD_FIXED_POINT, "inner_tol": 4e-5}   # ... of its 512^3 mixed step
 SPEC = {"precond": vdp.VDP_PRECOND_SPECTRAL}
 MG = {"precond": vdp.VDP_PRECOND_MG}
 JAC = {"precond": vdp.VDP_PRECOND_JACOBI}
@@ -120,7 +121,7 @@ def test_256_sampled_cells_flux_form():
 
 
 C2_CASES = [
-    ("fixed point", "mixed", FP),        # the benchmark's headline solve
+    ("fixed point", "mixed", FP_512_MIXED),   # the benchmark's headline solve
     ("fixed point", "fp64", FP),         # the FP64 solve it is compared with, same tolerance
     ("fixed point", "mixed_bf16", FP),
     ("CG spectral", "mixed", SPEC),
