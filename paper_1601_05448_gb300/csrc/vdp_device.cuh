@@ -129,7 +129,7 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
   switch (phase) {
     case PH_MEANF:
       st->mu_f = S[0] / (double)I.ncell;
-      st->f2 = S[1];
+      st->f2 = (double)I.ncell * st->mu_f * st->mu_f;
       st->first_res = 1;
       st->phase = PH_RES64;
       break;
@@ -142,7 +142,7 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
       }
       st->outer += 1;
       const double fn2 = st->fn2;
-      if (fn2 <= 1e-28 * st->f2) {  // f is constant up to rounding: p = 0
+      if (fn2 <= 1e-28 * st->f2) {  // f is constant up to the rounding of its mean: p = 0
         st->zero_sol = 1;
         st->rel_res = 0.0;
         st->phase = PH_FINAL;
@@ -267,6 +267,7 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
     }
     case PH_CORRECT:
       st->sum_p = S[0];  // sum of the corrected p (for the gauge at the end)
+      st->p_set = 1;
       st->phase = PH_RES64;
       break;
     case PH_FINAL:
@@ -281,7 +282,7 @@ static __device__ void transition(const InstDesc& I, volatile InstState* st, int
 // partial-sum slots each phase produces
 __device__ __forceinline__ int phase_slots(int phase) {
   switch (phase) {
-    case PH_MEANF: return 2;
+    case PH_MEANF: return 1;
     case PH_RES64: return 4;
     case PH_STENCIL:
     case PH_UPDATE:
@@ -325,6 +326,7 @@ __device__ __forceinline__ InstState snapshot(const InstState* st) {
   s.beta = __ldcg(&st->beta);
   s.sum_p = __ldcg(&st->sum_p);
   s.cheb_j = __ldcg(&st->cheb_j);
+  s.p_set = __ldcg(&st->p_set);
   return s;
 }
 

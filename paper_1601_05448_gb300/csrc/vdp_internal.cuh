@@ -61,13 +61,14 @@ struct InstState {
   int precision;
   int fault;           // a unit's bounded wait expired (reported as VDP_ETIMEOUT)
   int cheb_j;          // Chebyshev sweep index (1 .. cheb_k - 1)
-  int pad1;
+  int p_set;           // p holds an iterate: the caller's guess, or a correction was applied
+                       // (from p = 0 the first correction writes p without reading it)
   double rz;           // <rt, z> (preconditioned inner product; = <rt, rt> for Jacobi)
   double tol;          // requested relative residual
   double inner_tol;    // mixed: minimum relative reduction per inner solve
   double mu_f;         // <f>
   double fn2;          // ||f - <f>||^2
-  double f2;           // ||f||^2
+  double f2;           // n <f>^2 (the constant-f test compares ||f - <f>||^2 with it)
   double rr64;         // ||r||^2 at the last RES64
   double rr64_prev;    // ... at the RES64 before
   double rr;           // <rt, rt> (current inner)

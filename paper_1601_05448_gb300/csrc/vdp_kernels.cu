@@ -235,10 +235,11 @@ __device__ __forceinline__ double widen_t(float v) { return widen(v); }
 __device__ __forceinline__ double widen_t(double v) { return v; }
 
 // <f>, ||f||^2; p := 0 unless p is the caller's initial guess.
-__device__ void sweep_meanf(const InstDesc& I, const InstState* st, long long c0, long long c1,
-                            double (&acc)[kSlots]) {
-  const bool zero_p = !st->use_guess;
-  double s[2] = {0.0, 0.0}, s2[2] = {0.0, 0.0};
+__device__ void sweep_meanf(const InstDesc& I, long long c0, long long c1, double& sum) {
+  // <f> in FP64, one addition per cell.  p is not cleared here: from p = 0 the first residual
+  // does not read it, the first correction writes it without reading it, and the gauge writes
+  // zeros if no correction ever came.
+  double s[2] = {0.0, 0.0};
   const long long step = 2LL * blockDim.x;
   for (long long cb = c0 + 2 * threadIdx.x; cb < c1; cb += kFlatU * step) {
     double2 fv[kFlatU];
@@ -251,19 +252,16 @@ __device__ void sweep_meanf(const InstDesc& I, const InstState* st, long long c0
     for (int u = 0; u < kFlatU; ++u) {
       s[0] += fv[u].x;
       s[1] += fv[u].y;
-      s2[0] = fma(fv[u].x, fv[u].x, s2[0]);
-      s2[1] = fma(fv[u].y, fv[u].y, s2[1]);
-      const long long c = cb + u * step;
-      if (zero_p && c < c1) *reinterpret_cast<double2*>(I.p + c) = make_double2(0.0, 0.0);
     }
   }
-  acc[0] = s[0] + s[1];
-  acc[1] = s2[0] + s2[1];
+  sum = s[0] + s[1];
 }
 
-// p -= D^-1/2 x (x in the inner type); sums the new p (the final gauge needs its mean)
+// p -= D^-1/2 x (x in the inner type); sums the new p (the final gauge needs its mean).  fresh:
+// p is still the zero start (never written), so p = -D^-1/2 x without reading it.
 template <class T>
-__device__ void sweep_correct(const InstDesc& I, long long c0, long long c1, double& psum) {
+__device__ void sweep_correct(const InstDesc& I, long long c0, long long c1, bool fresh,
+                              double& psum) {
   const T* x = static_cast<const T*>(I.x);
   double s = 0.0;
   const long long step = 2LL * blockDim.x;
@@ -276,7 +274,7 @@ __device__ void sweep_correct(const InstDesc& I, long long c0, long long c1, dou
       const long long c = cb + u * step;
       if (c < c1) {
         sv[u] = __ldg(reinterpret_cast<const double2*>(I.sinv + c));
-        pv[u] = *reinterpret_cast<const double2*>(I.p + c);
+        pv[u] = fresh ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(I.p + c);
         xa[u] = x[c];
         xb[u] = x[c + 1];
       }
@@ -299,7 +297,7 @@ __device__ void sweep_correct(const InstDesc& I, long long c0, long long c1, dou
 // p -= <p>   (or p = 0 when the right-hand side was constant)
 __device__ void sweep_final(const InstDesc& I, const InstState* st, long long c0, long long c1) {
   const double mp = st->sum_p / (double)I.ncell;
-  const bool zero = st->zero_sol != 0;
+  const bool zero = st->zero_sol != 0 || st->p_set == 0;  // no iterate: the answer is p = 0
   const long long step = 2LL * blockDim.x;
   for (long long cb = c0 + 2 * threadIdx.x; cb < c1; cb += kFlatU * step) {
     double2 pv[kFlatU];
@@ -1165,10 +1163,9 @@ __device__ __forceinline__ void flat_kind_unit(const InstDesc& I, int unit) {
   const long long c0 = flat_begin(I, unit), c1 = flat_begin(I, unit + 1);
   switch (phase) {
     case PH_MEANF: {
-      double acc[kSlots] = {0.0, 0.0, 0.0, 0.0};
-      sweep_meanf(I, &sn, c0, c1, acc);
-      const double two[2] = {acc[0], acc[1]};
-      store_partials<2, double>(two, I.part, I.nunits_f, unit);
+      double sum[1] = {0.0};
+      sweep_meanf(I, c0, c1, sum[0]);
+      store_partials<1, double>(sum, I.part, I.nunits_f, unit);
       break;
     }
     case PH_UPDATE: {
@@ -1179,7 +1176,7 @@ __device__ __forceinline__ void flat_kind_unit(const InstDesc& I, int unit) {
     }
     case PH_CORRECT: {
       double ps[1] = {0.0};
-      sweep_correct<T>(I, c0, c1, ps[0]);
+      sweep_correct<T>(I, c0, c1, sn.p_set == 0, ps[0]);
       store_partials<1, double>(ps, I.part, I.nunits_f, unit);
       break;
     }
@@ -1310,6 +1307,7 @@ __global__ void k_init(InstDesc* desc, const double* rhs, double* p, double tol,
   s.max_iter = max_iter;
   s.inner_max = inner_max;
   s.use_guess = use_guess;
+  s.p_set = use_guess ? 1 : 0;
   s.precision = precision;
   s.tol = tol;
   s.inner_tol = inner_tol;
