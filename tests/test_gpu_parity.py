@@ -170,6 +170,27 @@ def test_initial_guess_and_errors():
         assert e.value.status == vdp.VDP_EINVAL
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("opts", [{}, {"method": vdp.VDP_METHOD_FIXED_POINT}], ids=["cg", "fixed_point"])
+def test_output_buffer_is_not_read(precision, opts):
+    """Without use_guess the solve never reads p (the first correction writes it): a p filled with
+    NaN gives bitwise the answer of a zeroed p, and a solve that ends before any correction (a
+    tolerance the zero start already meets) returns p = 0."""
+    prob = V.smooth_problem((16, 24, 32), seed=70)
+    nz, ny, nx = prob.shape
+    with vdp.Solver(nx, ny, nz, prob.L, precision=precision, **opts) as s:
+        s.set_density(torch.from_numpy(prob.rho).to(DEV))
+        f = torch.from_numpy(prob.f).to(DEV)
+        p0 = torch.zeros(prob.shape, dtype=torch.float64, device=DEV)
+        st0 = s.solve(f, p0, 1e-9)
+        pn = torch.full(prob.shape, float("nan"), dtype=torch.float64, device=DEV)
+        stn = s.solve(f, pn, 1e-9)
+        assert st0.ok and torch.equal(p0, pn) and stn.iters == st0.iters
+        pz = torch.full(prob.shape, float("nan"), dtype=torch.float64, device=DEV)
+        stz = s.solve(f, pz, 2.0)
+        assert stz.ok and stz.iters == 0 and bool((pz == 0).all())
+
+
 def test_iteration_cap_reports_notconv():
     prob = V.smooth_problem((32, 32, 32), seed=6)
     nz, ny, nx = prob.shape
