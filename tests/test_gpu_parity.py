@@ -176,7 +176,7 @@ def test_output_buffer_is_not_read(precision, opts):
     """Without use_guess the solve never reads p (the first correction writes it): a p filled with
     NaN gives bitwise the answer of a zeroed p, and a solve that ends before any correction (a
     tolerance the zero start already meets) returns p = 0."""
-    prob = V.smooth_problem((16, 24, 32), seed=70)
+    prob = V.smooth_problem((32, 48, 64), seed=70)
     nz, ny, nx = prob.shape
     with vdp.Solver(nx, ny, nz, prob.L, precision=precision, **opts) as s:
         s.set_density(torch.from_numpy(prob.rho).to(DEV))
