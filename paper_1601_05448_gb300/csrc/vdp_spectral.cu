@@ -24,7 +24,9 @@
 // 32): M2-point DFTs in registers, twiddles W_n^(j1 k2), an exchange through shared memory,
 // M1-point DFTs in registers.  Global accesses are coalesced: rows are contiguous in the X
 // passes and the Y/Z tiles read 8 consecutive complex values (64 bytes) per line element.
-// The passes are HBM bound: about 52 bytes per cell for the FP32 inner solve.
+// One application moves about 49 bytes per cell for the FP32 inner solve; at 512^3 the X and Y
+// passes run at 0.85-0.91 of the copy bandwidth and Z, which does two transforms per element,
+// is bound by its instruction issue.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -425,29 +427,10 @@ __device__ __forceinline__ void x_inv_rows(const SpecArgs& a, const Tables& tb, 
   }
 }
 
-// X-: one group of RY rows per block, tables read through L1.
-template <class T, int M1, int M2, bool MIRROR>
-__global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
-    k_spec_x_inv(SpecArgs a) {
-  constexpr int RY = inv_rows_per_block<M1, M2>();
-  constexpr int SB = pad_stride(M2 * (M1 + 1));
-  __shared__ float2 sb[RY * SB];
-  if (!spec_active(a)) return;
-  const Tables tb = tables(a);
-  const int t = threadIdx.x % M1, r = threadIdx.x / M1;
-  const long long row = (long long)a.z0 * a.ny + (long long)blockIdx.x * RY + r;
-  const bool live = row < (long long)a.z1 * a.ny;
-  x_inv_rows<T, M1, M2, MIRROR>(a, tb, sb + r * SB, a.spec + row * a.nxp, row, live, t);
-  if (a.st) {  // the solve: the last block of the application's X- launches completes the
-               // preconditioner sweep, with <rt, z> from the partial sums the Z pass stored
-    const InstDesc& I = *a.I;
-    finish_sweep(I, I.st, PH_SPEC, a.xunits, a.zunits);
-  }
-}
-
 // X- on a persistent grid: groups of RY rows (group = block, block + grid, ...), tables in
-// shared memory.  The 512^3 mixed solve: 33.6 ms against 34.1 ms with the form above; and a
-// launch in another phase of the solve exits after 3 us instead of 29 us.
+// shared memory.  The 512^3 mixed solve: 33.6 ms against 34.1 ms with one row group per block
+// and the tables read through L1; and a launch in another phase of the solve exits after 3 us
+// instead of 29 us.
 template <class T, int M1, int M2, bool MIRROR>
 __global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
     k_spec_x_inv_persistent(SpecArgs a) {
@@ -465,15 +448,15 @@ __global__ void __launch_bounds__(M1 * inv_rows_per_block<M1, M2>())
     x_inv_rows<T, M1, M2, MIRROR>(a, tb, sb + r * SB, a.spec + row * a.nxp, row, live, t);
     __syncthreads();  // the exchange buffers are reused by the next group
   }
-  if (a.st) {  // as above
+  if (a.st) {  // the solve: the last block of the application's X- launches completes the
+               // preconditioner sweep, with <rt, z> from the partial sums the Z pass stored
     const InstDesc& I = *a.I;
     finish_sweep(I, I.st, PH_SPEC, a.xunits, a.zunits);
   }
 }
 
-// Which X kernels run on persistent grids (measured at 512^3, see the forms above; X+ of FP64
-// rows always does).
-constexpr bool kXInvPersistent = true;
+// Whether X+ of FP32 rows also runs on a persistent grid (measured at 512^3, see the X+ forms:
+// it does not; X+ of FP64 rows and X- always do).
 constexpr bool kXFwdF32Persistent = false;
 
 // ---- Y and Z: tiles of TX consecutive kx columns, whole lines -----------------------------------
@@ -725,13 +708,9 @@ SpecKernel x_kernel(int m, bool inverse, bool mirror, int* threads) {
 #define VDP_X(M1, M2)                                                                       \
   if (m1 == M1 && m2 == M2) {                                                               \
     *threads = M1 * (inverse ? inv_rows_per_block<M1, M2>() : rows_per_block<M1, M2>());     \
-    if (inverse) {                                                                          \
-      if constexpr (kXInvPersistent)                                                        \
-        return mirror ? k_spec_x_inv_persistent<T, M1, M2, true>                            \
-                      : k_spec_x_inv_persistent<T, M1, M2, false>;                          \
-      else                                                                                  \
-        return mirror ? k_spec_x_inv<T, M1, M2, true> : k_spec_x_inv<T, M1, M2, false>;    \
-    }                                                                                       \
+    if (inverse)                                                                            \
+      return mirror ? k_spec_x_inv_persistent<T, M1, M2, true>                              \
+                    : k_spec_x_inv_persistent<T, M1, M2, false>;                            \
     if constexpr (sizeof(T) == 8 || kXFwdF32Persistent)                                     \
       return mirror ? k_spec_x_fwd_persistent<T, M1, M2, true>                              \
                     : k_spec_x_fwd_persistent<T, M1, M2, false>;                            \
@@ -814,7 +793,7 @@ long long x_grid(int prec, bool inv, const SpecArgs& a, long long rows) {
   const SpecKernel k = x_pass_kernel(prec, inv, a, &threads);
   const int dev = current_device(), ry = x_rows_per_block(a.nx / 2, inv);
   if (!k || dev < 0 || ry <= 0) return 0;
-  const bool persistent = inv ? kXInvPersistent : (x_f64(prec, inv, a) || kXFwdF32Persistent);
+  const bool persistent = inv || x_f64(prec, inv, a) || kXFwdF32Persistent;
   if (!persistent) return (rows + ry - 1) / ry;
   int per_sm = 0;
   for (const auto& e : g_x_per_sm[dev])
