@@ -456,7 +456,7 @@ int vdp_probe_fp64(void *stream, double *tflops);
  * threads, or on two streams -- race and corrupt each other, so serialise them.
  */
 #define VDP_NOALLOC_MAX_CELLS 65536
-#define VDP_NOALLOC_SCRATCH_BYTES 7276288
+#define VDP_NOALLOC_SCRATCH_BYTES 7276544
 int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double *rho, const double *rhs,
                       double *p, double tol, int precision, void *stream, vdp_stats *stats);
 

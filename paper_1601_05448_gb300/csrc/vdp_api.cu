@@ -111,7 +111,7 @@ void free_ctx(vdp_ctx* c) {
     mg_free(c->mg);
     delete c->mg;
   }
-  void* bufs[] = {c->bx, c->by, c->bz, c->sinv, c->dg, c->sx, c->sy, c->sz, c->sd, c->x, c->r, c->d0, c->d1,
+  void* bufs[] = {c->bx, c->by, c->bz, c->sinv, c->dg, c->f0, c->sx, c->sy, c->sz, c->sd, c->x, c->r, c->d0, c->d1,
                   c->za, c->zb, c->dch, c->spec, c->omega, c->sptab, c->rho_w, c->d_rounds,
                   c->q, c->part, c->ticket, c->st, c->desc, c->units, c->flag, c->stage_a,
                   c->stage_b, c->proj_f};
@@ -161,6 +161,7 @@ int configure_layout(vdp_ctx* c, int prec) {
   d.bz = c->bz;
   d.sinv = c->sinv;
   d.dg = c->dg;
+  d.f0 = c->f0;
   d.sx = c->sx;
   d.sy = c->sy;
   d.sz = c->sz;
@@ -479,7 +480,7 @@ int vdp_create_bc(int nx, int ny, int nz, double Lx, double Ly, double Lz, int b
   size_t bytes = sizeof(double) * (size_t)c->n;
   size_t maxunits = (size_t)std::max(ny * (size_t)nz, (size_t)kSMs * 16);
   cudaError_t e = cudaSuccess;
-  double** f64[] = {&c->bx, &c->by, &c->bz, &c->sinv, &c->dg};
+  double** f64[] = {&c->bx, &c->by, &c->bz, &c->sinv, &c->dg, &c->f0};
   for (double** b : f64)
     if (e == cudaSuccess) e = cudaMalloc((void**)b, bytes);
   // (the Chebyshev buffers za, zb, dch are allocated by vdp_set_options when that

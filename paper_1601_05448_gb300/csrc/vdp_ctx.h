@@ -36,6 +36,7 @@ struct vdp_ctx {
   // FP64 operator data
   double *bx = nullptr, *by = nullptr, *bz = nullptr, *sinv = nullptr;
   double* dg = nullptr;  // D: the sum of the six face coefficients of each cell (FP64 residual)
+  double* f0 = nullptr;  // f - <f>, written by the first residual of a solve from p = 0
   // inner-precision data (sized for FP64, reinterpreted for FP32 / BF16)
   void *sx = nullptr, *sy = nullptr, *sz = nullptr, *sd = nullptr;
   void *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr, *q = nullptr;

@@ -101,6 +101,8 @@ struct InstDesc {
   const double* bz;
   const double* sinv;  // D^-1/2, D = sum of the six face coefficients of a cell
   const double* dg;    // D itself (the FP64 residual's diagonal term)
+  double* f0;          // f - <f> (null: the residual subtracts <f> itself); written by the first
+                       // residual of a solve from p = 0, read by the later ones
   const void* sx;      // scaled coefficients bt = b sinv_l sinv_r in the inner storage type
   const void* sy;
   const void* sz;

@@ -854,7 +854,7 @@ __device__ void sweep_stencil_direct(const InstDesc& I, const InstState* st, int
 // diagonal form r = (f - <f>) + D p_c - sum of b_face p_neighbour (D stored per cell): one FMA
 // per term, 8 FP64 operations per cell against 13 for the face-difference form; in the mixed
 // precisions the scaling rt = D^-1/2 r is an FP32 product; the norms are summed in FP32.
-template <class T, bool FIRST>
+template <class T, bool FIRST, bool F0 = false>
 __device__ __forceinline__ void res64_march(const InstDesc& I, const InstState* st, int unit,
                                             double (&acc)[kSlots]) {
   constexpr int VR = VecW<T>::V;  // cells per thread (4 for FP32 inner, 2 for FP64)
@@ -914,7 +914,8 @@ __device__ __forceinline__ void res64_march(const InstDesc& I, const InstState* 
       const double2 bz = *reinterpret_cast<const double2*>(I.bz + o);
       const double2 bzp = *reinterpret_cast<const double2*>(I.bz + op + x0 + h);
       const double2 dg = *reinterpret_cast<const double2*>(I.dg + o);
-      const double2 f = *reinterpret_cast<const double2*>(I.rhs + o);
+      // F0: f - <f> as the first residual stored it (one FP64 operation fewer per cell)
+      const double2 f = *reinterpret_cast<const double2*>((F0 ? I.f0 : I.rhs) + o);
       const double2 si = *reinterpret_cast<const double2*>(I.sinv + o);
       const double l0 = h == 0 ? left : pc[h - 1];
       const double r1 = h + 2 == VR ? right : pc[h + 2];
@@ -923,7 +924,7 @@ __device__ __forceinline__ void res64_march(const InstDesc& I, const InstState* 
       // r = (f - <f>) - A p with (A p)_c = sum of b_face p_neighbour - D_c p_c: the diagonal
       // term first, then one FMA per face (8 FP64 operations per cell; rounding error of order
       // eps D |p|, below 1e-12 of ||f - <f>|| on the grids here)
-      double res0 = fma(dg.x, c0, f.x - mu), res1 = fma(dg.y, c1, f.y - mu);
+      double res0 = fma(dg.x, c0, F0 ? f.x : f.x - mu), res1 = fma(dg.y, c1, F0 ? f.y : f.y - mu);
       res0 = fma(-bx.x, l0, res0);
       res0 = fma(-bx.y, c1, res0);
       res1 = fma(-bx.y, c0, res1);
@@ -996,6 +997,7 @@ __device__ void res64_zero_p(const InstDesc& I, const InstState* st, int unit,
         const double2 f = *reinterpret_cast<const double2*>(I.rhs + o + h);
         const double2 si = *reinterpret_cast<const double2*>(I.sinv + o + h);
         const double f0 = f.x - mu, f1 = f.y - mu;
+        if (I.f0) *reinterpret_cast<double2*>(I.f0 + o + h) = make_double2(f0, f1);
         if constexpr (IsF64<T>::value) {
           const T t0 = si.x * f0, t1 = si.y * f1;
           rt[o + h] = t0;
@@ -1027,6 +1029,8 @@ __device__ void sweep_res64_direct(const InstDesc& I, const InstState* st, int u
     res64_zero_p<T>(I, st, unit, acc);
   else if (st->first_res != 0)
     res64_march<T, true>(I, st, unit, acc);
+  else if (I.f0 && !st->use_guess)  // f - <f> stored by the first residual
+    res64_march<T, false, true>(I, st, unit, acc);
   else
     res64_march<T, false>(I, st, unit, acc);
 }

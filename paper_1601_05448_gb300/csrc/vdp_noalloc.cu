@@ -154,7 +154,7 @@ bool on_this_device(const void* p, size_t bytes) {
 
 }  // namespace
 
-static_assert(sizeof(InstDesc) <= kAlign && sizeof(InstState) <= kAlign, "scratch slots");
+static_assert(sizeof(InstState) <= kAlign, "scratch slots");
 static_assert(kScratchBytes == VDP_NOALLOC_SCRATCH_BYTES, "keep the header's size in sync");
 
 extern "C" int vdp_solve_noalloc(int nx, int ny, int nz, double L, const double* rho,

@@ -4,7 +4,7 @@ Requests (a grid, a density, a right-hand side, a tolerance) arrive over time.  
 keeps a pool of solver contexts resident on the device (face coefficients, Jacobi scaling,
 spectral tables and iteration vectors stay in HBM; a context is reused by later requests of the
 same grid size) and admits requests first come, first served while a slot and the HBM budget
-allow -- a new context costs 106 bytes per cell, plus about 16 and the half spectrum with the
+allow -- a new context costs 114 bytes per cell, plus about 16 and the half spectrum with the
 FFT passes -- freeing idle contexts, oldest first, when the budget needs room.  Requests that
 arrive while others are on the GPU start as soon as a slot frees up; their work overlaps on the
 device.  Two engines run the admitted work:
@@ -33,7 +33,7 @@ import numpy as np
 from . import PRECISIONS, VDP_ENOMEM, VDP_METHOD_FIXED_POINT, VDP_PRECOND_JACOBI, VDP_PRECOND_MG, \
     VDP_PRECOND_SPECTRAL, Batch, Solver, VdpError, spectral_extra_bytes, spectral_supported, vdp_mg_levels
 
-BYTES_PER_CELL = 104 + 2  # device memory of one context per cell (FP64-sized buffers + BF16 diag)
+BYTES_PER_CELL = 112 + 2  # device memory of one context per cell (FP64-sized buffers + BF16 diag)
 # the multigrid levels (about 25 B per fine cell), z (8 B) and the weights (4 B)
 MG_EXTRA_BYTES_PER_CELL = 25 + 8 + 4
 CANCELLED = -2           # ServeRequest.status of a request cancelled before it finished
