@@ -59,12 +59,12 @@ L2_BYTES = 129e6
 #            rt -= At z: 6 FMA, x += z: 1 add, rt - q: 1 add; FP64 <rt,rt> is summed in FP32
 #                                                                        -> 14 flop, 8 FP64 pipe ops
 #   update : read x, d, q, rt; write x, rt                                -> 6T;  3 FMA -> 6 flop
-#   res64  : read p, f, sinv, D, 3 FP64 coefficients; write rt             -> 56 + T
-#            r = (f - <f>) + D p - sum of 6 b p_nb: 1 add + 7 FMA (+ the FP64 inner's scaling
-#            multiply)                                                     -> 15 flop (16), 8 FP64 ops (9)
-#            the first residual of a solve from p = 0 is f - <f>: read f, sinv; write rt -> 16 + T,
-#            FP64 inner: subtraction, scaling, |r|^2, |rt|^2 in FP64      -> 6 flop, 4 FP64 ops;
-#            FP32 inner: the subtraction in FP64, scaling and norms in FP32 -> 1 FP64 flop
+#   res64  : read p, f - <f> (stored), sinv, D, 3 FP64 coefficients; write rt -> 56 + T
+#            r = (f - <f>) + D p - sum of 6 b p_nb: 7 FMA (+ the FP64 inner's scaling multiply)
+#                                                                          -> 14 flop (15), 7 FP64 ops (8)
+#            the first residual of a solve from p = 0 is f - <f>: read f, sinv; write f - <f>, rt
+#            -> 24 + T; FP64 inner: subtraction, scaling, |r|^2, |rt|^2 in FP64 -> 6 flop, 4 FP64
+#            ops; FP32 inner: subtraction and |r|^2 in FP64, scaling and |rt|^2 in FP32 -> 3 flop
 #   cheb   : sweep 1 reads rt and 3 coefficients, writes z, dz           -> 3T + 3B (+B)
 #            later sweeps also read z and dz                              -> 5T + 3B (+B); 18 flop
 #   other  : rhs mean removal, refinement correction, gauge: not in the roofline
@@ -80,7 +80,7 @@ KERNEL_NAMES = {"res64": "k_res64_direct", "stencil": "k_stencil_direct", "cheb"
                 "update": "k_flat", "other": "k_flat", "spec_x": "k_spec_x_fwd(_persistent) / k_spec_x_inv_persistent",
                 "spec_y": "k_spec_y", "spec_z": "k_spec_z",
                 "mg": "k_mg_down / k_mg_restrict / k_mg_coarse / k_mg_prolong / k_mg_up"}
-FP64_PIPE_OPS = {"stencil_fixed": 8.0, "res64": 9.0, "res64_first": 4.0}  # FP64 inner type
+FP64_PIPE_OPS = {"stencil_fixed": 8.0, "res64": 8.0, "res64_first": 4.0}  # FP64 inner type
 
 
 def fixed_inner_tol(workload: str, prec: str) -> float:
@@ -165,10 +165,10 @@ def sweep_cost(prec: str, kind: str, cheb_k: int = 1, nx: int = 256, fixed: bool
         return 6 * T, 6.0, 6 * T
     if kind == "res64":
         f64 = prec == "fp64"
-        return 56 + T, 16.0 if f64 else 15.0, 56 + T
+        return 56 + T, 15.0 if f64 else 14.0, 56 + T
     if kind == "res64_first":
         f64 = prec == "fp64"
-        return 16 + T, 6.0 if f64 else 1.0, 16 + T
+        return 24 + T, 6.0 if f64 else 3.0, 24 + T
     if kind == "cheb":
         k = max(cheb_k - 1, 1)
         b = ((3 * T + 3 * B + Bd) + (k - 1) * (5 * T + 3 * B + Bd)) / k
