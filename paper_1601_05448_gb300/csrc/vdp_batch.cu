@@ -90,7 +90,7 @@ int rebuild(vdp_batch* b) {
   for (size_t i = 0; i < b->members.size(); ++i)
     if (!b->members[i].done) b->active.push_back((int)i);
   const int n = (int)b->active.size();
-  long long cd = b->cap_desc, cs = b->cap_states;
+  long long cd = b->cap_desc;
   int s;
   if ((s = grow(&b->d_desc, &cd, std::max(n, 1))) != VDP_OK) return s;
   b->cap_desc = (int)cd;
@@ -104,7 +104,6 @@ int rebuild(vdp_batch* b) {
     VDP_CK(cudaMallocHost((void**)&b->h_states, sizeof(InstState) * n));
     b->cap_states = n;
   }
-  (void)cs;
   std::vector<InstDesc> desc(n);
   std::vector<UnitRef> su, fu;
   for (int k = 0; k < n; ++k) {
