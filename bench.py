@@ -110,7 +110,7 @@ def spectrum_bytes(nx: int) -> float:
 # kernel drops its entries until it is re-captured, and the residual is left out (the capture
 # holds the residual from p = 0 only, the table averages both kinds).
 _SCALE_256 = (256 / 192) ** 3
-_TRAFFIC_192 = {("fp64", "stencil", True): 259.5e6 + 84.7e6}
+_TRAFFIC_192 = {("fp64", "stencil", True): 317.8e6 + 85.3e6}
 TRAFFIC = {(p, k, 192, f): v for (p, k, f), v in _TRAFFIC_192.items()}
 TRAFFIC.update({(p, k, 256, f): v * _SCALE_256 for (p, k, f), v in _TRAFFIC_192.items()})
 # the fused FP32 sweep of the mixed fixed-point solve: captured at 256^3 (a launch with x read and
