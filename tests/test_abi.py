@@ -46,6 +46,26 @@ def test_binding_covers_the_header():
     assert sorted(vdp.exported_symbols()) == declared_functions()
 
 
+def declared_constants():
+    """Every VDP_* enumerator with an explicit value and every integer #define of the header."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(VDP_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    consts.update({m.group(1): int(m.group(2))
+                   for m in re.finditer(r"^#define\s+(VDP_[A-Z0-9_]+)\s+(\d+)\s*$", text, flags=re.M)})
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    consts = declared_constants()
+    assert consts["VDP_SWEEP_KINDS"] == len(vdp.SWEEP_NAMES)
+    checked = 0
+    for name, value in consts.items():
+        if hasattr(vdp, name):
+            assert getattr(vdp, name) == value, name
+            checked += 1
+    assert checked >= 25
+
+
 def test_host_only_entry_points(lib):
     assert vdp.vdp_version() >= 1
     assert vdp.vdp_strerror(vdp.VDP_EDENSITY).startswith("VDP_EDENSITY")
