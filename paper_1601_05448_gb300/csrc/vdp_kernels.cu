@@ -1037,15 +1037,16 @@ __device__ void sweep_res64_direct(const InstDesc& I, const InstState* st, int u
 
 // ---- the FP64 residual sweep (a few times per solve): z march through a three-plane ring ---------
 
+// zero: the solve starts from p = 0 and p has not been written yet (it is not read)
 __device__ __forceinline__ void fill_p(const InstDesc& I, const Seg& sg, double* ring, int stride,
-                                       int slot, int zg) {
+                                       int slot, int zg, bool zero) {
   const int nx = I.nx;
   const int cells = (sg.ty + 2) * nx;
   const long long pz = (long long)zg * nx * I.ny;
   double* dst = ring + slot * stride;
   for (int m = threadIdx.x; m < cells; m += blockDim.x) {
     const int ry = m / nx, x = m - ry * nx;
-    dst[m] = I.p[pz + (long long)ring_gy(ry, sg.y0, I.ny) * nx + x];
+    dst[m] = zero ? 0.0 : I.p[pz + (long long)ring_gy(ry, sg.y0, I.ny) * nx + x];
   }
 }
 
@@ -1059,20 +1060,21 @@ __device__ void sweep_res64(const InstDesc& I, const InstState* st, int unit,
   const long long plane = (long long)nx * ny;
   const double mu = st->mu_f;
   const bool first = st->first_res != 0;
+  const bool zero = st->p_set == 0;  // from p = 0, before the first correction
   T* rt = static_cast<T*>(I.r);
   double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
   for_each_segment(I, unit, [&](const Seg& sg) {
     int zm = sg.z0 - 1;
     if (zm < 0) zm += nz;
     __syncthreads();  // ring reuse across segments
-    fill_p(I, sg, ring, stride, 0, zm);
-    fill_p(I, sg, ring, stride, 1, sg.z0);
+    fill_p(I, sg, ring, stride, 0, zm, zero);
+    fill_p(I, sg, ring, stride, 1, sg.z0, zero);
     const int own = sg.ty * nx;
     for (int k = 0; k < sg.nzs; ++k) {
       const int z = sg.z0 + k;
       const int zp = z + 1 == nz ? 0 : z + 1;
       const int sm = k % 3, sc = (k + 1) % 3, sp = (k + 2) % 3;
-      fill_p(I, sg, ring, stride, sp, zp);
+      fill_p(I, sg, ring, stride, sp, zp, zero);
       __syncthreads();
       const double* Rm = ring + sm * stride;
       const double* Rc = ring + sc * stride;

@@ -171,11 +171,13 @@ def test_initial_guess_and_errors():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("opts", [{}, {"method": vdp.VDP_METHOD_FIXED_POINT}], ids=["cg", "fixed_point"])
+@pytest.mark.parametrize("opts", [{}, {"method": vdp.VDP_METHOD_FIXED_POINT}, {"stencil": 1}],
+                         ids=["cg", "fixed_point", "cg_tma_stencil"])
 def test_output_buffer_is_not_read(precision, opts):
     """Without use_guess the solve never reads p (the first correction writes it): a p filled with
     NaN gives bitwise the answer of a zeroed p, and a solve that ends before any correction (a
-    tolerance the zero start already meets) returns p = 0."""
+    tolerance the zero start already meets) returns p = 0 -- also with the TMA-staged stencil,
+    whose residual sweep stages p in shared memory (the zero start is staged as zeros)."""
     prob = V.smooth_problem((32, 48, 64), seed=70)
     nz, ny, nx = prob.shape
     with vdp.Solver(nx, ny, nz, prob.L, precision=precision, **opts) as s:
